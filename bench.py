@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""G-ICP tracking benchmark on one B300: frames/s of the whole per-frame hot path.
+
+Workload (Replica-shaped single frame): a seeded synthetic 1200x680 depth image
+(fx = fy = 600, cx = 599.5, cy = 339.5, depth noise sigma = 1 mm * z^2), stride 2
+(~204k source points), registered against a map of ~2.04M Gaussians built from
+10 prior views of the same room; initial pose offset 2 deg / 2 cm.  A step is
+one frame through the C ABI: depth -> points, source k-NN covariances (plane
+regularisation, scale aligning p = 1.5), map-index rebuild, and the
+Gauss-Newton loop with per-iteration nearest-neighbour search.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica of
+the workload (independent frames, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import signal
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G-ICP tracking frames/s (1200x680 frame, ~204k points, vs 2.04M-Gaussian map)"
+WORKLOAD = "replica-shaped frame: 1200x680 depth, stride 2 (~204k pts), 2.04M-Gaussian map from 10 views, offset 2deg/2cm"
+STRIDE, Z_MIN, Z_MAX = 2, 0.1, 10.0
+K_NN, EPS, P_ALIGN = 20, 1e-3, 1.5
+MAX_DIST, MAX_ITERS, TOL = 0.1, 30, 1e-6
+# bytes the method must move per unit:
+BYTES_PER_POINT_ITER = 72      # x 12 + C_s 24 + mu 12 + C_t 24
+BYTES_PER_POINT_COV = 40       # read x 12 + z 4, write C 24
+BYTES_PER_MAP_GAUSSIAN = 84 + 48  # read mean 12 + cov 24 (x2: bbox/morton and gather) + write 16 + 32
+REGSTATE_BYTES = 544 + 4       # pose/H/b/cost/iters/status record + point count read back per frame
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def build_map_gpu(g, ctx, f, torch):
+    """Map Gaussians from the prior views with the library itself (keyframe insertion path)."""
+    intr = f["intr"].as_array()
+    cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
+    means, covs = [], []
+    for d, P in zip(f["view_depths"], f["view_poses"]):
+        pts, z = g.gsicp_depth_to_points(ctx, torch.from_numpy(d).cuda(), intr, STRIDE, Z_MIN, Z_MAX)
+        pts, z = pts.clone(), z.clone()
+        c = g.gsicp_source_covariances(ctx, pts, z, cp)
+        mw, cw = g.gsicp_transform_gaussians(P, pts, c)
+        means.append(mw)
+        covs.append(cw)
+    return torch.cat(means).contiguous(), torch.cat(covs).contiguous()
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2403_12550_b300 as g
+    from synth import frame_config2
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    f = frame_config2(args.seed)
+    ctx = g.Context()
+    means, covs = build_map_gpu(g, ctx, f, torch)
+    m = g.gsicp_build_map_index(ctx, means, covs)
+    n_map = m.size
+    intr = f["intr"].as_array()
+    cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
+    rp = g.RegParams(MAX_DIST, MAX_ITERS, TOL, TOL, 6)
+    depth_dev = torch.from_numpy(f["depth"]).cuda()
+    depth_host = torch.from_numpy(f["depth"]).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        # a1 -> a2+a3 -> a5-a7 for one frame
+        return g.gsicp_track_frame(ctx, depth_dev, intr, STRIDE, Z_MIN, Z_MAX, cp, m, f["T0"], rp)
+
+    def rebuild():
+        # a4: rebuild the map index over the map's resident Gaussians (no allocation)
+        g.gsicp_map_rebuild(ctx, m)
+
+    # warm-up (also instantiates the Gauss-Newton graph and grows every scratch buffer)
+    for _ in range(args.warmup):
+        rebuild()
+        r = step()
+    g.gsicp_ctx_set_timing(ctx, True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases, iters, npts = [], [], 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()                       # L2 flush between timed steps (not timed)
+            a, b, c = ev[i]
+            a.record(stream)
+            rebuild()                           # a4: map index over 2.04M Gaussians
+            b.record(stream)
+            r = step()                          # a1 -> a2+a3 -> a5-a7 (synchronises)
+            c.record(stream)
+            phases.append(g.gsicp_ctx_phase_times(ctx))
+            iters.append(r["iters"])
+            npts = r["n_points"]
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    index_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    g.gsicp_ctx_set_timing(ctx, False)
+
+    # ---- end-to-end through the host-buffer entry point (H2D depth + D2H results inside)
+    e2e_ms = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rebuild()
+        rh = g.gsicp_track_frame_host(ctx, depth_host, intr, STRIDE, Z_MIN, Z_MAX, cp, m, f["T0"], rp)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    assert np.array_equal(rh["T"], r["T"])
+    e2e_s = sum(e2e_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- roofline of the dominant kernel, from the event-timed phases of the timed steps
+    keys = ("depth_to_points", "source_index", "knn_cov", "gauss_newton")
+    ph = {k: float(np.mean([p[k] for p in phases])) for k in keys}
+    ph["map_index"] = float(np.mean(index_ms))
+    it_mean = float(np.mean(iters))
+    peak, peak_kind = load_peaks()
+    dominant = max(("gauss_newton", "knn_cov", "map_index", "source_index"), key=lambda k: ph[k])
+    if dominant == "gauss_newton":
+        per_launch_ms = ph["gauss_newton"] / max(it_mean, 1)
+        alg = npts * BYTES_PER_POINT_ITER
+        kname = "gicp_iter_kernel"
+    elif dominant == "knn_cov":
+        per_launch_ms, alg, kname = ph["knn_cov"], npts * BYTES_PER_POINT_COV, "knn_cov_kernel"
+    elif dominant == "map_index":
+        per_launch_ms, alg, kname = ph["map_index"], n_map * BYTES_PER_MAP_GAUSSIAN, "map index build"
+    else:
+        per_launch_ms, alg, kname = ph["source_index"], npts * 64, "source index build"
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        traffic = json.load(open(tpath)).get(kname)
+    # launches of our kernels per frame: a1 (5), source index (27), k-NN cov (1), GN set-up (1) + 1 per
+    # iteration; map index rebuild: 1 set + 28
+    launches = int(sum(5 + 27 + 1 + 1 + it for it in iters) + args.steps * 29)
+    K = args.steps
+    out = {
+        "metric": METRIC, "value": world * K / total_s, "unit": "frames/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_points": int(npts), "map_gaussians": int(n_map), "k": K_NN,
+                   "reg": "plane", "eps": EPS, "p": P_ALIGN, "max_corr_dist": MAX_DIST,
+                   "gn_iters_mean": it_mean, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write)", "step": "a4 map-index rebuild + a1..a7"},
+        "point_iters_per_s": world * float(npts) * sum(iters) / total_s,
+        "phases_ms": {k: round(v, 4) for k, v in ph.items()},
+        "tracking_only_frames_per_s": world * K / (total_s - sum(index_ms) / 1e3),
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": int(alg), "avg_launch_ms": per_launch_ms},
+        "e2e": {"value": world * K / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(f["depth"].nbytes),
+                "d2h_bytes_per_step": REGSTATE_BYTES},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(f, args.seed)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    m.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- the oracle (CPU)
+
+def oracle_setup(f):
+    import oracle as orc
+    intr = f["intr"].as_array()
+    means, covs = [], []
+    for d, P in zip(f["view_depths"], f["view_poses"]):
+        pts, z = orc.depth_to_points(d, intr, STRIDE, Z_MIN, Z_MAX)
+        pts, z = pts.astype(np.float32), z.astype(np.float32)
+        c = orc.source_covariances(pts, z, k=K_NN, eps=EPS, reg_mode=orc.PLANE, p=P_ALIGN)["covs"]
+        mw, cw = orc.transform_gaussians(P, pts, c)
+        means.append(mw)
+        covs.append(cw)
+    return orc.Map(np.concatenate(means).astype(np.float32), np.concatenate(covs).astype(np.float32))
+
+
+def oracle_frame(f, omap, frac: float = 1.0, seed: int = 0):
+    """One frame through the oracle: a1, covariances, Gauss-Newton registration.
+    With frac < 1 the registration runs on a seeded random subset of the points."""
+    import oracle as orc
+    pts, z = orc.depth_to_points(f["depth"], f["intr"].as_array(), STRIDE, Z_MIN, Z_MAX)
+    pts, z = pts.astype(np.float32), z.astype(np.float32)
+    cs = orc.source_covariances(pts, z, k=K_NN, eps=EPS, reg_mode=orc.PLANE, p=P_ALIGN)["covs"]
+    if frac < 1.0:
+        sel = np.random.default_rng(seed).choice(len(pts), int(frac * len(pts)), replace=False)
+        pts, cs = pts[sel], cs[sel]
+    return orc.register(pts, cs, omap, f["T0"], MAX_DIST, MAX_ITERS, TOL, TOL, 6)
+
+
+def oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(f, seed):
+    omap = oracle_setup(f)
+    t0 = time.perf_counter()
+    r = oracle_frame(f, omap)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"one full frame (a1 + k-NN covariances of ~204k points + {r['iters']} GN iterations "
+                      f"against the 2.04M-Gaussian map), FP64 C oracle with OpenMP over points; "
+                      f"map construction untimed"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from synth import frame_config2
+    f = frame_config2(args.seed)
+    omap = oracle_setup(f)
+    t0 = time.perf_counter()
+    oracle_frame(f, omap)
+    t_full = time.perf_counter() - t0
+    budget = 150.0  # seconds for the whole run
+    frac = min(1.0, budget / max((args.steps + args.warmup) * t_full, 1e-9))
+    for _ in range(max(args.warmup - 1, 0)):
+        oracle_frame(f, omap, frac)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_frame(f, omap, frac, seed=i)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * frac / total if frac < 1 else args.steps / total
+    sample = ("full frame per step" if frac >= 1 else
+              f"per step: a1 + covariances of the full frame, GN registration on a random {frac:.3f} of its points; "
+              f"frames/s scaled by that fraction")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * gsicp.h -- C ABI of libgsicp.so: the G-ICP tracking hot path of
+ * "RGBD GS-ICP SLAM" (Ha, Yeon, Yu; arXiv 2403.12550) on one B300 (sm_103a).
+ *
+ * Per frame the path is: depth image -> point cloud (Sec. 3, Fig. 2) ->
+ * per-point k-NN covariances with scale regularisation (Sec. 3.1) and scale
+ * aligning (Sec. 3.2) -> Gauss-Newton minimisation of Eq. (MLE_for_T) against
+ * the target Gaussians of the map, with nearest-neighbour correspondences
+ * re-searched at every iteration (Sec. 3).
+ *
+ * General conventions
+ *   - Device pointers ("_dev") are CUDA global-memory addresses on the
+ *     context's device, owned by the caller; the library never frees them.
+ *     Host pointers ("_host" or plain arrays) are ordinary CPU memory.
+ *   - Points are n x 3 float32 row-major (x, y, z).  Symmetric 3x3 matrices
+ *     are 6 float32 (xx, xy, xz, yy, yz, zz).  Poses are 4x4 float64
+ *     row-major; a pose T maps source (camera) coordinates into map (world)
+ *     coordinates: p_w = R p_c + t.
+ *   - Twists are ordered xi = (omega, v) and act on the left, T <- exp(xi^) T;
+ *     the 6x6 H returned uses that order.
+ *   - Every call is ordered on the caller's CUDA stream (`stream` is a
+ *     cudaStream_t; NULL = legacy default stream).  Calls that return host
+ *     values synchronise that stream once before returning.
+ *   - A context owns reusable device scratch and the CUDA graphs of the
+ *     Gauss-Newton loop; use one context from one host thread and one
+ *     stream at a time.  Scratch grows on demand and is never shrunk; in the
+ *     steady state no call allocates.
+ *   - Errors are returned as gsicp_status; no function aborts or traps.  On
+ *     GSICP_ERR_CUDA the CUDA error text is available from
+ *     gsicp_last_error().
+ */
+#ifndef GSICP_H
+#define GSICP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSICP_OK = 0,
+    GSICP_ERR_INVALID_ARG = 1,    /* null pointer, negative size, bad parameter */
+    GSICP_ERR_CUDA = 2,           /* a CUDA runtime call failed (see gsicp_last_error) */
+    GSICP_ERR_OOM = 3,            /* device allocation failed */
+    GSICP_ERR_DEGENERATE = 4,     /* fewer than min_inliers correspondences, or H not positive definite */
+    GSICP_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    GSICP_ERR_NOT_IMPLEMENTED = 6,
+    GSICP_ERR_CAPACITY = 7        /* an output buffer is too small for the result */
+} gsicp_status;
+
+typedef enum {
+    GSICP_REG_PLANE = 0,   /* Sec. 3.1: scales [1, 1, eps] -> eigenvalues (eps, 1, 1) */
+    GSICP_REG_ELLIPSE = 1, /* Sec. 3.1: Lambda' = Lambda / median(S) -> C / middle eigenvalue */
+    GSICP_REG_NONE = 2     /* raw k-NN covariance (the unregularised row of Table 5) */
+} gsicp_reg_mode;
+
+/* Source-covariance parameters (Sec. 3, 3.1, 3.2). */
+typedef struct {
+    int k;          /* neighbours per point, the point itself included; 1 <= k <= 32 (paper: not stated; 20) */
+    float eps;      /* plane/ellipse regularisation constant (1e-3) */
+    int reg_mode;   /* gsicp_reg_mode */
+    float p;        /* scale-aligning exponent: covariance *= z^(-2p); 0 disables (paper's best: 1.5, Table 6) */
+} gsicp_cov_params;
+
+/* Registration parameters (Sec. 3, Eq. MLE_for_T). */
+typedef struct {
+    float max_corr_dist; /* a source point has a correspondence iff its nearest map mean is within this distance (m) */
+    int max_iters;       /* Gauss-Newton iteration cap (>= 1) */
+    double tol_rot;      /* converged when |d omega| < tol_rot (rad) ... */
+    double tol_trans;    /* ... and |d v| < tol_trans (m) */
+    int min_inliers;     /* fewer correspondences than this -> GSICP_ERR_DEGENERATE */
+} gsicp_reg_params;
+
+/* Spatial-index parameters (Morton-ordered bounding-volume hierarchy). */
+typedef struct {
+    int bucket;          /* points per leaf: 8, 16 or 32 (0 = default) */
+} gsicp_index_params;
+
+typedef struct gsicp_ctx_s* gsicp_ctx;
+typedef struct gsicp_map_s* gsicp_map;
+
+/* ---------------------------------------------------------------------------------------------
+ * Context and status
+ * ------------------------------------------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  *out receives the handle. */
+gsicp_status gsicp_ctx_create(gsicp_ctx* out);
+/* Free a context and all its scratch (synchronises the device first). NULL is ignored. */
+void gsicp_ctx_destroy(gsicp_ctx ctx);
+const char* gsicp_status_string(gsicp_status s);
+/* Text of the last CUDA error seen by this library in the calling thread ("" if none). */
+const char* gsicp_last_error(void);
+/* Library version, e.g. "0.1.0". */
+const char* gsicp_version(void);
+
+/* Profiling: when enabled, gsicp_track_frame / gsicp_track_frame_host record CUDA events on the
+ * call's stream between their phases, and gsicp_ctx_phase_times returns the device time (ms) of
+ * the last such frame: out[0] a1 depth->points, out[1] source index build, out[2] k-NN
+ * covariances, out[3] Gauss-Newton loop, out[4] whole frame; out[5] = Gauss-Newton iterations.
+ * Disabled by default (no events are recorded). */
+gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable);
+gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6]);
+
+/* ---------------------------------------------------------------------------------------------
+ * a1  Depth image -> point cloud   (Sec. 3, Fig. 2: "downsampling and reprojecting the depth image")
+ *
+ * Every stride-th pixel (u, v) = (stride*i, stride*j) of the W x H float32 depth image
+ * (metres, row-major) is kept iff its depth d is finite and z_min <= d <= z_max, and
+ * back-projected to ((u - cx) d / fx, (v - cy) d / fy, d), intr = {fx, fy, cx, cy}.
+ * Kept points are written in row-major pixel order to pts_dev (cap x 3) and their depth to
+ * z_dev (cap, may be NULL).  The count goes to n_dev (device int32, may be NULL) and, if
+ * n_host is non-NULL, to *n_host after a stream synchronisation.  If more than cap points
+ * survive, GSICP_ERR_CAPACITY is returned (only detectable when n_host is given) and at most
+ * cap points are written.
+ * ------------------------------------------------------------------------------------------- */
+gsicp_status gsicp_depth_to_points(gsicp_ctx ctx, const float* depth_dev, int W, int H,
+                                   const float intr[4], int stride, float z_min, float z_max,
+                                   float* pts_dev, float* z_dev, int64_t cap, int32_t* n_dev,
+                                   int64_t* n_host, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * a2+a3  Source Gaussians   (Sec. 3: covariance of the k nearest neighbours; Sec. 3.1 scale
+ * regularisation; Sec. 3.2 scale aligning)
+ *
+ * For each of the n points (pts_dev, n x 3): its k nearest neighbours among the n points by
+ * squared Euclidean distance, the point itself included, ties broken by smaller index; the
+ * covariance C = (1/k) sum (x_j - mu)(x_j - mu)^T of those neighbours; C' by the
+ * regularisation of params->reg_mode; C'' = C' * z^(-2p) with z = z_dev[i] (z_dev may be NULL
+ * when p == 0).  Fewer than 3 points, or a line-like neighbourhood (middle eigenvalue <= 1e-5
+ * x largest) under PLANE/ELLIPSE, give C' = I.  ELLIPSE floors the smallest eigenvalue ratio at
+ * eps.  Writes covs_dev (n x 6).  If knn_dev is non-NULL it receives the neighbour indices
+ * (n x k int32, nearest first; -1 padding when n < k).
+ * ------------------------------------------------------------------------------------------- */
+gsicp_status gsicp_source_covariances(gsicp_ctx ctx, const float* pts_dev, const float* z_dev,
+                                      int64_t n, const gsicp_cov_params* params, float* covs_dev,
+                                      int32_t* knn_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * a4  Map index   (target Gaussians G^t = {X^t, C^t}, Sec. 3)
+ *
+ * Builds the spatial index over m map Gaussians (means_dev m x 3, covs_dev m x 6) and keeps a
+ * packed, index-ordered copy of both, so the caller's buffers may be reused after the call.
+ * *out receives a handle owned by the caller (free with gsicp_map_destroy).  params may be NULL.
+ * ------------------------------------------------------------------------------------------- */
+gsicp_status gsicp_build_map_index(gsicp_ctx ctx, const float* means_dev, const float* covs_dev,
+                                   int64_t m, const gsicp_index_params* params, void* stream,
+                                   gsicp_map* out);
+/* Append m_add Gaussians to a map and rebuild its index (keyframe insertion, Fig. 2). */
+gsicp_status gsicp_map_append(gsicp_ctx ctx, gsicp_map map, const float* means_dev,
+                              const float* covs_dev, int64_t m_add, void* stream);
+/* Rebuild a map's index over the Gaussians it already holds (the a4 step alone; no allocation
+ * once the map exists).  Stream-ordered, no synchronisation. */
+gsicp_status gsicp_map_rebuild(gsicp_ctx ctx, gsicp_map map, void* stream);
+/* Number of Gaussians in a map. */
+int64_t gsicp_map_size(gsicp_map map);
+void gsicp_map_destroy(gsicp_map map);
+
+/* Helper for map insertion: y = R x + t and C' = R C R^T for n Gaussians (covs may be NULL). */
+gsicp_status gsicp_transform_gaussians(const double T[16], const float* pts_dev,
+                                       const float* covs_dev, int64_t n, float* pts_out_dev,
+                                       float* covs_out_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * a5-a7  Registration   (Sec. 3: d_i = x^t_i - T x^s_i ~ N(0, C^t_i + T C^s_i T^T);
+ * Eq. MLE_for_T minimised by Gauss-Newton)
+ *
+ * Starting from T0, each iteration: y_i = R x_i + t; j* = nearest map mean (ties -> smaller map
+ * index) with |mu_j* - y_i| <= max_corr_dist, else no correspondence; d_i = mu_j* - y_i;
+ * W_i = (C^t_j* + R C^s_i R^T)^-1; J_i = [[y_i]x, -I]; H = sum J^T W J, b = sum J^T W d,
+ * cost = sum d^T W d.  Then delta = -H^-1 b (FP64 Cholesky) and T <- exp(delta^) T (FP64).
+ * Stops when |d omega| < tol_rot and |d v| < tol_trans, or after max_iters iterations (not an
+ * error: *iters_out == max_iters).
+ *
+ * Outputs (host): T_out[16] final pose; H_out[36] (nullable) and b_out[6] (nullable) of the last
+ * linearisation; iters_out, cost_out (cost at the last linearisation), inliers_out (its
+ * correspondence count); all nullable except T_out.  GSICP_ERR_DEGENERATE leaves T_out at the
+ * last valid pose.  Synchronises the stream.
+ * ------------------------------------------------------------------------------------------- */
+gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev,
+                            int64_t n, gsicp_map map, const double T0[16],
+                            const gsicp_reg_params* params, double T_out[16], double H_out[36],
+                            double b_out[6], int* iters_out, double* cost_out,
+                            int64_t* inliers_out, void* stream);
+
+/* One linearisation at pose T (no update): H (6x6), b, cost and inlier count as in
+ * gsicp_register's first iteration.  corr_dev (n int32, nullable) receives each source point's
+ * map index (-1 if none).  Synchronises the stream. */
+gsicp_status gsicp_linearise(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev,
+                             int64_t n, gsicp_map map, const double T[16], float max_corr_dist,
+                             double H_out[36], double b_out[6], double* cost_out,
+                             int64_t* inliers_out, int32_t* corr_dev, void* stream);
+
+/* Nearest map mean of each of q query points (queries_dev q x 3, map frame) within max_dist:
+ * idx_dev (q int32, -1 if none, ties -> smaller index) and d2_dev (q float32 squared
+ * distances, +inf if none; nullable).  Stream-ordered, no synchronisation. */
+gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* queries_dev, int64_t q,
+                               float max_dist, int32_t* idx_dev, float* d2_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * One whole tracking frame: a1 -> a2+a3 -> a5-a7 with every intermediate kept on the device
+ * (one stream synchronisation at the end).  Same semantics as calling gsicp_depth_to_points,
+ * gsicp_source_covariances (z = the points' depth) and gsicp_register in sequence.
+ * depth_dev is a device image; gsicp_track_frame_host takes a host image (copied inside the
+ * call).  n_points_out (nullable) receives the frame's point count.
+ * ------------------------------------------------------------------------------------------- */
+gsicp_status gsicp_track_frame(gsicp_ctx ctx, const float* depth_dev, int W, int H,
+                               const float intr[4], int stride, float z_min, float z_max,
+                               const gsicp_cov_params* cov_params, gsicp_map map,
+                               const double T0[16], const gsicp_reg_params* reg_params,
+                               double T_out[16], double H_out[36], int* iters_out,
+                               double* cost_out, int64_t* inliers_out, int64_t* n_points_out,
+                               void* stream);
+gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int W, int H,
+                                    const float intr[4], int stride, float z_min, float z_max,
+                                    const gsicp_cov_params* cov_params, gsicp_map map,
+                                    const double T0[16], const gsicp_reg_params* reg_params,
+                                    double T_out[16], double H_out[36], int* iters_out,
+                                    double* cost_out, int64_t* inliers_out,
+                                    int64_t* n_points_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSICP_H */

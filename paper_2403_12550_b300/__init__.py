@@ -1,0 +1,342 @@
+"""B300-native G-ICP tracking hot path of "RGBD GS-ICP SLAM" (arXiv 2403.12550).
+
+Thin Python binding over the C ABI of ``libgsicp.so`` (``include/gsicp.h``):
+the functions below carry the C entry points' names and only marshal
+arguments (torch CUDA tensors -> device pointers, the current torch stream ->
+``cudaStream_t``).  Every step of the path runs in the library's CUDA kernels;
+there is no fallback.  Importing this package raises if the library has not
+been built (``python -m paper_2403_12550_b300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+__all__ = [
+    "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
+    "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_depth_to_points", "gsicp_source_covariances", "gsicp_build_map_index", "gsicp_map_append",
+    "gsicp_map_rebuild", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_linearise",
+    "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
+]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgsicp.so")
+
+PLANE, ELLIPSE, NONE = 0, 1, 2
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_TIMEOUT, ERR_NOT_IMPLEMENTED, ERR_CAPACITY = range(8)
+
+
+class GsicpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {gsicp_status_string(status)}"
+        detail = gsicp_last_error()
+        if status == ERR_CUDA and detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class CovParams(C.Structure):
+    _fields_ = [("k", C.c_int), ("eps", C.c_float), ("reg_mode", C.c_int), ("p", C.c_float)]
+
+    def __init__(self, k: int = 20, eps: float = 1e-3, reg_mode: int = PLANE, p: float = 0.0):
+        super().__init__(k, eps, reg_mode, p)
+
+
+class RegParams(C.Structure):
+    _fields_ = [("max_corr_dist", C.c_float), ("max_iters", C.c_int), ("tol_rot", C.c_double),
+                ("tol_trans", C.c_double), ("min_inliers", C.c_int)]
+
+    def __init__(self, max_corr_dist: float = 0.1, max_iters: int = 30, tol_rot: float = 1e-6,
+                 tol_trans: float = 1e-6, min_inliers: int = 6):
+        super().__init__(max_corr_dist, max_iters, tol_rot, tol_trans, min_inliers)
+
+
+class IndexParams(C.Structure):
+    _fields_ = [("bucket", C.c_int)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2403_12550_b300.build` "
+                      "(there is no non-CUDA fallback)")
+
+lib = C.CDLL(LIB_PATH)
+
+_vp, _i32p, _i64p, _fp, _dp = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_float), \
+    C.POINTER(C.c_double)
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("gsicp_ctx_create", C.c_int, [C.POINTER(C.c_void_p)])
+_sig("gsicp_ctx_destroy", None, [_vp])
+_sig("gsicp_status_string", C.c_char_p, [C.c_int])
+_sig("gsicp_last_error", C.c_char_p, [])
+_sig("gsicp_version", C.c_char_p, [])
+_sig("gsicp_ctx_set_timing", C.c_int, [_vp, C.c_int])
+_sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
+_sig("gsicp_depth_to_points", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, _vp, _vp,
+                                        C.c_int64, _vp, _i64p, _vp])
+_sig("gsicp_source_covariances", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(CovParams), _vp, _vp, _vp])
+_sig("gsicp_build_map_index", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(IndexParams), _vp,
+                                        C.POINTER(C.c_void_p)])
+_sig("gsicp_map_append", C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp])
+_sig("gsicp_map_size", C.c_int64, [_vp])
+_sig("gsicp_map_rebuild", C.c_int, [_vp, _vp, _vp])
+_sig("gsicp_map_destroy", None, [_vp])
+_sig("gsicp_transform_gaussians", C.c_int, [_dp, _vp, _vp, C.c_int64, _vp, _vp, _vp])
+_sig("gsicp_register", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(RegParams), _dp, _dp, _dp,
+                                 C.POINTER(C.c_int), _dp, _i64p, _vp])
+_sig("gsicp_linearise", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.c_float, _dp, _dp, _dp, _i64p, _vp, _vp])
+_sig("gsicp_map_nearest", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp])
+for _n in ("gsicp_track_frame", "gsicp_track_frame_host"):
+    _sig(_n, C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, C.POINTER(CovParams), _vp,
+                       _dp, C.POINTER(RegParams), _dp, _dp, C.POINTER(C.c_int), _dp, _i64p, _i64p, _vp])
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t: torch.Tensor | None, dtype=torch.float32, cols: int | None = None) -> C.c_void_p | None:
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"expected shape (n, {cols}), got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _pose(T) -> C.Array:
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    return (C.c_double * 16)(*a)
+
+
+def _check(st: int, where: str, allow=()):
+    if st != OK and st not in allow:
+        raise GsicpError(st, where)
+    return st
+
+
+def gsicp_status_string(st: int) -> str:
+    return lib.gsicp_status_string(st).decode()
+
+
+def gsicp_last_error() -> str:
+    return lib.gsicp_last_error().decode()
+
+
+def gsicp_version() -> str:
+    return lib.gsicp_version().decode()
+
+
+class Context:
+    """Owns a ``gsicp_ctx`` (device scratch + the Gauss-Newton CUDA graph)."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        _check(lib.gsicp_ctx_create(C.byref(h)), "gsicp_ctx_create")
+        self.ptr = h
+
+    def close(self):
+        if self.ptr:
+            lib.gsicp_ctx_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MapHandle:
+    """Owns a ``gsicp_map`` (the map index and its packed copy of the Gaussians)."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    @property
+    def size(self) -> int:
+        return int(lib.gsicp_map_size(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            lib.gsicp_map_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gsicp_ctx_create() -> Context:
+    return Context()
+
+
+def gsicp_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def gsicp_ctx_set_timing(ctx: Context, enable: bool):
+    _check(lib.gsicp_ctx_set_timing(ctx.ptr, int(bool(enable))), "gsicp_ctx_set_timing")
+
+
+def gsicp_ctx_phase_times(ctx: Context) -> dict:
+    """Device times (ms) of the last timed frame's phases and its iteration count."""
+    out = (C.c_double * 6)()
+    _check(lib.gsicp_ctx_phase_times(ctx.ptr, out), "gsicp_ctx_phase_times")
+    keys = ("depth_to_points", "source_index", "knn_cov", "gauss_newton", "frame", "iters")
+    return dict(zip(keys, list(out)))
+
+
+def gsicp_depth_to_points(ctx: Context, depth: torch.Tensor, intr, stride: int, z_min: float, z_max: float,
+                          pts_out: torch.Tensor | None = None, z_out: torch.Tensor | None = None):
+    """a1.  Returns ``(pts[:n], z[:n])`` (views of the output buffers)."""
+    H, W = depth.shape
+    cap = ((W + stride - 1) // stride) * ((H + stride - 1) // stride)
+    if pts_out is None:
+        pts_out = torch.empty((cap, 3), device=depth.device, dtype=torch.float32)
+    if z_out is None:
+        z_out = torch.empty((cap,), device=depth.device, dtype=torch.float32)
+    fi = (C.c_float * 4)(*[float(v) for v in intr])
+    n = C.c_int64(0)
+    _check(lib.gsicp_depth_to_points(ctx.ptr, _dev(depth), W, H, fi, stride, z_min, z_max, _dev(pts_out, cols=3),
+                                     _dev(z_out), pts_out.shape[0], None, C.byref(n), _stream()),
+           "gsicp_depth_to_points")
+    return pts_out[:n.value], z_out[:n.value]
+
+
+def gsicp_source_covariances(ctx: Context, pts: torch.Tensor, z: torch.Tensor | None, params: CovParams,
+                             covs_out: torch.Tensor | None = None, want_knn: bool = False):
+    """a2+a3.  Returns covs (n x 6), or (covs, knn n x k int32) with ``want_knn``."""
+    n = pts.shape[0]
+    if covs_out is None:
+        covs_out = torch.empty((n, 6), device=pts.device, dtype=torch.float32)
+    knn = torch.empty((n, params.k), device=pts.device, dtype=torch.int32) if want_knn else None
+    _check(lib.gsicp_source_covariances(ctx.ptr, _dev(pts, cols=3), _dev(z), n, C.byref(params),
+                                        _dev(covs_out, cols=6), _dev(knn, torch.int32), _stream()),
+           "gsicp_source_covariances")
+    return (covs_out, knn) if want_knn else covs_out
+
+
+def gsicp_build_map_index(ctx: Context, means: torch.Tensor, covs: torch.Tensor, bucket: int = 0) -> MapHandle:
+    """a4.  Returns a MapHandle (the library keeps its own copy of the Gaussians)."""
+    h = C.c_void_p()
+    ip = IndexParams(bucket)
+    _check(lib.gsicp_build_map_index(ctx.ptr, _dev(means, cols=3), _dev(covs, cols=6), means.shape[0],
+                                     C.byref(ip), _stream(), C.byref(h)), "gsicp_build_map_index")
+    return MapHandle(h)
+
+
+def gsicp_map_append(ctx: Context, map_: MapHandle, means: torch.Tensor, covs: torch.Tensor):
+    _check(lib.gsicp_map_append(ctx.ptr, map_.ptr, _dev(means, cols=3), _dev(covs, cols=6), means.shape[0],
+                                _stream()), "gsicp_map_append")
+
+
+def gsicp_map_rebuild(ctx: Context, map_: MapHandle):
+    """a4 alone: rebuild the map's index over the Gaussians it holds."""
+    _check(lib.gsicp_map_rebuild(ctx.ptr, map_.ptr, _stream()), "gsicp_map_rebuild")
+
+
+def gsicp_map_size(map_: MapHandle) -> int:
+    return map_.size
+
+
+def gsicp_map_destroy(map_: MapHandle):
+    map_.close()
+
+
+def gsicp_transform_gaussians(T, pts: torch.Tensor, covs: torch.Tensor | None = None):
+    po = torch.empty_like(pts)
+    co = None if covs is None else torch.empty_like(covs)
+    _check(lib.gsicp_transform_gaussians(_pose(T), _dev(pts, cols=3), _dev(covs, cols=6), pts.shape[0],
+                                         _dev(po, cols=3), _dev(co, cols=6), _stream()), "gsicp_transform_gaussians")
+    return po, co
+
+
+def _reg_outputs():
+    return (C.c_double * 16)(), (C.c_double * 36)(), (C.c_double * 6)(), C.c_int(0), C.c_double(0.0), C.c_int64(0)
+
+
+def gsicp_register(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: MapHandle, T0,
+                   params: RegParams) -> dict:
+    """a5-a7.  Returns dict(T, H, b, iters, cost, inliers, status); raises on errors other
+    than a degenerate system (status ERR_DEGENERATE, T = last valid pose)."""
+    T, H, b, it, cost, cnt = _reg_outputs()
+    st = lib.gsicp_register(ctx.ptr, _dev(src, cols=3), _dev(covs, cols=6), src.shape[0], map_.ptr, _pose(T0),
+                            C.byref(params), T, H, b, C.byref(it), C.byref(cost), C.byref(cnt), _stream())
+    _check(st, "gsicp_register", allow=(ERR_DEGENERATE,))
+    return dict(T=np.array(T).reshape(4, 4), H=np.array(H).reshape(6, 6), b=np.array(b), iters=it.value,
+                cost=cost.value, inliers=cnt.value, status=st)
+
+
+def gsicp_linearise(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: MapHandle, T,
+                    max_corr_dist: float, want_corr: bool = True) -> dict:
+    _, H, b, _, cost, cnt = _reg_outputs()
+    corr = torch.empty((src.shape[0],), device=src.device, dtype=torch.int32) if want_corr else None
+    _check(lib.gsicp_linearise(ctx.ptr, _dev(src, cols=3), _dev(covs, cols=6), src.shape[0], map_.ptr, _pose(T),
+                               max_corr_dist, H, b, C.byref(cost), C.byref(cnt), _dev(corr, torch.int32), _stream()),
+           "gsicp_linearise")
+    return dict(H=np.array(H).reshape(6, 6), b=np.array(b), cost=cost.value, inliers=cnt.value, corr=corr)
+
+
+def gsicp_map_nearest(ctx: Context, map_: MapHandle, queries: torch.Tensor, max_dist: float):
+    q = queries.shape[0]
+    idx = torch.empty((q,), device=queries.device, dtype=torch.int32)
+    d2 = torch.empty((q,), device=queries.device, dtype=torch.float32)
+    _check(lib.gsicp_map_nearest(ctx.ptr, map_.ptr, _dev(queries, cols=3), q, max_dist, _dev(idx, torch.int32),
+                                 _dev(d2), _stream()), "gsicp_map_nearest")
+    return idx, d2
+
+
+def _frame(fn, ctx, depth_ptr, W, H, intr, stride, z_min, z_max, cov_params, map_, T0, reg_params):
+    T, Hm, _, it, cost, cnt = _reg_outputs()
+    npts = C.c_int64(0)
+    fi = (C.c_float * 4)(*[float(v) for v in intr])
+    st = fn(ctx.ptr, depth_ptr, W, H, fi, stride, z_min, z_max, C.byref(cov_params), map_.ptr, _pose(T0),
+            C.byref(reg_params), T, Hm, C.byref(it), C.byref(cost), C.byref(cnt), C.byref(npts), _stream())
+    _check(st, fn.__name__, allow=(ERR_DEGENERATE,))
+    return dict(T=np.array(T).reshape(4, 4), H=np.array(Hm).reshape(6, 6), iters=it.value, cost=cost.value,
+                inliers=cnt.value, n_points=npts.value, status=st)
+
+
+def gsicp_track_frame(ctx: Context, depth: torch.Tensor, intr, stride: int, z_min: float, z_max: float,
+                      cov_params: CovParams, map_: MapHandle, T0, reg_params: RegParams) -> dict:
+    """One whole frame (a1 -> a2+a3 -> a5-a7) from a device depth image."""
+    H, W = depth.shape
+    return _frame(lib.gsicp_track_frame, ctx, _dev(depth), W, H, intr, stride, z_min, z_max, cov_params, map_, T0,
+                  reg_params)
+
+
+def gsicp_track_frame_host(ctx: Context, depth_host, intr, stride: int, z_min: float, z_max: float,
+                           cov_params: CovParams, map_: MapHandle, T0, reg_params: RegParams) -> dict:
+    """One whole frame from a host depth image (a CPU torch tensor, pinned for async copies,
+    or a numpy array); the host-to-device copy happens inside the call."""
+    if isinstance(depth_host, torch.Tensor):
+        if depth_host.is_cuda or depth_host.dtype != torch.float32 or not depth_host.is_contiguous():
+            raise TypeError("expected a contiguous CPU float32 tensor")
+        H, W = depth_host.shape
+        ptr = C.c_void_p(depth_host.data_ptr())
+    else:
+        arr = np.ascontiguousarray(depth_host, dtype=np.float32)
+        H, W = arr.shape
+        ptr = C.c_void_p(arr.ctypes.data)
+    return _frame(lib.gsicp_track_frame_host, ctx, ptr, W, H, intr, stride, z_min, z_max, cov_params, map_, T0,
+                  reg_params)

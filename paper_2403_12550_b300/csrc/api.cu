@@ -1,0 +1,456 @@
+// api.cu -- the C ABI of libgsicp.so (declared in include/gsicp.h): argument
+// checks, context / map lifetime, and the sequencing of the kernels of each
+// entry point on the caller's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace gsicp {
+
+static thread_local std::string g_last_error;
+
+gsicp_status cuda_status(cudaError_t e, const char* where)
+{
+    g_last_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e) + " (" + where + ")";
+    cudaGetLastError();  // clear a non-sticky error
+    return e == cudaErrorMemoryAllocation ? GSICP_ERR_OOM : GSICP_ERR_CUDA;
+}
+
+gsicp_status DevBuf::ensure(size_t want)
+{
+    if (want <= bytes && ptr) return GSICP_OK;
+    release();
+    size_t b = std::max<size_t>(want, 256);
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_status(e, "cudaMalloc");
+    }
+    bytes = b;
+    return GSICP_OK;
+}
+
+void DevBuf::release()
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+int device_sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+    if (dev < 64 && cache[dev]) return cache[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    if (dev < 64) cache[dev] = sms;
+    return sms;
+}
+
+static bool valid_pose(const double T[16])
+{
+    for (int i = 0; i < 16; ++i)
+        if (!isfinite(T[i])) return false;
+    return T[12] == 0.0 && T[13] == 0.0 && T[14] == 0.0 && T[15] == 1.0;
+}
+
+static bool valid_cov_params(const gsicp_cov_params* p)
+{
+    return p && p->k >= 1 && p->k <= 32 && p->eps > 0.f && p->eps < 1.f && isfinite(p->p) &&
+           (p->reg_mode == GSICP_REG_PLANE || p->reg_mode == GSICP_REG_ELLIPSE || p->reg_mode == GSICP_REG_NONE);
+}
+
+static bool valid_reg_params(const gsicp_reg_params* p)
+{
+    return p && p->max_corr_dist > 0.f && isfinite(p->max_corr_dist) && p->max_iters >= 1 && p->tol_rot >= 0.0 &&
+           p->tol_trans >= 0.0 && p->min_inliers >= 0;
+}
+
+static gsicp_status finish_registration(gsicp_ctx ctx, cudaStream_t s, double T_out[16], double H_out[36],
+                                        double b_out[6], int* iters_out, double* cost_out, int64_t* inliers_out)
+{
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    const RegState& st = *ctx->reg.state_host;
+    if (T_out) memcpy(T_out, st.T, sizeof(double) * 16);
+    if (H_out) memcpy(H_out, st.H, sizeof(double) * 36);
+    if (b_out) memcpy(b_out, st.b, sizeof(double) * 6);
+    if (iters_out) *iters_out = st.iter;
+    if (cost_out) *cost_out = st.cost;
+    if (inliers_out) *inliers_out = st.inliers;
+    if (st.status == REG_ST_DEGENERATE) return GSICP_ERR_DEGENERATE;
+    return GSICP_OK;
+}
+
+static RegJob make_job(const float* src, const float* covs_s, const int* n_dev, gsicp_map map,
+                       const gsicp_reg_params* prm)
+{
+    RegJob job;
+    memset(&job, 0, sizeof(job));
+    job.src = src;
+    job.covs_s = covs_s;
+    job.n = n_dev;
+    job.map = map->index.view();
+    job.corr_out = nullptr;
+    const float d = prm ? prm->max_corr_dist : 0.f;
+    job.max_d2 = d * d;
+    job.max_iters = prm ? prm->max_iters : 1;
+    job.tol_rot = prm ? prm->tol_rot : 0.0;
+    job.tol_trans = prm ? prm->tol_trans : 0.0;
+    job.min_inliers = prm ? prm->min_inliers : 0;
+    return job;
+}
+
+static gsicp_status map_build(gsicp_ctx ctx, gsicp_map map, int bucket, cudaStream_t s)
+{
+    GSICP_CHECK(launch_set_int(map->count.as<int>(), (int)map->m, s));
+    return build_index(map->means.as<float>(), map->covs.as<float>(), (int)map->m, map->count.as<int>(), bucket,
+                       map->index, ctx->build, s);
+}
+
+}  // namespace gsicp
+
+using namespace gsicp;
+
+extern "C" {
+
+const char* gsicp_version(void) { return "0.1.0"; }
+
+const char* gsicp_last_error(void) { return g_last_error.c_str(); }
+
+const char* gsicp_status_string(gsicp_status s)
+{
+    switch (s) {
+        case GSICP_OK: return "ok";
+        case GSICP_ERR_INVALID_ARG: return "invalid argument";
+        case GSICP_ERR_CUDA: return "CUDA error";
+        case GSICP_ERR_OOM: return "out of device memory";
+        case GSICP_ERR_DEGENERATE: return "degenerate registration (too few correspondences or H not positive definite)";
+        case GSICP_ERR_TIMEOUT: return "bounded device wait expired";
+        case GSICP_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case GSICP_ERR_CAPACITY: return "output capacity too small";
+    }
+    return "unknown status";
+}
+
+gsicp_status gsicp_ctx_create(gsicp_ctx* out)
+{
+    if (!out) return GSICP_ERR_INVALID_ARG;
+    *out = nullptr;
+    gsicp_ctx c = new (std::nothrow) gsicp_ctx_s();
+    if (!c) return GSICP_ERR_OOM;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_status(e, "cudaGetDevice");
+    }
+    gsicp_status st = c->n_dev.ensure(sizeof(int) * 4);
+    if (st == GSICP_OK) st = c->total_dev.ensure(sizeof(int) * 4);
+    if (st == GSICP_OK) {
+        e = cudaMallocHost((void**)&c->host_pinned, sizeof(int64_t) * 8);
+        if (e != cudaSuccess) st = cuda_status(e, "cudaMallocHost");
+    }
+    if (st == GSICP_OK) st = c->reg.init();
+    if (st != GSICP_OK) {
+        gsicp_ctx_destroy(c);
+        return st;
+    }
+    *out = c;
+    return GSICP_OK;
+}
+
+void gsicp_ctx_destroy(gsicp_ctx ctx)
+{
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    ctx->reg.release();
+    BuildScratch& b = ctx->build;
+    b.k0.release(); b.k1.release(); b.v0.release(); b.v1.release(); b.hist.release(); b.sums.release();
+    b.bbox.release();
+    ctx->src_index.pts.release(); ctx->src_index.boxes.release(); ctx->src_index.covs.release();
+    ctx->a1_counts.release(); ctx->a1_sums.release(); ctx->n_dev.release(); ctx->total_dev.release();
+    ctx->frame_pts.release(); ctx->frame_z.release(); ctx->frame_covs.release(); ctx->frame_depth.release();
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    for (cudaEvent_t& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable)
+{
+    if (!ctx) return GSICP_ERR_INVALID_ARG;
+    if (enable && !ctx->ev[0])
+        for (cudaEvent_t& e : ctx->ev) GSICP_CUDA(cudaEventCreate(&e));
+    ctx->timing = enable != 0;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6])
+{
+    if (!ctx || !out) return GSICP_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i) out[i] = ctx->phase_ms[i];
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_depth_to_points(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
+                                   int stride, float z_min, float z_max, float* pts_dev, float* z_dev, int64_t cap,
+                                   int32_t* n_dev, int64_t* n_host, void* stream)
+{
+    if (!ctx || !depth_dev || !intr || !pts_dev || W <= 0 || H <= 0 || stride <= 0 || cap < 0 || cap > INT32_MAX)
+        return GSICP_ERR_INVALID_ARG;
+    if (!(intr[0] != 0.f) || !(intr[1] != 0.f)) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* nd = n_dev ? (int*)n_dev : ctx->n_dev.as<int>();
+    GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, pts_dev, z_dev, (int)cap, nd,
+                                       ctx->total_dev.as<int>(), ctx->a1_counts, ctx->a1_sums, s));
+    if (n_host) {
+        int* h = (int*)ctx->host_pinned;
+        GSICP_CUDA(cudaMemcpyAsync(h, ctx->total_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GSICP_CUDA(cudaStreamSynchronize(s));
+        const int total = h[0];
+        *n_host = std::min<int64_t>(total, cap);
+        if (total > cap) return GSICP_ERR_CAPACITY;
+    }
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_source_covariances(gsicp_ctx ctx, const float* pts_dev, const float* z_dev, int64_t n,
+                                      const gsicp_cov_params* params, float* covs_dev, int32_t* knn_dev, void* stream)
+{
+    if (!ctx || !valid_cov_params(params) || n < 0 || n > (1 << 30)) return GSICP_ERR_INVALID_ARG;
+    if (n == 0) return GSICP_OK;
+    if (!pts_dev || !covs_dev || (params->p != 0.f && !z_dev)) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), (int)n, s));
+    GSICP_CHECK(build_index(pts_dev, nullptr, (int)n, ctx->n_dev.as<int>(), 32, ctx->src_index, ctx->build, s));
+    return launch_knn_cov(ctx->src_index.view(), pts_dev, z_dev, (int)n, *params, covs_dev, knn_dev, s);
+}
+
+gsicp_status gsicp_build_map_index(gsicp_ctx ctx, const float* means_dev, const float* covs_dev, int64_t m,
+                                   const gsicp_index_params* params, void* stream, gsicp_map* out)
+{
+    if (!out) return GSICP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctx || m < 0 || m > (1 << 30) || (m > 0 && (!means_dev || !covs_dev))) return GSICP_ERR_INVALID_ARG;
+    int bucket = params && params->bucket ? params->bucket : 16;
+    if (bucket != 8 && bucket != 16 && bucket != 32) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    gsicp_map map = new (std::nothrow) gsicp_map_s();
+    if (!map) return GSICP_ERR_OOM;
+    map->device = ctx->device;
+    map->m = m;
+    gsicp_status st = map->count.ensure(sizeof(int) * 4);
+    if (st == GSICP_OK) st = map->means.ensure(sizeof(float) * 3 * (size_t)std::max<int64_t>(m, 1));
+    if (st == GSICP_OK) st = map->covs.ensure(sizeof(float) * 6 * (size_t)std::max<int64_t>(m, 1));
+    if (st == GSICP_OK && m > 0) {
+        cudaError_t e = cudaMemcpyAsync(map->means.ptr, means_dev, sizeof(float) * 3 * m, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(map->covs.ptr, covs_dev, sizeof(float) * 6 * m, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) st = cuda_status(e, "cudaMemcpyAsync");
+    }
+    if (st == GSICP_OK) st = map_build(ctx, map, bucket, s);
+    if (st != GSICP_OK) {
+        gsicp_map_destroy(map);
+        return st;
+    }
+    *out = map;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_map_append(gsicp_ctx ctx, gsicp_map map, const float* means_dev, const float* covs_dev,
+                              int64_t m_add, void* stream)
+{
+    if (!ctx || !map || m_add < 0 || map->m + m_add > (1 << 30) || (m_add > 0 && (!means_dev || !covs_dev)))
+        return GSICP_ERR_INVALID_ARG;
+    if (m_add == 0) return GSICP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t m = map->m + m_add;
+    DevBuf nm, nc;
+    GSICP_CHECK(nm.ensure(sizeof(float) * 3 * (size_t)m));
+    gsicp_status st = nc.ensure(sizeof(float) * 6 * (size_t)m);
+    if (st != GSICP_OK) {
+        nm.release();
+        return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (map->m > 0) {
+        e = cudaMemcpyAsync(nm.ptr, map->means.ptr, sizeof(float) * 3 * map->m, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(nc.ptr, map->covs.ptr, sizeof(float) * 6 * map->m, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(nm.as<float>() + 3 * map->m, means_dev, sizeof(float) * 3 * m_add,
+                            cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(nc.as<float>() + 6 * map->m, covs_dev, sizeof(float) * 6 * m_add,
+                            cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // old buffers are read by the copies above
+    if (e != cudaSuccess) {
+        nm.release();
+        nc.release();
+        return cuda_status(e, "gsicp_map_append copy");
+    }
+    map->means.release();
+    map->covs.release();
+    map->means = nm;
+    map->covs = nc;
+    map->m = m;
+    return map_build(ctx, map, map->index.B, s);
+}
+
+gsicp_status gsicp_map_rebuild(gsicp_ctx ctx, gsicp_map map, void* stream)
+{
+    if (!ctx || !map) return GSICP_ERR_INVALID_ARG;
+    return map_build(ctx, map, map->index.B, (cudaStream_t)stream);
+}
+
+int64_t gsicp_map_size(gsicp_map map) { return map ? map->m : 0; }
+
+void gsicp_map_destroy(gsicp_map map)
+{
+    if (!map) return;
+    cudaDeviceSynchronize();
+    map->index.pts.release();
+    map->index.boxes.release();
+    map->index.covs.release();
+    map->means.release();
+    map->covs.release();
+    map->count.release();
+    delete map;
+}
+
+gsicp_status gsicp_transform_gaussians(const double T[16], const float* pts_dev, const float* covs_dev, int64_t n,
+                                       float* pts_out_dev, float* covs_out_dev, void* stream)
+{
+    if (!T || n < 0 || n > INT32_MAX || (n > 0 && (!pts_dev || !pts_out_dev)) || !valid_pose(T))
+        return GSICP_ERR_INVALID_ARG;
+    return launch_transform(T, pts_dev, covs_dev, (int)n, pts_out_dev, covs_out_dev, (cudaStream_t)stream);
+}
+
+gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev, int64_t n,
+                            gsicp_map map, const double T0[16], const gsicp_reg_params* params, double T_out[16],
+                            double H_out[36], double b_out[6], int* iters_out, double* cost_out,
+                            int64_t* inliers_out, void* stream)
+{
+    if (!ctx || !map || !T0 || !T_out || !valid_reg_params(params) || n < 0 || n > (1 << 30) || !valid_pose(T0))
+        return GSICP_ERR_INVALID_ARG;
+    if (n > 0 && (!src_pts_dev || !src_covs_dev)) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), (int)n, s));
+    RegJob job = make_job(src_pts_dev, src_covs_dev, ctx->n_dev.as<int>(), map, params);
+    GSICP_CHECK(reg_run(ctx->reg, job, T0, (int)n, true, s));
+    return finish_registration(ctx, s, T_out, H_out, b_out, iters_out, cost_out, inliers_out);
+}
+
+gsicp_status gsicp_linearise(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev, int64_t n,
+                             gsicp_map map, const double T[16], float max_corr_dist, double H_out[36],
+                             double b_out[6], double* cost_out, int64_t* inliers_out, int32_t* corr_dev, void* stream)
+{
+    if (!ctx || !map || !T || n < 0 || n > (1 << 30) || !(max_corr_dist > 0.f) || !valid_pose(T))
+        return GSICP_ERR_INVALID_ARG;
+    if (n > 0 && (!src_pts_dev || !src_covs_dev)) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    gsicp_reg_params prm = {max_corr_dist, 1, 0.0, 0.0, 0};
+    GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), (int)n, s));
+    RegJob job = make_job(src_pts_dev, src_covs_dev, ctx->n_dev.as<int>(), map, &prm);
+    job.corr_out = corr_dev;
+    GSICP_CHECK(reg_run(ctx->reg, job, T, (int)n, false, s));
+    gsicp_status st = finish_registration(ctx, s, nullptr, H_out, b_out, nullptr, cost_out, inliers_out);
+    return st == GSICP_ERR_DEGENERATE ? GSICP_OK : st;
+}
+
+gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* queries_dev, int64_t q, float max_dist,
+                               int32_t* idx_dev, float* d2_dev, void* stream)
+{
+    if (!ctx || !map || q < 0 || q > INT32_MAX || !(max_dist > 0.f) || (q > 0 && (!queries_dev || !idx_dev)))
+        return GSICP_ERR_INVALID_ARG;
+    return launch_nearest(map->index.view(), queries_dev, (int)q, max_dist * max_dist, idx_dev, d2_dev,
+                          (cudaStream_t)stream);
+}
+
+static gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
+                                     int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
+                                     gsicp_map map, const double T0[16], const gsicp_reg_params* reg_params,
+                                     double T_out[16], double H_out[36], int* iters_out, double* cost_out,
+                                     int64_t* inliers_out, int64_t* n_points_out, cudaStream_t s)
+{
+    const int64_t cap64 = (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride);
+    if (cap64 > (1 << 30)) return GSICP_ERR_INVALID_ARG;
+    const int cap = (int)cap64;
+    GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)cap));
+    GSICP_CHECK(ctx->frame_z.ensure(sizeof(float) * (size_t)cap));
+    GSICP_CHECK(ctx->frame_covs.ensure(sizeof(float) * 6 * (size_t)cap));
+    int* nd = ctx->n_dev.as<int>();
+    const bool tm = ctx->timing;
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[0], s));
+    GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, ctx->frame_pts.as<float>(),
+                                       ctx->frame_z.as<float>(), cap, nd, ctx->total_dev.as<int>(), ctx->a1_counts,
+                                       ctx->a1_sums, s));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
+    GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
+    GSICP_CHECK(launch_knn_cov(ctx->src_index.view(), ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap,
+                               *cov_params, ctx->frame_covs.as<float>(), nullptr, s));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], s));
+    RegJob job = make_job(ctx->frame_pts.as<float>(), ctx->frame_covs.as<float>(), nd, map, reg_params);
+    GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));
+    if (n_points_out) GSICP_CUDA(cudaMemcpyAsync(ctx->host_pinned, nd, sizeof(int), cudaMemcpyDeviceToHost, s));
+    gsicp_status st = finish_registration(ctx, s, T_out, H_out, nullptr, iters_out, cost_out, inliers_out);
+    if (n_points_out) *n_points_out = ((int*)ctx->host_pinned)[0];
+    if (tm) {
+        float ms = 0.f;
+        for (int i = 0; i < 4; ++i) {
+            GSICP_CUDA(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+            ctx->phase_ms[i] = ms;
+        }
+        GSICP_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[4]));
+        ctx->phase_ms[4] = ms;
+        ctx->phase_ms[5] = ctx->reg.state_host->iter;
+    }
+    return st;
+}
+
+static bool valid_frame_args(gsicp_ctx ctx, const float* depth, int W, int H, const float intr[4], int stride,
+                             const gsicp_cov_params* cp, gsicp_map map, const double T0[16],
+                             const gsicp_reg_params* rp, const double* T_out)
+{
+    return ctx && depth && W > 0 && H > 0 && intr && intr[0] != 0.f && intr[1] != 0.f && stride > 0 &&
+           valid_cov_params(cp) && map && T0 && valid_pose(T0) && valid_reg_params(rp) && T_out;
+}
+
+gsicp_status gsicp_track_frame(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
+                               float z_min, float z_max, const gsicp_cov_params* cov_params, gsicp_map map,
+                               const double T0[16], const gsicp_reg_params* reg_params, double T_out[16],
+                               double H_out[36], int* iters_out, double* cost_out, int64_t* inliers_out,
+                               int64_t* n_points_out, void* stream)
+{
+    if (!valid_frame_args(ctx, depth_dev, W, H, intr, stride, cov_params, map, T0, reg_params, T_out))
+        return GSICP_ERR_INVALID_ARG;
+    return track_frame_impl(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, map, T0, reg_params, T_out,
+                            H_out, iters_out, cost_out, inliers_out, n_points_out, (cudaStream_t)stream);
+}
+
+gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int W, int H, const float intr[4],
+                                    int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
+                                    gsicp_map map, const double T0[16], const gsicp_reg_params* reg_params,
+                                    double T_out[16], double H_out[36], int* iters_out, double* cost_out,
+                                    int64_t* inliers_out, int64_t* n_points_out, void* stream)
+{
+    if (!valid_frame_args(ctx, depth_host, W, H, intr, stride, cov_params, map, T0, reg_params, T_out))
+        return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * (size_t)W * (size_t)H;
+    GSICP_CHECK(ctx->frame_depth.ensure(bytes));
+    GSICP_CUDA(cudaMemcpyAsync(ctx->frame_depth.ptr, depth_host, bytes, cudaMemcpyHostToDevice, s));
+    return track_frame_impl(ctx, ctx->frame_depth.as<float>(), W, H, intr, stride, z_min, z_max, cov_params, map, T0,
+                            reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out, s);
+}
+
+}  // extern "C"

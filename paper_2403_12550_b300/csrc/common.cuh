@@ -1,0 +1,138 @@
+// common.cuh -- device-side building blocks shared by the libgsicp kernels.
+//
+// Spatial index: a bounding-volume hierarchy over points sorted along a
+// Morton (Z-order) curve.  Points are cut into fixed-size buckets of B
+// consecutive sorted points (the leaves); the tree over the L = 2^levels
+// leaves is implicit (1-indexed heap: node i has children 2i, 2i+1, leaves
+// are nodes L .. 2L-1).  Every node stores the exact axis-aligned bounding box
+// of its points, so a box's squared distance to a query is a lower bound on
+// the squared distance of every point inside it, computed with the same
+// rounded operations (see sq3) -- pruning never drops an admissible point.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define GSICP_INF __int_as_float(0x7f800000)
+
+namespace gsicp {
+
+// Sorted point record: x, y, z and the point's original index (int bits in w).
+// Node box: two float4 per node, lo.xyz and hi.xyz (w unused).  Empty boxes
+// have lo = +inf, hi = -inf, so their distance to any query is +inf.
+struct IndexView {
+    const float4* pts;    // L*B sorted points (only the first *n are valid)
+    const float4* boxes;  // 2 * (2L) float4: node i -> boxes[2i] (lo), boxes[2i+1] (hi)
+    const float4* covs;   // optional: 2 float4 per sorted point (xx,xy,xz,yy | yz,zz,-,-)
+    const int* n;         // device count of valid points
+    int L;                // leaves (power of two)
+    int B;                // points per leaf (8, 16 or 32)
+};
+
+// Squared norm with a fixed, monotone evaluation order: used for both point
+// and box distances so that box bounds are never above a contained point's
+// distance after rounding.
+__device__ __forceinline__ float sq3(float dx, float dy, float dz)
+{
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ float point_d2(float qx, float qy, float qz, float4 p)
+{
+    return sq3(__fsub_rn(p.x, qx), __fsub_rn(p.y, qy), __fsub_rn(p.z, qz));
+}
+
+__device__ __forceinline__ float box_d2(float qx, float qy, float qz, float4 lo, float4 hi)
+{
+    float dx = fmaxf(fmaxf(__fsub_rn(lo.x, qx), __fsub_rn(qx, hi.x)), 0.f);
+    float dy = fmaxf(fmaxf(__fsub_rn(lo.y, qy), __fsub_rn(qy, hi.y)), 0.f);
+    float dz = fmaxf(fmaxf(__fsub_rn(lo.z, qz), __fsub_rn(qz, hi.z)), 0.f);
+    return sq3(dx, dy, dz);
+}
+
+// (d, i) strictly before (e, j) in the order "squared distance, then index".
+__device__ __forceinline__ bool before(float d, int i, float e, int j)
+{
+    return d < e || (d == e && i < j);
+}
+
+// Interleave the low 10 bits of v with two zero bits between each.
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Order-preserving map float -> uint32 (for atomicMin/atomicMax on floats).
+__device__ __forceinline__ uint32_t f2ord(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Compensated (double-float) summation: value = hi + lo with |lo| <= ulp(hi)/2.
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add(dfloat& a, float x)
+{
+    float s = __fadd_rn(a.hi, x);
+    float bb = __fsub_rn(s, a.hi);
+    float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, err);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Registration job and state (device memory, written by the host-side set-up
+// kernel, read by every Gauss-Newton iteration).
+
+struct Pose16 {
+    double v[16];
+};
+
+enum { REG_MODE_SOLVE = 0, REG_MODE_LINEARISE = 1 };
+enum { REG_ST_RUNNING = 0, REG_ST_CONVERGED = 1, REG_ST_MAXITER = 2, REG_ST_DEGENERATE = 3 };
+
+constexpr int NACC = 29;  // 21 (upper triangle of H) + 6 (b) + cost + count
+
+struct RegState {
+    double T[16];      // current pose
+    double H[36];      // last linearisation
+    double b[6];
+    double cost;
+    long long inliers;
+    float Rf[9], tf[3];  // float copy of the current pose for the per-point work
+    int iter;          // completed iterations
+    int status;        // REG_ST_*
+    unsigned int counter;  // blocks finished in the current iteration
+    int pad;
+};
+
+struct RegJob {
+    const float* src;      // n x 3
+    const float* covs_s;   // n x 6
+    const int* n;          // device count
+    IndexView map;
+    int* corr_cache;       // n: sorted map position of the last correspondence (-1 none)
+    int* corr_out;         // optional: original map index per source point
+    float* partials;       // grid x NACC
+    RegState* st;
+    float max_d2;
+    int max_iters;
+    double tol_rot, tol_trans;
+    int min_inliers;
+    int mode;              // REG_MODE_*
+    int use_cond;          // 1 when launched inside the conditional-while graph
+};
+
+}  // namespace gsicp

@@ -1,0 +1,86 @@
+// depth.cu -- a1: depth image -> point cloud (Sec. 3, Fig. 2: "a point cloud by
+// downsampling and reprojecting the current depth image").
+//
+// Every stride-th pixel (u, v) whose depth d is finite and within
+// [z_min, z_max] becomes ((u - cx) d / fx, (v - cy) d / fy, d), in row-major
+// pixel order.  The two products/quotients are evaluated in double and
+// rounded once to float, so each coordinate is the correctly rounded value of
+// the formula.  Order-preserving compaction: per-block counts -> scan -> write.
+#include "internal.h"
+
+namespace gsicp {
+
+constexpr int D2P_THREADS = 256;
+
+__device__ __forceinline__ bool pixel_valid(const float* depth, int W, int stride, int Ws, long idx, float z_min,
+                                            float z_max, int& u, int& v, float& d)
+{
+    const int j = (int)(idx / Ws), i = (int)(idx % Ws);
+    u = i * stride;
+    v = j * stride;
+    d = depth[(long)v * W + u];
+    return isfinite(d) && d >= z_min && d <= z_max;
+}
+
+__global__ void d2p_count_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+                                 float z_min, float z_max, uint32_t* __restrict__ counts)
+{
+    const long idx = (long)blockIdx.x * D2P_THREADS + threadIdx.x;
+    int u, v;
+    float d;
+    bool ok = idx < total && pixel_valid(depth, W, stride, Ws, idx, z_min, z_max, u, v, d);
+    int c = __syncthreads_count(ok);
+    if (threadIdx.x == 0) counts[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+                                 float z_min, float z_max, double fx, double fy, double cx, double cy,
+                                 const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int nblocks,
+                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev)
+{
+    __shared__ uint32_t wsum[D2P_THREADS / 32];
+    const long idx = (long)blockIdx.x * D2P_THREADS + threadIdx.x;
+    int u = 0, v = 0;
+    float d = 0.f;
+    const bool ok = idx < total && pixel_valid(depth, W, stride, Ws, idx, z_min, z_max, u, v, d);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const uint32_t pos = offs[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+    if (ok && pos < (uint32_t)cap) {
+        const double dd = (double)d;
+        pts[3l * pos + 0] = (float)(((double)u - cx) * dd / fx);
+        pts[3l * pos + 1] = (float)(((double)v - cy) * dd / fy);
+        pts[3l * pos + 2] = d;
+        if (z) z[pos] = d;
+    }
+    if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
+        const uint32_t all = offs[nblocks - 1] + counts[nblocks - 1];
+        if (n_dev) *n_dev = (int)min(all, (uint32_t)cap);
+        if (total_dev) *total_dev = (int)all;
+    }
+}
+
+gsicp_status launch_depth_to_points(const float* depth, int W, int H, const float intr[4], int stride,
+                                    float z_min, float z_max, float* pts, float* z, int cap, int* n_dev,
+                                    int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s)
+{
+    const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
+    const long total = (long)Ws * Hs;
+    const int nb = (int)((total + D2P_THREADS - 1) / D2P_THREADS);
+    GSICP_CHECK(counts.ensure(sizeof(uint32_t) * 2 * (size_t)nb));
+    uint32_t* cnt = counts.as<uint32_t>();
+    uint32_t* off = cnt + nb;
+    d2p_count_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, Ws, total, z_min, z_max, cnt);
+    GSICP_CHECK(exclusive_scan_u32(cnt, off, nb, sums, s));
+    d2p_write_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, Ws, total, z_min, z_max, (double)intr[0],
+                                                (double)intr[1], (double)intr[2], (double)intr[3], off, cnt, nb, pts,
+                                                z, cap, n_dev, total_dev);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+}  // namespace gsicp

@@ -1,0 +1,520 @@
+// gicp.cu -- a5-a7: Gauss-Newton G-ICP registration against the map index.
+//
+// Sec. 3: with correspondences from nearest-neighbour search, the error
+// d_i = x^t_i - T x^s_i is Gaussian with covariance C^t_i + T C^s_i T^T (only
+// the rotation acts on a covariance), and the pose is the MLE of Eq.
+// (MLE_for_T): argmin_T sum_i d_i^T (C^t_i + R C^s_i R^T)^-1 d_i.  It is
+// minimised by Gauss-Newton with left perturbations T <- exp(xi^) T,
+// xi = (omega, v): J_i = dd_i/dxi = [[y_i]x, -I] with y_i = R x_i + t.
+//
+// One kernel launch per iteration.  Every thread handles source points in a
+// grid-stride loop: transform, exact nearest map mean (best-first descent of
+// the map's bounding-volume hierarchy, seeded with the previous iteration's
+// correspondence as an initial bound), residual, weight, J^T W J (21 unique),
+// J^T W d (6), d^T W d and the inlier count -> warp shuffles -> one FP32
+// partial per block.  The last block to finish (threadfence + atomic
+// counter, no waiting) sums the partials with compensation, solves the 6x6
+// system by FP64 Cholesky, applies the FP64 SE(3) exponential and, inside a
+// CUDA graph, sets the conditional-while handle that decides whether the
+// next iteration runs.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace gsicp {
+
+constexpr int REG_THREADS = 256;
+
+// Exact nearest point of `ix` to q with (d2, original index) lexicographically
+// smallest among points with d2 <= the incoming (best_d2, best_oi).
+__device__ __forceinline__ void nn_search(const IndexView& ix, int n, float qx, float qy, float qz, float& best_d2,
+                                          int& best_oi, int& best_pos)
+{
+    const int L = ix.L, B = ix.B;
+    int stk[32];
+    float sdist[32];
+    int sp = 0, node = 1;
+    while (true) {
+        if (node >= L) {
+            const int beg = (node - L) * B, end = min(beg + B, n);
+            for (int t = beg; t < end; ++t) {
+                const float4 p = ix.pts[t];
+                const float d2 = point_d2(qx, qy, qz, p);
+                const int oi = __float_as_int(p.w);
+                if (before(d2, oi, best_d2, best_oi)) {
+                    best_d2 = d2;
+                    best_oi = oi;
+                    best_pos = t;
+                }
+            }
+        } else {
+            const int c0 = 2 * node;
+            const float4* bx = ix.boxes + 2 * c0;
+            const float d0 = box_d2(qx, qy, qz, bx[0], bx[1]);
+            const float d1 = box_d2(qx, qy, qz, bx[2], bx[3]);
+            const bool first0 = d0 <= d1;
+            const int cn = first0 ? c0 : c0 + 1, cf = first0 ? c0 + 1 : c0;
+            const float dn = first0 ? d0 : d1, df = first0 ? d1 : d0;
+            if (dn <= best_d2) {
+                if (df <= best_d2 && sp < 32) {
+                    stk[sp] = cf;
+                    sdist[sp] = df;
+                    ++sp;
+                }
+                node = cn;
+                continue;
+            }
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (sdist[sp] <= best_d2) {
+                node = stk[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+// Index of (r, c), r <= c, in the row-major upper triangle of a 6x6 matrix.
+__host__ __device__ constexpr int ut(int r, int c) { return r * 6 - (r * (r - 1)) / 2 + (c - r); }
+
+// ---------------------------------------------------------------------------------------------
+// FP64 6x6 solve and SE(3) exponential (single thread)
+
+__device__ bool chol_solve6(const double H[36], const double rhs[6], double x[6])
+{
+    double L[21];  // lower triangle, row-major packed: L(i, j) at i*(i+1)/2 + j
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = H[6 * i + j];
+            for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+            if (i == j) {
+                if (!(s > 0.0) || !isfinite(s)) return false;
+                L[i * (i + 1) / 2 + i] = sqrt(s);
+            } else {
+                L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
+            }
+        }
+    }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = rhs[i];
+        for (int k = 0; k < i; ++k) s -= L[i * (i + 1) / 2 + k] * y[k];
+        y[i] = s / L[i * (i + 1) / 2 + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= L[k * (k + 1) / 2 + i] * x[k];
+        x[i] = s / L[i * (i + 1) / 2 + i];
+    }
+    return true;
+}
+
+// T <- exp(xi^) T with xi = (omega, v): rotation by Rodrigues' formula,
+// translation V v with V = I + B K + C K^2 (K = [omega]x); series for small angles.
+__device__ void se3_left_update(const double xi[6], double T[16])
+{
+    const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double A, Bc, Cc;
+    if (th2 < 1e-6) {
+        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        Bc = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        Cc = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    } else {
+        const double th = sqrt(th2);
+        const double sn = sin(th), hs = sin(0.5 * th);
+        A = sn / th;
+        Bc = 2.0 * hs * hs / th2;
+        Cc = (th - sn) / (th2 * th);
+    }
+    const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    double K2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+    double E[16];
+    for (int r = 0; r < 3; ++r) {
+        double tv = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double id = r == c ? 1.0 : 0.0;
+            E[4 * r + c] = id + A * K[3 * r + c] + Bc * K2[3 * r + c];
+            tv += (id + Bc * K[3 * r + c] + Cc * K2[3 * r + c]) * xi[3 + c];
+        }
+        E[4 * r + 3] = tv;
+    }
+    E[12] = 0.0; E[13] = 0.0; E[14] = 0.0; E[15] = 1.0;
+    double M[16];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int j = 0; j < 4; ++j) s += E[4 * r + j] * T[4 * j + c];
+            M[4 * r + c] = s;
+        }
+    for (int i = 0; i < 16; ++i) T[i] = M[i];
+}
+
+__device__ __forceinline__ void pose_to_float(RegState* st)
+{
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) st->Rf[3 * r + c] = (float)st->T[4 * r + c];
+        st->tf[r] = (float)st->T[4 * r + 3];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+
+__global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegState* __restrict__ st, Pose16 T0)
+{
+    *job_dst = job;
+    for (int i = 0; i < 16; ++i) st->T[i] = T0.v[i];
+    for (int i = 0; i < 36; ++i) st->H[i] = 0.0;
+    for (int i = 0; i < 6; ++i) st->b[i] = 0.0;
+    st->cost = 0.0;
+    st->inliers = 0;
+    st->iter = 0;
+    st->status = REG_ST_RUNNING;
+    st->counter = 0u;
+    pose_to_float(st);
+}
+
+__global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __restrict__ jp,
+                                                                cudaGraphConditionalHandle cond)
+{
+    const RegJob& J = *jp;
+    RegState* st = J.st;
+    if (st->status != REG_ST_RUNNING) {
+        // every block sees the same status here, so only this thread touches the condition
+        if (J.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int n = *J.n;
+    const int nmap = *J.map.n;
+    float R[9], t[3];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) R[a] = st->Rf[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t[a] = st->tf[a];
+    float acc[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
+
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float x0 = J.src[3l * i], x1 = J.src[3l * i + 1], x2 = J.src[3l * i + 2];
+        const float y0 = fmaf(R[0], x0, fmaf(R[1], x1, fmaf(R[2], x2, t[0])));
+        const float y1 = fmaf(R[3], x0, fmaf(R[4], x1, fmaf(R[5], x2, t[1])));
+        const float y2 = fmaf(R[6], x0, fmaf(R[7], x1, fmaf(R[8], x2, t[2])));
+        float best_d2 = J.max_d2;
+        int best_oi = 0x7fffffff, best_pos = -1;
+        const int prev = J.corr_cache[i];
+        if (prev >= 0) {  // previous correspondence: an admissible candidate, so a valid initial bound
+            const float4 p = J.map.pts[prev];
+            const float d2 = point_d2(y0, y1, y2, p);
+            if (d2 <= best_d2) {
+                best_d2 = d2;
+                best_oi = __float_as_int(p.w);
+                best_pos = prev;
+            }
+        }
+        nn_search(J.map, nmap, y0, y1, y2, best_d2, best_oi, best_pos);
+        J.corr_cache[i] = best_pos;
+        if (J.corr_out) J.corr_out[i] = best_pos >= 0 ? best_oi : -1;
+        if (best_pos < 0) continue;
+
+        acc[28] += 1.f;
+        const float4 mu = J.map.pts[best_pos];
+        const float4 ca = J.map.covs[2 * best_pos], cb = J.map.covs[2 * best_pos + 1];
+        const float* cs = J.covs_s + 6l * i;
+        const float S[9] = {cs[0], cs[1], cs[2], cs[1], cs[3], cs[4], cs[2], cs[4], cs[5]};
+        float RS[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                RS[3 * r + c] = fmaf(R[3 * r], S[c], fmaf(R[3 * r + 1], S[3 + c], R[3 * r + 2] * S[6 + c]));
+        auto rcr = [&](int r, int c) {
+            return fmaf(RS[3 * r], R[3 * c], fmaf(RS[3 * r + 1], R[3 * c + 1], RS[3 * r + 2] * R[3 * c + 2]));
+        };
+        // Sigma = C^t + R C^s R^T
+        const float s00 = ca.x + rcr(0, 0), s01 = ca.y + rcr(0, 1), s02 = ca.z + rcr(0, 2);
+        const float s11 = ca.w + rcr(1, 1), s12 = cb.x + rcr(1, 2), s22 = cb.y + rcr(2, 2);
+        // W = Sigma^-1 (cofactors / determinant)
+        const float c00 = s11 * s22 - s12 * s12, c01 = s02 * s12 - s01 * s22, c02 = s01 * s12 - s02 * s11;
+        const float det = s00 * c00 + s01 * c01 + s02 * c02;
+        if (!(fabsf(det) > 0.f)) continue;
+        const float id = 1.f / det;
+        const float W00 = c00 * id, W01 = c01 * id, W02 = c02 * id;
+        const float W11 = (s00 * s22 - s02 * s02) * id, W12 = (s01 * s02 - s00 * s12) * id;
+        const float W22 = (s00 * s11 - s01 * s01) * id;
+        const float W[9] = {W00, W01, W02, W01, W11, W12, W02, W12, W22};
+        const float d0 = mu.x - y0, d1 = mu.y - y1, d2 = mu.z - y2;
+        const float Wd0 = W00 * d0 + W01 * d1 + W02 * d2;
+        const float Wd1 = W01 * d0 + W11 * d1 + W12 * d2;
+        const float Wd2 = W02 * d0 + W12 * d1 + W22 * d2;
+        // A = [y]x ; WA = W A
+        const float A[9] = {0.f, -y2, y1, y2, 0.f, -y0, -y1, y0, 0.f};
+        float WA[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                WA[3 * r + c] = W[3 * r] * A[c] + W[3 * r + 1] * A[3 + c] + W[3 * r + 2] * A[6 + c];
+        // A^T W A = -A (W A): column c is -(y x WA[:, c])
+        float AWA[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float m0 = WA[c], m1 = WA[3 + c], m2 = WA[6 + c];
+            AWA[c] = -(y1 * m2 - y2 * m1);
+            AWA[3 + c] = -(y2 * m0 - y0 * m2);
+            AWA[6 + c] = -(y0 * m1 - y1 * m0);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = r; c < 3; ++c) acc[ut(r, c)] += AWA[3 * r + c];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[ut(r, 3 + c)] -= WA[3 * c + r];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = r; c < 3; ++c) acc[ut(3 + r, 3 + c)] += W[3 * r + c];
+        // b = [A^T W d ; -W d],  A^T u = u x y
+        acc[21] += Wd1 * y2 - Wd2 * y1;
+        acc[22] += Wd2 * y0 - Wd0 * y2;
+        acc[23] += Wd0 * y1 - Wd1 * y0;
+        acc[24] -= Wd0;
+        acc[25] -= Wd1;
+        acc[26] -= Wd2;
+        acc[27] += d0 * Wd0 + d1 * Wd1 + d2 * Wd2;
+    }
+
+    // ---- block reduction -> one partial per block
+    __shared__ float red[REG_THREADS / 32][NACC];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) {
+        float v = acc[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][a] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NACC) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < REG_THREADS / 32; ++w) v += red[w][threadIdx.x];
+        J.partials[32l * blockIdx.x + threadIdx.x] = v;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+
+    // ---- last block: compensated sum of all partials
+    __shared__ float shi[NACC][8], slo[NACC][8];
+    __shared__ double tot[NACC];
+    {
+        const int v = threadIdx.x >> 3, sub = threadIdx.x & 7;
+        if (v < NACC) {
+            dfloat s = {0.f, 0.f};
+            for (int b = sub; b < (int)gridDim.x; b += 8) df_add(s, __ldcg(J.partials + 32l * b + v));
+            shi[v][sub] = s.hi;
+            slo[v][sub] = s.lo;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NACC) {
+        double s = 0.0;
+        for (int j = 0; j < 8; ++j) s += (double)shi[threadIdx.x][j] + (double)slo[threadIdx.x][j];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+
+    double H[36], b[6];
+    for (int r = 0; r < 6; ++r)
+        for (int c = r; c < 6; ++c) H[6 * r + c] = H[6 * c + r] = tot[ut(r, c)];
+    for (int a = 0; a < 6; ++a) b[a] = tot[21 + a];
+    for (int a = 0; a < 36; ++a) st->H[a] = H[a];
+    for (int a = 0; a < 6; ++a) st->b[a] = b[a];
+    st->cost = tot[27];
+    st->inliers = (long long)llrint(tot[28]);
+    st->counter = 0u;
+    bool more = false;
+    if (J.mode == REG_MODE_SOLVE) {
+        st->iter += 1;
+        double nb[6], delta[6];
+        for (int a = 0; a < 6; ++a) nb[a] = -b[a];
+        if (st->inliers < J.min_inliers || !chol_solve6(H, nb, delta)) {
+            st->status = REG_ST_DEGENERATE;
+        } else {
+            se3_left_update(delta, st->T);
+            pose_to_float(st);
+            const double dw = sqrt(delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2]);
+            const double dv = sqrt(delta[3] * delta[3] + delta[4] * delta[4] + delta[5] * delta[5]);
+            if (dw < J.tol_rot && dv < J.tol_trans) st->status = REG_ST_CONVERGED;
+            else if (st->iter >= J.max_iters || st->iter >= 10000) st->status = REG_ST_MAXITER;
+            else more = true;
+        }
+    }
+    __threadfence();
+    if (J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------------------------
+
+gsicp_status RegMachine::init()
+{
+    if (exec) return GSICP_OK;
+    int dev = 0, sms = 0, per_sm = 0;
+    GSICP_CUDA(cudaGetDevice(&dev));
+    GSICP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GSICP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gicp_iter_kernel, REG_THREADS, 0));
+    grid = sms * std::max(1, per_sm);
+    GSICP_CHECK(partials.ensure(sizeof(float) * 32 * (size_t)grid));
+    GSICP_CHECK(job.ensure(sizeof(RegJob)));
+    GSICP_CHECK(state.ensure(sizeof(RegState)));
+    if (!state_host) GSICP_CUDA(cudaMallocHost((void**)&state_host, sizeof(RegState)));
+    GSICP_CUDA(cudaGraphCreate(&graph, 0));
+    GSICP_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    GSICP_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const RegJob* jptr = job.as<const RegJob>();
+    void* args[] = {(void*)&jptr, (void*)&cond};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)gicp_iter_kernel;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(REG_THREADS);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaGraphNode_t knode;
+    GSICP_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
+    GSICP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    return GSICP_OK;
+}
+
+void RegMachine::release()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    if (state_host) cudaFreeHost(state_host);
+    state_host = nullptr;
+    partials.release();
+    job.release();
+    state.release();
+    corr.release();
+}
+
+gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], int n_cap, bool solve,
+                     cudaStream_t s)
+{
+    GSICP_CHECK(rm.init());
+    GSICP_CHECK(rm.corr.ensure(sizeof(int) * (size_t)std::max(n_cap, 1)));
+    RegJob job = job_in;
+    job.corr_cache = rm.corr.as<int>();
+    job.partials = rm.partials.as<float>();
+    job.st = rm.state.as<RegState>();
+    job.mode = solve ? REG_MODE_SOLVE : REG_MODE_LINEARISE;
+    job.use_cond = solve ? 1 : 0;
+    Pose16 P;
+    for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
+    if (n_cap > 0) GSICP_CUDA(cudaMemsetAsync(rm.corr.ptr, 0xff, sizeof(int) * (size_t)n_cap, s));
+    reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
+    GSICP_CUDA(cudaGetLastError());
+    if (solve) {
+        GSICP_CUDA(cudaGraphLaunch(rm.exec, s));
+    } else {
+        gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
+        GSICP_CUDA(cudaGetLastError());
+    }
+    GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, sizeof(RegState), cudaMemcpyDeviceToHost, s));
+    return GSICP_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+
+__global__ void nearest_kernel(IndexView ix, const float* __restrict__ q, int nq, float max_d2,
+                               int32_t* __restrict__ idx, float* __restrict__ d2out)
+{
+    const int nmap = *ix.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+        float bd = max_d2;
+        int bo = 0x7fffffff, bp = -1;
+        nn_search(ix, nmap, q[3l * i], q[3l * i + 1], q[3l * i + 2], bd, bo, bp);
+        idx[i] = bp >= 0 ? bo : -1;
+        if (d2out) d2out[i] = bp >= 0 ? bd : GSICP_INF;
+    }
+}
+
+gsicp_status launch_nearest(const IndexView& map, const float* q, int nq, float max_d2, int32_t* idx, float* d2,
+                            cudaStream_t s)
+{
+    if (nq <= 0) return GSICP_OK;
+    const int grid = std::max(1, std::min((nq + 255) / 256, device_sm_count() * 8));
+    nearest_kernel<<<grid, 256, 0, s>>>(map, q, nq, max_d2, idx, d2);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+__global__ void transform_kernel(Pose16 T, const float* __restrict__ pts, const float* __restrict__ covs, int n,
+                                 float* __restrict__ po, float* __restrict__ co)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double x[3] = {pts[3l * i], pts[3l * i + 1], pts[3l * i + 2]};
+        for (int r = 0; r < 3; ++r)
+            po[3l * i + r] = (float)(T.v[4 * r] * x[0] + T.v[4 * r + 1] * x[1] + T.v[4 * r + 2] * x[2] + T.v[4 * r + 3]);
+        if (covs && co) {
+            const float* c = covs + 6l * i;
+            const double S[9] = {c[0], c[1], c[2], c[1], c[3], c[4], c[2], c[4], c[5]};
+            double RS[9];
+            for (int r = 0; r < 3; ++r)
+                for (int cc = 0; cc < 3; ++cc)
+                    RS[3 * r + cc] = T.v[4 * r] * S[cc] + T.v[4 * r + 1] * S[3 + cc] + T.v[4 * r + 2] * S[6 + cc];
+            double M[9];
+            for (int r = 0; r < 3; ++r)
+                for (int cc = 0; cc < 3; ++cc)
+                    M[3 * r + cc] = RS[3 * r] * T.v[4 * cc] + RS[3 * r + 1] * T.v[4 * cc + 1] + RS[3 * r + 2] * T.v[4 * cc + 2];
+            float* o = co + 6l * i;
+            o[0] = (float)M[0]; o[1] = (float)M[1]; o[2] = (float)M[2];
+            o[3] = (float)M[4]; o[4] = (float)M[5]; o[5] = (float)M[8];
+        }
+    }
+}
+
+gsicp_status launch_transform(const double T[16], const float* pts, const float* covs, int n, float* pts_out,
+                              float* covs_out, cudaStream_t s)
+{
+    if (n <= 0) return GSICP_OK;
+    Pose16 P;
+    for (int i = 0; i < 16; ++i) P.v[i] = T[i];
+    const int grid = std::max(1, std::min((n + 255) / 256, device_sm_count() * 8));
+    transform_kernel<<<grid, 256, 0, s>>>(P, pts, covs, n, pts_out, covs_out);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+__global__ void set_int_kernel(int* dst, int v) { *dst = v; }
+
+gsicp_status launch_set_int(int* dst, int value, cudaStream_t s)
+{
+    set_int_kernel<<<1, 1, 0, s>>>(dst, value);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+}  // namespace gsicp

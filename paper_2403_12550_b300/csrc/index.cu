@@ -1,0 +1,409 @@
+// index.cu -- device-built spatial index over a point set (map Gaussians or
+// the current frame's points): Morton codes -> stable LSD radix sort ->
+// bucketed leaves -> bottom-up bounding boxes.  Used for the nearest-neighbour
+// correspondence search of the registration (Sec. 3: correspondences "determined
+// by nearest neighbor search") and for the k-nearest-neighbour covariances
+// (Sec. 3: covariance "of k-nearest neighbors").
+#include <algorithm>
+
+#include "internal.h"
+
+namespace gsicp {
+
+// ------------------------------------------------------------------------------------------
+// device-wide exclusive scan (uint32)
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    uint32_t warp_prefix = warp > 0 ? warp_sums[warp - 1] : 0u;
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, int n, uint32_t* __restrict__ sums)
+{
+    __shared__ uint32_t ws[32];
+    const long base = (long)blockIdx.x * SCAN_TILE + (long)threadIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < n) s += in[base + j];
+    uint32_t total;
+    block_exclusive_scan(s, ws, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_kernel(uint32_t* sums, int nb)
+{
+    __shared__ uint32_t ws[32];
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan(v, ws, total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int n,
+                                  const uint32_t* __restrict__ sums)
+{
+    __shared__ uint32_t ws[32];
+    const long base = (long)blockIdx.x * SCAN_TILE + (long)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = base + j < n ? in[base + j] : 0u;
+        s += v[j];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, ws, total) + sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+}
+
+gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf& sums, cudaStream_t s)
+{
+    if (n <= 0) return GSICP_OK;
+    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    GSICP_CHECK(sums.ensure(sizeof(uint32_t) * nb));
+    scan_reduce_kernel<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums.as<uint32_t>());
+    scan_sums_kernel<<<1, 1024, 0, s>>>(sums.as<uint32_t>(), nb);
+    scan_apply_kernel<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, sums.as<uint32_t>());
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// stable LSD radix sort of (uint32 key, uint32 value), 8 bits per pass
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 8;                      // 32-key rounds per warp
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 2048 keys per block
+
+__global__ void rs_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* __restrict__ hist,
+                               int tiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long base = (long)blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        long i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(long)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Each warp ranks a contiguous run of 256 keys in order (32 at a time, peers
+// found with match.any), so equal digits keep their input order: stable.
+__global__ void rs_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int n, int shift,
+                                  const uint32_t* __restrict__ offs, int tiles)
+{
+    __shared__ uint32_t wc[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < RS_WARPS * 256; j += RS_THREADS) (&wc[0][0])[j] = 0;
+    __syncthreads();
+    const long sub = (long)blockIdx.x * RS_TILE + (long)warp * (32 * RS_ROUNDS);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t key[RS_ROUNDS], dig[RS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        long i = sub + r * 32 + lane;
+        key[r] = i < n ? kin[i] : 0u;
+        dig[r] = i < n ? ((key[r] >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        if (dig[r] < 256u && lane == __ffs(peers) - 1) wc[warp][dig[r]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // per digit: exclusive prefix over warps, offset by this tile's global base
+        const int d = threadIdx.x;
+        uint32_t run = offs[(long)d * tiles + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t c = wc[w][d];
+            wc[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        long i = sub + r * 32 + lane;
+        uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        if (dig[r] < 256u) {
+            uint32_t pos = wc[warp][dig[r]] + __popc(peers & lt_mask);
+            kout[pos] = key[r];
+            vout[pos] = vin[i];
+        }
+        __syncwarp();
+        if (dig[r] < 256u && lane == __ffs(peers) - 1) wc[warp][dig[r]] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// Sorts (k0, v0) into (k0, v0) using (k1, v1) as the ping-pong buffer; `bits` <= 32.
+static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int bits,
+                                     DevBuf& hist, DevBuf& sums, cudaStream_t s)
+{
+    if (n <= 1) return GSICP_OK;
+    const int tiles = (n + RS_TILE - 1) / RS_TILE;
+    GSICP_CHECK(hist.ensure(sizeof(uint32_t) * 256 * (size_t)tiles));
+    int passes = (bits + 7) / 8;
+    if (passes & 1) ++passes;  // even count: the result lands back in (k0, v0)
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        uint32_t* ki = (p & 1) ? k1 : k0;
+        uint32_t* vi = (p & 1) ? v1 : v0;
+        uint32_t* ko = (p & 1) ? k0 : k1;
+        uint32_t* vo = (p & 1) ? v0 : v1;
+        if (shift >= 32) {  // no bits left: plain copy keeps the ping-pong parity
+            GSICP_CUDA(cudaMemcpyAsync(ko, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+            GSICP_CUDA(cudaMemcpyAsync(vo, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+            continue;
+        }
+        rs_hist_kernel<<<tiles, RS_THREADS, 0, s>>>(ki, n, shift, hist.as<uint32_t>(), tiles);
+        GSICP_CHECK(exclusive_scan_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), 256 * tiles, sums, s));
+        rs_scatter_kernel<<<tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist.as<uint32_t>(), tiles);
+    }
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// index build kernels
+
+__global__ void bbox_init_kernel(uint32_t* bb)
+{
+    if (threadIdx.x < 3) bb[threadIdx.x] = 0xffffffffu;      // min (ordered encoding)
+    else if (threadIdx.x < 6) bb[threadIdx.x] = 0u;          // max
+}
+
+__global__ void bbox_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, uint32_t* bb)
+{
+    const int n = *n_dev;
+    float lo[3] = {GSICP_INF, GSICP_INF, GSICP_INF}, hi[3] = {-GSICP_INF, -GSICP_INF, -GSICP_INF};
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float c = pts[3 * i + a];
+            lo[a] = fminf(lo[a], c);
+            hi[a] = fmaxf(hi[a], c);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bb[a], f2ord(lo[a]));
+            atomicMax(&bb[3 + a], f2ord(hi[a]));
+        }
+    }
+}
+
+// 30-bit Morton key of each valid point over the bounding cube; padding slots get
+// 0xffffffff so they sort after every valid point.
+__global__ void morton_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, int cap,
+                              const uint32_t* __restrict__ bb, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    const int n = *n_dev;
+    const float lx = ord2f(bb[0]), ly = ord2f(bb[1]), lz = ord2f(bb[2]);
+    const float ext = fmaxf(fmaxf(ord2f(bb[3]) - lx, ord2f(bb[4]) - ly), ord2f(bb[5]) - lz);
+    const float scale = ext > 0.f ? 1024.f / ext : 0.f;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (long)gridDim.x * blockDim.x) {
+        uint32_t key = 0xffffffffu;
+        if (i < n) {
+            uint32_t qx = (uint32_t)min(1023, max(0, (int)((pts[3 * i + 0] - lx) * scale)));
+            uint32_t qy = (uint32_t)min(1023, max(0, (int)((pts[3 * i + 1] - ly) * scale)));
+            uint32_t qz = (uint32_t)min(1023, max(0, (int)((pts[3 * i + 2] - lz) * scale)));
+            key = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+        }
+        keys[i] = key;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void gather_kernel(const float* __restrict__ pts, const float* __restrict__ covs,
+                              const uint32_t* __restrict__ order, const int* __restrict__ n_dev, int total,
+                              float4* __restrict__ spts, float4* __restrict__ scovs)
+{
+    const int n = *n_dev;
+    for (long s = (long)blockIdx.x * blockDim.x + threadIdx.x; s < total; s += (long)gridDim.x * blockDim.x) {
+        if (s < n) {
+            const uint32_t i = order[s];
+            spts[s] = make_float4(pts[3l * i], pts[3l * i + 1], pts[3l * i + 2], __int_as_float((int)i));
+            if (scovs) {
+                const float* c = covs + 6l * i;
+                scovs[2 * s] = make_float4(c[0], c[1], c[2], c[3]);
+                scovs[2 * s + 1] = make_float4(c[4], c[5], 0.f, 0.f);
+            }
+        } else {
+            spts[s] = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, __int_as_float(-1));
+            if (scovs) {
+                scovs[2 * s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                scovs[2 * s + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+}
+
+__global__ void leaf_box_kernel(const float4* __restrict__ spts, const int* __restrict__ n_dev, int L, int B,
+                                float4* __restrict__ boxes)
+{
+    const int n = *n_dev;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
+        float4 lo = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, 0.f);
+        float4 hi = make_float4(-GSICP_INF, -GSICP_INF, -GSICP_INF, 0.f);
+        const int beg = l * B, end = min(beg + B, n);
+        for (int s = beg; s < end; ++s) {
+            float4 p = spts[s];
+            lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+            hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+        }
+        boxes[2l * (L + l)] = lo;
+        boxes[2l * (L + l) + 1] = hi;
+    }
+}
+
+// Reduce up to 8 levels of the implicit tree: level `count` (heap nodes
+// [count, 2count)) is read, each block merges a group of g = min(256, count)
+// consecutive nodes into their ancestors down to one node per group.
+__global__ void level_reduce_kernel(float4* __restrict__ boxes, int count)
+{
+    __shared__ float4 slo[256], shi[256];
+    const int g = min(256, count);
+    const int t = threadIdx.x;
+    const long first = (long)count + (long)blockIdx.x * g;
+    if (t < g) {
+        slo[t] = boxes[2 * (first + t)];
+        shi[t] = boxes[2 * (first + t) + 1];
+    }
+    __syncthreads();
+    int level = count, width = g;
+    long lfirst = first;
+    while (width > 1) {
+        const int half = width >> 1;
+        float4 lo, hi;
+        if (t < half) {
+            float4 a = slo[2 * t], b = slo[2 * t + 1], c = shi[2 * t], d = shi[2 * t + 1];
+            lo = make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.f);
+            hi = make_float4(fmaxf(c.x, d.x), fmaxf(c.y, d.y), fmaxf(c.z, d.z), 0.f);
+        }
+        __syncthreads();
+        level >>= 1;
+        lfirst >>= 1;
+        if (t < half) {
+            slo[t] = lo;
+            shi[t] = hi;
+            boxes[2 * (lfirst + t)] = lo;
+            boxes[2 * (lfirst + t) + 1] = hi;
+        }
+        __syncthreads();
+        width = half;
+    }
+}
+
+static int ceil_pow2(long x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+gsicp_status build_index(const float* pts, const float* covs, int cap, const int* n_dev, int bucket,
+                         IndexBufs& out, BuildScratch& scr, cudaStream_t s)
+{
+    if (bucket != 8 && bucket != 16 && bucket != 32) return GSICP_ERR_INVALID_ARG;
+    const int B = bucket;
+    const int L = std::max(1, ceil_pow2(((long)cap + B - 1) / B));
+    const int total = L * B;  // sorted slots incl. padding
+    GSICP_CHECK(out.pts.ensure(sizeof(float4) * (size_t)total));
+    GSICP_CHECK(out.boxes.ensure(sizeof(float4) * 4 * (size_t)L));
+    if (covs) GSICP_CHECK(out.covs.ensure(sizeof(float4) * 2 * (size_t)total));
+    out.L = L;
+    out.B = B;
+    out.cap = cap;
+    out.n_ptr = n_dev;
+    const int sort_n = std::max(cap, 1);
+    GSICP_CHECK(scr.k0.ensure(sizeof(uint32_t) * sort_n));
+    GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * sort_n));
+    GSICP_CHECK(scr.v0.ensure(sizeof(uint32_t) * sort_n));
+    GSICP_CHECK(scr.v1.ensure(sizeof(uint32_t) * sort_n));
+    GSICP_CHECK(scr.bbox.ensure(sizeof(uint32_t) * 8));
+    const int sms = device_sm_count();
+    const int grid = std::max(1, std::min((cap + 255) / 256, sms * 8));
+    bbox_init_kernel<<<1, 32, 0, s>>>(scr.bbox.as<uint32_t>());
+    bbox_kernel<<<grid, 256, 0, s>>>(pts, n_dev, scr.bbox.as<uint32_t>());
+    morton_kernel<<<grid, 256, 0, s>>>(pts, n_dev, cap, scr.bbox.as<uint32_t>(), scr.k0.as<uint32_t>(),
+                                       scr.v0.as<uint32_t>());
+    GSICP_CUDA(cudaGetLastError());
+    GSICP_CHECK(radix_sort_pairs(scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
+                                 scr.v1.as<uint32_t>(), cap, 30, scr.hist, scr.sums, s));
+    const int ggrid = std::max(1, std::min((total + 255) / 256, sms * 8));
+    gather_kernel<<<ggrid, 256, 0, s>>>(pts, covs, scr.v0.as<uint32_t>(), n_dev, total, out.pts.as<float4>(),
+                                        covs ? out.covs.as<float4>() : nullptr);
+    leaf_box_kernel<<<std::max(1, std::min((L + 255) / 256, sms * 8)), 256, 0, s>>>(out.pts.as<float4>(), n_dev,
+                                                                                    L, B, out.boxes.as<float4>());
+    for (int count = L; count > 1; count = count / std::min(256, count)) {
+        const int blocks = count / std::min(256, count);
+        level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
+    }
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+IndexView IndexBufs::view() const
+{
+    IndexView v;
+    v.pts = pts.as<const float4>();
+    v.boxes = boxes.as<const float4>();
+    v.covs = covs.ptr ? covs.as<const float4>() : nullptr;
+    v.n = n_ptr;
+    v.L = L;
+    v.B = B;
+    return v;
+}
+
+}  // namespace gsicp

@@ -1,0 +1,115 @@
+// internal.h -- host-side declarations shared by the libgsicp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gsicp.h"
+#include "common.cuh"
+
+namespace gsicp {
+
+// Record a CUDA error for gsicp_last_error() and map it to a status.
+gsicp_status cuda_status(cudaError_t e, const char* where);
+
+#define GSICP_CUDA(call)                                                \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::gsicp::cuda_status(e_, #call); \
+    } while (0)
+
+#define GSICP_CHECK(st)                          \
+    do {                                         \
+        gsicp_status s_ = (st);                  \
+        if (s_ != GSICP_OK) return s_;           \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    gsicp_status ensure(size_t want);
+    void release();
+    template <class T>
+    T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Buffers of one spatial index (either owned by a map or scratch of a context).
+struct IndexBufs {
+    DevBuf pts, boxes, covs;
+    const int* n_ptr = nullptr;  // device count of valid points (set by build_index)
+    int L = 0, B = 16, cap = 0;
+    IndexView view() const;
+};
+
+// Scratch for building an index: sort keys/values (double-buffered), histogram, scan sums, bbox.
+struct BuildScratch {
+    DevBuf k0, k1, v0, v1, hist, sums, bbox;
+};
+
+// Build an index over the first *n_dev of `cap` points (pts n x 3, covs n x 6 optional).
+gsicp_status build_index(const float* pts, const float* covs, int cap, const int* n_dev, int bucket,
+                         IndexBufs& out, BuildScratch& scr, cudaStream_t s);
+
+// Device-wide exclusive scan of uint32 values; in may equal out.  `sums` is scratch.
+gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf& sums, cudaStream_t s);
+
+// a1: depth -> points (row-major compaction).  Writes *n_dev (clamped to cap) and *total_dev (unclamped).
+gsicp_status launch_depth_to_points(const float* depth, int W, int H, const float intr[4], int stride,
+                                    float z_min, float z_max, float* pts, float* z, int cap, int* n_dev,
+                                    int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s);
+
+// a2+a3: k-NN covariances of the points of `ix` (its pts hold the n points; orig gives the
+// unsorted xyz for neighbour gathering).
+gsicp_status launch_knn_cov(const IndexView& ix, const float* orig_pts, const float* z, int cap,
+                            const gsicp_cov_params& prm, float* covs, int32_t* knn, cudaStream_t s);
+
+// Registration machinery.
+struct RegMachine {
+    int grid = 0;
+    DevBuf partials, job, state, corr;
+    RegState* state_host = nullptr;  // pinned
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond{};
+    gsicp_status init();
+    void release();
+};
+
+gsicp_status reg_run(RegMachine& rm, const RegJob& job, const double T0[16], int n_cap, bool solve,
+                     cudaStream_t s);
+
+gsicp_status launch_nearest(const IndexView& map, const float* q, int nq, float max_d2, int32_t* idx,
+                            float* d2, cudaStream_t s);
+
+gsicp_status launch_transform(const double T[16], const float* pts, const float* covs, int n, float* pts_out,
+                              float* covs_out, cudaStream_t s);
+
+gsicp_status launch_set_int(int* dst, int value, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace gsicp
+
+struct gsicp_ctx_s {
+    int device = 0;
+    gsicp::BuildScratch build;
+    gsicp::IndexBufs src_index;       // per-frame source index
+    gsicp::DevBuf a1_counts, a1_sums, n_dev, total_dev;
+    gsicp::DevBuf frame_pts, frame_z, frame_covs, frame_depth;
+    gsicp::RegMachine reg;
+    int64_t* host_pinned = nullptr;   // small pinned scratch for counts
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+};
+
+struct gsicp_map_s {
+    int device = 0;
+    int64_t m = 0;
+    gsicp::IndexBufs index;
+    gsicp::DevBuf means, covs;        // unsorted copies (for appends)
+    gsicp::DevBuf count;              // device int: number of Gaussians
+};

@@ -1,0 +1,74 @@
+"""Shared helpers for the parity tests: input preparation through the oracle only,
+and pose / covariance comparisons."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as orc
+from synth import REPLICA_INTR, frame_config2, pair_config1, transform_points
+
+# Tolerances ("Parity bars").
+POSE_ROT_TOL = 1e-4      # rad
+POSE_TRANS_TOL = 1e-5    # m
+COV_REL_TOL = 1e-4       # relative Frobenius
+KNN_TIE_REL = 1e-6       # kNN set swaps allowed between oracle distances this close
+PLANE_GAP_EXCLUDE = 1e-3
+
+
+def rot_angle(R: np.ndarray) -> float:
+    return float(np.arccos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)))
+
+
+def pose_diff(Ta: np.ndarray, Tb: np.ndarray):
+    """(rotation angle of Ra^T Rb, |ta - tb|)."""
+    return rot_angle(Ta[:3, :3].T @ Tb[:3, :3]), float(np.linalg.norm(Ta[:3, 3] - Tb[:3, 3]))
+
+
+def sym(c6):
+    c6 = np.asarray(c6)
+    return np.stack([np.stack([c6[..., 0], c6[..., 1], c6[..., 2]], -1),
+                     np.stack([c6[..., 1], c6[..., 3], c6[..., 4]], -1),
+                     np.stack([c6[..., 2], c6[..., 4], c6[..., 5]], -1)], -2)
+
+
+def cov_rel_err(a6, b6):
+    """Relative Frobenius error of symmetric 3x3 matrices given as 6-vectors (per row)."""
+    A, B = sym(a6), sym(b6)
+    return np.linalg.norm((A - B).reshape(len(A), -1), axis=1) / np.maximum(np.linalg.norm(B.reshape(len(B), -1), axis=1), 1e-300)
+
+
+def config1_inputs(scene_seed: int, pose_seed: int, n: int = 10_000, reg_mode: int = orc.PLANE):
+    """Config-1 pair with oracle-made covariances, everything float32 as the GPU reads it."""
+    src, tgt, T_gt = pair_config1(scene_seed, pose_seed, n=n)
+    cs = orc.source_covariances(src, k=20, eps=1e-3, reg_mode=reg_mode)["covs"].astype(np.float32)
+    ct = orc.source_covariances(tgt, k=20, eps=1e-3, reg_mode=reg_mode)["covs"].astype(np.float32)
+    return src, cs, tgt, ct, T_gt
+
+
+def oracle_frame_points(depth, intr=REPLICA_INTR, stride=2, z_min=0.1, z_max=10.0):
+    pts, z = orc.depth_to_points(depth, intr.as_array(), stride, z_min, z_max)
+    return pts.astype(np.float32), z.astype(np.float32)
+
+
+def oracle_map_from_views(view_depths, view_poses, intr=REPLICA_INTR, stride=2, p=1.5, reg_mode=orc.PLANE):
+    """Map Gaussians built by the oracle: each prior view back-projected, its
+    covariances computed and scale-aligned, then moved into the world frame."""
+    means, covs = [], []
+    for d, P in zip(view_depths, view_poses):
+        pts, z = oracle_frame_points(d, intr, stride)
+        c = orc.source_covariances(pts, z, k=20, eps=1e-3, reg_mode=reg_mode, p=p)["covs"]
+        mw, cw = orc.transform_gaussians(P, pts, c)
+        means.append(mw)
+        covs.append(cw)
+    return np.concatenate(means).astype(np.float32), np.concatenate(covs).astype(np.float32)
+
+
+def config2_inputs(seed: int = 0):
+    f = frame_config2(seed)
+    means, covs = oracle_map_from_views(f["view_depths"], f["view_poses"])
+    return f, means, covs
+
+
+__all__ = ["POSE_ROT_TOL", "POSE_TRANS_TOL", "COV_REL_TOL", "KNN_TIE_REL", "PLANE_GAP_EXCLUDE", "rot_angle",
+           "pose_diff", "sym", "cov_rel_err", "config1_inputs", "oracle_frame_points", "oracle_map_from_views",
+           "config2_inputs", "transform_points"]

@@ -1,0 +1,80 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point that
+include/gsicp.h declares, and rejects bad arguments before touching a device."""
+import ctypes as C
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsicp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_12550_b300.build import build
+    return C.CDLL(build())
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsicp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_path(lib):
+    names = declared_functions()
+    for required in ("gsicp_build_map_index", "gsicp_source_covariances", "gsicp_register",
+                     "gsicp_depth_to_points", "gsicp_track_frame"):
+        assert required in names
+    assert len(names) >= 15
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_invalid_arguments_are_rejected_without_a_device(lib):
+    INVALID = 1
+    lib.gsicp_ctx_create.argtypes = [C.c_void_p]
+    assert lib.gsicp_ctx_create(None) == INVALID
+    lib.gsicp_register.argtypes = [C.c_void_p] * 5 + [C.c_void_p] * 9
+    lib.gsicp_register.restype = C.c_int
+    assert lib.gsicp_register(*([None] * 14)) == INVALID
+    lib.gsicp_build_map_index.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
+    assert lib.gsicp_build_map_index(None, None, None, 0, None, None, None) == INVALID
+    lib.gsicp_source_covariances.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]
+    assert lib.gsicp_source_covariances(None, None, None, 10, None, None, None, None) == INVALID
+    lib.gsicp_map_size.restype = C.c_int64
+    assert lib.gsicp_map_size(None) == 0
+    lib.gsicp_map_destroy(None)
+    lib.gsicp_ctx_destroy(None)
+    lib.gsicp_status_string.restype = C.c_char_p
+    assert b"degenerate" in lib.gsicp_status_string(4)
+    lib.gsicp_version.restype = C.c_char_p
+    assert lib.gsicp_version().startswith(b"0.")
+
+
+def test_package_fails_loudly_without_the_library(tmp_path):
+    """With no libgsicp.so next to it the binding refuses to import: there is no fallback."""
+    import shutil
+    pkg = os.path.join(ROOT, "paper_2403_12550_b300")
+    dst = tmp_path / "paper_2403_12550_b300"
+    shutil.copytree(pkg, dst, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_2403_12550_b300"], cwd=tmp_path,
+                       capture_output=True, text=True)
+    assert r.returncode != 0 and "libgsicp.so is missing" in r.stderr
+
+
+def test_product_never_touches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2403_12550_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower(), f

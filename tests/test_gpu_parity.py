@@ -1,0 +1,357 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Inputs come from the seeded generators (synth) and, where the method's own
+arithmetic is needed to make an input (covariances of a map), from the oracle;
+nothing the CUDA library produced is ever fed to the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from synth import (Intrinsics, REPLICA_INTR, add_depth_noise, frame_config2, make_room, random_offset, raycast_depth,
+                   circle_poses, transform_points)
+
+from ._util import (COV_REL_TOL, KNN_TIE_REL, PLANE_GAP_EXCLUDE, POSE_ROT_TOL, POSE_TRANS_TOL, config1_inputs,
+                    config2_inputs, cov_rel_err, oracle_frame_points, pose_diff, sym)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_12550_b300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(g):
+    c = g.Context()
+    yield c
+    c.close()
+
+
+def cu(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ----------------------------------------------------------------------------- a1
+
+def _depth_case(W, H, seed, dropout=0.02):
+    intr = Intrinsics(W, H, 0.5 * W, 0.5 * W, (W - 1) / 2, (H - 1) / 2)
+    scene = make_room(seed)
+    rng = np.random.default_rng(seed)
+    P = circle_poses(rng, scene, 1)[0]
+    d = add_depth_noise(raycast_depth(scene, P, intr), rng, 1e-3, dropout=dropout)
+    d[rng.random(d.shape) < 0.01] = np.nan
+    d[rng.random(d.shape) < 0.01] = 50.0  # beyond z_max
+    return intr, d
+
+
+@pytest.mark.parametrize("W,H,stride", [(1, 1, 1), (37, 23, 1), (64, 48, 2), (101, 77, 3), (1200, 680, 2),
+                                        (640, 480, 2), (640, 480, 1)])
+def test_depth_to_points_bit_exact(g, ctx, W, H, stride):
+    intr, d = _depth_case(W, H, W + H)
+    pts_o, z_o = orc.depth_to_points(d, intr.as_array(), stride, 0.1, 10.0)
+    pts, z = g.gsicp_depth_to_points(ctx, cu(d), intr.as_array(), stride, 0.1, 10.0)
+    assert pts.shape[0] == len(pts_o)
+    # each coordinate is the correctly rounded value of the formula on both sides
+    np.testing.assert_array_equal(pts.cpu().numpy(), pts_o.astype(np.float32))
+    np.testing.assert_array_equal(z.cpu().numpy(), z_o.astype(np.float32))
+
+
+def test_depth_to_points_empty_and_capacity(g, ctx):
+    d = np.full((48, 64), np.nan, dtype=np.float32)
+    pts, z = g.gsicp_depth_to_points(ctx, cu(d), [50, 50, 31.5, 23.5], 2, 0.1, 10.0)
+    assert pts.shape[0] == 0
+    d = np.ones((48, 64), dtype=np.float32)
+    small = torch.empty((10, 3), device="cuda")
+    with pytest.raises(g.GsicpError) as e:
+        g.gsicp_depth_to_points(ctx, cu(d), [50, 50, 31.5, 23.5], 2, 0.1, 10.0, pts_out=small,
+                                z_out=torch.empty(10, device="cuda"))
+    assert e.value.status == g.ERR_CAPACITY
+
+
+# ----------------------------------------------------------------------------- a2 + a3
+
+def _check_knn_and_covs(pts, z, mode, p, k, g, ctx, gap_exclude=True):
+    ref = orc.source_covariances(pts, z, k=k, eps=1e-3, reg_mode=mode, p=p)
+    idx_o, d2_o = orc.KDTree(pts).knn(pts, k)
+    params = g.CovParams(k, 1e-3, mode, p)
+    covs, knn = g.gsicp_source_covariances(ctx, cu(pts), None if z is None else cu(z), params, want_knn=True)
+    covs, knn = covs.cpu().numpy().astype(np.float64), knn.cpu().numpy()
+    n = len(pts)
+    kk = min(k, n)
+    # kNN: identical lists, except swaps among candidates whose oracle distances tie within 1e-6
+    same = np.all(knn == idx_o, axis=1)
+    bad = np.nonzero(~same)[0]
+    P = pts.astype(np.float64)
+    for i in bad:
+        gi = knn[i, :kk]
+        assert np.all(gi >= 0) and len(set(gi.tolist())) == kk
+        dg = np.sort(np.sum((P[gi] - P[i]) ** 2, axis=1))
+        kth = d2_o[i, kk - 1]
+        assert np.all(dg <= kth * (1 + KNN_TIE_REL) + 1e-30), (i, dg, kth)
+        assert np.allclose(dg, d2_o[i, :kk], rtol=KNN_TIE_REL, atol=1e-30)
+    if k > n:
+        assert np.all(knn[:, n:] == -1)
+    # covariances: relative Frobenius, excluding ill-posed normals under PLANE and tie-swapped sets
+    keep = same.copy()
+    if mode == orc.PLANE and gap_exclude:
+        keep &= ref["gap"] >= PLANE_GAP_EXCLUDE
+    if mode != orc.NONE:  # the line-like test (middle/largest eigenvalue <= 1e-5) is a threshold: skip its edge
+        w = np.linalg.eigvalsh(sym(ref["raw"]))
+        ratio = w[:, 1] / np.maximum(w[:, 2], 1e-300)
+        keep &= ~((ratio > 0.5e-5) & (ratio < 2e-5))
+    err = cov_rel_err(covs, ref["covs"])
+    worst = float(err[keep].max()) if keep.any() else 0.0
+    assert worst <= COV_REL_TOL, (worst, np.argmax(np.where(keep, err, 0)))
+    return dict(n=n, knn_mismatch=len(bad), excluded=int((~keep).sum()), worst=worst)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 19, 20, 21, 33, 100, 1000, 4097])
+def test_source_covariances_small_and_ragged(g, ctx, n):
+    rng = np.random.default_rng(n)
+    pts = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    if n > 10:
+        pts[rng.integers(0, n, n // 10)] = pts[rng.integers(0, n, n // 10)]  # exact duplicates
+    for mode in (orc.PLANE, orc.ELLIPSE, orc.NONE):
+        _check_knn_and_covs(pts, None, mode, 0.0, 20, g, ctx)
+
+
+@pytest.mark.parametrize("k", [1, 5, 8, 16, 20, 32])
+def test_source_covariances_k(g, ctx, k):
+    src, _, _ = __import__("synth").pair_config1(3, 0, n=3000)
+    _check_knn_and_covs(src, None, orc.ELLIPSE, 0.0, k, g, ctx)
+
+
+@pytest.mark.parametrize("mode", [orc.PLANE, orc.ELLIPSE, orc.NONE])
+def test_source_covariances_config1(g, ctx, mode):
+    src, _, _ = __import__("synth").pair_config1(0, 0, n=10_000)
+    r = _check_knn_and_covs(src, None, mode, 0.0, 20, g, ctx)
+    assert r["excluded"] < 0.01 * r["n"]
+
+
+@pytest.mark.parametrize("p", [1.0, 1.5])
+def test_source_covariances_frame_with_scale_aligning(g, ctx, p):
+    f = frame_config2(0, n_views=0)
+    pts, z = oracle_frame_points(f["depth"])
+    r = _check_knn_and_covs(pts, z, orc.PLANE, p, 20, g, ctx)
+    assert r["excluded"] < 0.01 * r["n"]
+
+
+def test_source_covariances_collinear_and_coincident(g, ctx):
+    t = np.linspace(0, 1, 50, dtype=np.float32)
+    line = np.stack([t, 2 * t, -t], 1)
+    same = np.ones((25, 3), dtype=np.float32)
+    for pts in (line, same):
+        for mode in (orc.PLANE, orc.ELLIPSE):
+            ref = orc.source_covariances(pts, k=20, reg_mode=mode)["covs"]
+            covs = g.gsicp_source_covariances(ctx, cu(pts), None, g.CovParams(20, 1e-3, mode, 0.0)).cpu().numpy()
+            np.testing.assert_allclose(covs, ref, atol=1e-6)
+
+
+# ----------------------------------------------------------------------------- a4 + a5 nearest neighbours
+
+def _check_nearest(map_pts, queries, max_dist, g, ctx, bucket=0):
+    covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (len(map_pts), 1))
+    m = g.gsicp_build_map_index(ctx, cu(map_pts), cu(covs), bucket=bucket)
+    idx, d2 = g.gsicp_map_nearest(ctx, m, cu(queries), max_dist)
+    idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    io, do = orc.KDTree(map_pts).nn(queries, float(np.float32(max_dist)))
+    r2 = float(np.float32(max_dist)) ** 2
+    diff = np.nonzero(idx != io)[0]
+    P, Q = map_pts.astype(np.float64), queries.astype(np.float64)
+    for i in diff:
+        if idx[i] < 0 or io[i] < 0:  # inlier decision differs only at the radius boundary
+            dd = do[i] if io[i] >= 0 else np.sum((P[idx[i]] - Q[i]) ** 2)
+            assert abs(dd - r2) <= 1e-6 * r2
+        else:
+            dg = np.sum((P[idx[i]] - Q[i]) ** 2)
+            assert dg <= do[i] * (1 + 1e-6)
+    fin = idx >= 0
+    np.testing.assert_allclose(d2[fin], np.sum((P[idx[fin]] - Q[fin]) ** 2, axis=1), rtol=1e-6, atol=1e-12)
+    m.close()
+    return len(diff)
+
+
+@pytest.mark.parametrize("bucket", [8, 16, 32])
+def test_map_nearest_small(g, ctx, bucket):
+    rng = np.random.default_rng(bucket)
+    for m_n in (1, 7, 100, 5000):
+        mp = rng.uniform(-1, 1, size=(m_n, 3)).astype(np.float32)
+        q = np.concatenate([rng.uniform(-1.2, 1.2, size=(3000, 3)), mp[: min(m_n, 500)]]).astype(np.float32)
+        assert _check_nearest(mp, q, 0.1, g, ctx, bucket) <= 2
+
+
+def test_map_nearest_ties(g, ctx):
+    mp = np.array([[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [1, 0, 0]], np.float32)
+    q = np.zeros((1, 3), np.float32)
+    m = g.gsicp_build_map_index(ctx, cu(mp), cu(np.tile([1, 0, 0, 1, 0, 1], (6, 1)).astype(np.float32)))
+    idx, _ = g.gsicp_map_nearest(ctx, m, cu(q), 2.0)
+    assert idx.item() == 0
+    idx, _ = g.gsicp_map_nearest(ctx, m, cu(q), 1.0)  # boundary inclusive
+    assert idx.item() == 0
+    idx, _ = g.gsicp_map_nearest(ctx, m, cu(q), 0.999)
+    assert idx.item() == -1
+
+
+def test_map_nearest_config2_full_size(g, ctx):
+    """2M-Gaussian map, 200k queries: every answer checked against the oracle."""
+    f, means, _ = _cfg2()
+    pts, _ = oracle_frame_points(f["depth"])
+    q = transform_points(f["T0"], pts.astype(np.float64)).astype(np.float32)
+    nd = _check_nearest(means, q, 0.1, g, ctx)
+    assert nd < 1e-4 * len(q)
+
+
+# ----------------------------------------------------------------------------- a5 + a6 linearisation
+
+def test_linearise_matches_oracle(g, ctx):
+    src, cs, tgt, ct, T_gt = config1_inputs(0, 0)
+    m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    om = orc.Map(tgt, ct)
+    for T in (np.eye(4), T_gt, T_gt @ random_offset(np.random.default_rng(1), 1.0, 0.01)):
+        lg = g.gsicp_linearise(ctx, cu(src), cu(cs), m, T, 0.1)
+        lo = orc.linearise(src, cs, om, T, 0.1)
+        corr = lg["corr"].cpu().numpy()
+        mism = np.count_nonzero(corr != lo["corr"])
+        assert mism <= 1e-3 * len(src)
+        assert abs(lg["inliers"] - lo["inliers"]) <= mism
+        herr = np.linalg.norm(lg["H"] - lo["H"]) / np.linalg.norm(lo["H"])
+        berr = np.linalg.norm(lg["b"] - lo["b"]) / max(np.linalg.norm(lo["b"]), 1e-12)
+        cerr = abs(lg["cost"] - lo["cost"]) / max(lo["cost"], 1e-12)
+        assert herr < 1e-3 and cerr < 1e-3 and (berr < 1e-2 or np.linalg.norm(lo["b"]) < 1e-3 * np.linalg.norm(lo["H"])), \
+            (herr, berr, cerr, mism)
+    m.close()
+
+
+# ----------------------------------------------------------------------------- a5-a7 registration
+
+@pytest.mark.parametrize("scene_seed,pose_seed", [(0, 0), (1, 1), (2, 2), (3, 0), (4, 1)])
+def test_register_config1_matches_oracle(g, ctx, scene_seed, pose_seed):
+    src, cs, tgt, ct, T_gt = config1_inputs(scene_seed, pose_seed)
+    rg_ = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    rg = g.gsicp_register(ctx, cu(src), cu(cs), m, np.eye(4), rg_)
+    ro = orc.register(src, cs, orc.Map(tgt, ct), np.eye(4), 0.1, 30, 1e-6, 1e-6, 6)
+    assert rg["status"] == g.OK and ro["status"] == orc.OK
+    dr, dt = pose_diff(rg["T"], ro["T"])
+    assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (dr, dt, rg["iters"], ro["iters"])
+    # and the oracle itself recovers the ground truth to the sampling-noise level
+    gr, gt = pose_diff(ro["T"], T_gt)
+    assert gr < np.deg2rad(0.5) and gt < 0.01
+    m.close()
+
+
+def test_register_end_to_end_gpu_covariances(g, ctx):
+    """GPU covariances -> GPU registration vs oracle covariances -> oracle registration."""
+    import synth
+    src, tgt, T_gt = synth.pair_config1(5, 0, n=10_000)
+    p = g.CovParams(20, 1e-3, g.PLANE, 0.0)
+    cs_g = g.gsicp_source_covariances(ctx, cu(src), None, p)
+    ct_g = g.gsicp_source_covariances(ctx, cu(tgt), None, p)
+    m = g.gsicp_build_map_index(ctx, cu(tgt), ct_g)
+    rg = g.gsicp_register(ctx, cu(src), cs_g, m, np.eye(4), g.RegParams())
+    cs = orc.source_covariances(src, k=20, reg_mode=orc.PLANE)["covs"]
+    ct = orc.source_covariances(tgt, k=20, reg_mode=orc.PLANE)["covs"]
+    ro = orc.register(src, cs, orc.Map(tgt, ct), np.eye(4))
+    dr, dt = pose_diff(rg["T"], ro["T"])
+    assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (dr, dt)
+
+
+def test_register_degenerate_and_edge_cases(g, ctx):
+    src, cs, tgt, ct, _ = config1_inputs(0, 0, n=2000)
+    m = g.gsicp_build_map_index(ctx, cu(tgt + 10.0), cu(ct))  # far away: no correspondences
+    r = g.gsicp_register(ctx, cu(src), cu(cs), m, np.eye(4), g.RegParams())
+    assert r["status"] == g.ERR_DEGENERATE and r["inliers"] == 0 and r["iters"] == 1
+    np.testing.assert_array_equal(r["T"], np.eye(4))
+    # empty source
+    m2 = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    r = g.gsicp_register(ctx, cu(src[:0]), cu(cs[:0]), m2, np.eye(4), g.RegParams())
+    assert r["status"] == g.ERR_DEGENERATE
+    # empty map
+    m3 = g.gsicp_build_map_index(ctx, cu(tgt[:0]), cu(ct[:0]))
+    r = g.gsicp_register(ctx, cu(src), cu(cs), m3, np.eye(4), g.RegParams())
+    assert r["status"] == g.ERR_DEGENERATE
+    # a single iteration equals the oracle's single iteration
+    r = g.gsicp_register(ctx, cu(src), cu(cs), m2, np.eye(4), g.RegParams(max_iters=1))
+    ro = orc.register(src, cs, orc.Map(tgt, ct), np.eye(4), max_iters=1)
+    assert r["iters"] == 1 and ro["iters"] == 1
+    dr, dt = pose_diff(r["T"], ro["T"])
+    assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL
+    # invalid arguments are rejected without touching the device
+    with pytest.raises(g.GsicpError) as e:
+        g.gsicp_register(ctx, cu(src), cu(cs), m2, np.eye(4), g.RegParams(max_iters=0))
+    assert e.value.status == g.ERR_INVALID_ARG
+    for mm in (m, m2, m3):
+        mm.close()
+
+
+def test_map_append_equals_full_build(g, ctx):
+    src, cs, tgt, ct, _ = config1_inputs(1, 0, n=4000)
+    a = g.gsicp_build_map_index(ctx, cu(tgt[:1500]), cu(ct[:1500]))
+    g.gsicp_map_append(ctx, a, cu(tgt[1500:]), cu(ct[1500:]))
+    b = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    assert a.size == b.size == 4000
+    ra = g.gsicp_register(ctx, cu(src), cu(cs), a, np.eye(4), g.RegParams())
+    rb = g.gsicp_register(ctx, cu(src), cu(cs), b, np.eye(4), g.RegParams())
+    np.testing.assert_array_equal(ra["T"], rb["T"])
+
+
+def test_transform_gaussians(g, ctx):
+    rng = np.random.default_rng(0)
+    pts = rng.normal(size=(1000, 3)).astype(np.float32)
+    covs = rng.normal(size=(1000, 6)).astype(np.float32)
+    T = random_offset(rng, 30, 1.0)
+    po, co = g.gsicp_transform_gaussians(T, cu(pts), cu(covs))
+    ro, rc = orc.transform_gaussians(T, pts, covs)
+    np.testing.assert_allclose(po.cpu().numpy(), ro, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(co.cpu().numpy(), rc, rtol=1e-5, atol=1e-5)
+
+
+# ----------------------------------------------------------------------------- whole frame (config 2, full size)
+
+_CFG2 = {}
+
+
+def _cfg2():
+    if not _CFG2:
+        _CFG2["v"] = config2_inputs(0)
+    return _CFG2["v"]
+
+
+def test_track_frame_config2_matches_oracle(g, ctx):
+    """1200x680 frame (~204k points) against a 2M-Gaussian map, in the launch
+    configuration the benchmark times."""
+    f, means, covs = _cfg2()
+    m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    r = g.gsicp_track_frame(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
+    pts, z = oracle_frame_points(f["depth"])
+    cs = orc.source_covariances(pts, z, k=20, eps=1e-3, reg_mode=orc.PLANE, p=1.5)["covs"]
+    ro = orc.register(pts, cs, orc.Map(means, covs), f["T0"], 0.1, 30, 1e-6, 1e-6, 6)
+    assert r["status"] == g.OK and ro["status"] == orc.OK
+    assert r["n_points"] == len(pts)
+    dr, dt = pose_diff(r["T"], ro["T"])
+    assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (dr, dt, r["iters"], ro["iters"])
+    # host-buffer entry point gives the same answer
+    rh = g.gsicp_track_frame_host(ctx, f["depth"], REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
+    np.testing.assert_array_equal(rh["T"], r["T"])
+    m.close()
+
+
+def test_track_frame_empty_depth(g, ctx):
+    src, cs, tgt, ct, _ = config1_inputs(0, 0, n=2000)
+    m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    d = np.zeros((68, 120), np.float32)
+    r = g.gsicp_track_frame(ctx, cu(d), [60, 60, 59.5, 33.5], 2, 0.1, 10.0, g.CovParams(), m, np.eye(4),
+                            g.RegParams())
+    assert r["status"] == g.ERR_DEGENERATE and r["n_points"] == 0
