@@ -88,13 +88,16 @@ static gsicp_status finish_registration(gsicp_ctx ctx, cudaStream_t s, double T_
     return GSICP_OK;
 }
 
-static RegJob make_job(const float* src, const float* covs_s, const int* n_dev, gsicp_map map,
+constexpr float FIRST_PASS_RADIUS = 0.015f;  // m; see the nearest-neighbour walk in gicp.cu
+
+static RegJob make_job(const float4* src, const float4* covs_s, const int* n_dev, gsicp_map map,
                        const gsicp_reg_params* prm)
 {
     RegJob job;
     memset(&job, 0, sizeof(job));
     job.src = src;
     job.covs_s = covs_s;
+    job.cap2 = FIRST_PASS_RADIUS * FIRST_PASS_RADIUS;
     job.n = n_dev;
     job.map = map->index.view();
     job.corr_out = nullptr;
@@ -105,6 +108,15 @@ static RegJob make_job(const float* src, const float* covs_s, const int* n_dev, 
     job.tol_trans = prm ? prm->tol_trans : 0.0;
     job.min_inliers = prm ? prm->min_inliers : 0;
     return job;
+}
+
+// Morton-ordered copy of a caller's source cloud and its covariances (for gsicp_register/linearise).
+static gsicp_status prepare_source(gsicp_ctx ctx, const float* pts, const float* covs, int n, cudaStream_t s)
+{
+    GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), n, s));
+    GSICP_CHECK(build_index(pts, nullptr, n, ctx->n_dev.as<int>(), 32, ctx->src_index, ctx->build, s));
+    GSICP_CHECK(ctx->covs_sorted.ensure(sizeof(float4) * 2 * (size_t)std::max(n, 1)));
+    return launch_permute_covs(ctx->src_index.view(), covs, n, ctx->covs_sorted.as<float4>(), s);
 }
 
 static gsicp_status map_build(gsicp_ctx ctx, gsicp_map map, int bucket, cudaStream_t s)
@@ -176,6 +188,7 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     ctx->src_index.pts.release(); ctx->src_index.boxes.release(); ctx->src_index.covs.release();
     ctx->a1_counts.release(); ctx->a1_sums.release(); ctx->n_dev.release(); ctx->total_dev.release();
     ctx->frame_pts.release(); ctx->frame_z.release(); ctx->frame_covs.release(); ctx->frame_depth.release();
+    ctx->covs_sorted.release();
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -229,7 +242,7 @@ gsicp_status gsicp_source_covariances(gsicp_ctx ctx, const float* pts_dev, const
     cudaStream_t s = (cudaStream_t)stream;
     GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), (int)n, s));
     GSICP_CHECK(build_index(pts_dev, nullptr, (int)n, ctx->n_dev.as<int>(), 32, ctx->src_index, ctx->build, s));
-    return launch_knn_cov(ctx->src_index.view(), pts_dev, z_dev, (int)n, *params, covs_dev, knn_dev, s);
+    return launch_knn_cov(ctx->src_index.view(), pts_dev, z_dev, (int)n, *params, covs_dev, knn_dev, nullptr, s);
 }
 
 gsicp_status gsicp_build_map_index(gsicp_ctx ctx, const float* means_dev, const float* covs_dev, int64_t m,
@@ -342,8 +355,9 @@ gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float
         return GSICP_ERR_INVALID_ARG;
     if (n > 0 && (!src_pts_dev || !src_covs_dev)) return GSICP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), (int)n, s));
-    RegJob job = make_job(src_pts_dev, src_covs_dev, ctx->n_dev.as<int>(), map, params);
+    GSICP_CHECK(prepare_source(ctx, src_pts_dev, src_covs_dev, (int)n, s));
+    RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
+                          map, params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, (int)n, true, s));
     return finish_registration(ctx, s, T_out, H_out, b_out, iters_out, cost_out, inliers_out);
 }
@@ -357,8 +371,9 @@ gsicp_status gsicp_linearise(gsicp_ctx ctx, const float* src_pts_dev, const floa
     if (n > 0 && (!src_pts_dev || !src_covs_dev)) return GSICP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     gsicp_reg_params prm = {max_corr_dist, 1, 0.0, 0.0, 0};
-    GSICP_CHECK(launch_set_int(ctx->n_dev.as<int>(), (int)n, s));
-    RegJob job = make_job(src_pts_dev, src_covs_dev, ctx->n_dev.as<int>(), map, &prm);
+    GSICP_CHECK(prepare_source(ctx, src_pts_dev, src_covs_dev, (int)n, s));
+    RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
+                          map, &prm);
     job.corr_out = corr_dev;
     GSICP_CHECK(reg_run(ctx->reg, job, T, (int)n, false, s));
     gsicp_status st = finish_registration(ctx, s, nullptr, H_out, b_out, nullptr, cost_out, inliers_out);
@@ -395,10 +410,11 @@ static gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int 
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
     GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
+    GSICP_CHECK(ctx->covs_sorted.ensure(sizeof(float4) * 2 * (size_t)cap));
     GSICP_CHECK(launch_knn_cov(ctx->src_index.view(), ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap,
-                               *cov_params, ctx->frame_covs.as<float>(), nullptr, s));
+                               *cov_params, ctx->frame_covs.as<float>(), nullptr, ctx->covs_sorted.as<float4>(), s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], s));
-    RegJob job = make_job(ctx->frame_pts.as<float>(), ctx->frame_covs.as<float>(), nd, map, reg_params);
+    RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));
     if (n_points_out) GSICP_CUDA(cudaMemcpyAsync(ctx->host_pinned, nd, sizeof(int), cudaMemcpyDeviceToHost, s));

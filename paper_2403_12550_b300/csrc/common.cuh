@@ -119,8 +119,8 @@ struct RegState {
 };
 
 struct RegJob {
-    const float* src;      // n x 3
-    const float* covs_s;   // n x 6
+    const float4* src;     // source points in Morton order (x, y, z, original index), n
+    const float4* covs_s;  // their covariances in the same order, 2 float4 each (xx,xy,xz,yy | yz,zz,-,-)
     const int* n;          // device count
     IndexView map;
     int* corr_cache;       // n: sorted map position of the last correspondence (-1 none)
@@ -128,6 +128,7 @@ struct RegJob {
     float* partials;       // grid x NACC
     RegState* st;
     float max_d2;
+    float cap2;            // first-pass search bound of the cooperative nearest-neighbour walk
     int max_iters;
     double tol_rot, tol_trans;
     int min_inliers;

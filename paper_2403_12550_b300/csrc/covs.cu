@@ -7,14 +7,15 @@
 // covariance by its middle eigenvalue.  Sec. 3.2: scale aligning divides the
 // scales by z^p, i.e. multiplies the covariance by z^(-2p).
 //
-// One thread per query, queries taken in Morton order so that neighbouring
-// threads walk the same part of the tree.  The k best candidates live in
-// registers as a sorted list; the list is padded at the front with "phantom"
-// entries so that the k-th best always sits in the last slot (static register
-// indexing for any k <= KMAX).
+// One thread per query, queries taken in the index's Morton order so that a
+// warp's threads walk the same part of the tree (traverse.cuh).  Each thread
+// keeps its k best candidates in registers as a sorted list, padded at the
+// front with "phantom" entries so that the k-th best always sits in the last
+// slot (static register indexing for any k <= KMAX).
 #include <algorithm>
 
 #include "internal.h"
+#include "traverse.cuh"
 
 namespace gsicp {
 
@@ -89,10 +90,11 @@ template <int KMAX>
 __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, const float* __restrict__ orig,
                                                               const float* __restrict__ zin, int k, float eps,
                                                               int mode, float p, float* __restrict__ covs,
-                                                              int32_t* __restrict__ knn_out)
+                                                              int32_t* __restrict__ knn_out,
+                                                              float4* __restrict__ covs_sorted)
 {
     const int n = *ix.n;
-    const int L = ix.L, B = ix.B;
+    const int B = ix.B;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const float4 q = ix.pts[s];
         const int qi = __float_as_int(q.w);
@@ -104,58 +106,29 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
             D[j] = phantom ? -1.f : GSICP_INF;
             I[j] = phantom ? -1 : 0x7fffffff;
         }
-        // ---- exact k-NN by best-first descent with box pruning
-        int stk[32];
-        float sdist[32];
-        int sp = 0, node = 1;
-        while (true) {
-            if (node >= L) {
-                const int beg = (node - L) * B, end = min(beg + B, n);
-                for (int t = beg; t < end; ++t) {
-                    const float4 pp = ix.pts[t];
-                    const float d2 = point_d2(q.x, q.y, q.z, pp);
-                    const int oi = __float_as_int(pp.w);
-                    if (before(d2, oi, D[KMAX - 1], I[KMAX - 1])) {
-                        D[KMAX - 1] = d2;
-                        I[KMAX - 1] = oi;
+        // ---- exact k-NN (ties -> smaller original index)
+        float bound = GSICP_INF;
+        auto scan = [&](int lf) {
+            const int beg = lf * B, end = min(beg + B, n);
+            for (int t = beg; t < end; ++t) {
+                const float4 pp = ix.pts[t];
+                const float d2 = point_d2(q.x, q.y, q.z, pp);
+                const int oi = __float_as_int(pp.w);
+                if (before(d2, oi, D[KMAX - 1], I[KMAX - 1])) {
+                    D[KMAX - 1] = d2;
+                    I[KMAX - 1] = oi;
 #pragma unroll
-                        for (int j = KMAX - 1; j > 0; --j) {
-                            if (before(D[j], I[j], D[j - 1], I[j - 1])) {
-                                float td = D[j]; D[j] = D[j - 1]; D[j - 1] = td;
-                                int ti = I[j]; I[j] = I[j - 1]; I[j - 1] = ti;
-                            }
+                    for (int u = KMAX - 1; u > 0; --u) {
+                        if (before(D[u], I[u], D[u - 1], I[u - 1])) {
+                            float td = D[u]; D[u] = D[u - 1]; D[u - 1] = td;
+                            int ti = I[u]; I[u] = I[u - 1]; I[u - 1] = ti;
                         }
                     }
                 }
-            } else {
-                const int c0 = 2 * node;
-                const float d0 = box_d2(q.x, q.y, q.z, ix.boxes[2 * c0], ix.boxes[2 * c0 + 1]);
-                const float d1 = box_d2(q.x, q.y, q.z, ix.boxes[2 * c0 + 2], ix.boxes[2 * c0 + 3]);
-                const float bound = D[KMAX - 1];
-                const bool first0 = d0 <= d1;
-                const int cn = first0 ? c0 : c0 + 1, cf = first0 ? c0 + 1 : c0;
-                const float dn = first0 ? d0 : d1, df = first0 ? d1 : d0;
-                if (dn <= bound) {
-                    if (df <= bound && sp < 32) {
-                        stk[sp] = cf;
-                        sdist[sp] = df;
-                        ++sp;
-                    }
-                    node = cn;
-                    continue;
-                }
             }
-            bool found = false;
-            while (sp > 0) {
-                --sp;
-                if (sdist[sp] <= D[KMAX - 1]) {
-                    node = stk[sp];
-                    found = true;
-                    break;
-                }
-            }
-            if (!found) break;
-        }
+            bound = D[KMAX - 1];
+        };
+        traverse(ix, q.x, q.y, q.z, bound, scan);
         // ---- covariance of the neighbourhood (two-pass, float), neighbours gathered by original index
         int kk = 0;
         float m0 = 0.f, m1 = 0.f, m2 = 0.f;
@@ -264,6 +237,10 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
         }
 #pragma unroll
         for (int a = 0; a < 6; ++a) covs[6l * qi + a] = out[a];
+        if (covs_sorted) {
+            covs_sorted[2l * s] = make_float4(out[0], out[1], out[2], out[3]);
+            covs_sorted[2l * s + 1] = make_float4(out[4], out[5], 0.f, 0.f);
+        }
         if (knn_out) {
 #pragma unroll
             for (int j = 0; j < KMAX; ++j)
@@ -273,19 +250,24 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
 }
 
 gsicp_status launch_knn_cov(const IndexView& ix, const float* orig_pts, const float* z, int cap,
-                            const gsicp_cov_params& prm, float* covs, int32_t* knn, cudaStream_t s)
+                            const gsicp_cov_params& prm, float* covs, int32_t* knn, float4* covs_sorted,
+                            cudaStream_t s)
 {
     if (cap <= 0) return GSICP_OK;
     const int grid = std::max(1, std::min((cap + COV_THREADS - 1) / COV_THREADS, device_sm_count() * 16));
     const int k = prm.k;
     if (k <= 8)
-        knn_cov_kernel<8><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn);
+        knn_cov_kernel<8><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn,
+                                                         covs_sorted);
     else if (k <= 16)
-        knn_cov_kernel<16><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn);
+        knn_cov_kernel<16><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn,
+                                                         covs_sorted);
     else if (k <= 20)
-        knn_cov_kernel<20><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn);
+        knn_cov_kernel<20><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn,
+                                                         covs_sorted);
     else
-        knn_cov_kernel<32><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn);
+        knn_cov_kernel<32><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn,
+                                                         covs_sorted);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

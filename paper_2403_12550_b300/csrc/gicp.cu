@@ -7,12 +7,12 @@
 // minimised by Gauss-Newton with left perturbations T <- exp(xi^) T,
 // xi = (omega, v): J_i = dd_i/dxi = [[y_i]x, -I] with y_i = R x_i + t.
 //
-// One kernel launch per iteration.  Every thread handles source points in a
-// grid-stride loop: transform, exact nearest map mean (best-first descent of
-// the map's bounding-volume hierarchy, seeded with the previous iteration's
-// correspondence as an initial bound), residual, weight, J^T W J (21 unique),
-// J^T W d (6), d^T W d and the inlier count -> warp shuffles -> one FP32
-// partial per block.  The last block to finish (threadfence + atomic
+// One kernel launch per iteration.  One thread per source point, points in
+// the source index's Morton order: transform, exact nearest map mean by a walk
+// of the map's bounding-volume hierarchy (traverse.cuh) whose bound starts at
+// the distance to the previous iteration's correspondence, then the residual,
+// weight, J^T W J (21 unique), J^T W d (6), d^T W d and the inlier count ->
+// warp shuffles -> one FP32 partial per block.  The last block to finish (threadfence + atomic
 // counter, no waiting) sums the partials with compensation, solves the 6x6
 // system by FP64 Cholesky, applies the FP64 SE(3) exponential and, inside a
 // CUDA graph, sets the conditional-while handle that decides whether the
@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "traverse.cuh"
 
 namespace gsicp {
 
@@ -30,52 +31,21 @@ constexpr int REG_THREADS = 256;
 __device__ __forceinline__ void nn_search(const IndexView& ix, int n, float qx, float qy, float qz, float& best_d2,
                                           int& best_oi, int& best_pos)
 {
-    const int L = ix.L, B = ix.B;
-    int stk[32];
-    float sdist[32];
-    int sp = 0, node = 1;
-    while (true) {
-        if (node >= L) {
-            const int beg = (node - L) * B, end = min(beg + B, n);
-            for (int t = beg; t < end; ++t) {
-                const float4 p = ix.pts[t];
-                const float d2 = point_d2(qx, qy, qz, p);
-                const int oi = __float_as_int(p.w);
-                if (before(d2, oi, best_d2, best_oi)) {
-                    best_d2 = d2;
-                    best_oi = oi;
-                    best_pos = t;
-                }
-            }
-        } else {
-            const int c0 = 2 * node;
-            const float4* bx = ix.boxes + 2 * c0;
-            const float d0 = box_d2(qx, qy, qz, bx[0], bx[1]);
-            const float d1 = box_d2(qx, qy, qz, bx[2], bx[3]);
-            const bool first0 = d0 <= d1;
-            const int cn = first0 ? c0 : c0 + 1, cf = first0 ? c0 + 1 : c0;
-            const float dn = first0 ? d0 : d1, df = first0 ? d1 : d0;
-            if (dn <= best_d2) {
-                if (df <= best_d2 && sp < 32) {
-                    stk[sp] = cf;
-                    sdist[sp] = df;
-                    ++sp;
-                }
-                node = cn;
-                continue;
+    const int B = ix.B;
+    auto scan = [&](int lf) {
+        const int beg = lf * B, end = min(beg + B, n);
+        for (int u = beg; u < end; ++u) {
+            const float4 p = ix.pts[u];
+            const float d2 = point_d2(qx, qy, qz, p);
+            const int oi = __float_as_int(p.w);
+            if (before(d2, oi, best_d2, best_oi)) {
+                best_d2 = d2;
+                best_oi = oi;
+                best_pos = u;
             }
         }
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (sdist[sp] <= best_d2) {
-                node = stk[sp];
-                found = true;
-                break;
-            }
-        }
-        if (!found) break;
-    }
+    };
+    traverse(ix, qx, qy, qz, best_d2, scan);
 }
 
 // Index of (r, c), r <= c, in the row-major upper triangle of a 6x6 matrix.
@@ -201,15 +171,16 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
 
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float x0 = J.src[3l * i], x1 = J.src[3l * i + 1], x2 = J.src[3l * i + 2];
-        const float y0 = fmaf(R[0], x0, fmaf(R[1], x1, fmaf(R[2], x2, t[0])));
-        const float y1 = fmaf(R[3], x0, fmaf(R[4], x1, fmaf(R[5], x2, t[1])));
-        const float y2 = fmaf(R[6], x0, fmaf(R[7], x1, fmaf(R[8], x2, t[2])));
+    // one thread per source point, points in Morton order
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const float4 x = J.src[s];
+        const float y0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t[0])));
+        const float y1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t[1])));
+        const float y2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t[2])));
         float best_d2 = J.max_d2;
         int best_oi = 0x7fffffff, best_pos = -1;
-        const int prev = J.corr_cache[i];
-        if (prev >= 0) {  // previous correspondence: an admissible candidate, so a valid initial bound
+        const int prev = J.corr_cache[s];
+        if (prev >= 0) {  // last iteration's correspondence is admissible: a valid initial bound
             const float4 p = J.map.pts[prev];
             const float d2 = point_d2(y0, y1, y2, p);
             if (d2 <= best_d2) {
@@ -218,16 +189,30 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
                 best_pos = prev;
             }
         }
-        nn_search(J.map, nmap, y0, y1, y2, best_d2, best_oi, best_pos);
-        J.corr_cache[i] = best_pos;
-        if (J.corr_out) J.corr_out[i] = best_pos >= 0 ? best_oi : -1;
+        const int B = J.map.B;
+        auto scan = [&](int lf) {
+            const int beg = lf * B, end = min(beg + B, nmap);
+            for (int u = beg; u < end; ++u) {
+                const float4 p = J.map.pts[u];
+                const float d2 = point_d2(y0, y1, y2, p);
+                const int oi = __float_as_int(p.w);
+                if (before(d2, oi, best_d2, best_oi)) {
+                    best_d2 = d2;
+                    best_oi = oi;
+                    best_pos = u;
+                }
+            }
+        };
+        traverse(J.map, y0, y1, y2, best_d2, scan);
+        J.corr_cache[s] = best_pos;
+        if (J.corr_out) J.corr_out[__float_as_int(x.w)] = best_pos >= 0 ? best_oi : -1;
         if (best_pos < 0) continue;
 
         acc[28] += 1.f;
         const float4 mu = J.map.pts[best_pos];
         const float4 ca = J.map.covs[2 * best_pos], cb = J.map.covs[2 * best_pos + 1];
-        const float* cs = J.covs_s + 6l * i;
-        const float S[9] = {cs[0], cs[1], cs[2], cs[1], cs[3], cs[4], cs[2], cs[4], cs[5]};
+        const float4 sa = J.covs_s[2l * s], sb = J.covs_s[2l * s + 1];
+        const float S[9] = {sa.x, sa.y, sa.z, sa.y, sa.w, sb.x, sa.z, sb.x, sb.y};
         float RS[9];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -504,6 +489,27 @@ gsicp_status launch_transform(const double T[16], const float* pts, const float*
     for (int i = 0; i < 16; ++i) P.v[i] = T[i];
     const int grid = std::max(1, std::min((n + 255) / 256, device_sm_count() * 8));
     transform_kernel<<<grid, 256, 0, s>>>(P, pts, covs, n, pts_out, covs_out);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+__global__ void permute_covs_kernel(IndexView ix, const float* __restrict__ covs, int cap,
+                                    float4* __restrict__ out)
+{
+    const int n = *ix.n;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < min(n, cap); s += gridDim.x * blockDim.x) {
+        const long i = __float_as_int(ix.pts[s].w);
+        const float* c = covs + 6 * i;
+        out[2l * s] = make_float4(c[0], c[1], c[2], c[3]);
+        out[2l * s + 1] = make_float4(c[4], c[5], 0.f, 0.f);
+    }
+}
+
+gsicp_status launch_permute_covs(const IndexView& ix, const float* covs, int cap, float4* out, cudaStream_t s)
+{
+    if (cap <= 0) return GSICP_OK;
+    const int grid = std::max(1, std::min((cap + 255) / 256, device_sm_count() * 8));
+    permute_covs_kernel<<<grid, 256, 0, s>>>(ix, covs, cap, out);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

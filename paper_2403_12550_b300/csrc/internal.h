@@ -64,7 +64,11 @@ gsicp_status launch_depth_to_points(const float* depth, int W, int H, const floa
 // a2+a3: k-NN covariances of the points of `ix` (its pts hold the n points; orig gives the
 // unsorted xyz for neighbour gathering).
 gsicp_status launch_knn_cov(const IndexView& ix, const float* orig_pts, const float* z, int cap,
-                            const gsicp_cov_params& prm, float* covs, int32_t* knn, cudaStream_t s);
+                            const gsicp_cov_params& prm, float* covs, int32_t* knn, float4* covs_sorted,
+                            cudaStream_t s);
+
+// Copy covariances (n x 6, original order) into the index's Morton order (2 float4 per point).
+gsicp_status launch_permute_covs(const IndexView& ix, const float* covs, int cap, float4* out, cudaStream_t s);
 
 // Registration machinery.
 struct RegMachine {
@@ -99,6 +103,7 @@ struct gsicp_ctx_s {
     gsicp::IndexBufs src_index;       // per-frame source index
     gsicp::DevBuf a1_counts, a1_sums, n_dev, total_dev;
     gsicp::DevBuf frame_pts, frame_z, frame_covs, frame_depth;
+    gsicp::DevBuf covs_sorted;         // source covariances in the source index's order
     gsicp::RegMachine reg;
     int64_t* host_pinned = nullptr;   // small pinned scratch for counts
     bool timing = false;
