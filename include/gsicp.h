@@ -102,6 +102,15 @@ const char* gsicp_version(void);
 gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable);
 gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6]);
 
+/* Telemetry of the last registration on this context (gsicp_register, gsicp_track_frame*): for
+ * each of the first min(n, 64) Gauss-Newton iterations, the number of source points whose cached
+ * map candidates had to be searched again (refreshes_out), the device time in ns from the first
+ * block's start to the last block's arrival at the reduction (main_ns_out), of the final
+ * reduction and solve by the last block (tail_ns_out) and of the FP64 solve and pose update alone
+ * (solve_ns_out).  Any output may be NULL. */
+gsicp_status gsicp_ctx_reg_stats(gsicp_ctx ctx, int n, int32_t* refreshes_out, int32_t* tail_ns_out,
+                                 int32_t* solve_ns_out, int32_t* main_ns_out);
+
 /* ---------------------------------------------------------------------------------------------
  * a1  Depth image -> point cloud   (Sec. 3, Fig. 2: "downsampling and reprojecting the depth image")
  *
@@ -152,6 +161,13 @@ gsicp_status gsicp_map_append(gsicp_ctx ctx, gsicp_map map, const float* means_d
 /* Rebuild a map's index over the Gaussians it already holds (the a4 step alone; no allocation
  * once the map exists).  Stream-ordered, no synchronisation. */
 gsicp_status gsicp_map_rebuild(gsicp_ctx ctx, gsicp_map map, void* stream);
+/* Introspection of a map's index (tests and tools).  pts_dev (nullable) receives the index-ordered
+ * means as 4 float32 per Gaussian (x, y, z, original index as int32 bits); boxes_dev (nullable)
+ * receives the axis-aligned boxes of the 2L heap nodes (node i: lo.xyz, 0, hi.xyz, 0; node 1 is
+ * the root, nodes L..2L-1 the leaves, node 0 unused); *n_leaves_out = L, *bucket_out = points per
+ * leaf.  Stream-ordered, no synchronisation. */
+gsicp_status gsicp_map_inspect(gsicp_map map, float* pts_dev, float* boxes_dev, int64_t* n_leaves_out,
+                               int* bucket_out, void* stream);
 /* Number of Gaussians in a map. */
 int64_t gsicp_map_size(gsicp_map map);
 void gsicp_map_destroy(gsicp_map map);

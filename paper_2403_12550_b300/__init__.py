@@ -18,9 +18,9 @@ import torch
 __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
-    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_source_covariances", "gsicp_build_map_index", "gsicp_map_append",
-    "gsicp_map_rebuild", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_linearise",
+    "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
 ]
 
@@ -84,6 +84,7 @@ _sig("gsicp_last_error", C.c_char_p, [])
 _sig("gsicp_version", C.c_char_p, [])
 _sig("gsicp_ctx_set_timing", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
+_sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
 _sig("gsicp_depth_to_points", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, _vp, _vp,
                                         C.c_int64, _vp, _i64p, _vp])
 _sig("gsicp_source_covariances", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(CovParams), _vp, _vp, _vp])
@@ -92,6 +93,7 @@ _sig("gsicp_build_map_index", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(Inde
 _sig("gsicp_map_append", C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp])
 _sig("gsicp_map_size", C.c_int64, [_vp])
 _sig("gsicp_map_rebuild", C.c_int, [_vp, _vp, _vp])
+_sig("gsicp_map_inspect", C.c_int, [_vp, _vp, _vp, _i64p, C.POINTER(C.c_int), _vp])
 _sig("gsicp_map_destroy", None, [_vp])
 _sig("gsicp_transform_gaussians", C.c_int, [_dp, _vp, _vp, C.c_int64, _vp, _vp, _vp])
 _sig("gsicp_register", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(RegParams), _dp, _dp, _dp,
@@ -206,6 +208,13 @@ def gsicp_ctx_phase_times(ctx: Context) -> dict:
     return dict(zip(keys, list(out)))
 
 
+def gsicp_ctx_reg_stats(ctx: Context, n: int = 64) -> dict:
+    """Per-iteration telemetry of the last registration: cache refreshes and tail time (ns)."""
+    rf, tl, sv, mn = ((C.c_int32 * n)() for _ in range(4))
+    _check(lib.gsicp_ctx_reg_stats(ctx.ptr, n, rf, tl, sv, mn), "gsicp_ctx_reg_stats")
+    return dict(refreshes=list(rf), tail_ns=list(tl), solve_ns=list(sv), main_ns=list(mn))
+
+
 def gsicp_depth_to_points(ctx: Context, depth: torch.Tensor, intr, stride: int, z_min: float, z_max: float,
                           pts_out: torch.Tensor | None = None, z_out: torch.Tensor | None = None):
     """a1.  Returns ``(pts[:n], z[:n])`` (views of the output buffers)."""
@@ -253,6 +262,18 @@ def gsicp_map_append(ctx: Context, map_: MapHandle, means: torch.Tensor, covs: t
 def gsicp_map_rebuild(ctx: Context, map_: MapHandle):
     """a4 alone: rebuild the map's index over the Gaussians it holds."""
     _check(lib.gsicp_map_rebuild(ctx.ptr, map_.ptr, _stream()), "gsicp_map_rebuild")
+
+
+def gsicp_map_inspect(map_: MapHandle) -> dict:
+    """The map index's Morton-ordered means (m x 4: x, y, z, original index bits) and node boxes
+    (2L x 8: lo.xyz, 0, hi.xyz, 0), with L and the bucket size."""
+    L = C.c_int64(0)
+    B = C.c_int(0)
+    _check(lib.gsicp_map_inspect(map_.ptr, None, None, C.byref(L), C.byref(B), _stream()), "gsicp_map_inspect")
+    pts = torch.empty((map_.size, 4), device="cuda", dtype=torch.float32)
+    boxes = torch.empty((2 * L.value, 8), device="cuda", dtype=torch.float32)
+    _check(lib.gsicp_map_inspect(map_.ptr, _dev(pts), _dev(boxes), None, None, _stream()), "gsicp_map_inspect")
+    return dict(pts=pts, boxes=boxes, L=L.value, B=B.value)
 
 
 def gsicp_map_size(map_: MapHandle) -> int:

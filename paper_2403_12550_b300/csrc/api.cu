@@ -2,6 +2,7 @@
 // checks, context / map lifetime, and the sequencing of the kernels of each
 // entry point on the caller's stream.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -88,7 +89,7 @@ static gsicp_status finish_registration(gsicp_ctx ctx, cudaStream_t s, double T_
     return GSICP_OK;
 }
 
-constexpr float FIRST_PASS_RADIUS = 0.015f;  // m; see the nearest-neighbour walk in gicp.cu
+constexpr float CACHE_SLACK = 0.01f;  // m beyond max_corr_dist kept in the candidate cache (gicp.cu)
 
 static RegJob make_job(const float4* src, const float4* covs_s, const int* n_dev, gsicp_map map,
                        const gsicp_reg_params* prm)
@@ -97,7 +98,7 @@ static RegJob make_job(const float4* src, const float4* covs_s, const int* n_dev
     memset(&job, 0, sizeof(job));
     job.src = src;
     job.covs_s = covs_s;
-    job.cap2 = FIRST_PASS_RADIUS * FIRST_PASS_RADIUS;
+    job.slack = CACHE_SLACK;
     job.n = n_dev;
     job.map = map->index.view();
     job.corr_out = nullptr;
@@ -123,7 +124,7 @@ static gsicp_status map_build(gsicp_ctx ctx, gsicp_map map, int bucket, cudaStre
 {
     GSICP_CHECK(launch_set_int(map->count.as<int>(), (int)map->m, s));
     return build_index(map->means.as<float>(), map->covs.as<float>(), (int)map->m, map->count.as<int>(), bucket,
-                       map->index, ctx->build, s);
+                       map->index, ctx->build, s, true);
 }
 
 }  // namespace gsicp
@@ -168,7 +169,9 @@ gsicp_status gsicp_ctx_create(gsicp_ctx* out)
         e = cudaMallocHost((void**)&c->host_pinned, sizeof(int64_t) * 8);
         if (e != cudaSuccess) st = cuda_status(e, "cudaMallocHost");
     }
-    if (st == GSICP_OK) st = c->reg.init();
+    if (st == GSICP_OK) st = c->reg.init(1 << 18);
+    const char* unrolled = getenv("GSICP_UNROLLED_GN");
+    c->reg.unrolled = unrolled && unrolled[0] == '1';
     if (st != GSICP_OK) {
         gsicp_ctx_destroy(c);
         return st;
@@ -186,6 +189,7 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     b.k0.release(); b.k1.release(); b.v0.release(); b.v1.release(); b.hist.release(); b.sums.release();
     b.bbox.release();
     ctx->src_index.pts.release(); ctx->src_index.boxes.release(); ctx->src_index.covs.release();
+    ctx->src_index.quant.release();
     ctx->a1_counts.release(); ctx->a1_sums.release(); ctx->n_dev.release(); ctx->total_dev.release();
     ctx->frame_pts.release(); ctx->frame_z.release(); ctx->frame_covs.release(); ctx->frame_depth.release();
     ctx->covs_sorted.release();
@@ -208,6 +212,22 @@ gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6])
 {
     if (!ctx || !out) return GSICP_ERR_INVALID_ARG;
     for (int i = 0; i < 6; ++i) out[i] = ctx->phase_ms[i];
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_reg_stats(gsicp_ctx ctx, int n, int32_t* refreshes_out, int32_t* tail_ns_out,
+                                 int32_t* solve_ns_out, int32_t* main_ns_out)
+{
+    if (!ctx || n < 0 || !ctx->reg.state_host) return GSICP_ERR_INVALID_ARG;
+    const RegState& st = *ctx->reg.state_host;
+    for (int i = 0; i < n; ++i) {
+        const bool in = i < REG_STATS;
+        if (refreshes_out) refreshes_out[i] = in ? st.refreshes[i] : 0;
+        if (tail_ns_out) tail_ns_out[i] = in ? st.tail_ns[i] : 0;
+        if (solve_ns_out) solve_ns_out[i] = in ? st.solve_ns[i] : 0;
+        if (main_ns_out)
+            main_ns_out[i] = in && st.t_arrive[i] >= st.t_first[i] ? (int32_t)(st.t_arrive[i] - st.t_first[i]) : 0;
+    }
     return GSICP_OK;
 }
 
@@ -323,6 +343,22 @@ gsicp_status gsicp_map_rebuild(gsicp_ctx ctx, gsicp_map map, void* stream)
     return map_build(ctx, map, map->index.B, (cudaStream_t)stream);
 }
 
+gsicp_status gsicp_map_inspect(gsicp_map map, float* pts_dev, float* boxes_dev, int64_t* n_leaves_out,
+                               int* bucket_out, void* stream)
+{
+    if (!map) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (pts_dev && map->m > 0)
+        GSICP_CUDA(cudaMemcpyAsync(pts_dev, map->index.pts.ptr, sizeof(float4) * (size_t)map->m,
+                                   cudaMemcpyDeviceToDevice, s));
+    if (boxes_dev)
+        GSICP_CUDA(cudaMemcpyAsync(boxes_dev, map->index.boxes.ptr, sizeof(float4) * 4 * (size_t)map->index.L,
+                                   cudaMemcpyDeviceToDevice, s));
+    if (n_leaves_out) *n_leaves_out = map->index.L;
+    if (bucket_out) *bucket_out = map->index.B;
+    return GSICP_OK;
+}
+
 int64_t gsicp_map_size(gsicp_map map) { return map ? map->m : 0; }
 
 void gsicp_map_destroy(gsicp_map map)
@@ -332,6 +368,9 @@ void gsicp_map_destroy(gsicp_map map)
     map->index.pts.release();
     map->index.boxes.release();
     map->index.covs.release();
+    map->index.keys.release();
+    map->index.cell.release();
+    map->index.quant.release();
     map->means.release();
     map->covs.release();
     map->count.release();

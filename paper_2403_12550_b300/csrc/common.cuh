@@ -17,6 +17,17 @@
 
 namespace gsicp {
 
+// Interleave the low 10 bits of v with two zero bits between each.
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
 // Sorted point record: x, y, z and the point's original index (int bits in w).
 // Node box: two float4 per node, lo.xyz and hi.xyz (w unused).  Empty boxes
 // have lo = +inf, hi = -inf, so their distance to any query is +inf.
@@ -25,9 +36,24 @@ struct IndexView {
     const float4* boxes;  // 2 * (2L) float4: node i -> boxes[2i] (lo), boxes[2i+1] (hi)
     const float4* covs;   // optional: 2 float4 per sorted point (xx,xy,xz,yy | yz,zz,-,-)
     const int* n;         // device count of valid points
+    const uint32_t* keys; // sorted 30-bit Morton keys of the valid points (map indices only)
+    const int* cell;      // SEED_BITS-bit key prefix -> first sorted position with that prefix or above
+                          // (2^SEED_BITS + 1 entries; map indices only)
+    const float4* quant;  // (lo.x, lo.y, lo.z, scale): Morton quantisation of this index
     int L;                // leaves (power of two)
     int B;                // points per leaf (8, 16 or 32)
 };
+
+constexpr int SEED_BITS = 21;  // 7 bits per axis: cells of 1/128 of the bounding cube
+
+// 30-bit Morton key of a point under the index's quantisation (clamped to the cube).
+__device__ __forceinline__ uint32_t morton_of(float4 qz, float x, float y, float z)
+{
+    const uint32_t qx = (uint32_t)min(1023, max(0, (int)((x - qz.x) * qz.w)));
+    const uint32_t qy = (uint32_t)min(1023, max(0, (int)((y - qz.y) * qz.w)));
+    const uint32_t qq = (uint32_t)min(1023, max(0, (int)((z - qz.z) * qz.w)));
+    return (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qq);
+}
 
 // Squared norm with a fixed, monotone evaluation order: used for both point
 // and box distances so that box bounds are never above a contained point's
@@ -56,17 +82,6 @@ __device__ __forceinline__ bool before(float d, int i, float e, int j)
     return d < e || (d == e && i < j);
 }
 
-// Interleave the low 10 bits of v with two zero bits between each.
-__device__ __forceinline__ uint32_t spread10(uint32_t v)
-{
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
 // Order-preserving map float -> uint32 (for atomicMin/atomicMax on floats).
 __device__ __forceinline__ uint32_t f2ord(float f)
 {
@@ -90,6 +105,13 @@ __device__ __forceinline__ void df_add(dfloat& a, float x)
     float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
     a.hi = s;
     a.lo = __fadd_rn(a.lo, err);
+}
+
+// a += (bhi + blo)
+__device__ __forceinline__ void df_merge(dfloat& a, float bhi, float blo)
+{
+    df_add(a, bhi);
+    a.lo = __fadd_rn(a.lo, blo);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -116,19 +138,31 @@ struct RegState {
     int status;        // REG_ST_*
     unsigned int counter;  // blocks finished in the current iteration
     int pad;
+    // telemetry, per iteration (first REG_STATS iterations): points whose candidate cache was
+    // rebuilt, and nanoseconds spent in the final reduction + solve by the last block
+    int refreshes[64];
+    int tail_ns[64];
+    int solve_ns[64];                      // part of tail_ns spent in the FP64 solve + update
+    unsigned long long t_first[64];        // earliest block start (globaltimer, ns)
+    unsigned long long t_arrive[64];       // latest block arrival at the reduction
 };
+constexpr int REG_STATS = 64;
+
+constexpr int KC = 8;  // map candidates cached per source point
 
 struct RegJob {
     const float4* src;     // source points in Morton order (x, y, z, original index), n
     const float4* covs_s;  // their covariances in the same order, 2 float4 each (xx,xy,xz,yy | yz,zz,-,-)
     const int* n;          // device count
     IndexView map;
-    int* corr_cache;       // n: sorted map position of the last correspondence (-1 none)
+    int* cand;             // n x KC: sorted map positions of each point's cached nearest map points (-1 none)
+    float4* anchor;        // n: (query position the cache was filled at, radius within which it is complete);
+                           // radius <= 0 means "search" (cand[0] then holds a seed position or -1)
     int* corr_out;         // optional: original map index per source point
     float* partials;       // grid x NACC
     RegState* st;
     float max_d2;
-    float cap2;            // first-pass search bound of the cooperative nearest-neighbour walk
+    float slack;           // extra search radius beyond max_corr_dist kept in the cache (m)
     int max_iters;
     double tol_rot, tol_trans;
     int min_inliers;

@@ -106,9 +106,11 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
             D[j] = phantom ? -1.f : GSICP_INF;
             I[j] = phantom ? -1 : 0x7fffffff;
         }
-        // ---- exact k-NN (ties -> smaller original index)
+        // ---- exact k-NN (ties -> smaller original index): the query's own leaf and its two
+        // Morton neighbours first (a tight bound), then the tree walk skipping those three
         float bound = GSICP_INF;
-        auto scan = [&](int lf) {
+        const int own = s / B;
+        auto scan_leaf = [&](int lf) {
             const int beg = lf * B, end = min(beg + B, n);
             for (int t = beg; t < end; ++t) {
                 const float4 pp = ix.pts[t];
@@ -128,7 +130,12 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
             }
             bound = D[KMAX - 1];
         };
-        traverse(ix, q.x, q.y, q.z, bound, scan);
+        scan_leaf(own);
+        if (own > 0) scan_leaf(own - 1);
+        if ((own + 1) * B < n) scan_leaf(own + 1);
+        traverse(ix, q.x, q.y, q.z, bound, [&](int lf) {
+            if (lf < own - 1 || lf > own + 1) scan_leaf(lf);
+        });
         // ---- covariance of the neighbourhood (two-pass, float), neighbours gathered by original index
         int kk = 0;
         float m0 = 0.f, m1 = 0.f, m2 = 0.f;

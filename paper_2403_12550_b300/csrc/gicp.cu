@@ -8,11 +8,20 @@
 // xi = (omega, v): J_i = dd_i/dxi = [[y_i]x, -I] with y_i = R x_i + t.
 //
 // One kernel launch per iteration.  One thread per source point, points in
-// the source index's Morton order: transform, exact nearest map mean by a walk
-// of the map's bounding-volume hierarchy (traverse.cuh) whose bound starts at
-// the distance to the previous iteration's correspondence, then the residual,
-// weight, J^T W J (21 unique), J^T W d (6), d^T W d and the inlier count ->
-// warp shuffles -> one FP32 partial per block.  The last block to finish (threadfence + atomic
+// the source index's Morton order:
+// transform, exact nearest map mean, then the residual, weight, J^T W J (21
+// unique), J^T W d (6), d^T W d and the inlier count -> warp shuffles -> one
+// FP32 partial per block.
+//
+// Nearest-neighbour search with a per-point candidate cache: each point keeps
+// its KC nearest map points within max_corr_dist + slack and the radius within
+// which that list is complete, measured from where the point was when the list
+// was made.  Once the point has moved by delta, no map point outside the list
+// can be closer than radius - delta, so when the best cached candidate is
+// within that (with float-rounding margins) it is the exact answer and the
+// tree is not walked; otherwise the list is rebuilt by an exact KC-nearest walk
+// of the map's bounding-volume hierarchy (traverse.cuh) starting from the
+// cached leaves.  The first iteration starts from a Morton-key seed.  The last block to finish (threadfence + atomic
 // counter, no waiting) sums the partials with compensation, solves the 6x6
 // system by FP64 Cholesky, applies the FP64 SE(3) exponential and, inside a
 // CUDA graph, sets the conditional-while handle that decides whether the
@@ -57,57 +66,71 @@ __host__ __device__ constexpr int ut(int r, int c) { return r * 6 - (r * (r - 1)
 __device__ bool chol_solve6(const double H[36], const double rhs[6], double x[6])
 {
     double L[21];  // lower triangle, row-major packed: L(i, j) at i*(i+1)/2 + j
-    for (int i = 0; i < 6; ++i) {
-        for (int j = 0; j <= i; ++j) {
-            double s = H[6 * i + j];
-            for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
-            if (i == j) {
-                if (!(s > 0.0) || !isfinite(s)) return false;
-                L[i * (i + 1) / 2 + i] = sqrt(s);
-            } else {
-                L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
-            }
+    double inv[6]; // 1 / L(j, j)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double d = H[6 * j + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+        if (!(d > 0.0) || !isfinite(d)) return false;
+        inv[j] = rsqrt(d);
+        L[j * (j + 1) / 2 + j] = d * inv[j];
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            double v = H[6 * i + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+            L[i * (i + 1) / 2 + j] = v * inv[j];
         }
     }
     double y[6];
+#pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double s = rhs[i];
-        for (int k = 0; k < i; ++k) s -= L[i * (i + 1) / 2 + k] * y[k];
-        y[i] = s / L[i * (i + 1) / 2 + i];
+        double v = rhs[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v -= L[i * (i + 1) / 2 + k] * y[k];
+        y[i] = v * inv[i];
     }
+#pragma unroll
     for (int i = 5; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < 6; ++k) s -= L[k * (k + 1) / 2 + i] * x[k];
-        x[i] = s / L[i * (i + 1) / 2 + i];
+        double v = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) v -= L[k * (k + 1) / 2 + i] * x[k];
+        x[i] = v * inv[i];
     }
     return true;
 }
 
 // T <- exp(xi^) T with xi = (omega, v): rotation by Rodrigues' formula,
-// translation V v with V = I + B K + C K^2 (K = [omega]x); series for small angles.
+// translation V v with V = I + B K + C K^2 (K = [omega]x); series below 1e-2 rad.
 __device__ void se3_left_update(const double xi[6], double T[16])
 {
     const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
     double A, Bc, Cc;
-    if (th2 < 1e-6) {
-        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-        Bc = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-        Cc = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    if (th2 < 1e-4) {
+        A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
+        Bc = 0.5 - th2 * (1.0 / 24.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0)));
+        Cc = 1.0 / 6.0 - th2 * (1.0 / 120.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0)));
     } else {
-        const double th = sqrt(th2);
-        const double sn = sin(th), hs = sin(0.5 * th);
+        const double th = sqrt(th2), ith2 = 1.0 / th2;
+        double sn, cs;
+        sincos(th, &sn, &cs);
         A = sn / th;
-        Bc = 2.0 * hs * hs / th2;
-        Cc = (th - sn) / (th2 * th);
+        Bc = (1.0 - cs) * ith2;
+        Cc = (1.0 - A) * ith2;
     }
     const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
     double K2[9];
+#pragma unroll
     for (int r = 0; r < 3; ++r)
+#pragma unroll
         for (int c = 0; c < 3; ++c) K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-    double E[16];
+    double E[12];
+#pragma unroll
     for (int r = 0; r < 3; ++r) {
         double tv = 0.0;
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double id = r == c ? 1.0 : 0.0;
             E[4 * r + c] = id + A * K[3 * r + c] + Bc * K2[3 * r + c];
@@ -115,15 +138,14 @@ __device__ void se3_left_update(const double xi[6], double T[16])
         }
         E[4 * r + 3] = tv;
     }
-    E[12] = 0.0; E[13] = 0.0; E[14] = 0.0; E[15] = 1.0;
-    double M[16];
-    for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) {
-            double s = 0.0;
-            for (int j = 0; j < 4; ++j) s += E[4 * r + j] * T[4 * j + c];
-            M[4 * r + c] = s;
-        }
-    for (int i = 0; i < 16; ++i) T[i] = M[i];
+    double M[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            M[4 * r + c] = E[4 * r] * T[c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c] + (c == 3 ? E[4 * r + 3] : 0.0);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) T[i] = M[i];
 }
 
 __device__ __forceinline__ void pose_to_float(RegState* st)
@@ -147,10 +169,15 @@ __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegSt
     st->iter = 0;
     st->status = REG_ST_RUNNING;
     st->counter = 0u;
+    for (int i = 0; i < REG_STATS; ++i) {
+        st->refreshes[i] = st->tail_ns[i] = st->solve_ns[i] = 0;
+        st->t_first[i] = ~0ull;
+        st->t_arrive[i] = 0ull;
+    }
     pose_to_float(st);
 }
 
-__global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __restrict__ jp,
+__global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob* __restrict__ jp,
                                                                 cudaGraphConditionalHandle cond)
 {
     const RegJob& J = *jp;
@@ -162,6 +189,12 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
     }
     const int n = *J.n;
     const int nmap = *J.map.n;
+    const int it_now = st->iter;
+    if (threadIdx.x == 0 && it_now < REG_STATS) {
+        unsigned long long t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        atomicMin(&st->t_first[it_now], t0);
+    }
     float R[9], t[3];
 #pragma unroll
     for (int a = 0; a < 9; ++a) R[a] = st->Rf[a];
@@ -171,42 +204,101 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
 
-    // one thread per source point, points in Morton order
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    // One source point per thread (the grid covers the context's capacity; the hardware block
+    // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
+    // the reduction order, hence the result, deterministic).
+    int refreshed = 0;
+    const int B = J.map.B;
+    const float max_d = sqrtf(J.max_d2);
+    const float Rs = max_d + J.slack, Rs2 = Rs * Rs;
+    do {
+        const int s = blockIdx.x * blockDim.x + threadIdx.x;
+        if (s >= n) break;
         const float4 x = J.src[s];
         const float y0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t[0])));
         const float y1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t[1])));
         const float y2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t[2])));
+        const int4 ca4 = reinterpret_cast<const int4*>(J.cand)[2l * s];
+        const int4 cb4 = reinterpret_cast<const int4*>(J.cand)[2l * s + 1];
+        const int cp[KC] = {ca4.x, ca4.y, ca4.z, ca4.w, cb4.x, cb4.y, cb4.z, cb4.w};
+        const float4 anc = J.anchor[s];
         float best_d2 = J.max_d2;
         int best_oi = 0x7fffffff, best_pos = -1;
-        const int prev = J.corr_cache[s];
-        if (prev >= 0) {  // last iteration's correspondence is admissible: a valid initial bound
-            const float4 p = J.map.pts[prev];
-            const float d2 = point_d2(y0, y1, y2, p);
-            if (d2 <= best_d2) {
-                best_d2 = d2;
-                best_oi = __float_as_int(p.w);
-                best_pos = prev;
-            }
-        }
-        const int B = J.map.B;
-        auto scan = [&](int lf) {
-            const int beg = lf * B, end = min(beg + B, nmap);
-            for (int u = beg; u < end; ++u) {
-                const float4 p = J.map.pts[u];
+        bool resolved = false;
+        if (anc.w > 0.f) {
+            // Cached candidates were complete within radius anc.w of the anchor; the query has
+            // moved by delta, so every map point outside them is at least anc.w - delta away.
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                if (cp[j] < 0) continue;
+                const float4 p = J.map.pts[cp[j]];
                 const float d2 = point_d2(y0, y1, y2, p);
                 const int oi = __float_as_int(p.w);
                 if (before(d2, oi, best_d2, best_oi)) {
                     best_d2 = d2;
                     best_oi = oi;
-                    best_pos = u;
+                    best_pos = cp[j];
                 }
             }
-        };
-        traverse(J.map, y0, y1, y2, best_d2, scan);
-        J.corr_cache[s] = best_pos;
+            const float delta = sqrtf(sq3(y0 - anc.x, y1 - anc.y, y2 - anc.z)) + 2e-6f;
+            const float bnd = best_pos >= 0 ? sqrtf(best_d2) : max_d;
+            // margins (1e-5 relative, 2e-6 m) exceed float rounding of the distances, so the
+            // cached answer is the one the full search would return
+            resolved = anc.w - delta >= bnd * (1.f + 1e-5f);
+        }
+        if (!resolved) {
+            refreshed = 1;
+            // exact KC nearest map points within Rs, starting from the cached (or seed) leaves
+            float D[KC];
+            int I[KC], P[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                D[j] = Rs2;
+                I[j] = 0x7fffffff;
+                P[j] = -1;
+            }
+            float bound = Rs2;
+            auto scan_leaf = [&](int lf) {
+                const int beg = lf * B, end = min(beg + B, nmap);
+                for (int u = beg; u < end; ++u) {
+                    const float4 p = J.map.pts[u];
+                    const float d2 = point_d2(y0, y1, y2, p);
+                    const int oi = __float_as_int(p.w);
+                    if (before(d2, oi, D[KC - 1], I[KC - 1])) {
+                        D[KC - 1] = d2;
+                        I[KC - 1] = oi;
+                        P[KC - 1] = u;
+#pragma unroll
+                        for (int v = KC - 1; v > 0; --v) {
+                            if (before(D[v], I[v], D[v - 1], I[v - 1])) {
+                                float td = D[v]; D[v] = D[v - 1]; D[v - 1] = td;
+                                int ti = I[v]; I[v] = I[v - 1]; I[v - 1] = ti;
+                                int tp = P[v]; P[v] = P[v - 1]; P[v - 1] = tp;
+                            }
+                        }
+                    }
+                }
+                bound = D[KC - 1];
+            };
+            const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
+            const int h1 = (cp[KC - 1] >= 0 && cp[KC - 1] / B != h0) ? cp[KC - 1] / B : -1;
+            if (h0 >= 0) scan_leaf(h0);
+            if (h1 >= 0) scan_leaf(h1);
+            traverse(J.map, y0, y1, y2, bound, [&](int lf) {
+                if (lf != h0 && lf != h1) scan_leaf(lf);
+            });
+            const float rc = (I[KC - 1] != 0x7fffffff ? sqrtf(D[KC - 1]) : Rs) * (1.f - 1e-6f);
+            reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
+            reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
+            J.anchor[s] = make_float4(y0, y1, y2, rc);
+            if (I[0] != 0x7fffffff && D[0] <= J.max_d2) {
+                best_d2 = D[0];
+                best_oi = I[0];
+                best_pos = P[0];
+            }
+        }
         if (J.corr_out) J.corr_out[__float_as_int(x.w)] = best_pos >= 0 ? best_oi : -1;
-        if (best_pos < 0) continue;
+        if (best_pos < 0) break;
 
         acc[28] += 1.f;
         const float4 mu = J.map.pts[best_pos];
@@ -228,7 +320,7 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
         // W = Sigma^-1 (cofactors / determinant)
         const float c00 = s11 * s22 - s12 * s12, c01 = s02 * s12 - s01 * s22, c02 = s01 * s12 - s02 * s11;
         const float det = s00 * c00 + s01 * c01 + s02 * c02;
-        if (!(fabsf(det) > 0.f)) continue;
+        if (!(fabsf(det) > 0.f)) break;
         const float id = 1.f / det;
         const float W00 = c00 * id, W01 = c01 * id, W02 = c02 * id;
         const float W11 = (s00 * s22 - s02 * s02) * id, W12 = (s01 * s02 - s00 * s12) * id;
@@ -275,7 +367,7 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
         acc[25] -= Wd1;
         acc[26] -= Wd2;
         acc[27] += d0 * Wd0 + d1 * Wd1 + d2 * Wd2;
-    }
+    } while (false);
 
     // ---- block reduction -> one partial per block
     __shared__ float red[REG_THREADS / 32][NACC];
@@ -288,41 +380,84 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][a] = v;
     }
-    __syncthreads();
-    if (threadIdx.x < NACC) {
+    const int block_refreshed = __syncthreads_count(refreshed);
+    if (threadIdx.x == 0 && block_refreshed > 0 && st->iter < REG_STATS) atomicAdd(&st->refreshes[st->iter], block_refreshed);
+    if (threadIdx.x < 32) {
         float v = 0.f;
+        if (threadIdx.x < NACC) {
 #pragma unroll
-        for (int w = 0; w < REG_THREADS / 32; ++w) v += red[w][threadIdx.x];
+            for (int w = 0; w < REG_THREADS / 32; ++w) v += red[w][threadIdx.x];
+        }
         J.partials[32l * blockIdx.x + threadIdx.x] = v;
         __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) am_last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        if (it_now < REG_STATS) {
+            unsigned long long t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+            atomicMax(&st->t_arrive[it_now], t1);
+        }
+        am_last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    unsigned long long t_start = 0;
+    if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
 
-    // ---- last block: compensated sum of all partials
-    __shared__ float shi[NACC][8], slo[NACC][8];
+    // ---- last block: compensated sum of all partials.  Thread t owns component group g = t % 8
+    // (components 4g..4g+3, one float4 of a block's 32-float partial) and blocks t/8, t/8 + 32, ...;
+    // all its loads are independent and issued in batches of 8.
+    __shared__ float shi[REG_THREADS / 32][32], slo[REG_THREADS / 32][32];
     __shared__ double tot[NACC];
     {
-        const int v = threadIdx.x >> 3, sub = threadIdx.x & 7;
-        if (v < NACC) {
-            dfloat s = {0.f, 0.f};
-            for (int b = sub; b < (int)gridDim.x; b += 8) df_add(s, __ldcg(J.partials + 32l * b + v));
-            shi[v][sub] = s.hi;
-            slo[v][sub] = s.lo;
+        const int grp = threadIdx.x & 7, row = threadIdx.x >> 3;
+        dfloat a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, a2 = {0.f, 0.f}, a3 = {0.f, 0.f};
+        const float4* P4 = reinterpret_cast<const float4*>(J.partials);
+        const int nb = (int)gridDim.x;
+        for (int b0 = row; b0 < nb; b0 += 8 * (REG_THREADS / 8)) {
+            float4 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int b = b0 + j * (REG_THREADS / 8);
+                v[j] = b < nb ? __ldcg(P4 + 8l * b + grp) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                df_add(a0, v[j].x);
+                df_add(a1, v[j].y);
+                df_add(a2, v[j].z);
+                df_add(a3, v[j].w);
+            }
+        }
+        // lanes l, l^8, l^16, l^24 hold the same group: combine them
+#pragma unroll
+        for (int o = 8; o < 32; o <<= 1) {
+            df_merge(a0, __shfl_xor_sync(0xffffffffu, a0.hi, o), __shfl_xor_sync(0xffffffffu, a0.lo, o));
+            df_merge(a1, __shfl_xor_sync(0xffffffffu, a1.hi, o), __shfl_xor_sync(0xffffffffu, a1.lo, o));
+            df_merge(a2, __shfl_xor_sync(0xffffffffu, a2.hi, o), __shfl_xor_sync(0xffffffffu, a2.lo, o));
+            df_merge(a3, __shfl_xor_sync(0xffffffffu, a3.hi, o), __shfl_xor_sync(0xffffffffu, a3.lo, o));
+        }
+        if (lane < 8) {
+            shi[warp][4 * lane + 0] = a0.hi; slo[warp][4 * lane + 0] = a0.lo;
+            shi[warp][4 * lane + 1] = a1.hi; slo[warp][4 * lane + 1] = a1.lo;
+            shi[warp][4 * lane + 2] = a2.hi; slo[warp][4 * lane + 2] = a2.lo;
+            shi[warp][4 * lane + 3] = a3.hi; slo[warp][4 * lane + 3] = a3.lo;
         }
     }
     __syncthreads();
     if (threadIdx.x < NACC) {
-        double s = 0.0;
-        for (int j = 0; j < 8; ++j) s += (double)shi[threadIdx.x][j] + (double)slo[threadIdx.x][j];
-        tot[threadIdx.x] = s;
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < REG_THREADS / 32; ++w) sum += (double)shi[w][threadIdx.x] + (double)slo[w][threadIdx.x];
+        tot[threadIdx.x] = sum;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
 
+    unsigned long long t_solve;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_solve));
     double H[36], b[6];
     for (int r = 0; r < 6; ++r)
         for (int c = r; c < 6; ++c) H[6 * r + c] = H[6 * c + r] = tot[ut(r, c)];
@@ -342,11 +477,20 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
         } else {
             se3_left_update(delta, st->T);
             pose_to_float(st);
-            const double dw = sqrt(delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2]);
-            const double dv = sqrt(delta[3] * delta[3] + delta[4] * delta[4] + delta[5] * delta[5]);
-            if (dw < J.tol_rot && dv < J.tol_trans) st->status = REG_ST_CONVERGED;
+            const double dw2 = delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2];
+            const double dv2 = delta[3] * delta[3] + delta[4] * delta[4] + delta[5] * delta[5];
+            if (dw2 < J.tol_rot * J.tol_rot && dv2 < J.tol_trans * J.tol_trans) st->status = REG_ST_CONVERGED;
             else if (st->iter >= J.max_iters || st->iter >= 10000) st->status = REG_ST_MAXITER;
             else more = true;
+        }
+    }
+    {
+        unsigned long long t_end;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+        const int it = J.mode == REG_MODE_SOLVE ? st->iter - 1 : 0;
+        if (it >= 0 && it < REG_STATS) {
+            st->tail_ns[it] = (int)(t_end - t_start);
+            st->solve_ns[it] = (int)(t_end - t_solve);
         }
     }
     __threadfence();
@@ -355,14 +499,15 @@ __global__ void __launch_bounds__(REG_THREADS) gicp_iter_kernel(const RegJob* __
 
 // ---------------------------------------------------------------------------------------------
 
-gsicp_status RegMachine::init()
+gsicp_status RegMachine::init(int capacity)
 {
-    if (exec) return GSICP_OK;
-    int dev = 0, sms = 0, per_sm = 0;
-    GSICP_CUDA(cudaGetDevice(&dev));
-    GSICP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GSICP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gicp_iter_kernel, REG_THREADS, 0));
-    grid = sms * std::max(1, per_sm);
+    const int want = std::max(1, (std::max(capacity, 1) + REG_THREADS - 1) / REG_THREADS);
+    if (exec && want <= grid) return GSICP_OK;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    grid = std::max(want, grid);
     GSICP_CHECK(partials.ensure(sizeof(float) * 32 * (size_t)grid));
     GSICP_CHECK(job.ensure(sizeof(RegJob)));
     GSICP_CHECK(state.ensure(sizeof(RegState)));
@@ -402,26 +547,36 @@ void RegMachine::release()
     partials.release();
     job.release();
     state.release();
-    corr.release();
+    cand.release();
+    anchor.release();
 }
 
 gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], int n_cap, bool solve,
                      cudaStream_t s)
 {
-    GSICP_CHECK(rm.init());
-    GSICP_CHECK(rm.corr.ensure(sizeof(int) * (size_t)std::max(n_cap, 1)));
+    GSICP_CHECK(rm.init(n_cap));
+    GSICP_CHECK(rm.cand.ensure(sizeof(int) * KC * (size_t)std::max(n_cap, 1)));
+    GSICP_CHECK(rm.anchor.ensure(sizeof(float4) * (size_t)std::max(n_cap, 1)));
     RegJob job = job_in;
-    job.corr_cache = rm.corr.as<int>();
+    job.cand = rm.cand.as<int>();
+    job.anchor = rm.anchor.as<float4>();
     job.partials = rm.partials.as<float>();
     job.st = rm.state.as<RegState>();
     job.mode = solve ? REG_MODE_SOLVE : REG_MODE_LINEARISE;
     job.use_cond = solve ? 1 : 0;
     Pose16 P;
     for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
-    if (n_cap > 0) GSICP_CUDA(cudaMemsetAsync(rm.corr.ptr, 0xff, sizeof(int) * (size_t)n_cap, s));
+    GSICP_CHECK(launch_seed(job.map, job.src, job.n, n_cap, T0, job.cand, job.anchor, s));
     reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
     GSICP_CUDA(cudaGetLastError());
-    if (solve) {
+    if (solve && rm.unrolled) {
+        // profiling mode: one plain launch per iteration (finished launches exit at once)
+        job.use_cond = 0;
+        reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
+        for (int i = 0; i < job.max_iters; ++i)
+            gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
+        GSICP_CUDA(cudaGetLastError());
+    } else if (solve) {
         GSICP_CUDA(cudaGraphLaunch(rm.exec, s));
     } else {
         gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
@@ -489,6 +644,49 @@ gsicp_status launch_transform(const double T[16], const float* pts, const float*
     for (int i = 0; i < 16; ++i) P.v[i] = T[i];
     const int grid = std::max(1, std::min((n + 255) / 256, device_sm_count() * 8));
     transform_kernel<<<grid, 256, 0, s>>>(P, pts, covs, n, pts_out, covs_out);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+__global__ void seed_kernel(IndexView map, const float4* __restrict__ src, const int* __restrict__ n_dev, Pose16 T,
+                            int* __restrict__ cand, float4* __restrict__ anchor)
+{
+    const int n = *n_dev, m = *map.n;
+    const float4 qz = *map.quant;
+    const float R0 = (float)T.v[0], R1 = (float)T.v[1], R2 = (float)T.v[2], t0 = (float)T.v[3];
+    const float R3 = (float)T.v[4], R4 = (float)T.v[5], R5 = (float)T.v[6], t1 = (float)T.v[7];
+    const float R6 = (float)T.v[8], R7 = (float)T.v[9], R8 = (float)T.v[10], t2 = (float)T.v[11];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        int seed = -1;
+        if (m > 0 && map.keys && map.cell) {
+            const float4 x = src[s];
+            const float y0 = fmaf(R0, x.x, fmaf(R1, x.y, fmaf(R2, x.z, t0)));
+            const float y1 = fmaf(R3, x.x, fmaf(R4, x.y, fmaf(R5, x.z, t1)));
+            const float y2 = fmaf(R6, x.x, fmaf(R7, x.y, fmaf(R8, x.z, t2)));
+            const uint32_t key = morton_of(qz, y0, y1, y2);
+            const uint32_t pre = key >> (30 - SEED_BITS);
+            int lo = map.cell[pre], hi = map.cell[pre + 1];
+            while (lo < hi) {  // Morton-nearest position within the query's cell
+                const int mid = (lo + hi) >> 1;
+                if (map.keys[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            seed = min(lo, m - 1);
+        }
+        reinterpret_cast<int4*>(cand)[2l * s] = make_int4(seed, -1, -1, -1);
+        reinterpret_cast<int4*>(cand)[2l * s + 1] = make_int4(-1, -1, -1, -1);
+        anchor[s] = make_float4(0.f, 0.f, 0.f, -1.f);
+    }
+}
+
+gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_dev, int cap, const double T0[16],
+                         int* cand, float4* anchor, cudaStream_t s)
+{
+    if (cap <= 0) return GSICP_OK;
+    Pose16 P;
+    for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
+    const int grid = std::max(1, std::min((cap + 255) / 256, device_sm_count() * 8));
+    seed_kernel<<<grid, 256, 0, s>>>(map, src, n_dev, P, cand, anchor);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

@@ -265,6 +265,31 @@ __global__ void morton_kernel(const float* __restrict__ pts, const int* __restri
     }
 }
 
+__global__ void quant_kernel(const uint32_t* __restrict__ bb, float4* __restrict__ quant)
+{
+    const float lx = ord2f(bb[0]), ly = ord2f(bb[1]), lz = ord2f(bb[2]);
+    const float ext = fmaxf(fmaxf(ord2f(bb[3]) - lx, ord2f(bb[4]) - ly), ord2f(bb[5]) - lz);
+    *quant = make_float4(lx, ly, lz, ext > 0.f ? 1024.f / ext : 0.f);
+}
+
+// cell[p] = first sorted position whose key prefix (top SEED_BITS bits) is >= p.
+__global__ void cell_table_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
+                                  int* __restrict__ cell)
+{
+    const int n = *n_dev;
+    const int ncell = 1 << SEED_BITS;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p <= ncell; p += gridDim.x * blockDim.x) {
+        const uint32_t target = (uint32_t)p << (30 - SEED_BITS);
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (keys[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        cell[p] = p == ncell ? n : lo;
+    }
+}
+
 __global__ void gather_kernel(const float* __restrict__ pts, const float* __restrict__ covs,
                               const uint32_t* __restrict__ order, const int* __restrict__ n_dev, int total,
                               float4* __restrict__ spts, float4* __restrict__ scovs)
@@ -353,7 +378,7 @@ static int ceil_pow2(long x)
 }
 
 gsicp_status build_index(const float* pts, const float* covs, int cap, const int* n_dev, int bucket,
-                         IndexBufs& out, BuildScratch& scr, cudaStream_t s)
+                         IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed)
 {
     if (bucket != 8 && bucket != 16 && bucket != 32) return GSICP_ERR_INVALID_ARG;
     const int B = bucket;
@@ -390,6 +415,16 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
         const int blocks = count / std::min(256, count);
         level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
     }
+    GSICP_CHECK(out.quant.ensure(sizeof(float4)));
+    quant_kernel<<<1, 1, 0, s>>>(scr.bbox.as<uint32_t>(), out.quant.as<float4>());
+    if (with_seed) {
+        GSICP_CHECK(out.keys.ensure(sizeof(uint32_t) * (size_t)sort_n));
+        GSICP_CHECK(out.cell.ensure(sizeof(int) * ((size_t(1) << SEED_BITS) + 1)));
+        GSICP_CUDA(cudaMemcpyAsync(out.keys.ptr, scr.k0.ptr, sizeof(uint32_t) * (size_t)sort_n,
+                                   cudaMemcpyDeviceToDevice, s));
+        cell_table_kernel<<<std::min(((1 << SEED_BITS) + 256) / 256, sms * 8), 256, 0, s>>>(
+            out.keys.as<uint32_t>(), n_dev, out.cell.as<int>());
+    }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }
@@ -401,6 +436,9 @@ IndexView IndexBufs::view() const
     v.boxes = boxes.as<const float4>();
     v.covs = covs.ptr ? covs.as<const float4>() : nullptr;
     v.n = n_ptr;
+    v.keys = keys.ptr ? keys.as<const uint32_t>() : nullptr;
+    v.cell = cell.ptr ? cell.as<const int>() : nullptr;
+    v.quant = quant.as<const float4>();
     v.L = L;
     v.B = B;
     return v;

@@ -39,6 +39,7 @@ struct DevBuf {
 // Buffers of one spatial index (either owned by a map or scratch of a context).
 struct IndexBufs {
     DevBuf pts, boxes, covs;
+    DevBuf keys, cell, quant;    // seeding structures (built when with_seed is set)
     const int* n_ptr = nullptr;  // device count of valid points (set by build_index)
     int L = 0, B = 16, cap = 0;
     IndexView view() const;
@@ -51,7 +52,12 @@ struct BuildScratch {
 
 // Build an index over the first *n_dev of `cap` points (pts n x 3, covs n x 6 optional).
 gsicp_status build_index(const float* pts, const float* covs, int cap, const int* n_dev, int bucket,
-                         IndexBufs& out, BuildScratch& scr, cudaStream_t s);
+                         IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed = false);
+
+// First-iteration search seeds: for each Morton-ordered source point x_s, the map position found by
+// a Morton-key lookup of T0 x_s (cand[s][0], -1 if none); every cache entry is marked "search".
+gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_dev, int cap, const double T0[16],
+                         int* cand, float4* anchor, cudaStream_t s);
 
 // Device-wide exclusive scan of uint32 values; in may equal out.  `sums` is scratch.
 gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf& sums, cudaStream_t s);
@@ -73,12 +79,13 @@ gsicp_status launch_permute_covs(const IndexView& ix, const float* covs, int cap
 // Registration machinery.
 struct RegMachine {
     int grid = 0;
-    DevBuf partials, job, state, corr;
+    DevBuf partials, job, state, cand, anchor;
     RegState* state_host = nullptr;  // pinned
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond{};
-    gsicp_status init();
+    bool unrolled = false;  // GSICP_UNROLLED_GN=1: plain launches instead of the graph (for profilers)
+    gsicp_status init(int capacity);  // (re)builds the graph when the point capacity grows
     void release();
 };
 

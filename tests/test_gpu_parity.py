@@ -157,6 +157,55 @@ def test_source_covariances_collinear_and_coincident(g, ctx):
             np.testing.assert_allclose(covs, ref, atol=1e-6)
 
 
+# ----------------------------------------------------------------------------- a4 index structure
+
+def _morton30(p, lo, ext):
+    """Reference 30-bit Morton key (10 bits per axis over the bounding cube), integer bit interleaving."""
+    scale = np.float32(1024.0) / np.float32(ext) if ext > 0 else np.float32(0)
+    q = np.clip(((p - lo).astype(np.float32) * scale).astype(np.int64), 0, 1023)
+    key = np.zeros(len(p), dtype=np.int64)
+    for b in range(10):
+        for a, sh in ((0, 2), (1, 1), (2, 0)):
+            key |= ((q[:, a] >> b) & 1) << (3 * b + sh)
+    return key
+
+
+@pytest.mark.parametrize("m,bucket", [(1, 16), (33, 8), (5000, 16), (100_000, 32)])
+def test_map_index_is_morton_sorted_with_tight_boxes(g, ctx, m, bucket):
+    rng = np.random.default_rng(m)
+    means = rng.uniform([-1, 0, 2], [3, 2, 2.5], size=(m, 3)).astype(np.float32)
+    covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (m, 1))
+    mp = g.gsicp_build_map_index(ctx, cu(means), cu(covs), bucket=bucket)
+    ins = g.gsicp_map_inspect(mp)
+    pts = ins["pts"].cpu().numpy()
+    order = pts[:, 3].copy().view(np.int32)
+    assert sorted(order.tolist()) == list(range(m))  # a permutation
+    np.testing.assert_array_equal(pts[:, :3], means[order])
+    lo = means.min(0)
+    ext = float((means.max(0) - lo).max())
+    key = _morton30(means[order], lo, ext)
+    assert np.all(np.diff(key) >= 0)  # Morton order
+    # stable: equal keys keep input order
+    same = np.diff(key) == 0
+    assert np.all(np.diff(order)[same] > 0)
+    L, B = ins["L"], ins["B"]
+    assert B == bucket and L >= (m + B - 1) // B and (L & (L - 1)) == 0
+    boxes = ins["boxes"].cpu().numpy()
+    for leaf in range(L):
+        seg = pts[leaf * B:min((leaf + 1) * B, m), :3]
+        blo, bhi = boxes[L + leaf, :3], boxes[L + leaf, 4:7]
+        if len(seg):
+            np.testing.assert_array_equal(blo, seg.min(0))
+            np.testing.assert_array_equal(bhi, seg.max(0))
+        else:
+            assert np.all(np.isinf(blo)) and np.all(blo > 0) and np.all(bhi < 0)
+    for node in range(1, L):
+        c0, c1 = boxes[2 * node], boxes[2 * node + 1]
+        np.testing.assert_array_equal(boxes[node, :3], np.minimum(c0[:3], c1[:3]))
+        np.testing.assert_array_equal(boxes[node, 4:7], np.maximum(c0[4:7], c1[4:7]))
+    mp.close()
+
+
 # ----------------------------------------------------------------------------- a4 + a5 nearest neighbours
 
 def _check_nearest(map_pts, queries, max_dist, g, ctx, bucket=0):
