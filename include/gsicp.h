@@ -72,9 +72,12 @@ typedef struct {
     int min_inliers;     /* fewer correspondences than this -> GSICP_ERR_DEGENERATE */
 } gsicp_reg_params;
 
-/* Spatial-index parameters (Morton-ordered bounding-volume hierarchy). */
+/* Spatial-index parameters: a bounding-volume hierarchy over the Gaussians in Morton order, plus a
+ * hash grid of the Morton cells for the common short-range searches. */
 typedef struct {
-    int bucket;          /* points per leaf: 8, 16 or 32 (0 = default) */
+    int bucket;          /* points per leaf: 8, 16 or 32 (0 = default 16) */
+    float cell;          /* grid cell size in metres (0 = default 0.008); coarsened automatically
+                            when 1024 cells per axis do not cover the map's bounding cube */
 } gsicp_index_params;
 
 typedef struct gsicp_ctx_s* gsicp_ctx;

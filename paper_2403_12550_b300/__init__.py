@@ -57,7 +57,7 @@ class RegParams(C.Structure):
 
 
 class IndexParams(C.Structure):
-    _fields_ = [("bucket", C.c_int)]
+    _fields_ = [("bucket", C.c_int), ("cell", C.c_float)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -245,10 +245,11 @@ def gsicp_source_covariances(ctx: Context, pts: torch.Tensor, z: torch.Tensor | 
     return (covs_out, knn) if want_knn else covs_out
 
 
-def gsicp_build_map_index(ctx: Context, means: torch.Tensor, covs: torch.Tensor, bucket: int = 0) -> MapHandle:
+def gsicp_build_map_index(ctx: Context, means: torch.Tensor, covs: torch.Tensor, bucket: int = 0,
+                          cell: float = 0.0) -> MapHandle:
     """a4.  Returns a MapHandle (the library keeps its own copy of the Gaussians)."""
     h = C.c_void_p()
-    ip = IndexParams(bucket)
+    ip = IndexParams(bucket, cell)
     _check(lib.gsicp_build_map_index(ctx.ptr, _dev(means, cols=3), _dev(covs, cols=6), means.shape[0],
                                      C.byref(ip), _stream(), C.byref(h)), "gsicp_build_map_index")
     return MapHandle(h)

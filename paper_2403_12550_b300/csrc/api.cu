@@ -90,6 +90,8 @@ static gsicp_status finish_registration(gsicp_ctx ctx, cudaStream_t s, double T_
 }
 
 constexpr float CACHE_SLACK = 0.01f;  // m beyond max_corr_dist kept in the candidate cache (gicp.cu)
+constexpr float CACHE_STEP = 0.002f;  // m: points that moved more since their last search skip the cache
+constexpr float MAP_CELL = 0.008f;    // m: default map grid cell
 
 static RegJob make_job(const float4* src, const float4* covs_s, const int* n_dev, gsicp_map map,
                        const gsicp_reg_params* prm)
@@ -99,6 +101,7 @@ static RegJob make_job(const float4* src, const float4* covs_s, const int* n_dev
     job.src = src;
     job.covs_s = covs_s;
     job.slack = CACHE_SLACK;
+    job.cache_step = CACHE_STEP;
     job.n = n_dev;
     job.map = map->index.view();
     job.corr_out = nullptr;
@@ -124,7 +127,7 @@ static gsicp_status map_build(gsicp_ctx ctx, gsicp_map map, int bucket, cudaStre
 {
     GSICP_CHECK(launch_set_int(map->count.as<int>(), (int)map->m, s));
     return build_index(map->means.as<float>(), map->covs.as<float>(), (int)map->m, map->count.as<int>(), bucket,
-                       map->index, ctx->build, s, true);
+                       map->index, ctx->build, s, true, map->cell, true);
 }
 
 }  // namespace gsicp
@@ -273,11 +276,14 @@ gsicp_status gsicp_build_map_index(gsicp_ctx ctx, const float* means_dev, const 
     if (!ctx || m < 0 || m > (1 << 30) || (m > 0 && (!means_dev || !covs_dev))) return GSICP_ERR_INVALID_ARG;
     int bucket = params && params->bucket ? params->bucket : 16;
     if (bucket != 8 && bucket != 16 && bucket != 32) return GSICP_ERR_INVALID_ARG;
+    const float cell = params && params->cell > 0.f ? params->cell : MAP_CELL;
+    if (!isfinite(cell)) return GSICP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     gsicp_map map = new (std::nothrow) gsicp_map_s();
     if (!map) return GSICP_ERR_OOM;
     map->device = ctx->device;
     map->m = m;
+    map->cell = cell;
     gsicp_status st = map->count.ensure(sizeof(int) * 4);
     if (st == GSICP_OK) st = map->means.ensure(sizeof(float) * 3 * (size_t)std::max<int64_t>(m, 1));
     if (st == GSICP_OK) st = map->covs.ensure(sizeof(float) * 6 * (size_t)std::max<int64_t>(m, 1));
@@ -371,6 +377,7 @@ void gsicp_map_destroy(gsicp_map map)
     map->index.keys.release();
     map->index.cell.release();
     map->index.quant.release();
+    map->index.grid.release();
     map->means.release();
     map->covs.release();
     map->count.release();

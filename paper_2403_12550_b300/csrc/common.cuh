@@ -40,9 +40,35 @@ struct IndexView {
     const int* cell;      // SEED_BITS-bit key prefix -> first sorted position with that prefix or above
                           // (2^SEED_BITS + 1 entries; map indices only)
     const float4* quant;  // (lo.x, lo.y, lo.z, scale): Morton quantisation of this index
+    const int4* grid;     // hash table of occupied grid cells (map indices only), see grid_find
+    uint32_t grid_mask;   // table capacity - 1 (power of two); 0 when there is no grid
     int L;                // leaves (power of two)
     int B;                // points per leaf (8, 16 or 32)
 };
+
+// Grid cells.  A map index quantises positions to cells of size 1/scale (the Morton grid), so
+// the points of one cell are a contiguous run of the sorted array; the hash table maps a cell's
+// 30-bit Morton key to that run: entries (key, start, end, -), empty slots have key 0xffffffff.
+constexpr uint32_t GRID_EMPTY = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t grid_hash(uint32_t key)
+{
+    uint32_t h = key * 2654435761u;
+    return h ^ (h >> 16);
+}
+
+// [start, end) of the cell with this key (empty range if the cell holds no point).
+__device__ __forceinline__ int2 grid_find(const int4* __restrict__ table, uint32_t mask, uint32_t key)
+{
+    uint32_t slot = grid_hash(key) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int4 e = table[slot];
+        if ((uint32_t)e.x == key) return make_int2(e.y, e.z);
+        if ((uint32_t)e.x == GRID_EMPTY) break;
+        slot = (slot + 1) & mask;
+    }
+    return make_int2(0, 0);
+}
 
 constexpr int SEED_BITS = 21;  // 7 bits per axis: cells of 1/128 of the bounding cube
 
@@ -156,13 +182,15 @@ struct RegJob {
     const int* n;          // device count
     IndexView map;
     int* cand;             // n x KC: sorted map positions of each point's cached nearest map points (-1 none)
-    float4* anchor;        // n: (query position the cache was filled at, radius within which it is complete);
-                           // radius <= 0 means "search" (cand[0] then holds a seed position or -1)
+    float4* anchor;        // n: (query position of the last search, radius within which the cached
+                           // candidates are complete); radius -1: searched without a cache, -2: never
+                           // searched (cand[0] then holds a seed position or -1)
     int* corr_out;         // optional: original map index per source point
     float* partials;       // grid x NACC
     RegState* st;
     float max_d2;
     float slack;           // extra search radius beyond max_corr_dist kept in the cache (m)
+    float cache_step;      // a point that moved more than this since its last search searches 1-NN only (m)
     int max_iters;
     double tol_rot, tol_trans;
     int min_inliers;

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
     // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
     // the reduction order, hence the result, deterministic).
     int refreshed = 0;
+    const float4 qq = *J.map.quant;
     const int B = J.map.B;
     const float max_d = sqrtf(J.max_d2);
     const float Rs = max_d + J.slack, Rs2 = Rs * Rs;
@@ -248,20 +249,68 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         }
         if (!resolved) {
             refreshed = 1;
-            // exact KC nearest map points within Rs, starting from the cached (or seed) leaves
-            float D[KC];
-            int I[KC], P[KC];
+            // A point that moved more than cache_step since its last search will likely move that
+            // much again: search its nearest point only (a cache built now would not survive).
+            const bool one_nn = !(anc.w != -2.f &&
+                                  sq3(y0 - anc.x, y1 - anc.y, y2 - anc.z) < J.cache_step * J.cache_step);
+            // Grid fast path: the 2x2x2 block of map cells around y (the octant of y's cell it lies
+            // in).  Every map point outside the block is at least `cert` from y: the distance to the
+            // block's faces less a margin for the float cell assignment of the points.
+            int2 rng[8];
+            const float cert = grid_block8(J.map, qq, y0, y1, y2, rng);
+            const float cert2 = cert > 0.f ? cert * cert * (1.f - 2e-5f) : -1.f;
+            if (one_nn) {
+                // the pose is still moving a lot: only the nearest point, no cache
+                if (cert2 > 0.f) {
 #pragma unroll
-            for (int j = 0; j < KC; ++j) {
-                D[j] = Rs2;
-                I[j] = 0x7fffffff;
-                P[j] = -1;
-            }
-            float bound = Rs2;
-            auto scan_leaf = [&](int lf) {
-                const int beg = lf * B, end = min(beg + B, nmap);
-                for (int u = beg; u < end; ++u) {
-                    const float4 p = J.map.pts[u];
+                    for (int c = 0; c < 8; ++c)
+                        for (int u = rng[c].x; u < rng[c].y; ++u) {
+                            const float4 p = J.map.pts[u];
+                            const float d2 = point_d2(y0, y1, y2, p);
+                            const int oi = __float_as_int(p.w);
+                            if (before(d2, oi, best_d2, best_oi)) {
+                                best_d2 = d2;
+                                best_oi = oi;
+                                best_pos = u;
+                            }
+                        }
+                }
+                if (!(best_pos >= 0 && best_d2 <= cert2)) {
+                    best_d2 = J.max_d2;
+                    best_oi = 0x7fffffff;
+                    best_pos = -1;
+                    auto scan1 = [&](int lf) {
+                        scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), [&](int u, const float4& p) {
+                            const float d2 = point_d2(y0, y1, y2, p);
+                            const int oi = __float_as_int(p.w);
+                            if (before(d2, oi, best_d2, best_oi)) {
+                                best_d2 = d2;
+                                best_oi = oi;
+                                best_pos = u;
+                            }
+                        });
+                    };
+                    const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
+                    if (h0 >= 0) scan1(h0);
+                    traverse8(J.map, y0, y1, y2, best_d2, [&](int lf) {
+                        if (lf != h0) scan1(lf);
+                    });
+                }
+                reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+                J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
+            } else {
+                // exact KC nearest map points, grid block first, else a tree walk within Rs
+                float D[KC];
+                int I[KC], P[KC];
+                auto reset = [&](float lim) {
+#pragma unroll
+                    for (int j = 0; j < KC; ++j) {
+                        D[j] = lim;
+                        I[j] = 0x7fffffff;
+                        P[j] = -1;
+                    }
+                };
+                auto offer = [&](int u, const float4& p) {
                     const float d2 = point_d2(y0, y1, y2, p);
                     const int oi = __float_as_int(p.w);
                     if (before(d2, oi, D[KC - 1], I[KC - 1])) {
@@ -277,24 +326,41 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                             }
                         }
                     }
+                };
+                float rc;
+                reset(GSICP_INF);
+                if (cert2 > 0.f) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        for (int u = rng[c].x; u < rng[c].y; ++u) offer(u, J.map.pts[u]);
                 }
-                bound = D[KC - 1];
-            };
-            const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
-            const int h1 = (cp[KC - 1] >= 0 && cp[KC - 1] / B != h0) ? cp[KC - 1] / B : -1;
-            if (h0 >= 0) scan_leaf(h0);
-            if (h1 >= 0) scan_leaf(h1);
-            traverse(J.map, y0, y1, y2, bound, [&](int lf) {
-                if (lf != h0 && lf != h1) scan_leaf(lf);
-            });
-            const float rc = (I[KC - 1] != 0x7fffffff ? sqrtf(D[KC - 1]) : Rs) * (1.f - 1e-6f);
-            reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
-            reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
-            J.anchor[s] = make_float4(y0, y1, y2, rc);
-            if (I[0] != 0x7fffffff && D[0] <= J.max_d2) {
-                best_d2 = D[0];
-                best_oi = I[0];
-                best_pos = P[0];
+                if (I[0] != 0x7fffffff && D[0] <= cert2) {
+                    // points outside the list: outside the block (>= cert) or beaten by the KC-th
+                    rc = fminf(cert, I[KC - 1] != 0x7fffffff ? sqrtf(D[KC - 1]) : GSICP_INF) * (1.f - 1e-6f);
+                } else {
+                    reset(Rs2);
+                    float bound = Rs2;
+                    auto scan_leaf = [&](int lf) {
+                        scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), offer);
+                        bound = D[KC - 1];
+                    };
+                    const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
+                    const int h1 = (cp[KC - 1] >= 0 && cp[KC - 1] / B != h0) ? cp[KC - 1] / B : -1;
+                    if (h0 >= 0) scan_leaf(h0);
+                    if (h1 >= 0) scan_leaf(h1);
+                    traverse8(J.map, y0, y1, y2, bound, [&](int lf) {
+                        if (lf != h0 && lf != h1) scan_leaf(lf);
+                    });
+                    rc = (I[KC - 1] != 0x7fffffff ? sqrtf(D[KC - 1]) : Rs) * (1.f - 1e-6f);
+                }
+                reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
+                reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
+                J.anchor[s] = make_float4(y0, y1, y2, rc);
+                if (I[0] != 0x7fffffff && D[0] <= J.max_d2) {
+                    best_d2 = D[0];
+                    best_oi = I[0];
+                    best_pos = P[0];
+                }
             }
         }
         if (J.corr_out) J.corr_out[__float_as_int(x.w)] = best_pos >= 0 ? best_oi : -1;
@@ -592,10 +658,33 @@ __global__ void nearest_kernel(IndexView ix, const float* __restrict__ q, int nq
                                int32_t* __restrict__ idx, float* __restrict__ d2out)
 {
     const int nmap = *ix.n;
+    const float4 qz = *ix.quant;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
         float bd = max_d2;
         int bo = 0x7fffffff, bp = -1;
-        nn_search(ix, nmap, q[3l * i], q[3l * i + 1], q[3l * i + 2], bd, bo, bp);
+        const float q0 = q[3l * i], q1 = q[3l * i + 1], q2 = q[3l * i + 2];
+        int2 rng[8];
+        const float cert = grid_block8(ix, qz, q0, q1, q2, rng);
+        if (cert > 0.f) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                for (int u = rng[c].x; u < rng[c].y; ++u) {
+                    const float4 p = ix.pts[u];
+                    const float d2 = point_d2(q0, q1, q2, p);
+                    const int oi = __float_as_int(p.w);
+                    if (before(d2, oi, bd, bo)) {
+                        bd = d2;
+                        bo = oi;
+                        bp = u;
+                    }
+                }
+        }
+        if (!(bp >= 0 && bd <= cert * cert * (1.f - 2e-5f))) {  // not certified by the block: full search
+            bd = max_d2;
+            bo = 0x7fffffff;
+            bp = -1;
+            nn_search(ix, nmap, q0, q1, q2, bd, bo, bp);
+        }
         idx[i] = bp >= 0 ? bo : -1;
         if (d2out) d2out[i] = bp >= 0 ? bd : GSICP_INF;
     }
@@ -675,7 +764,7 @@ __global__ void seed_kernel(IndexView map, const float4* __restrict__ src, const
         }
         reinterpret_cast<int4*>(cand)[2l * s] = make_int4(seed, -1, -1, -1);
         reinterpret_cast<int4*>(cand)[2l * s + 1] = make_int4(-1, -1, -1, -1);
-        anchor[s] = make_float4(0.f, 0.f, 0.f, -1.f);
+        anchor[s] = make_float4(0.f, 0.f, 0.f, -2.f);  // no previous search
     }
 }
 

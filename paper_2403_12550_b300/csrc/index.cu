@@ -246,30 +246,63 @@ __global__ void bbox_kernel(const float* __restrict__ pts, const int* __restrict
 // 30-bit Morton key of each valid point over the bounding cube; padding slots get
 // 0xffffffff so they sort after every valid point.
 __global__ void morton_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, int cap,
-                              const uint32_t* __restrict__ bb, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+                              const float4* __restrict__ quant, uint32_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals)
 {
     const int n = *n_dev;
-    const float lx = ord2f(bb[0]), ly = ord2f(bb[1]), lz = ord2f(bb[2]);
-    const float ext = fmaxf(fmaxf(ord2f(bb[3]) - lx, ord2f(bb[4]) - ly), ord2f(bb[5]) - lz);
-    const float scale = ext > 0.f ? 1024.f / ext : 0.f;
+    const float4 qz = *quant;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (long)gridDim.x * blockDim.x) {
-        uint32_t key = 0xffffffffu;
-        if (i < n) {
-            uint32_t qx = (uint32_t)min(1023, max(0, (int)((pts[3 * i + 0] - lx) * scale)));
-            uint32_t qy = (uint32_t)min(1023, max(0, (int)((pts[3 * i + 1] - ly) * scale)));
-            uint32_t qz = (uint32_t)min(1023, max(0, (int)((pts[3 * i + 2] - lz) * scale)));
-            key = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
-        }
-        keys[i] = key;
+        keys[i] = i < n ? morton_of(qz, pts[3 * i + 0], pts[3 * i + 1], pts[3 * i + 2]) : 0xffffffffu;
         vals[i] = (uint32_t)i;
     }
 }
 
-__global__ void quant_kernel(const uint32_t* __restrict__ bb, float4* __restrict__ quant)
+// Quantisation of the Morton grid: cells of size `cell` when 1024 of them cover the bounding
+// cube, else 1024 cells across the cube.
+__global__ void quant_kernel(const uint32_t* __restrict__ bb, float cell, float4* __restrict__ quant)
 {
     const float lx = ord2f(bb[0]), ly = ord2f(bb[1]), lz = ord2f(bb[2]);
     const float ext = fmaxf(fmaxf(ord2f(bb[3]) - lx, ord2f(bb[4]) - ly), ord2f(bb[5]) - lz);
-    *quant = make_float4(lx, ly, lz, ext > 0.f ? 1024.f / ext : 0.f);
+    float scale = ext > 0.f ? 1024.f / ext : 0.f;
+    if (cell > 0.f && !(ext > 1024.f * cell)) scale = 1.f / cell;
+    *quant = make_float4(lx, ly, lz, scale);
+}
+
+__global__ void grid_insert_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
+                                   int4* __restrict__ table, uint32_t mask)
+{
+    const int n = *n_dev;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const uint32_t key = keys[s];
+        if (s > 0 && keys[s - 1] == key) continue;  // not the first point of its cell
+        uint32_t slot = grid_hash(key) & mask;
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+            const uint32_t prev = atomicCAS(reinterpret_cast<unsigned int*>(&table[slot].x), GRID_EMPTY, key);
+            if (prev == GRID_EMPTY || prev == key) {
+                table[slot].y = s;
+                break;
+            }
+            slot = (slot + 1) & mask;
+        }
+    }
+}
+
+__global__ void grid_end_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
+                                int4* __restrict__ table, uint32_t mask)
+{
+    const int n = *n_dev;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const uint32_t key = keys[s];
+        if (s + 1 < n && keys[s + 1] == key) continue;  // not the last point of its cell
+        uint32_t slot = grid_hash(key) & mask;
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+            if ((uint32_t)table[slot].x == key) {
+                table[slot].z = s + 1;
+                break;
+            }
+            slot = (slot + 1) & mask;
+        }
+    }
 }
 
 // cell[p] = first sorted position whose key prefix (top SEED_BITS bits) is >= p.
@@ -378,7 +411,8 @@ static int ceil_pow2(long x)
 }
 
 gsicp_status build_index(const float* pts, const float* covs, int cap, const int* n_dev, int bucket,
-                         IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed)
+                         IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed, float cell,
+                         bool with_grid)
 {
     if (bucket != 8 && bucket != 16 && bucket != 32) return GSICP_ERR_INVALID_ARG;
     const int B = bucket;
@@ -399,9 +433,11 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
     GSICP_CHECK(scr.bbox.ensure(sizeof(uint32_t) * 8));
     const int sms = device_sm_count();
     const int grid = std::max(1, std::min((cap + 255) / 256, sms * 8));
+    GSICP_CHECK(out.quant.ensure(sizeof(float4)));
     bbox_init_kernel<<<1, 32, 0, s>>>(scr.bbox.as<uint32_t>());
     bbox_kernel<<<grid, 256, 0, s>>>(pts, n_dev, scr.bbox.as<uint32_t>());
-    morton_kernel<<<grid, 256, 0, s>>>(pts, n_dev, cap, scr.bbox.as<uint32_t>(), scr.k0.as<uint32_t>(),
+    quant_kernel<<<1, 1, 0, s>>>(scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>());
+    morton_kernel<<<grid, 256, 0, s>>>(pts, n_dev, cap, out.quant.as<float4>(), scr.k0.as<uint32_t>(),
                                        scr.v0.as<uint32_t>());
     GSICP_CUDA(cudaGetLastError());
     GSICP_CHECK(radix_sort_pairs(scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
@@ -415,8 +451,17 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
         const int blocks = count / std::min(256, count);
         level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
     }
-    GSICP_CHECK(out.quant.ensure(sizeof(float4)));
-    quant_kernel<<<1, 1, 0, s>>>(scr.bbox.as<uint32_t>(), out.quant.as<float4>());
+    if (with_grid) {
+        uint32_t capacity = 1024;
+        while (capacity < 2u * (uint32_t)sort_n) capacity <<= 1;
+        GSICP_CHECK(out.grid.ensure(sizeof(int4) * (size_t)capacity));
+        out.grid_mask = capacity - 1;
+        GSICP_CUDA(cudaMemsetAsync(out.grid.ptr, 0xff, sizeof(int4) * (size_t)capacity, s));
+        grid_insert_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(), out.grid_mask);
+        grid_end_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(), out.grid_mask);
+    } else {
+        out.grid_mask = 0;
+    }
     if (with_seed) {
         GSICP_CHECK(out.keys.ensure(sizeof(uint32_t) * (size_t)sort_n));
         GSICP_CHECK(out.cell.ensure(sizeof(int) * ((size_t(1) << SEED_BITS) + 1)));
@@ -439,6 +484,8 @@ IndexView IndexBufs::view() const
     v.keys = keys.ptr ? keys.as<const uint32_t>() : nullptr;
     v.cell = cell.ptr ? cell.as<const int>() : nullptr;
     v.quant = quant.as<const float4>();
+    v.grid = grid_mask ? grid.as<const int4>() : nullptr;
+    v.grid_mask = grid_mask;
     v.L = L;
     v.B = B;
     return v;

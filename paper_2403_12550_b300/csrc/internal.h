@@ -40,6 +40,8 @@ struct DevBuf {
 struct IndexBufs {
     DevBuf pts, boxes, covs;
     DevBuf keys, cell, quant;    // seeding structures (built when with_seed is set)
+    DevBuf grid;                 // cell hash table (built when with_grid is set)
+    uint32_t grid_mask = 0;
     const int* n_ptr = nullptr;  // device count of valid points (set by build_index)
     int L = 0, B = 16, cap = 0;
     IndexView view() const;
@@ -51,8 +53,11 @@ struct BuildScratch {
 };
 
 // Build an index over the first *n_dev of `cap` points (pts n x 3, covs n x 6 optional).
+// cell > 0 quantises the Morton grid to cells of that size (coarsened if the bounding cube needs
+// more than 1024 cells per axis); with_grid then also builds the cell hash table.
 gsicp_status build_index(const float* pts, const float* covs, int cap, const int* n_dev, int bucket,
-                         IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed = false);
+                         IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed = false,
+                         float cell = 0.f, bool with_grid = false);
 
 // First-iteration search seeds: for each Morton-ordered source point x_s, the map position found by
 // a Morton-key lookup of T0 x_s (cand[s][0], -1 if none); every cache entry is marked "search".
@@ -121,6 +126,7 @@ struct gsicp_ctx_s {
 struct gsicp_map_s {
     int device = 0;
     int64_t m = 0;
+    float cell = 0.f;                 // requested grid cell size (m)
     gsicp::IndexBufs index;
     gsicp::DevBuf means, covs;        // unsorted copies (for appends)
     gsicp::DevBuf count;              // device int: number of Gaussians

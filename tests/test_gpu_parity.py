@@ -159,9 +159,12 @@ def test_source_covariances_collinear_and_coincident(g, ctx):
 
 # ----------------------------------------------------------------------------- a4 index structure
 
-def _morton30(p, lo, ext):
-    """Reference 30-bit Morton key (10 bits per axis over the bounding cube), integer bit interleaving."""
+def _morton30(p, lo, ext, cell):
+    """Reference 30-bit Morton key (10 bits per axis) on cells of size `cell`, or of 1/1024 of the
+    bounding cube when 1024 cells do not cover it; integer bit interleaving."""
     scale = np.float32(1024.0) / np.float32(ext) if ext > 0 else np.float32(0)
+    if cell > 0 and not (np.float32(ext) > np.float32(1024.0) * np.float32(cell)):
+        scale = np.float32(1.0) / np.float32(cell)
     q = np.clip(((p - lo).astype(np.float32) * scale).astype(np.int64), 0, 1023)
     key = np.zeros(len(p), dtype=np.int64)
     for b in range(10):
@@ -170,12 +173,13 @@ def _morton30(p, lo, ext):
     return key
 
 
-@pytest.mark.parametrize("m,bucket", [(1, 16), (33, 8), (5000, 16), (100_000, 32)])
-def test_map_index_is_morton_sorted_with_tight_boxes(g, ctx, m, bucket):
+@pytest.mark.parametrize("m,bucket,cell", [(1, 16, 0.008), (33, 8, 0.008), (5000, 16, 0.008), (100_000, 32, 0.002),
+                                          (100_000, 16, 0.05)])
+def test_map_index_is_morton_sorted_with_tight_boxes(g, ctx, m, bucket, cell):
     rng = np.random.default_rng(m)
     means = rng.uniform([-1, 0, 2], [3, 2, 2.5], size=(m, 3)).astype(np.float32)
     covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (m, 1))
-    mp = g.gsicp_build_map_index(ctx, cu(means), cu(covs), bucket=bucket)
+    mp = g.gsicp_build_map_index(ctx, cu(means), cu(covs), bucket=bucket, cell=cell)
     ins = g.gsicp_map_inspect(mp)
     pts = ins["pts"].cpu().numpy()
     order = pts[:, 3].copy().view(np.int32)
@@ -183,7 +187,7 @@ def test_map_index_is_morton_sorted_with_tight_boxes(g, ctx, m, bucket):
     np.testing.assert_array_equal(pts[:, :3], means[order])
     lo = means.min(0)
     ext = float((means.max(0) - lo).max())
-    key = _morton30(means[order], lo, ext)
+    key = _morton30(means[order], lo, ext, cell)
     assert np.all(np.diff(key) >= 0)  # Morton order
     # stable: equal keys keep input order
     same = np.diff(key) == 0
@@ -208,9 +212,9 @@ def test_map_index_is_morton_sorted_with_tight_boxes(g, ctx, m, bucket):
 
 # ----------------------------------------------------------------------------- a4 + a5 nearest neighbours
 
-def _check_nearest(map_pts, queries, max_dist, g, ctx, bucket=0):
+def _check_nearest(map_pts, queries, max_dist, g, ctx, bucket=0, cell=0.0):
     covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (len(map_pts), 1))
-    m = g.gsicp_build_map_index(ctx, cu(map_pts), cu(covs), bucket=bucket)
+    m = g.gsicp_build_map_index(ctx, cu(map_pts), cu(covs), bucket=bucket, cell=cell)
     idx, d2 = g.gsicp_map_nearest(ctx, m, cu(queries), max_dist)
     idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
     io, do = orc.KDTree(map_pts).nn(queries, float(np.float32(max_dist)))
@@ -230,13 +234,14 @@ def _check_nearest(map_pts, queries, max_dist, g, ctx, bucket=0):
     return len(diff)
 
 
-@pytest.mark.parametrize("bucket", [8, 16, 32])
-def test_map_nearest_small(g, ctx, bucket):
+@pytest.mark.parametrize("bucket,cell", [(8, 0.0), (16, 0.0), (32, 0.0), (16, 0.02), (16, 0.1), (16, 0.5)])
+def test_map_nearest_small(g, ctx, bucket, cell):
     rng = np.random.default_rng(bucket)
     for m_n in (1, 7, 100, 5000):
         mp = rng.uniform(-1, 1, size=(m_n, 3)).astype(np.float32)
-        q = np.concatenate([rng.uniform(-1.2, 1.2, size=(3000, 3)), mp[: min(m_n, 500)]]).astype(np.float32)
-        assert _check_nearest(mp, q, 0.1, g, ctx, bucket) <= 2
+        q = np.concatenate([rng.uniform(-1.2, 1.2, size=(3000, 3)), mp[: min(m_n, 500)],
+                            mp[: min(m_n, 500)] + rng.normal(0, 0.01, size=(min(m_n, 500), 3))]).astype(np.float32)
+        assert _check_nearest(mp, q, 0.1, g, ctx, bucket, cell) <= 2
 
 
 def test_map_nearest_ties(g, ctx):
@@ -270,8 +275,15 @@ def test_linearise_matches_oracle(g, ctx):
         lg = g.gsicp_linearise(ctx, cu(src), cu(cs), m, T, 0.1)
         lo = orc.linearise(src, cs, om, T, 0.1)
         corr = lg["corr"].cpu().numpy()
-        mism = np.count_nonzero(corr != lo["corr"])
+        bad = np.nonzero(corr != lo["corr"])[0]
+        mism = len(bad)
         assert mism <= 1e-3 * len(src)
+        # a differing correspondence is a near-tie under the float transform (|y| * 1e-6 m)
+        y = transform_points(T, src.astype(np.float64))
+        for i in bad:
+            dg = np.linalg.norm(tgt[corr[i]] - y[i]) if corr[i] >= 0 else 0.1
+            do = np.linalg.norm(tgt[lo["corr"][i]] - y[i]) if lo["corr"][i] >= 0 else 0.1
+            assert abs(dg - do) <= 1e-6 * (1 + np.linalg.norm(y[i])), (i, dg, do)
         assert abs(lg["inliers"] - lo["inliers"]) <= mism
         herr = np.linalg.norm(lg["H"] - lo["H"]) / np.linalg.norm(lo["H"])
         berr = np.linalg.norm(lg["b"] - lo["b"]) / max(np.linalg.norm(lo["b"]), 1e-12)
