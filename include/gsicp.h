@@ -131,6 +131,25 @@ gsicp_status gsicp_depth_to_points(gsicp_ctx ctx, const float* depth_dev, int W,
                                    float* pts_dev, float* z_dev, int64_t cap, int32_t* n_dev,
                                    int64_t* n_host, void* stream);
 
+/* Allocation-free variant of gsicp_depth_to_points (the paper has no counterpart: this is a
+ * deployment aid).  For callers that must not allocate device memory when they need the result:
+ * a tracking loop with a hard per-frame deadline (cudaMalloc / cudaFree may synchronise the
+ * device and take an unbounded time), an application whose own memory pool owns the device, or
+ * code that may not allocate after initialisation.  No context is needed and nothing is
+ * allocated: the step's scratch (128 KB) is a fixed array inside the library, present on every
+ * GPU that loads it until the process exits.  Same arguments and results as
+ * gsicp_depth_to_points, except that the count goes to n_dev (device int32, required) and the
+ * count before clamping to cap to total_dev (device int32, nullable); nothing is synchronised.
+ * The sampled grid ceil(W/stride) * ceil(H/stride) may hold at most 4194304 pixels; larger
+ * images are rejected with GSICP_ERR_INVALID_ARG (message in gsicp_last_error()).  The first
+ * call on a device looks up the array's device address; make that call before any stream
+ * capture.  All calls on a device share the array: calls that may overlap on the GPU (e.g. on
+ * unordered streams) race on it and must be serialised by the caller. */
+gsicp_status gsicp_depth_to_points_noalloc(const float* depth_dev, int W, int H, const float intr[4],
+                                           int stride, float z_min, float z_max, float* pts_dev,
+                                           float* z_dev, int64_t cap, int32_t* n_dev,
+                                           int32_t* total_dev, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * a2+a3  Source Gaussians   (Sec. 3: covariance of the k nearest neighbours; Sec. 3.1 scale
  * regularisation; Sec. 3.2 scale aligning)

@@ -19,7 +19,7 @@ __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
     "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
-    "gsicp_depth_to_points", "gsicp_source_covariances", "gsicp_build_map_index", "gsicp_map_append",
+    "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_build_map_index", "gsicp_map_append",
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
 ]
@@ -87,6 +87,8 @@ _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
 _sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
 _sig("gsicp_depth_to_points", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, _vp, _vp,
                                         C.c_int64, _vp, _i64p, _vp])
+_sig("gsicp_depth_to_points_noalloc", C.c_int, [_vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, _vp,
+                                                _vp, C.c_int64, _vp, _vp, _vp])
 _sig("gsicp_source_covariances", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(CovParams), _vp, _vp, _vp])
 _sig("gsicp_build_map_index", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(IndexParams), _vp,
                                         C.POINTER(C.c_void_p)])
@@ -230,6 +232,20 @@ def gsicp_depth_to_points(ctx: Context, depth: torch.Tensor, intr, stride: int, 
                                      _dev(z_out), pts_out.shape[0], None, C.byref(n), _stream()),
            "gsicp_depth_to_points")
     return pts_out[:n.value], z_out[:n.value]
+
+
+def gsicp_depth_to_points_noalloc(depth: torch.Tensor, intr, stride: int, z_min: float, z_max: float,
+                                  pts_out: torch.Tensor, z_out: torch.Tensor | None, n_out: torch.Tensor,
+                                  total_out: torch.Tensor | None = None):
+    """a1 without any allocation by the library (its scratch is a fixed array inside it): for
+    callers that cannot allocate device memory when they run this step.  Results go to the
+    caller's buffers; n_out / total_out are one-element int32 device tensors.  No synchronisation."""
+    H, W = depth.shape
+    fi = (C.c_float * 4)(*[float(v) for v in intr])
+    _check(lib.gsicp_depth_to_points_noalloc(_dev(depth), W, H, fi, stride, z_min, z_max, _dev(pts_out, cols=3),
+                                             _dev(z_out), pts_out.shape[0], _dev(n_out, torch.int32),
+                                             _dev(total_out, torch.int32), _stream()),
+           "gsicp_depth_to_points_noalloc")
 
 
 def gsicp_source_covariances(ctx: Context, pts: torch.Tensor, z: torch.Tensor | None, params: CovParams,

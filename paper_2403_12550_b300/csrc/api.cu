@@ -22,6 +22,12 @@ gsicp_status cuda_status(cudaError_t e, const char* where)
     return e == cudaErrorMemoryAllocation ? GSICP_ERR_OOM : GSICP_ERR_CUDA;
 }
 
+gsicp_status set_error(gsicp_status st, const char* msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
 gsicp_status DevBuf::ensure(size_t want)
 {
     if (want <= bytes && ptr) return GSICP_OK;
