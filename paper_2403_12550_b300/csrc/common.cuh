@@ -108,6 +108,81 @@ __device__ __forceinline__ bool before(float d, int i, float e, int j)
     return d < e || (d == e && i < j);
 }
 
+// (squared distance, index) as one 64-bit key whose unsigned order is the order "distance, then
+// index" (non-negative float bits order like unsigned integers).
+__device__ __forceinline__ unsigned long long dkey(float d2, int i)
+{
+    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)i;
+}
+__device__ __forceinline__ float key_d2(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
+__device__ __forceinline__ int key_idx(unsigned long long k) { return (int)(unsigned)(k & 0xffffffffu); }
+
+// Insert key k into the ascending list L of length K, dropping the last entry (the caller has
+// checked k < L[K-1]); an optional companion array P is shifted along.  Each slot is compared
+// with k independently and then shifted with selects: a few instructions deep, not K.
+template <int K>
+__device__ __forceinline__ void key_insert(unsigned long long (&L)[K], unsigned long long k)
+{
+    bool go[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) go[j] = k < L[j];
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) L[j] = go[j - 1] ? L[j - 1] : (go[j] ? k : L[j]);
+    L[0] = go[0] ? k : L[0];
+}
+
+template <int K>
+__device__ __forceinline__ void key_insert(unsigned long long (&L)[K], int (&P)[K], unsigned long long k, int p)
+{
+    bool go[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) go[j] = k < L[j];
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) {
+        L[j] = go[j - 1] ? L[j - 1] : (go[j] ? k : L[j]);
+        P[j] = go[j - 1] ? P[j - 1] : (go[j] ? p : P[j]);
+    }
+    L[0] = go[0] ? k : L[0];
+    P[0] = go[0] ? p : P[0];
+}
+
+// Insert (d, i[, p]) into the list (D, I[, P]) of length K sorted by (distance, index), dropping
+// the last entry; the caller has checked that the new entry precedes the last one.  Every slot is
+// compared with the new entry independently and then shifted with selects, so the dependency
+// chain is a few instructions deep instead of K compare-swaps long.
+template <int K>
+__device__ __forceinline__ void sorted_insert(float (&D)[K], int (&I)[K], float d, int i)
+{
+    bool go[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) go[j] = before(d, i, D[j], I[j]);
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) {
+        D[j] = go[j - 1] ? D[j - 1] : (go[j] ? d : D[j]);
+        I[j] = go[j - 1] ? I[j - 1] : (go[j] ? i : I[j]);
+    }
+    D[0] = go[0] ? d : D[0];
+    I[0] = go[0] ? i : I[0];
+}
+
+template <int K>
+__device__ __forceinline__ void sorted_insert(float (&D)[K], int (&I)[K], int (&P)[K], float d, int i, int p)
+{
+    bool go[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) go[j] = before(d, i, D[j], I[j]);
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) {
+        D[j] = go[j - 1] ? D[j - 1] : (go[j] ? d : D[j]);
+        I[j] = go[j - 1] ? I[j - 1] : (go[j] ? i : I[j]);
+        P[j] = go[j - 1] ? P[j - 1] : (go[j] ? p : P[j]);
+    }
+    D[0] = go[0] ? d : D[0];
+    I[0] = go[0] ? i : I[0];
+    P[0] = go[0] ? p : P[0];
+}
+
+
 // Order-preserving map float -> uint32 (for atomicMin/atomicMax on floats).
 __device__ __forceinline__ uint32_t f2ord(float f)
 {

@@ -7,11 +7,12 @@
 // covariance by its middle eigenvalue.  Sec. 3.2: scale aligning divides the
 // scales by z^p, i.e. multiplies the covariance by z^(-2p).
 //
-// One thread per query, queries taken in the index's Morton order so that a
-// warp's threads walk the same part of the tree (traverse.cuh).  Each thread
-// keeps its k best candidates in registers as a sorted list, padded at the
-// front with "phantom" entries so that the k-th best always sits in the last
-// slot (static register indexing for any k <= KMAX).
+// One thread per query, a warp's 32 queries being the 32 points of one leaf of
+// the source index (Morton order): the warp scans its own leaf and the two next
+// to it, then walks the tree once for all 32 queries (packet_traverse in
+// traverse.cuh).  Each thread keeps its k best candidates in registers as a
+// sorted list, padded at the front with "phantom" entries so that the k-th best
+// always sits in the last slot (static register indexing for any k <= KMAX).
 #include <algorithm>
 
 #include "internal.h"
@@ -94,48 +95,50 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
                                                               float4* __restrict__ covs_sorted)
 {
     const int n = *ix.n;
-    const int B = ix.B;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const float4 q = ix.pts[s];
+    const int B = ix.B;  // 32: a warp's queries are exactly the points of one leaf
+    const int lane = threadIdx.x & 31;
+    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = warp0 * 32; base < n; base += nwarps * 32) {  // warp-uniform loop
+        const int s = base + lane;
+        const bool active = s < n;
+        const float4 q = active ? ix.pts[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const int qi = __float_as_int(q.w);
-        float D[KMAX];
-        int I[KMAX];
+        // ascending (squared distance, index) keys; phantom entries (key 0) pad the front so the
+        // k-th best is always the last slot, empty slots hold (+inf, INT_MAX)
+        unsigned long long Lk[KMAX];
+        const unsigned long long empty = dkey(GSICP_INF, 0x7fffffff);
 #pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            const bool phantom = j < KMAX - k;
-            D[j] = phantom ? -1.f : GSICP_INF;
-            I[j] = phantom ? -1 : 0x7fffffff;
-        }
-        // ---- exact k-NN (ties -> smaller original index): the query's own leaf and its two
-        // Morton neighbours first (a tight bound), then the tree walk skipping those three
+        for (int j = 0; j < KMAX; ++j) Lk[j] = j < KMAX - k ? 0ull : empty;
+        // ---- exact k-NN (ties -> smaller original index): the warp's own leaf and its two Morton
+        // neighbours first (a tight bound for every lane), then one packet walk of the tree for
+        // the 32 queries, skipping those three leaves
         float bound = GSICP_INF;
-        const int own = s / B;
+        const int own = base / B;
         auto scan_leaf = [&](int lf) {
             const int beg = lf * B, end = min(beg + B, n);
             for (int t = beg; t < end; ++t) {
-                const float4 pp = ix.pts[t];
+                const float4 pp = ix.pts[t];  // same address in every lane: one broadcast load
+                if (!active) continue;
+        int I[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) I[j] = key_idx(Lk[j]);
                 const float d2 = point_d2(q.x, q.y, q.z, pp);
                 const int oi = __float_as_int(pp.w);
-                if (before(d2, oi, D[KMAX - 1], I[KMAX - 1])) {
-                    D[KMAX - 1] = d2;
-                    I[KMAX - 1] = oi;
-#pragma unroll
-                    for (int u = KMAX - 1; u > 0; --u) {
-                        if (before(D[u], I[u], D[u - 1], I[u - 1])) {
-                            float td = D[u]; D[u] = D[u - 1]; D[u - 1] = td;
-                            int ti = I[u]; I[u] = I[u - 1]; I[u - 1] = ti;
-                        }
-                    }
-                }
+                const unsigned long long key = dkey(d2, oi);
+                if (key < Lk[KMAX - 1]) key_insert(Lk, key);
             }
-            bound = D[KMAX - 1];
+            bound = key_d2(Lk[KMAX - 1]);
         };
         scan_leaf(own);
         if (own > 0) scan_leaf(own - 1);
         if ((own + 1) * B < n) scan_leaf(own + 1);
-        traverse(ix, q.x, q.y, q.z, bound, [&](int lf) {
+        packet_traverse(ix, active, q.x, q.y, q.z, bound, [&](int lf) {
             if (lf < own - 1 || lf > own + 1) scan_leaf(lf);
         });
+        if (!active) continue;
+        int I[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) I[j] = key_idx(Lk[j]);
         // ---- covariance of the neighbourhood (two-pass, float), neighbours gathered by original index
         int kk = 0;
         float m0 = 0.f, m1 = 0.f, m2 = 0.f;
@@ -261,6 +264,7 @@ gsicp_status launch_knn_cov(const IndexView& ix, const float* orig_pts, const fl
                             cudaStream_t s)
 {
     if (cap <= 0) return GSICP_OK;
+    if (ix.B != 32) return GSICP_ERR_INVALID_ARG;  // one leaf per warp
     const int grid = std::max(1, std::min((cap + COV_THREADS - 1) / COV_THREADS, device_sm_count() * 16));
     const int k = prm.k;
     if (k <= 8)

@@ -300,32 +300,18 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                 J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
             } else {
                 // exact KC nearest map points, grid block first, else a tree walk within Rs
-                float D[KC];
-                int I[KC], P[KC];
+                unsigned long long Lk[KC];  // ascending (squared distance, index) keys
+                int P[KC];                  // their sorted map positions
                 auto reset = [&](float lim) {
 #pragma unroll
                     for (int j = 0; j < KC; ++j) {
-                        D[j] = lim;
-                        I[j] = 0x7fffffff;
+                        Lk[j] = dkey(lim, 0x7fffffff);
                         P[j] = -1;
                     }
                 };
                 auto offer = [&](int u, const float4& p) {
-                    const float d2 = point_d2(y0, y1, y2, p);
-                    const int oi = __float_as_int(p.w);
-                    if (before(d2, oi, D[KC - 1], I[KC - 1])) {
-                        D[KC - 1] = d2;
-                        I[KC - 1] = oi;
-                        P[KC - 1] = u;
-#pragma unroll
-                        for (int v = KC - 1; v > 0; --v) {
-                            if (before(D[v], I[v], D[v - 1], I[v - 1])) {
-                                float td = D[v]; D[v] = D[v - 1]; D[v - 1] = td;
-                                int ti = I[v]; I[v] = I[v - 1]; I[v - 1] = ti;
-                                int tp = P[v]; P[v] = P[v - 1]; P[v - 1] = tp;
-                            }
-                        }
-                    }
+                    const unsigned long long key = dkey(point_d2(y0, y1, y2, p), __float_as_int(p.w));
+                    if (key < Lk[KC - 1]) key_insert(Lk, P, key, u);
                 };
                 float rc;
                 reset(GSICP_INF);
@@ -334,15 +320,16 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                     for (int c = 0; c < 8; ++c)
                         for (int u = rng[c].x; u < rng[c].y; ++u) offer(u, J.map.pts[u]);
                 }
-                if (I[0] != 0x7fffffff && D[0] <= cert2) {
+                if (key_idx(Lk[0]) != 0x7fffffff && key_d2(Lk[0]) <= cert2) {
                     // points outside the list: outside the block (>= cert) or beaten by the KC-th
-                    rc = fminf(cert, I[KC - 1] != 0x7fffffff ? sqrtf(D[KC - 1]) : GSICP_INF) * (1.f - 1e-6f);
+                    rc = fminf(cert, key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : GSICP_INF) *
+                         (1.f - 1e-6f);
                 } else {
                     reset(Rs2);
                     float bound = Rs2;
                     auto scan_leaf = [&](int lf) {
                         scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), offer);
-                        bound = D[KC - 1];
+                        bound = key_d2(Lk[KC - 1]);
                     };
                     const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
                     const int h1 = (cp[KC - 1] >= 0 && cp[KC - 1] / B != h0) ? cp[KC - 1] / B : -1;
@@ -351,14 +338,14 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                     traverse8(J.map, y0, y1, y2, bound, [&](int lf) {
                         if (lf != h0 && lf != h1) scan_leaf(lf);
                     });
-                    rc = (I[KC - 1] != 0x7fffffff ? sqrtf(D[KC - 1]) : Rs) * (1.f - 1e-6f);
+                    rc = (key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : Rs) * (1.f - 1e-6f);
                 }
                 reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
                 reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
                 J.anchor[s] = make_float4(y0, y1, y2, rc);
-                if (I[0] != 0x7fffffff && D[0] <= J.max_d2) {
-                    best_d2 = D[0];
-                    best_oi = I[0];
+                if (key_idx(Lk[0]) != 0x7fffffff && key_d2(Lk[0]) <= J.max_d2) {
+                    best_d2 = key_d2(Lk[0]);
+                    best_oi = key_idx(Lk[0]);
                     best_pos = P[0];
                 }
             }

@@ -159,6 +159,55 @@ __device__ __forceinline__ void scan_points4(const float4* __restrict__ pts, int
     }
 }
 
+// Packet walk: the warp walks the tree once for the queries of all its lanes.  A node is entered
+// when at least one searching lane's own bound reaches its box (per-lane box test + ballot); of
+// two needed children the one most of those lanes find nearer goes first.  Leaf points are read
+// by all lanes at once (same address: one broadcast load) and each lane updates only its own
+// result, so the walk costs the union of the lanes' node sets instead of their divergent sum.
+// Exactness is the per-lane argument of traverse(): a subtree is skipped only when no lane's
+// bound reaches it.  Must be called by all 32 lanes (converged); `active` selects searching lanes.
+template <class LeafFn>
+__device__ __forceinline__ void packet_traverse(const IndexView& ix, bool active, float qx, float qy, float qz,
+                                                const float& bound, LeafFn&& leaf_fn)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int L = ix.L;
+    int stk[32];    // same content in every lane (pushes are warp-uniform)
+    float sd[32];   // this lane's distance to each stacked node
+    int sp = 0;
+    int node = __any_sync(FULL, active) ? 1 : 0;
+    while (node != 0) {
+        if (node >= L) {
+            leaf_fn(node - L);
+        } else {
+            const float4* bx = ix.boxes + 4 * node;  // children 2node, 2node+1
+            const float d0 = box_d2(qx, qy, qz, bx[0], bx[1]);
+            const float d1 = box_d2(qx, qy, qz, bx[2], bx[3]);
+            const bool n0 = active && d0 <= bound, n1 = active && d1 <= bound;
+            const unsigned m0 = __ballot_sync(FULL, n0), m1 = __ballot_sync(FULL, n1);
+            if (m0 | m1) {
+                const unsigned vote0 = __ballot_sync(FULL, (n0 || n1) && d0 <= d1);
+                const bool first0 = m0 != 0u && (m1 == 0u || 2 * __popc(vote0) >= __popc(m0 | m1));
+                if ((first0 ? m1 : m0) != 0u && sp < 32) {
+                    stk[sp] = first0 ? 2 * node + 1 : 2 * node;
+                    sd[sp] = first0 ? d1 : d0;
+                    ++sp;
+                }
+                node = first0 ? 2 * node : 2 * node + 1;
+                continue;
+            }
+        }
+        node = 0;
+        while (sp > 0) {
+            --sp;
+            if (__any_sync(FULL, active && sd[sp] <= bound)) {
+                node = stk[sp];
+                break;
+            }
+        }
+    }
+}
+
 // Grid fast path.  Looks up the 2x2x2 block of grid cells around q (the octant of q's cell it
 // lies in) and returns their point ranges in rng and the radius `cert` within which the block is
 // exhaustive: every point outside it is at least cert from q (the distance from q to the block's
