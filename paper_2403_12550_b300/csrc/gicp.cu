@@ -8,10 +8,14 @@
 // xi = (omega, v): J_i = dd_i/dxi = [[y_i]x, -I] with y_i = R x_i + t.
 //
 // One kernel launch per iteration.  One thread per source point, points in
-// the source index's Morton order:
-// transform, exact nearest map mean, then the residual, weight, J^T W J (21
-// unique), J^T W d (6), d^T W d and the inlier count -> warp shuffles -> one
-// FP32 partial per block.
+// the source index's Morton order: transform, exact nearest map mean, then the
+// residual, weight, J^T W J (21 unique), J^T W d (6), d^T W d and the inlier
+// count -> warp shuffles -> one FP32 partial per block.  The last block to
+// finish (threadfence + atomic counter, no waiting) sums the partials with
+// compensation; its first warp solves the 6x6 system by FP64 Cholesky, applies
+// the FP64 SE(3) exponential (both spread over the warp's lanes) and, inside a
+// CUDA graph, sets the conditional-while handle that decides whether the next
+// iteration runs.
 //
 // Nearest-neighbour search with a per-point candidate cache: each point keeps
 // its KC nearest map points within max_corr_dist + slack and the radius within
@@ -19,13 +23,10 @@
 // was made.  Once the point has moved by delta, no map point outside the list
 // can be closer than radius - delta, so when the best cached candidate is
 // within that (with float-rounding margins) it is the exact answer and the
-// tree is not walked; otherwise the list is rebuilt by an exact KC-nearest walk
-// of the map's bounding-volume hierarchy (traverse.cuh) starting from the
-// cached leaves.  The first iteration starts from a Morton-key seed.  The last block to finish (threadfence + atomic
-// counter, no waiting) sums the partials with compensation, solves the 6x6
-// system by FP64 Cholesky, applies the FP64 SE(3) exponential and, inside a
-// CUDA graph, sets the conditional-while handle that decides whether the
-// next iteration runs.
+// tree is not walked; otherwise the list is rebuilt: from the 2x2x2 block of
+// map-grid cells around the point when the block certifies it, else by an
+// exact walk of the map's bounding-volume hierarchy (traverse.cuh) bounded by
+// what the block found.  The first iteration starts from a Morton-key seed.
 #include <algorithm>
 
 #include "internal.h"
@@ -61,57 +62,96 @@ __device__ __forceinline__ void nn_search(const IndexView& ix, int n, float qx, 
 __host__ __device__ constexpr int ut(int r, int c) { return r * 6 - (r * (r - 1)) / 2 + (c - r); }
 
 // ---------------------------------------------------------------------------------------------
-// FP64 6x6 solve and SE(3) exponential (single thread)
+// FP64 6x6 solve and SE(3) exponential, spread over the lanes of one warp.  FP64 arithmetic is
+// slow on this part and a warp instruction costs as much with one active lane as with 32, so
+// each step below is one instruction over every entry it updates.
 
-__device__ bool chol_solve6(const double H[36], const double rhs[6], double x[6])
+// Lane p < 27 holds entry (i, j) of the augmented matrix [H ; r^T] (7 rows, 6 columns): the
+// lower triangle of H in packed row order (p < 21), then r (p = 21 + j).
+__device__ __forceinline__ void chol_lane_coords(int p, int& i, int& j)
 {
-    double L[21];  // lower triangle, row-major packed: L(i, j) at i*(i+1)/2 + j
-    double inv[6]; // 1 / L(j, j)
+    if (p >= 21) {
+        i = 6;
+        j = p - 21;
+        return;
+    }
+    i = 0;
+    while ((i + 1) * (i + 2) / 2 <= p) ++i;
+    j = p - i * (i + 1) / 2;
+}
+__device__ __forceinline__ int chol_lane(int i, int j) { return i == 6 ? 21 + j : i * (i + 1) / 2 + j; }
+
+// Solves H x = r by the Cholesky factorisation H = L L^T.  Factorising [H ; r^T] leaves the
+// forward substitution L^-1 r in its last row; back substitution follows.  On entry lane p holds
+// entry p (see chol_lane_coords); every lane returns the same x.  Returns false on every lane
+// when a pivot is not positive (H not positive definite).
+__device__ bool warp_chol_solve6(double a, int lane, double x[6])
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    int li = 0, lj = 0;
+    const bool holds = lane < 27;
+    if (holds) chol_lane_coords(lane, li, lj);
+    double inv[6];  // 1 / L(j, j)
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        double d = H[6 * j + j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+        const double d = __shfl_sync(FULL, a, chol_lane(j, j));
         if (!(d > 0.0) || !isfinite(d)) return false;
         inv[j] = rsqrt(d);
-        L[j * (j + 1) / 2 + j] = d * inv[j];
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            double v = H[6 * i + j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) v -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
-            L[i * (i + 1) / 2 + j] = v * inv[j];
-        }
+        if (holds && lj == j && li > j) a *= inv[j];  // column j of L
+        // trailing update: a(i, k) -= L(i, j) L(k, j) for j < k <= i
+        const bool upd = holds && lj > j;
+        const double lij = __shfl_sync(FULL, a, upd ? chol_lane(li, j) : lane);
+        const double lkj = __shfl_sync(FULL, a, upd ? chol_lane(lj, j) : lane);
+        if (upd) a = fma(-lij, lkj, a);
     }
-    double y[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double v = rhs[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) v -= L[i * (i + 1) / 2 + k] * y[k];
-        y[i] = v * inv[i];
-    }
+    // L^T x = y, y_j on lane 21 + j
+    double y = a;
+    const int jj = lane - 21;
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
-        double v = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; ++k) v -= L[k * (k + 1) / 2 + i] * x[k];
-        x[i] = v * inv[i];
+        x[i] = __shfl_sync(FULL, y, 21 + i) * inv[i];
+        const bool upd = jj >= 0 && jj < i;
+        const double lij = __shfl_sync(FULL, a, upd ? chol_lane(i, jj) : lane);
+        if (upd) y = fma(-lij, x[i], y);
     }
     return true;
 }
 
-// T <- exp(xi^) T with xi = (omega, v): rotation by Rodrigues' formula,
-// translation V v with V = I + B K + C K^2 (K = [omega]x); series below 1e-2 rad.
-__device__ void se3_left_update(const double xi[6], double T[16])
+// Taylor coefficients in t^2 of sin(t)/t, (1 - cos t)/t^2 and (t - sin t)/t^3:
+// (-1)^m / (2m + o)!, o = 1, 2, 3.  Nine terms leave a remainder below 1e-22 for t < 0.5.
+constexpr int EXP_TERMS = 9;
+constexpr double inv_factorial(int k)
 {
+    double f = 1.0;
+    for (int q = 2; q <= k; ++q) f *= q;
+    return 1.0 / f;
+}
+#define GSICP_SERIES(o)                                                                                  \
+    {inv_factorial(o), -inv_factorial(o + 2), inv_factorial(o + 4), -inv_factorial(o + 6),              \
+     inv_factorial(o + 8), -inv_factorial(o + 10), inv_factorial(o + 12), -inv_factorial(o + 14),       \
+     inv_factorial(o + 16)}
+__constant__ double c_exp_series[3][EXP_TERMS] = {GSICP_SERIES(1), GSICP_SERIES(2), GSICP_SERIES(3)};
+#undef GSICP_SERIES
+
+// T <- exp(xi^) T with xi = (omega, v) the same on every lane: the rotation by Rodrigues'
+// formula E = I + A K + B K^2 and the translation V v with V = I + B K + C K^2 (K = [omega]x,
+// A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3, t = |omega|).  Lane 4r + c < 12
+// returns the new T(r, c); T is read from memory (row-major 4x4, last row 0 0 0 1).
+__device__ double warp_se3_left_update(const double xi[6], const double* T, int lane)
+{
+    constexpr unsigned FULL = 0xffffffffu;
     const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    auto wsel = [&](int i) { return i == 0 ? w0 : (i == 1 ? w1 : w2); };
+    const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
     double A, Bc, Cc;
-    if (th2 < 1e-4) {
-        A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
-        Bc = 0.5 - th2 * (1.0 / 24.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0)));
-        Cc = 1.0 / 6.0 - th2 * (1.0 / 120.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0)));
+    if (th2 < 0.25) {
+        const int o = min(lane, 2);  // lanes 0, 1, 2 evaluate A, B, C
+        double f = c_exp_series[o][EXP_TERMS - 1];
+#pragma unroll
+        for (int m = EXP_TERMS - 2; m >= 0; --m) f = fma(f, th2, c_exp_series[o][m]);
+        A = __shfl_sync(FULL, f, 0);
+        Bc = __shfl_sync(FULL, f, 1);
+        Cc = __shfl_sync(FULL, f, 2);
     } else {
         const double th = sqrt(th2), ith2 = 1.0 / th2;
         double sn, cs;
@@ -120,32 +160,22 @@ __device__ void se3_left_update(const double xi[6], double T[16])
         Bc = (1.0 - cs) * ith2;
         Cc = (1.0 - A) * ith2;
     }
-    const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-    double K2[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-    double E[12];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        double tv = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double id = r == c ? 1.0 : 0.0;
-            E[4 * r + c] = id + A * K[3 * r + c] + Bc * K2[3 * r + c];
-            tv += (id + Bc * K[3 * r + c] + Cc * K2[3 * r + c]) * xi[3 + c];
-        }
-        E[4 * r + 3] = tv;
-    }
-    double M[12];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            M[4 * r + c] = E[4 * r] * T[c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c] + (c == 3 ? E[4 * r + 3] : 0.0);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) T[i] = M[i];
+    // lane 3r + c (< 9): entries (r, c) of E and V, and V(r, c) v_c
+    const int r = min(lane / 3, 2), c = lane % 3;
+    const double k = c == r ? 0.0 : ((c - r + 3) % 3 == 1 ? -wsel(3 - r - c) : wsel(3 - r - c));
+    const double k2 = fma(wsel(r), wsel(c), r == c ? -th2 : 0.0);  // K^2 = w w^T - t^2 I
+    const double id = r == c ? 1.0 : 0.0;
+    const double E = fma(A, k, fma(Bc, k2, id));
+    const double V = fma(Bc, k, fma(Cc, k2, id));
+    const double p = V * (c == 0 ? xi[3] : (c == 1 ? xi[4] : xi[5]));
+    const double p1 = __shfl_down_sync(FULL, p, 1), p2 = __shfl_down_sync(FULL, p, 2);
+    const double Vv = p + p1 + p2;  // lane 3r: (V v)_r
+    // lane 4r + c (< 12): new T(r, c) = sum_k E(r, k) T(k, c) (+ (V v)_r for c = 3)
+    const int tr = min(lane >> 2, 2), tc = lane & 3;
+    const double e0 = __shfl_sync(FULL, E, 3 * tr), e1 = __shfl_sync(FULL, E, 3 * tr + 1),
+                 e2 = __shfl_sync(FULL, E, 3 * tr + 2);
+    const double tv = __shfl_sync(FULL, Vv, 3 * tr);
+    return fma(e0, T[tc], fma(e1, T[4 + tc], fma(e2, T[8 + tc], tc == 3 ? tv : 0.0)));
 }
 
 __device__ __forceinline__ void pose_to_float(RegState* st)
@@ -276,9 +306,6 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                         }
                 }
                 if (!(best_pos >= 0 && best_d2 <= cert2)) {
-                    best_d2 = J.max_d2;
-                    best_oi = 0x7fffffff;
-                    best_pos = -1;
                     auto scan1 = [&](int lf) {
                         scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), [&](int u, const float4& p) {
                             const float d2 = point_d2(y0, y1, y2, p);
@@ -325,8 +352,9 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                     rc = fminf(cert, key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : GSICP_INF) *
                          (1.f - 1e-6f);
                 } else {
-                    reset(Rs2);
-                    float bound = Rs2;
+                    const float lim = key_idx(Lk[KC - 1]) != 0x7fffffff ? fminf(key_d2(Lk[KC - 1]), Rs2) : Rs2;
+                    reset(lim);
+                    float bound = lim;
                     auto scan_leaf = [&](int lf) {
                         scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), offer);
                         bound = key_d2(Lk[KC - 1]);
@@ -507,47 +535,68 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         tot[threadIdx.x] = sum;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (warp != 0) return;
 
-    unsigned long long t_solve;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_solve));
-    double H[36], b[6];
-    for (int r = 0; r < 6; ++r)
-        for (int c = r; c < 6; ++c) H[6 * r + c] = H[6 * c + r] = tot[ut(r, c)];
-    for (int a = 0; a < 6; ++a) b[a] = tot[21 + a];
-    for (int a = 0; a < 36; ++a) st->H[a] = H[a];
-    for (int a = 0; a < 6; ++a) st->b[a] = b[a];
-    st->cost = tot[27];
-    st->inliers = (long long)llrint(tot[28]);
-    st->counter = 0u;
+    // ---- warp 0: H, b, cost and inliers of this linearisation, then the lane-parallel FP64 solve
+    const double tot_l = lane < NACC ? tot[lane] : 0.0;  // component `lane`
+    unsigned long long t_solve = 0;
+    if (lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_solve));
+    if (lane < 21) {
+        int r = 0;
+        while (ut(r, 5) < lane) ++r;
+        const int c = lane - ut(r, r) + r;
+        st->H[6 * r + c] = tot_l;
+        st->H[6 * c + r] = tot_l;
+    } else if (lane < 27) {
+        st->b[lane - 21] = tot_l;
+    } else if (lane == 27) {
+        st->cost = tot_l;
+    } else if (lane == 28) {
+        st->inliers = (long long)llrint(tot_l);
+    }
+    if (lane == 0) st->counter = 0u;
+    const long long inliers = (long long)llrint(tot[28]);
     bool more = false;
     if (J.mode == REG_MODE_SOLVE) {
-        st->iter += 1;
-        double nb[6], delta[6];
-        for (int a = 0; a < 6; ++a) nb[a] = -b[a];
-        if (st->inliers < J.min_inliers || !chol_solve6(H, nb, delta)) {
-            st->status = REG_ST_DEGENERATE;
+        // lane p < 27 takes entry (i, j) of [H ; -b^T]
+        int ci = 0, cj = 0;
+        if (lane < 27) chol_lane_coords(lane, ci, cj);
+        double a = lane < 27 ? tot[ci == 6 ? 21 + cj : ut(cj, ci)] : 0.0;
+        if (ci == 6) a = -a;
+        double delta[6];
+        int status = REG_ST_RUNNING;
+        if (inliers < J.min_inliers || !warp_chol_solve6(a, lane, delta)) {
+            status = REG_ST_DEGENERATE;
         } else {
-            se3_left_update(delta, st->T);
-            pose_to_float(st);
-            const double dw2 = delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2];
-            const double dv2 = delta[3] * delta[3] + delta[4] * delta[4] + delta[5] * delta[5];
-            if (dw2 < J.tol_rot * J.tol_rot && dv2 < J.tol_trans * J.tol_trans) st->status = REG_ST_CONVERGED;
-            else if (st->iter >= J.max_iters || st->iter >= 10000) st->status = REG_ST_MAXITER;
+            const double Tn = warp_se3_left_update(delta, st->T, lane);
+            __syncwarp();
+            if (lane < 12) {
+                st->T[lane] = Tn;
+                if ((lane & 3) == 3) st->tf[lane >> 2] = (float)Tn;
+                else st->Rf[3 * (lane >> 2) + (lane & 3)] = (float)Tn;
+            }
+            const double dw2 = fma(delta[0], delta[0], fma(delta[1], delta[1], delta[2] * delta[2]));
+            const double dv2 = fma(delta[3], delta[3], fma(delta[4], delta[4], delta[5] * delta[5]));
+            if (dw2 < J.tol_rot * J.tol_rot && dv2 < J.tol_trans * J.tol_trans) status = REG_ST_CONVERGED;
+            else if (it_now + 1 >= J.max_iters || it_now + 1 >= 10000) status = REG_ST_MAXITER;
             else more = true;
         }
+        if (lane == 0) {
+            st->iter = it_now + 1;
+            if (status != REG_ST_RUNNING) st->status = status;
+        }
     }
-    {
+    if (lane == 0) {
         unsigned long long t_end;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-        const int it = J.mode == REG_MODE_SOLVE ? st->iter - 1 : 0;
-        if (it >= 0 && it < REG_STATS) {
+        const int it = J.mode == REG_MODE_SOLVE ? it_now : 0;
+        if (it < REG_STATS) {
             st->tail_ns[it] = (int)(t_end - t_start);
             st->solve_ns[it] = (int)(t_end - t_solve);
         }
+        __threadfence();
+        if (J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
     }
-    __threadfence();
-    if (J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------------------

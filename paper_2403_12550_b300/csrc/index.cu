@@ -234,11 +234,31 @@ __global__ void bbox_kernel(const float* __restrict__ pts, const int* __restrict
             hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
     }
-    if ((threadIdx.x & 31) == 0) {
+    // one atomic per block and coordinate: same-address atomics from every warp serialise in L2
+    __shared__ float slo[3][32], shi[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { slo[a][warp] = lo[a]; shi[a][warp] = hi[a]; }
+    }
+    __syncthreads();
+    if (warp == 0) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            atomicMin(&bb[a], f2ord(lo[a]));
-            atomicMax(&bb[3 + a], f2ord(hi[a]));
+            lo[a] = lane < nw ? slo[a][lane] : GSICP_INF;
+            hi[a] = lane < nw ? shi[a][lane] : -GSICP_INF;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(&bb[a], f2ord(lo[a]));
+                atomicMax(&bb[3 + a], f2ord(hi[a]));
+            }
         }
     }
 }
@@ -435,7 +455,8 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
     const int grid = std::max(1, std::min((cap + 255) / 256, sms * 8));
     GSICP_CHECK(out.quant.ensure(sizeof(float4)));
     bbox_init_kernel<<<1, 32, 0, s>>>(scr.bbox.as<uint32_t>());
-    bbox_kernel<<<grid, 256, 0, s>>>(pts, n_dev, scr.bbox.as<uint32_t>());
+    bbox_kernel<<<std::max(1, std::min((cap + 255) / 256, sms * 2)), 256, 0, s>>>(pts, n_dev,
+                                                                                 scr.bbox.as<uint32_t>());
     quant_kernel<<<1, 1, 0, s>>>(scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>());
     morton_kernel<<<grid, 256, 0, s>>>(pts, n_dev, cap, out.quant.as<float4>(), scr.k0.as<uint32_t>(),
                                        scr.v0.as<uint32_t>());
