@@ -42,13 +42,22 @@ BYTES_PER_POINT_COV = 40       # read x 12 + z 4, write C 24
 BYTES_PER_MAP_GAUSSIAN = 84 + 48  # read mean 12 + cov 24 (x2: bbox/morton and gather) + write 16 + 32
 REGSTATE_BYTES = 544 + 4       # pose/H/b/cost/iters/status record + point count read back per frame
 L2_FLUSH_BYTES = 256 << 20
+# kernels launched per timed step (counted from the ncu launch list of this workload):
+LAUNCHES_MAP_REBUILD = 33  # count reset 1, bbox 2, quantise 1, Morton keys 1, 4 radix passes x 5, gather 1,
+                           # leaf boxes 1, box levels 3, grid insert/end 2, seed table 1
+LAUNCHES_FRAME = 36        # a1 5 (count, 3 scan, write), source index 28, k-NN covariances 1, GN seed 1,
+                           # GN set-up 1; plus one Gauss-Newton launch per iteration
+# DRAM bytes per gicp_iter_kernel launch (read + write, mean over the iterations of one frame of this
+# workload, ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the CUDA sources whose
+# SHA-256 is given; reported as null once any of them has changed.
+GN_TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -103,6 +112,35 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def sources_sha256() -> str:
+    """SHA-256 over the CUDA sources of the library (names and contents, sorted by name)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2403_12550_b300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    glob.glob(os.path.join(csrc, "*.h"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest of every rank's x (the job's time is its slowest replica's); x itself at N=1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, total_s: float) -> float:
+    """Whole-job frames/s: every rank tracks `steps` frames of its own replica in `total_s` (the max)."""
+    return world * steps / total_s
 
 
 def dist_setup(args):
@@ -189,11 +227,7 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     step_ms = [a.elapsed_time(c) for a, _, c in ev]
     index_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, "cuda")
     g.gsicp_ctx_set_timing(ctx, False)
 
     # ---- end-to-end through the host-buffer entry point (H2D depth + D2H results inside)
@@ -208,11 +242,7 @@ def run_ours(args, world, rank, local):
         if i > 0:
             e2e_ms.append((t1 - t0) * 1e3)
     assert np.array_equal(rh["T"], r["T"])
-    e2e_s = sum(e2e_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, world, "cuda")
 
     # ---- roofline of the dominant kernel, from the event-timed phases of the timed steps
     keys = ("depth_to_points", "source_index", "knn_cov", "gauss_newton")
@@ -233,15 +263,13 @@ def run_ours(args, world, rank, local):
         per_launch_ms, alg, kname = ph["source_index"], npts * 64, "source index build"
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get(kname)
-    # launches of our kernels per frame: a1 (5), source index (27), k-NN cov (1), GN set-up (1) + 1 per
-    # iteration; map index rebuild: 1 set + 28
-    launches = int(sum(5 + 27 + 1 + 1 + it for it in iters) + args.steps * 29)
+    if kname == "gicp_iter_kernel" and GN_TRAFFIC["bytes_per_launch"] and \
+            GN_TRAFFIC["sources_sha256"] == sources_sha256():
+        traffic = GN_TRAFFIC["bytes_per_launch"]
+    launches = int(sum(LAUNCHES_MAP_REBUILD + LAUNCHES_FRAME + it for it in iters))
     K = args.steps
     out = {
-        "metric": METRIC, "value": world * K / total_s, "unit": "frames/s", "n_gpus": world, "steps": K,
+        "metric": METRIC, "value": job_throughput(world, K, total_s), "unit": "frames/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_points": int(npts), "map_gaussians": int(n_map), "k": K_NN,
@@ -254,7 +282,7 @@ def run_ours(args, world, rank, local):
         "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": int(alg), "avg_launch_ms": per_launch_ms},
-        "e2e": {"value": world * K / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(f["depth"].nbytes),
+        "e2e": {"value": job_throughput(world, K, e2e_s), "unit": "frames/s", "h2d_bytes_per_step": int(f["depth"].nbytes),
                 "d2h_bytes_per_step": REGSTATE_BYTES},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -302,15 +330,21 @@ def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-def cpu_baseline(f, seed):
+def cpu_baseline(f, seed, budget_s: float = 10.0):
+    """The oracle on this host's cores: whole frames of the same workload, repeated until about
+    ``budget_s`` seconds have passed (at least one)."""
     omap = oracle_setup(f)
-    t0 = time.perf_counter()
-    r = oracle_frame(f, omap)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"one full frame (a1 + k-NN covariances of ~204k points + {r['iters']} GN iterations "
-                      f"against the 2.04M-Gaussian map), FP64 C oracle with OpenMP over points; "
-                      f"map construction untimed"}
+    frames, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle_frame(f, omap)
+        frames += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"value": frames / dt, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"{frames} full frames in {dt:.1f} s (each: a1 + k-NN covariances of ~204k points + "
+                      f"{r['iters']} GN iterations against the 2.04M-Gaussian map), FP64 C oracle with "
+                      f"OpenMP over points; map construction untimed"}
 
 
 def run_reference(args, world, rank):

@@ -208,6 +208,14 @@ __device__ __forceinline__ void df_add(dfloat& a, float x)
     a.lo = __fadd_rn(a.lo, err);
 }
 
+// s + e == a + b exactly (s the rounded sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 // a += (bhi + blo)
 __device__ __forceinline__ void df_merge(dfloat& a, float bhi, float blo)
 {
@@ -235,6 +243,7 @@ struct RegState {
     double cost;
     long long inliers;
     float Rf[9], tf[3];  // float copy of the current pose for the per-point work
+    float Rlo[9], tlo[3];  // remainders: Rf + Rlo and tf + tlo carry the pose to ~48 bits
     int iter;          // completed iterations
     int status;        // REG_ST_*
     unsigned int counter;  // blocks finished in the current iteration

@@ -181,9 +181,33 @@ __device__ double warp_se3_left_update(const double xi[6], const double* T, int 
 __device__ __forceinline__ void pose_to_float(RegState* st)
 {
     for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) st->Rf[3 * r + c] = (float)st->T[4 * r + c];
-        st->tf[r] = (float)st->T[4 * r + 3];
+        for (int c = 0; c < 3; ++c) {
+            const double v = st->T[4 * r + c];
+            st->Rf[3 * r + c] = (float)v;
+            st->Rlo[3 * r + c] = (float)(v - (double)(float)v);
+        }
+        const double v = st->T[4 * r + 3];
+        st->tf[r] = (float)v;
+        st->tlo[r] = (float)(v - (double)(float)v);
     }
+}
+
+// One coordinate of y = R x + t with R, t given as float pairs (hi + lo): the products of the
+// hi parts are split exactly (fmaf), their sum is carried with its rounding errors (two_sum),
+// and the lo parts and the errors are added in float.  Returns y as hi + lo, accurate to about
+// 1e-13 relative, so that distances and residuals taken as (p - hi) - lo match the FP64 ones.
+__device__ __forceinline__ void transform_df(const float* Rh, const float* Rl, float th, float tl, float x0,
+                                             float x1, float x2, float& hi, float& lo)
+{
+    const float p0 = __fmul_rn(Rh[0], x0), p1 = __fmul_rn(Rh[1], x1), p2 = __fmul_rn(Rh[2], x2);
+    const float e0 = fmaf(Rh[0], x0, -p0), e1 = fmaf(Rh[1], x1, -p1), e2 = fmaf(Rh[2], x2, -p2);
+    float s, c0, c1, c2;
+    two_sum(th, p0, s, c0);
+    two_sum(s, p1, s, c1);
+    two_sum(s, p2, s, c2);
+    const float low = fmaf(Rl[0], x0, fmaf(Rl[1], x1, fmaf(Rl[2], x2, tl))) + ((e0 + e1) + (e2 + c0)) + (c1 + c2);
+    hi = __fadd_rn(s, low);
+    lo = __fsub_rn(low, __fsub_rn(hi, s));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -225,11 +249,17 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
         atomicMin(&st->t_first[it_now], t0);
     }
-    float R[9], t[3];
+    float R[9], t[3], Rl[9], tl[3];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) R[a] = st->Rf[a];
+    for (int a = 0; a < 9; ++a) {
+        R[a] = st->Rf[a];
+        Rl[a] = st->Rlo[a];
+    }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) t[a] = st->tf[a];
+    for (int a = 0; a < 3; ++a) {
+        t[a] = st->tf[a];
+        tl[a] = st->tlo[a];
+    }
     float acc[NACC];
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
@@ -246,9 +276,17 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         const int s = blockIdx.x * blockDim.x + threadIdx.x;
         if (s >= n) break;
         const float4 x = J.src[s];
-        const float y0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t[0])));
-        const float y1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t[1])));
-        const float y2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t[2])));
+        // y = R x + t as hi + lo: the searches run on hi; the final choice among the candidates
+        // they return, the inlier test and the residual use hi + lo (distance differences at the
+        // level of float rounding of y would otherwise flip near-equidistant correspondences)
+        float y0, y1, y2, l0, l1, l2;
+        transform_df(R, Rl, t[0], tl[0], x.x, x.y, x.z, y0, l0);
+        transform_df(R + 3, Rl + 3, t[1], tl[1], x.x, x.y, x.z, y1, l1);
+        transform_df(R + 6, Rl + 6, t[2], tl[2], x.x, x.y, x.z, y2, l2);
+        auto exact_d2 = [&](const float4& p) {
+            return sq3(__fsub_rn(__fsub_rn(p.x, y0), l0), __fsub_rn(__fsub_rn(p.y, y1), l1),
+                       __fsub_rn(__fsub_rn(p.z, y2), l2));
+        };
         const int4 ca4 = reinterpret_cast<const int4*>(J.cand)[2l * s];
         const int4 cb4 = reinterpret_cast<const int4*>(J.cand)[2l * s + 1];
         const int cp[KC] = {ca4.x, ca4.y, ca4.z, ca4.w, cb4.x, cb4.y, cb4.z, cb4.w};
@@ -259,6 +297,8 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         if (anc.w > 0.f) {
             // Cached candidates were complete within radius anc.w of the anchor; the query has
             // moved by delta, so every map point outside them is at least anc.w - delta away.
+            float e_d2 = J.max_d2;
+            int e_oi = 0x7fffffff, e_pos = -1;
 #pragma unroll
             for (int j = 0; j < KC; ++j) {
                 if (cp[j] < 0) continue;
@@ -270,12 +310,23 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                     best_oi = oi;
                     best_pos = cp[j];
                 }
+                const float ed2 = exact_d2(p);
+                if (before(ed2, oi, e_d2, e_oi)) {
+                    e_d2 = ed2;
+                    e_oi = oi;
+                    e_pos = cp[j];
+                }
             }
             const float delta = sqrtf(sq3(y0 - anc.x, y1 - anc.y, y2 - anc.z)) + 2e-6f;
             const float bnd = best_pos >= 0 ? sqrtf(best_d2) : max_d;
             // margins (1e-5 relative, 2e-6 m) exceed float rounding of the distances, so the
-            // cached answer is the one the full search would return
+            // nearest point is among the cached ones (by either distance)
             resolved = anc.w - delta >= bnd * (1.f + 1e-5f);
+            if (resolved) {
+                best_d2 = e_d2;
+                best_oi = e_oi;
+                best_pos = e_pos;
+            }
         }
         if (!resolved) {
             refreshed = 1;
@@ -371,10 +422,21 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
                 reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
                 reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
                 J.anchor[s] = make_float4(y0, y1, y2, rc);
-                if (key_idx(Lk[0]) != 0x7fffffff && key_d2(Lk[0]) <= J.max_d2) {
-                    best_d2 = key_d2(Lk[0]);
-                    best_oi = key_idx(Lk[0]);
-                    best_pos = P[0];
+                // the nearest by hi + lo among the list
+                best_d2 = J.max_d2;
+                best_oi = 0x7fffffff;
+                best_pos = -1;
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    if (P[j] < 0) continue;
+                    const float4 p = J.map.pts[P[j]];
+                    const float ed2 = exact_d2(p);
+                    const int oi = __float_as_int(p.w);
+                    if (before(ed2, oi, best_d2, best_oi)) {
+                        best_d2 = ed2;
+                        best_oi = oi;
+                        best_pos = P[j];
+                    }
                 }
             }
         }
@@ -407,7 +469,8 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         const float W11 = (s00 * s22 - s02 * s02) * id, W12 = (s01 * s02 - s00 * s12) * id;
         const float W22 = (s00 * s11 - s01 * s01) * id;
         const float W[9] = {W00, W01, W02, W01, W11, W12, W02, W12, W22};
-        const float d0 = mu.x - y0, d1 = mu.y - y1, d2 = mu.z - y2;
+        const float d0 = __fsub_rn(__fsub_rn(mu.x, y0), l0), d1 = __fsub_rn(__fsub_rn(mu.y, y1), l1),
+                    d2 = __fsub_rn(__fsub_rn(mu.z, y2), l2);
         const float Wd0 = W00 * d0 + W01 * d1 + W02 * d2;
         const float Wd1 = W01 * d0 + W11 * d1 + W12 * d2;
         const float Wd2 = W02 * d0 + W12 * d1 + W22 * d2;
@@ -572,8 +635,14 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
             __syncwarp();
             if (lane < 12) {
                 st->T[lane] = Tn;
-                if ((lane & 3) == 3) st->tf[lane >> 2] = (float)Tn;
-                else st->Rf[3 * (lane >> 2) + (lane & 3)] = (float)Tn;
+                const float hi = (float)Tn, lo = (float)(Tn - (double)hi);
+                if ((lane & 3) == 3) {
+                    st->tf[lane >> 2] = hi;
+                    st->tlo[lane >> 2] = lo;
+                } else {
+                    st->Rf[3 * (lane >> 2) + (lane & 3)] = hi;
+                    st->Rlo[3 * (lane >> 2) + (lane & 3)] = lo;
+                }
             }
             const double dw2 = fma(delta[0], delta[0], fma(delta[1], delta[1], delta[2] * delta[2]));
             const double dv2 = fma(delta[3], delta[3], fma(delta[4], delta[4], delta[5] * delta[5]));

@@ -28,7 +28,7 @@ __all__ = [
     "Scene", "make_room", "sample_surface", "raycast_depth", "add_depth_noise",
     "look_pose", "circle_poses", "random_offset", "rot_axis_angle", "inv_pose", "make_pose",
     "transform_points", "Intrinsics", "REPLICA_INTR", "TUM_INTR",
-    "pair_config1", "frame_config2", "spline_trajectory",
+    "pair_config1", "frame_config2", "spline_trajectory", "sequence_config3", "const_velocity",
 ]
 
 
@@ -352,5 +352,39 @@ def spline_trajectory(seed: int, scene: Scene, n_frames: int = 500, fps: float =
         v = np.linalg.norm(sp_p(u, 1))
         w = abs(float(sp_y(u, 1)))
         du = min(vmax * dt / max(v, 1e-9), np.deg2rad(wmax_deg) * dt / max(w, 1e-9), 0.05)
+        # the rates change along the step: shrink it until the step itself keeps both caps
+        while du > 1e-9 and (np.linalg.norm(sp_p(min(u + du, n_knots - 1.0)) - sp_p(u)) > vmax * dt or
+                             abs(float(sp_y(min(u + du, n_knots - 1.0)) - sp_y(u))) > np.deg2rad(wmax_deg) * dt):
+            du *= 0.9
         u = min(u + du, n_knots - 1.0)
     return poses
+
+
+def sequence_config3(seed: int, n_frames: int = 500, intr: Intrinsics = TUM_INTR, noise_coeff: float = 1e-3):
+    """TUM-shaped tracking sequence: a 6 x 5 x 3 m room with boxes and spheres,
+    ``n_frames`` poses at 30 Hz along :func:`spline_trajectory` (<= 1 m/s,
+    <= 60 deg/s), and ``depth(f)``, the noisy 640x480 depth image of frame f
+    (ray-cast on demand; its noise is seeded by (seed, f)).
+
+    Returns a dict with keys ``scene, intr, poses, depth``."""
+    scene = make_room(seed + 100, size=(6.0, 5.0, 3.0))
+    poses = spline_trajectory(seed, scene, n_frames=n_frames)
+
+    def depth(f: int) -> np.ndarray:
+        rng = np.random.default_rng(7_000_001 * (seed + 1) + f)
+        return add_depth_noise(raycast_depth(scene, poses[f], intr), rng, noise_coeff)
+
+    return dict(scene=scene, intr=intr, poses=poses, depth=depth)
+
+
+def const_velocity(T_prev: np.ndarray, T_prev2: np.ndarray | None) -> np.ndarray:
+    """Constant-velocity prediction of the next pose from the last two: the
+    relative motion T_prev2^-1 T_prev applied once more (T_prev alone when
+    there is no earlier pose)."""
+    if T_prev2 is None:
+        return T_prev.copy()
+    T = T_prev @ (inv_pose(T_prev2) @ T_prev)
+    # nearest rotation (polar factor): products of estimated poses drift off orthonormal
+    U, _, Vt = np.linalg.svd(T[:3, :3])
+    T[:3, :3] = U @ Vt
+    return T

@@ -16,7 +16,11 @@ PLANE_GAP_EXCLUDE = 1e-3
 
 
 def rot_angle(R: np.ndarray) -> float:
-    return float(np.arccos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)))
+    """Rotation angle of R from both its antisymmetric part (sin) and its trace (cos): unlike
+    arccos of the trace alone, a common scale error of nearly orthonormal inputs (1 + e) does not
+    read as an angle of sqrt(6 e)."""
+    w = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]])
+    return float(np.arctan2(0.5 * np.linalg.norm(w), 0.5 * (np.trace(R) - 1.0)))
 
 
 def pose_diff(Ta: np.ndarray, Tb: np.ndarray):

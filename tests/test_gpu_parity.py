@@ -9,7 +9,7 @@ import pytest
 
 import oracle as orc
 from synth import (Intrinsics, REPLICA_INTR, add_depth_noise, frame_config2, make_room, random_offset, raycast_depth,
-                   circle_poses, transform_points)
+                   circle_poses, const_velocity, sequence_config3, transform_points)
 
 from ._util import (COV_REL_TOL, KNN_TIE_REL, PLANE_GAP_EXCLUDE, POSE_ROT_TOL, POSE_TRANS_TOL, config1_inputs,
                     config2_inputs, cov_rel_err, oracle_frame_points, pose_diff, sym)
@@ -416,3 +416,81 @@ def test_track_frame_empty_depth(g, ctx):
     r = g.gsicp_track_frame(ctx, cu(d), [60, 60, 59.5, 33.5], 2, 0.1, 10.0, g.CovParams(), m, np.eye(4),
                             g.RegParams())
     assert r["status"] == g.ERR_DEGENERATE and r["n_points"] == 0
+
+
+# ----------------------------------------------------------------------------- TUM-shaped sequence
+
+def test_sequence_config3_matches_oracle(g, ctx):
+    """640x480 sequence at 30 Hz (stride 2, ~77k points per frame), keyframes every 10th frame
+    appended to the map.  Per frame, the GPU registers against a map holding the oracle's
+    Gaussians from the oracle's start pose and must land on the oracle's pose; an independent
+    GPU run (its own keyframes, its own constant-velocity starts) must track as well as the
+    oracle's run (ATE against the ground truth)."""
+    F = 21
+    seq = sequence_config3(0, n_frames=F)
+    io = seq["intr"]
+    intr = io.as_array()
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    depths = [seq["depth"](f) for f in range(F)]
+
+    def ate(est):
+        return float(np.sqrt(np.mean([np.sum((est[f][:3, 3] - seq["poses"][f][:3, 3]) ** 2) for f in range(F)])))
+
+    # oracle run; the GPU is checked frame by frame against it
+    om_means, om_covs, omap, gm = [], [], None, None
+    est_o, worst = [], (0.0, 0.0)
+    for f in range(F):
+        pts, z = oracle_frame_points(depths[f], io)
+        cs = orc.source_covariances(pts, z, k=20, eps=1e-3, reg_mode=orc.PLANE, p=1.5)["covs"]
+        if f == 0:
+            To = seq["poses"][0].copy()
+        else:
+            T0 = const_velocity(est_o[-1], est_o[-2] if f >= 2 else None)
+            ro = orc.register(pts, cs, omap, T0, 0.1, 30, 1e-6, 1e-6, 6)
+            r = g.gsicp_track_frame(ctx, cu(depths[f]), intr, 2, 0.1, 10.0, cp, gm, T0, rp)
+            assert ro["status"] == orc.OK and r["status"] == g.OK, (f, ro["status"], r["status"])
+            assert r["n_points"] == len(pts)
+            dr, dt = pose_diff(r["T"], ro["T"])
+            worst = (max(worst[0], dr), max(worst[1], dt))
+            assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (f, dr, dt, r["iters"], ro["iters"])
+            To = ro["T"]
+        est_o.append(To)
+        if f % 10 == 0:
+            mw, cw = orc.transform_gaussians(To, pts, cs)
+            mw, cw = mw.astype(np.float32), cw.astype(np.float32)
+            om_means.append(mw)
+            om_covs.append(cw)
+            omap = orc.Map(np.concatenate(om_means), np.concatenate(om_covs))
+            if gm is None:
+                gm = g.gsicp_build_map_index(ctx, cu(mw), cu(cw))
+            else:
+                g.gsicp_map_append(ctx, gm, cu(mw), cu(cw))
+    assert gm.size == sum(len(a) for a in om_means)
+    gm.close()
+
+    # independent GPU run
+    est_g, m = [], None
+    for f in range(F):
+        d = cu(depths[f])
+        if f == 0:
+            T = seq["poses"][0].copy()
+        else:
+            T0 = const_velocity(est_g[-1], est_g[-2] if f >= 2 else None)
+            r = g.gsicp_track_frame(ctx, d, intr, 2, 0.1, 10.0, cp, m, T0, rp)
+            assert r["status"] == g.OK
+            T = r["T"]
+        est_g.append(T)
+        if f % 10 == 0:
+            pts, z = g.gsicp_depth_to_points(ctx, d, intr, 2, 0.1, 10.0)
+            pts, z = pts.clone(), z.clone()
+            c = g.gsicp_source_covariances(ctx, pts, z, cp)
+            mw, cw = g.gsicp_transform_gaussians(T, pts, c)
+            if m is None:
+                m = g.gsicp_build_map_index(ctx, mw, cw)
+            else:
+                g.gsicp_map_append(ctx, m, mw, cw)
+    m.close()
+    ate_o, ate_g = ate(est_o), ate(est_g)
+    assert ate_o < 0.01 and ate_g < 0.01, (ate_o, ate_g)
+    assert abs(ate_g - ate_o) < 10 * POSE_TRANS_TOL, (ate_g, ate_o, worst)
