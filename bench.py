@@ -45,8 +45,9 @@ L2_FLUSH_BYTES = 256 << 20
 # kernels launched per timed step (counted from the ncu launch list of this workload):
 LAUNCHES_MAP_REBUILD = 33  # count reset 1, bbox 2, quantise 1, Morton keys 1, 4 radix passes x 5, gather 1,
                            # leaf boxes 1, box levels 3, grid insert/end 2, seed table 1
-LAUNCHES_FRAME = 36        # a1 5 (count, 3 scan, write), source index 28, k-NN covariances 1, GN seed 1,
-                           # GN set-up 1; plus one Gauss-Newton launch per iteration
+LAUNCHES_FRAME = 39        # a1 5 (count, 3 scan, write), source index 28, k-NN covariances 4 (9x9 window,
+                           # 25x25 window, tree, reorder), GN seed 1, GN set-up 1; plus one Gauss-Newton
+                           # launch per iteration
 # DRAM bytes per gicp_iter_kernel launch (read + write, mean over the iterations of one frame of this
 # workload, ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the CUDA sources whose
 # SHA-256 is given; reported as null once any of them has changed.

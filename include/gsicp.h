@@ -105,6 +105,12 @@ const char* gsicp_version(void);
 gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable);
 gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6]);
 
+/* Telemetry of the last frame whose covariances this context computed (gsicp_frame_covariances,
+ * gsicp_track_frame*): out[0] the number of points the 9 x 9 window did not certify (searched in
+ * the 25 x 25 window), out[1] those that window did not certify either (searched in the tree).
+ * Synchronises the device. */
+gsicp_status gsicp_ctx_frame_stats(gsicp_ctx ctx, int64_t out[2]);
+
 /* Telemetry of the last registration on this context (gsicp_register, gsicp_track_frame*): for
  * each of the first min(n, 64) Gauss-Newton iterations, the number of source points whose cached
  * map candidates had to be searched again (refreshes_out), the device time in ns from the first
@@ -166,6 +172,21 @@ gsicp_status gsicp_depth_to_points_noalloc(const float* depth_dev, int W, int H,
 gsicp_status gsicp_source_covariances(gsicp_ctx ctx, const float* pts_dev, const float* z_dev,
                                       int64_t n, const gsicp_cov_params* params, float* covs_dev,
                                       int32_t* knn_dev, void* stream);
+
+/* a1 + a2 + a3 of one depth frame in one call (Sec. 3, Fig. 2; Sec. 3.1; Sec. 3.2): the frame's
+ * points exactly as gsicp_depth_to_points writes them (row-major, pts_dev cap x 3, z_dev cap,
+ * nullable) and their Gaussians exactly as gsicp_source_covariances of those points would give
+ * them (covs_dev cap x 6, same order, same neighbour sets and ties).  The k-NN search uses the
+ * image: for the point of sample (i, j) it takes the k nearest among the 9 x 9 samples around it,
+ * and that answer is exact when the k-th is nearer than the four planes through the camera
+ * centre that bound the samples outside the window; the other points are searched in a tree.
+ * *n_out (host) receives the number of points after a stream synchronisation; more than cap
+ * points give GSICP_ERR_CAPACITY with the first cap written (points, depths and covariances of
+ * the whole frame are computed, the covariances use all of them). */
+gsicp_status gsicp_frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H,
+                                     const float intr[4], int stride, float z_min, float z_max,
+                                     const gsicp_cov_params* params, float* pts_dev, float* z_dev,
+                                     float* covs_dev, int64_t cap, int64_t* n_out, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
  * a4  Map index   (target Gaussians G^t = {X^t, C^t}, Sec. 3)

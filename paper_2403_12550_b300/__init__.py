@@ -18,8 +18,9 @@ import torch
 __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
-    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
-    "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_build_map_index", "gsicp_map_append",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
+    "gsicp_build_map_index", "gsicp_map_append",
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
 ]
@@ -85,11 +86,14 @@ _sig("gsicp_version", C.c_char_p, [])
 _sig("gsicp_ctx_set_timing", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
 _sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
+_sig("gsicp_ctx_frame_stats", C.c_int, [_vp, _i64p])
 _sig("gsicp_depth_to_points", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, _vp, _vp,
                                         C.c_int64, _vp, _i64p, _vp])
 _sig("gsicp_depth_to_points_noalloc", C.c_int, [_vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, _vp,
                                                 _vp, C.c_int64, _vp, _vp, _vp])
 _sig("gsicp_source_covariances", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(CovParams), _vp, _vp, _vp])
+_sig("gsicp_frame_covariances", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float,
+                                          C.POINTER(CovParams), _vp, _vp, _vp, C.c_int64, _i64p, _vp])
 _sig("gsicp_build_map_index", C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(IndexParams), _vp,
                                         C.POINTER(C.c_void_p)])
 _sig("gsicp_map_append", C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp])
@@ -217,6 +221,14 @@ def gsicp_ctx_reg_stats(ctx: Context, n: int = 64) -> dict:
     return dict(refreshes=list(rf), tail_ns=list(tl), solve_ns=list(sv), main_ns=list(mn))
 
 
+def gsicp_ctx_frame_stats(ctx: Context) -> dict:
+    """Telemetry of the last frame's covariances: points the 9 x 9 window left to the 25 x 25 one,
+    and those left to the tree search."""
+    v = (C.c_int64 * 2)()
+    _check(lib.gsicp_ctx_frame_stats(ctx.ptr, v), "gsicp_ctx_frame_stats")
+    return dict(wide_window_queries=v[0], tree_queries=v[1])
+
+
 def gsicp_depth_to_points(ctx: Context, depth: torch.Tensor, intr, stride: int, z_min: float, z_max: float,
                           pts_out: torch.Tensor | None = None, z_out: torch.Tensor | None = None):
     """a1.  Returns ``(pts[:n], z[:n])`` (views of the output buffers)."""
@@ -259,6 +271,22 @@ def gsicp_source_covariances(ctx: Context, pts: torch.Tensor, z: torch.Tensor | 
                                         _dev(covs_out, cols=6), _dev(knn, torch.int32), _stream()),
            "gsicp_source_covariances")
     return (covs_out, knn) if want_knn else covs_out
+
+
+def gsicp_frame_covariances(ctx: Context, depth: torch.Tensor, intr, stride: int, z_min: float, z_max: float,
+                            params: CovParams):
+    """a1 + a2 + a3 of one depth frame.  Returns ``(pts[:n], z[:n], covs[:n])``."""
+    H, W = depth.shape
+    cap = ((W + stride - 1) // stride) * ((H + stride - 1) // stride)
+    pts = torch.empty((cap, 3), device=depth.device, dtype=torch.float32)
+    z = torch.empty((cap,), device=depth.device, dtype=torch.float32)
+    covs = torch.empty((cap, 6), device=depth.device, dtype=torch.float32)
+    fi = (C.c_float * 4)(*[float(v) for v in intr])
+    n = C.c_int64(0)
+    _check(lib.gsicp_frame_covariances(ctx.ptr, _dev(depth), W, H, fi, stride, z_min, z_max, C.byref(params),
+                                       _dev(pts, cols=3), _dev(z), _dev(covs, cols=6), cap, C.byref(n), _stream()),
+           "gsicp_frame_covariances")
+    return pts[:n.value], z[:n.value], covs[:n.value]
 
 
 def gsicp_build_map_index(ctx: Context, means: torch.Tensor, covs: torch.Tensor, bucket: int = 0,

@@ -201,6 +201,7 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     ctx->src_index.quant.release();
     ctx->a1_counts.release(); ctx->a1_sums.release(); ctx->n_dev.release(); ctx->total_dev.release();
     ctx->frame_pts.release(); ctx->frame_z.release(); ctx->frame_covs.release(); ctx->frame_depth.release();
+    ctx->frame_idx.release(); ctx->fb_list.release(); ctx->fb_count.release();
     ctx->covs_sorted.release();
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t& e : ctx->ev)
@@ -221,6 +222,16 @@ gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6])
 {
     if (!ctx || !out) return GSICP_ERR_INVALID_ARG;
     for (int i = 0; i < 6; ++i) out[i] = ctx->phase_ms[i];
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_frame_stats(gsicp_ctx ctx, int64_t out[2])
+{
+    if (!ctx || !out) return GSICP_ERR_INVALID_ARG;
+    int v[2] = {0, 0};
+    if (ctx->fb_count.ptr) GSICP_CUDA(cudaMemcpy(v, ctx->fb_count.ptr, sizeof(v), cudaMemcpyDeviceToHost));
+    out[0] = v[0];
+    out[1] = v[1];
     return GSICP_OK;
 }
 
@@ -441,6 +452,66 @@ gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* querie
                           (cudaStream_t)stream);
 }
 
+// a1 -> source index -> a2+a3 for one depth frame, into the context's frame buffers (points in
+// row-major order, their covariances in the same order and in the source index's order).
+static gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
+                                      int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
+                                      int cap, cudaStream_t s)
+{
+    const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
+    GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)cap));
+    GSICP_CHECK(ctx->frame_z.ensure(sizeof(float) * (size_t)cap));
+    GSICP_CHECK(ctx->frame_covs.ensure(sizeof(float) * 6 * (size_t)cap));
+    GSICP_CHECK(ctx->frame_idx.ensure(sizeof(int) * (size_t)cap));
+    GSICP_CHECK(ctx->fb_list.ensure(sizeof(int) * 4 * (size_t)cap));
+    GSICP_CHECK(ctx->fb_count.ensure(sizeof(int) * 2));
+    GSICP_CHECK(ctx->covs_sorted.ensure(sizeof(float4) * 2 * (size_t)cap));
+    int* nd = ctx->n_dev.as<int>();
+    const bool tm = ctx->timing;
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[0], s));
+    GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, ctx->frame_pts.as<float>(),
+                                       ctx->frame_z.as<float>(), cap, nd, ctx->total_dev.as<int>(), ctx->a1_counts,
+                                       ctx->a1_sums, s, ctx->frame_idx.as<int>()));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
+    GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
+    GSICP_CHECK(launch_frame_knn_cov(ctx->src_index.view(), ctx->frame_idx.as<int>(), Ws, Hs, stride, intr,
+                                     ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap, *cov_params,
+                                     ctx->frame_covs.as<float>(), nullptr, ctx->fb_list.as<int>(),
+                                     ctx->fb_count.as<int>(), s));
+    GSICP_CHECK(launch_permute_covs(ctx->src_index.view(), ctx->frame_covs.as<float>(), cap,
+                                    ctx->covs_sorted.as<float4>(), s));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], s));
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
+                                     int stride, float z_min, float z_max, const gsicp_cov_params* params,
+                                     float* pts_dev, float* z_dev, float* covs_dev, int64_t cap, int64_t* n_out,
+                                     void* stream)
+{
+    if (!ctx || !depth_dev || !intr || !pts_dev || !covs_dev || !n_out || W <= 0 || H <= 0 || stride <= 0 ||
+        cap < 0 || cap > INT32_MAX || !valid_cov_params(params))
+        return GSICP_ERR_INVALID_ARG;
+    if (!(intr[0] != 0.f) || !(intr[1] != 0.f)) return GSICP_ERR_INVALID_ARG;
+    const int64_t frame_cap = (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride);
+    if (frame_cap > (1 << 30)) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, params, (int)frame_cap, s));
+    int* h = (int*)ctx->host_pinned;
+    GSICP_CUDA(cudaMemcpyAsync(h, ctx->n_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    const int64_t n = h[0];
+    const int64_t m = std::min(n, cap);
+    if (m > 0) {
+        GSICP_CUDA(cudaMemcpyAsync(pts_dev, ctx->frame_pts.ptr, sizeof(float) * 3 * m, cudaMemcpyDeviceToDevice, s));
+        GSICP_CUDA(cudaMemcpyAsync(covs_dev, ctx->frame_covs.ptr, sizeof(float) * 6 * m, cudaMemcpyDeviceToDevice, s));
+        if (z_dev) GSICP_CUDA(cudaMemcpyAsync(z_dev, ctx->frame_z.ptr, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
+    }
+    *n_out = m;
+    return n > cap ? GSICP_ERR_CAPACITY : GSICP_OK;
+}
+
 static gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                      int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
                                      gsicp_map map, const double T0[16], const gsicp_reg_params* reg_params,
@@ -450,22 +521,9 @@ static gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int 
     const int64_t cap64 = (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride);
     if (cap64 > (1 << 30)) return GSICP_ERR_INVALID_ARG;
     const int cap = (int)cap64;
-    GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)cap));
-    GSICP_CHECK(ctx->frame_z.ensure(sizeof(float) * (size_t)cap));
-    GSICP_CHECK(ctx->frame_covs.ensure(sizeof(float) * 6 * (size_t)cap));
     int* nd = ctx->n_dev.as<int>();
     const bool tm = ctx->timing;
-    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[0], s));
-    GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, ctx->frame_pts.as<float>(),
-                                       ctx->frame_z.as<float>(), cap, nd, ctx->total_dev.as<int>(), ctx->a1_counts,
-                                       ctx->a1_sums, s));
-    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
-    GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
-    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
-    GSICP_CHECK(ctx->covs_sorted.ensure(sizeof(float4) * 2 * (size_t)cap));
-    GSICP_CHECK(launch_knn_cov(ctx->src_index.view(), ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap,
-                               *cov_params, ctx->frame_covs.as<float>(), nullptr, ctx->covs_sorted.as<float4>(), s));
-    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], s));
+    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s));
     RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));

@@ -87,6 +87,148 @@ __device__ __forceinline__ void eigh3f(const float C[6], float w[3], float V[3][
     sort_pair<0, 1>(w, V);
 }
 
+// Neighbour access for finish_cov when keys hold original indices.
+struct ByIndex {
+    const float* orig;
+    __device__ float3 operator()(int i) const { return make_float3(orig[3l * i], orig[3l * i + 1], orig[3l * i + 2]); }
+};
+struct SameIndex {
+    __device__ int operator()(int i) const { return i; }
+};
+
+// Covariance of the k neighbours in Lk (ascending keys, phantoms first), its regularisation
+// (Sec. 3.1) and scale aligning (Sec. 3.2), written for the query q (q.w: its original index) to
+// covs (original order), optionally to covs_sorted at position s and its neighbours to knn_out.
+// nb(id) gives the coordinates and oi(id) the original index of the neighbour whose key holds id.
+template <int KMAX, class Nb, class Oi>
+__device__ __forceinline__ void finish_cov(const unsigned long long (&Lk)[KMAX], int k, float4 q, Nb&& nb, Oi&& oi,
+                                           const float* __restrict__ zin, float eps, int mode, float p,
+                                           float* __restrict__ covs, int32_t* __restrict__ knn_out,
+                                           float4* __restrict__ covs_sorted, long s)
+{
+    const int qi = __float_as_int(q.w);
+    int I[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) I[j] = key_idx(Lk[j]);
+    // ---- covariance of the neighbourhood (two-pass, float), neighbours gathered by original index
+    int kk = 0;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j >= KMAX - k && I[j] != 0x7fffffff) {
+            const float3 P = nb(I[j]);
+            m0 += __fsub_rn(P.x, q.x);
+            m1 += __fsub_rn(P.y, q.y);
+            m2 += __fsub_rn(P.z, q.z);
+            ++kk;
+        }
+    }
+    const float inv_k = 1.f / (float)max(kk, 1);
+    m0 *= inv_k; m1 *= inv_k; m2 *= inv_k;
+    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j >= KMAX - k && I[j] != 0x7fffffff) {
+            const float3 P = nb(I[j]);
+            const float e0 = __fsub_rn(P.x, q.x) - m0;
+            const float e1 = __fsub_rn(P.y, q.y) - m1;
+            const float e2 = __fsub_rn(P.z, q.z) - m2;
+            C[0] = fmaf(e0, e0, C[0]); C[1] = fmaf(e0, e1, C[1]); C[2] = fmaf(e0, e2, C[2]);
+            C[3] = fmaf(e1, e1, C[3]); C[4] = fmaf(e1, e2, C[4]); C[5] = fmaf(e2, e2, C[5]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) C[a] *= inv_k;
+    // ---- regularisation (Sec. 3.1)
+    float out[6];
+    if (mode == GSICP_REG_NONE) {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) out[a] = C[a];
+    } else {
+        float w[3], V[3][3];
+        eigh3f(C, w, V);
+        if (kk < 3 || !(w[2] > 0.f) || w[1] <= RANK_TOL * w[2]) {
+            out[0] = 1.f; out[1] = 0.f; out[2] = 0.f; out[3] = 1.f; out[4] = 0.f; out[5] = 1.f;
+        } else if (mode == GSICP_REG_PLANE) {
+            float n0 = V[0][0], n1 = V[1][0], n2 = V[2][0];
+            if (w[1] - w[0] < REFINE_GAP * w[1]) {
+                // near-degenerate normal: one first-order correction of v0 against the
+                // covariance accumulated in double from exact coordinate differences
+                double s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+                for (int j = 0; j < KMAX; ++j) {
+                    if (j >= KMAX - k && I[j] != 0x7fffffff) {
+                        const float3 P = nb(I[j]);
+                        const double e0 = (double)P.x - (double)q.x;
+                        const double e1 = (double)P.y - (double)q.y;
+                        const double e2 = (double)P.z - (double)q.z;
+                        s1[0] += e0; s1[1] += e1; s1[2] += e2;
+                        s2[0] += e0 * e0; s2[1] += e0 * e1; s2[2] += e0 * e2;
+                        s2[3] += e1 * e1; s2[4] += e1 * e2; s2[5] += e2 * e2;
+                    }
+                }
+                const double ik = 1.0 / kk;
+                const double mu0 = s1[0] * ik, mu1 = s1[1] * ik, mu2 = s1[2] * ik;
+                const double Cd[6] = {s2[0] * ik - mu0 * mu0, s2[1] * ik - mu0 * mu1, s2[2] * ik - mu0 * mu2,
+                                      s2[3] * ik - mu1 * mu1, s2[4] * ik - mu1 * mu2, s2[5] * ik - mu2 * mu2};
+                double v[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[r][c] = V[r][c];
+                double u[3];  // Cd v0
+                u[0] = Cd[0] * v[0][0] + Cd[1] * v[1][0] + Cd[2] * v[2][0];
+                u[1] = Cd[1] * v[0][0] + Cd[3] * v[1][0] + Cd[4] * v[2][0];
+                u[2] = Cd[2] * v[0][0] + Cd[4] * v[1][0] + Cd[5] * v[2][0];
+                double x0 = v[0][0], x1 = v[1][0], x2 = v[2][0];
+                const double l0 = x0 * u[0] + x1 * u[1] + x2 * u[2];
+#pragma unroll
+                for (int c = 1; c < 3; ++c) {
+                    const double cc = v[0][c] * u[0] + v[1][c] * u[1] + v[2][c] * u[2];
+                    const double lc = (double)w[c];
+                    const double gap = l0 - lc;
+                    if (fabs(cc) < 0.1 * fabs(gap)) {
+                        const double f = cc / gap;
+                        x0 += f * v[0][c]; x1 += f * v[1][c]; x2 += f * v[2][c];
+                    }
+                }
+                const double nrm = rsqrt(x0 * x0 + x1 * x1 + x2 * x2);
+                n0 = (float)(x0 * nrm); n1 = (float)(x1 * nrm); n2 = (float)(x2 * nrm);
+            }
+            const float a = 1.f - eps;
+            out[0] = 1.f - a * n0 * n0; out[1] = -a * n0 * n1; out[2] = -a * n0 * n2;
+            out[3] = 1.f - a * n1 * n1; out[4] = -a * n1 * n2; out[5] = 1.f - a * n2 * n2;
+        } else {  // ELLIPSE: C / middle eigenvalue, smallest ratio floored at eps
+            const float il = 1.f / w[1];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) out[a] = C[a] * il;
+            const float r0 = w[0] * il;
+            if (r0 < eps) {
+                const float f = eps - r0, n0 = V[0][0], n1 = V[1][0], n2 = V[2][0];
+                out[0] += f * n0 * n0; out[1] += f * n0 * n1; out[2] += f * n0 * n2;
+                out[3] += f * n1 * n1; out[4] += f * n1 * n2; out[5] += f * n2 * n2;
+            }
+        }
+    }
+    // ---- scale aligning (Sec. 3.2)
+    if (p != 0.f) {
+        const float sc = powf(zin[qi], -2.f * p);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) out[a] *= sc;
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) covs[6l * qi + a] = out[a];
+    if (covs_sorted) {
+        covs_sorted[2l * s] = make_float4(out[0], out[1], out[2], out[3]);
+        covs_sorted[2l * s + 1] = make_float4(out[4], out[5], 0.f, 0.f);
+    }
+    if (knn_out) {
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+            if (j >= KMAX - k) knn_out[(long)qi * k + (j - (KMAX - k))] = I[j] == 0x7fffffff ? -1 : oi(I[j]);
+    }
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, const float* __restrict__ orig,
                                                               const float* __restrict__ zin, int k, float eps,
@@ -102,7 +244,6 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
         const int s = base + lane;
         const bool active = s < n;
         const float4 q = active ? ix.pts[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int qi = __float_as_int(q.w);
         // ascending (squared distance, index) keys; phantom entries (key 0) pad the front so the
         // k-th best is always the last slot, empty slots hold (+inf, INT_MAX)
         unsigned long long Lk[KMAX];
@@ -119,9 +260,6 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
             for (int t = beg; t < end; ++t) {
                 const float4 pp = ix.pts[t];  // same address in every lane: one broadcast load
                 if (!active) continue;
-        int I[KMAX];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) I[j] = key_idx(Lk[j]);
                 const float d2 = point_d2(q.x, q.y, q.z, pp);
                 const int oi = __float_as_int(pp.w);
                 const unsigned long long key = dkey(d2, oi);
@@ -136,126 +274,7 @@ __global__ void __launch_bounds__(COV_THREADS) knn_cov_kernel(IndexView ix, cons
             if (lf < own - 1 || lf > own + 1) scan_leaf(lf);
         });
         if (!active) continue;
-        int I[KMAX];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) I[j] = key_idx(Lk[j]);
-        // ---- covariance of the neighbourhood (two-pass, float), neighbours gathered by original index
-        int kk = 0;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            if (j >= KMAX - k && I[j] != 0x7fffffff) {
-                const long b = 3l * I[j];
-                m0 += __fsub_rn(orig[b], q.x);
-                m1 += __fsub_rn(orig[b + 1], q.y);
-                m2 += __fsub_rn(orig[b + 2], q.z);
-                ++kk;
-            }
-        }
-        const float inv_k = 1.f / (float)max(kk, 1);
-        m0 *= inv_k; m1 *= inv_k; m2 *= inv_k;
-        float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            if (j >= KMAX - k && I[j] != 0x7fffffff) {
-                const long b = 3l * I[j];
-                const float e0 = __fsub_rn(orig[b], q.x) - m0;
-                const float e1 = __fsub_rn(orig[b + 1], q.y) - m1;
-                const float e2 = __fsub_rn(orig[b + 2], q.z) - m2;
-                C[0] = fmaf(e0, e0, C[0]); C[1] = fmaf(e0, e1, C[1]); C[2] = fmaf(e0, e2, C[2]);
-                C[3] = fmaf(e1, e1, C[3]); C[4] = fmaf(e1, e2, C[4]); C[5] = fmaf(e2, e2, C[5]);
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 6; ++a) C[a] *= inv_k;
-        // ---- regularisation (Sec. 3.1)
-        float out[6];
-        if (mode == GSICP_REG_NONE) {
-#pragma unroll
-            for (int a = 0; a < 6; ++a) out[a] = C[a];
-        } else {
-            float w[3], V[3][3];
-            eigh3f(C, w, V);
-            if (kk < 3 || !(w[2] > 0.f) || w[1] <= RANK_TOL * w[2]) {
-                out[0] = 1.f; out[1] = 0.f; out[2] = 0.f; out[3] = 1.f; out[4] = 0.f; out[5] = 1.f;
-            } else if (mode == GSICP_REG_PLANE) {
-                float n0 = V[0][0], n1 = V[1][0], n2 = V[2][0];
-                if (w[1] - w[0] < REFINE_GAP * w[1]) {
-                    // near-degenerate normal: one first-order correction of v0 against the
-                    // covariance accumulated in double from exact coordinate differences
-                    double s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-                    for (int j = 0; j < KMAX; ++j) {
-                        if (j >= KMAX - k && I[j] != 0x7fffffff) {
-                            const long b = 3l * I[j];
-                            const double e0 = (double)orig[b] - (double)q.x;
-                            const double e1 = (double)orig[b + 1] - (double)q.y;
-                            const double e2 = (double)orig[b + 2] - (double)q.z;
-                            s1[0] += e0; s1[1] += e1; s1[2] += e2;
-                            s2[0] += e0 * e0; s2[1] += e0 * e1; s2[2] += e0 * e2;
-                            s2[3] += e1 * e1; s2[4] += e1 * e2; s2[5] += e2 * e2;
-                        }
-                    }
-                    const double ik = 1.0 / kk;
-                    const double mu0 = s1[0] * ik, mu1 = s1[1] * ik, mu2 = s1[2] * ik;
-                    const double Cd[6] = {s2[0] * ik - mu0 * mu0, s2[1] * ik - mu0 * mu1, s2[2] * ik - mu0 * mu2,
-                                          s2[3] * ik - mu1 * mu1, s2[4] * ik - mu1 * mu2, s2[5] * ik - mu2 * mu2};
-                    double v[3][3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) v[r][c] = V[r][c];
-                    double u[3];  // Cd v0
-                    u[0] = Cd[0] * v[0][0] + Cd[1] * v[1][0] + Cd[2] * v[2][0];
-                    u[1] = Cd[1] * v[0][0] + Cd[3] * v[1][0] + Cd[4] * v[2][0];
-                    u[2] = Cd[2] * v[0][0] + Cd[4] * v[1][0] + Cd[5] * v[2][0];
-                    double x0 = v[0][0], x1 = v[1][0], x2 = v[2][0];
-                    const double l0 = x0 * u[0] + x1 * u[1] + x2 * u[2];
-#pragma unroll
-                    for (int c = 1; c < 3; ++c) {
-                        const double cc = v[0][c] * u[0] + v[1][c] * u[1] + v[2][c] * u[2];
-                        const double lc = (double)w[c];
-                        const double gap = l0 - lc;
-                        if (fabs(cc) < 0.1 * fabs(gap)) {
-                            const double f = cc / gap;
-                            x0 += f * v[0][c]; x1 += f * v[1][c]; x2 += f * v[2][c];
-                        }
-                    }
-                    const double nrm = rsqrt(x0 * x0 + x1 * x1 + x2 * x2);
-                    n0 = (float)(x0 * nrm); n1 = (float)(x1 * nrm); n2 = (float)(x2 * nrm);
-                }
-                const float a = 1.f - eps;
-                out[0] = 1.f - a * n0 * n0; out[1] = -a * n0 * n1; out[2] = -a * n0 * n2;
-                out[3] = 1.f - a * n1 * n1; out[4] = -a * n1 * n2; out[5] = 1.f - a * n2 * n2;
-            } else {  // ELLIPSE: C / middle eigenvalue, smallest ratio floored at eps
-                const float il = 1.f / w[1];
-#pragma unroll
-                for (int a = 0; a < 6; ++a) out[a] = C[a] * il;
-                const float r0 = w[0] * il;
-                if (r0 < eps) {
-                    const float f = eps - r0, n0 = V[0][0], n1 = V[1][0], n2 = V[2][0];
-                    out[0] += f * n0 * n0; out[1] += f * n0 * n1; out[2] += f * n0 * n2;
-                    out[3] += f * n1 * n1; out[4] += f * n1 * n2; out[5] += f * n2 * n2;
-                }
-            }
-        }
-        // ---- scale aligning (Sec. 3.2)
-        if (p != 0.f) {
-            const float sc = powf(zin[qi], -2.f * p);
-#pragma unroll
-            for (int a = 0; a < 6; ++a) out[a] *= sc;
-        }
-#pragma unroll
-        for (int a = 0; a < 6; ++a) covs[6l * qi + a] = out[a];
-        if (covs_sorted) {
-            covs_sorted[2l * s] = make_float4(out[0], out[1], out[2], out[3]);
-            covs_sorted[2l * s + 1] = make_float4(out[4], out[5], 0.f, 0.f);
-        }
-        if (knn_out) {
-#pragma unroll
-            for (int j = 0; j < KMAX; ++j)
-                if (j >= KMAX - k) knn_out[(long)qi * k + (j - (KMAX - k))] = I[j] == 0x7fffffff ? -1 : I[j];
-        }
+        finish_cov<KMAX>(Lk, k, q, ByIndex{orig}, SameIndex{}, zin, eps, mode, p, covs, knn_out, covs_sorted, s);
     }
 }
 
@@ -279,6 +298,273 @@ gsicp_status launch_knn_cov(const IndexView& ix, const float* orig_pts, const fl
     else
         knn_cov_kernel<32><<<grid, COV_THREADS, 0, s>>>(ix, orig_pts, z, k, prm.eps, prm.reg_mode, prm.p, covs, knn,
                                                          covs_sorted);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Image-window k-NN for the points of one depth frame.
+//
+// The points of a frame come from a pinhole camera: the point of sample (i, j) lies on the ray of
+// pixel (u, v) = (s i, s j), x = (u - cx) z / fx, y = (v - cy) z / fy.  Every point of a sample
+// column >= i + R + 1 therefore lies in the half-space fx x - (U - cx) z >= 0 with
+// U = s (i + R + 1), while the query lies at distance (U - u) z_q / sqrt(fx^2 + (U - cx)^2) on the
+// other side of its plane (through the camera centre); likewise for the other three sides of the
+// (2R+1) x (2R+1) sample window around the query.  So if the k-th nearest point inside the window
+// is closer than the nearest of those four planes (less margins for float rounding of the points
+// and distances), no point outside the window can be among the k nearest, and the window's k
+// nearest are exactly the k nearest of the whole cloud (same float distances and tie order as the
+// tree search).  A 9 x 9 window certifies nearly every point; the rest (grazing surfaces, image
+// borders) get a 25 x 25 window, and what that leaves goes to the tree.
+
+// Radius within which the window of half-width R around sample (i, j) holds every point (+inf
+// when the window reaches every image border), with the float margins applied.
+__device__ __forceinline__ float window_cert(int i, int j, int R, int Ws, int Hs, int stride, float zq, float fx,
+                                             float fy, float cx, float cy)
+{
+    const float u = (float)(stride * i), v = (float)(stride * j);
+    const float gap = (float)(stride * (R + 1));
+    float cert = GSICP_INF;
+    if (i + R + 1 < Ws) cert = fminf(cert, gap * zq * rsqrtf(fx * fx + (u + gap - cx) * (u + gap - cx)));
+    if (i - R - 1 >= 0) cert = fminf(cert, gap * zq * rsqrtf(fx * fx + (u - gap - cx) * (u - gap - cx)));
+    if (j + R + 1 < Hs) cert = fminf(cert, gap * zq * rsqrtf(fy * fy + (v + gap - cy) * (v + gap - cy)));
+    if (j - R - 1 >= 0) cert = fminf(cert, gap * zq * rsqrtf(fy * fy + (v - gap - cy) * (v - gap - cy)));
+    // 1e-4 relative (rsqrtf, float products); 1e-5 m (points rounded to float lie up to
+    // |p| * 6e-8 off their ray)
+    return cert == GSICP_INF ? cert : cert * (1.f - 1e-4f) - 1e-5f;
+}
+
+template <int KMAX>
+__device__ __forceinline__ bool window_certifies(const unsigned long long (&Lk)[KMAX], float cert)
+{
+    return key_idx(Lk[KMAX - 1]) != 0x7fffffff && cert > 0.f &&
+           (cert == GSICP_INF || key_d2(Lk[KMAX - 1]) <= cert * cert);
+}
+
+// One block = 32 x 4 samples; the samples of the block and a halo of R are staged in shared
+// memory as float4 (x, y, z, original index), missing samples as (+inf, .., INT_MAX).  The 5 x 5
+// samples around the query are taken first, so the list is nearly final before the outer ring
+// and few of its points are inserted.  Uncertified queries go to fb_list as (original index,
+// sample index).
+constexpr int WIN_TX = 32, WIN_TY = 4;
+
+template <int KMAX, int R>
+__global__ void __launch_bounds__(WIN_TX * WIN_TY, 6) knn_window_kernel(
+    const int* __restrict__ idx_img, int Ws, int Hs, int stride, float fx, float fy, float cx, float cy,
+    const float* __restrict__ orig, const float* __restrict__ zin, int k, float eps, int mode, float p,
+    float* __restrict__ covs, int32_t* __restrict__ knn_out, int2* __restrict__ fb_list, int* __restrict__ fb_count)
+{
+    static_assert(R >= 2, "the first pass takes the 5 x 5 centre");
+    constexpr int SX = WIN_TX + 2 * R, SY = WIN_TY + 2 * R;
+    __shared__ float4 tile[SY][SX];
+    const int bx = blockIdx.x * WIN_TX - R, by = blockIdx.y * WIN_TY - R;
+    for (int t = threadIdx.x; t < SX * SY; t += WIN_TX * WIN_TY) {
+        const int tx = t % SX, ty = t / SX;
+        const int sx = bx + tx, sy = by + ty;
+        float4 v = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, __int_as_float(0x7fffffff));
+        if (sx >= 0 && sx < Ws && sy >= 0 && sy < Hs) {
+            const int pi = idx_img[(long)sy * Ws + sx];
+            if (pi >= 0) v = make_float4(orig[3l * pi], orig[3l * pi + 1], orig[3l * pi + 2], __int_as_float(pi));
+        }
+        tile[ty][tx] = v;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % WIN_TX, ly = threadIdx.x / WIN_TX;
+    const int i = blockIdx.x * WIN_TX + lx, j = blockIdx.y * WIN_TY + ly;
+    const float4 q = tile[ly + R][lx + R];
+    const bool active = i < Ws && j < Hs && __float_as_int(q.w) != 0x7fffffff;
+    bool certified = false;
+    if (active) {
+        unsigned long long Lk[KMAX];
+        const unsigned long long empty = dkey(GSICP_INF, 0x7fffffff);
+#pragma unroll
+        for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : empty;
+        // keys hold the tile position of the point: tile positions are ordered like the original
+        // (row-major) indices, so ties break exactly as by index, and the neighbours are read
+        // back from shared memory
+        const float4* tl = &tile[0][0];
+        auto visit = [&](int dy, int dx) {
+            const int pos = (ly + R + dy) * SX + (lx + R + dx);
+            const float4 pp = tl[pos];
+            if (__float_as_int(pp.w) == 0x7fffffff) return;  // no point at this sample
+            const unsigned long long key = dkey(point_d2(q.x, q.y, q.z, pp), pos);
+            if (key < Lk[KMAX - 1]) key_insert(Lk, key);
+        };
+        // loops kept rolled: one copy of the insertion code keeps the kernel in the instruction cache
+#pragma unroll 1
+        for (int c = 0; c < 25; ++c) visit(c / 5 - 2, c % 5 - 2);
+#pragma unroll 1
+        for (int dy = -R; dy <= R; ++dy) {
+            const bool mid = dy >= -2 && dy <= 2;
+#pragma unroll 1
+            for (int dx = -R; dx <= R; ++dx)
+                if (!mid || dx < -2 || dx > 2) visit(dy, dx);
+        }
+        certified = window_certifies(Lk, window_cert(i, j, R, Ws, Hs, stride, q.z, fx, fy, cx, cy));
+        if (certified)
+            finish_cov<KMAX>(
+                Lk, k, q, [&](int pos) { const float4 v = tl[pos]; return make_float3(v.x, v.y, v.z); },
+                [&](int pos) { return __float_as_int(tl[pos].w); }, zin, eps, mode, p, covs, knn_out, nullptr, 0);
+    }
+    // the rest go to the next pass (one atomic per warp)
+    const bool need = active && !certified;
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(fb_count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (need) fb_list[base + __popc(m & ((1u << lane) - 1u))] = make_int2(__float_as_int(q.w), j * Ws + i);
+    }
+}
+
+// Second pass: one warp per listed query, the (2 R2 + 1)^2 window read straight from memory,
+// each lane keeping the k best of its share, then the warp's k best taken one by one (warp
+// minimum of the lanes' heads).  Still uncertified queries go to fb2 as (original index, the
+// window's k-th squared distance or +inf) for the tree.
+template <int KMAX, int R2>
+__global__ void __launch_bounds__(COV_THREADS) knn_wide_window_kernel(
+    const int2* __restrict__ list, const int* __restrict__ count, const int* __restrict__ idx_img, int Ws, int Hs,
+    int stride, float fx, float fy, float cx, float cy, const float* __restrict__ orig, const float* __restrict__ zin,
+    int k, float eps, int mode, float p, float* __restrict__ covs, int32_t* __restrict__ knn_out,
+    int2* __restrict__ fb2, int* __restrict__ count2)
+{
+    constexpr int D = 2 * R2 + 1, NC = D * D;
+    const int lane = threadIdx.x & 31;
+    const int m = *count;
+    const unsigned long long empty = dkey(GSICP_INF, 0x7fffffff);
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < m; t += (gridDim.x * blockDim.x) >> 5) {
+        const int2 e = list[t];
+        const int qi = e.x, i = e.y % Ws, j = e.y / Ws;
+        const float4 q = make_float4(orig[3l * qi], orig[3l * qi + 1], orig[3l * qi + 2], __int_as_float(qi));
+        unsigned long long L[KMAX];  // this lane's best (no phantoms: ascending, empty at the end)
+#pragma unroll
+        for (int a = 0; a < KMAX; ++a) L[a] = empty;
+        for (int c0 = 0; c0 < NC; c0 += 32 * 4) {
+            int pi[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int c = c0 + 32 * h + lane;
+                const int sx = i + c % D - R2, sy = j + c / D - R2;
+                pi[h] = c < NC && sx >= 0 && sx < Ws && sy >= 0 && sy < Hs ? idx_img[(long)sy * Ws + sx] : -1;
+            }
+            float4 pp[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                pp[h] = pi[h] >= 0 ? make_float4(orig[3l * pi[h]], orig[3l * pi[h] + 1], orig[3l * pi[h] + 2], 0.f)
+                                   : make_float4(GSICP_INF, GSICP_INF, GSICP_INF, 0.f);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                if (pi[h] < 0) continue;
+                const unsigned long long key = dkey(point_d2(q.x, q.y, q.z, pp[h]), pi[h]);
+                if (key < L[KMAX - 1]) key_insert(L, key);
+            }
+        }
+        // merge: k rounds of warp minimum over the lanes' heads; the winner drops its head
+        unsigned long long Lk[KMAX];
+#pragma unroll
+        for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : empty;
+#pragma unroll
+        for (int r = 0; r < KMAX; ++r) {
+            if (r >= k) break;
+            unsigned long long best = L[0];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = other < best ? other : best;
+            }
+            Lk[KMAX - k + r] = best;
+            if (L[0] == best && best != empty) {  // keys are unique: exactly one lane holds it
+#pragma unroll
+                for (int a = 0; a < KMAX - 1; ++a) L[a] = L[a + 1];
+                L[KMAX - 1] = empty;
+            }
+        }
+        const bool cert = window_certifies(Lk, window_cert(i, j, R2, Ws, Hs, stride, q.z, fx, fy, cx, cy));
+        if (cert) {
+            if (lane == 0)
+                finish_cov<KMAX>(Lk, k, q, ByIndex{orig}, SameIndex{}, zin, eps, mode, p, covs, knn_out, nullptr, 0);
+        } else if (lane == 0) {
+            const float wk = key_idx(Lk[KMAX - 1]) != 0x7fffffff ? key_d2(Lk[KMAX - 1]) : GSICP_INF;
+            fb2[atomicAdd(count2, 1)] = make_int2(qi, __float_as_int(wk));
+        }
+    }
+}
+
+// Exact k-NN by the tree for the listed queries (one thread each; list[t] = (original index, an
+// upper bound on its k-th squared distance: the window's k-th, or +inf)).  The walk collects every
+// point within the bound, so it starts tight; leaves are read eight points at a time.
+template <int KMAX>
+__global__ void __launch_bounds__(COV_THREADS) knn_list_kernel(IndexView ix, const int2* __restrict__ list,
+                                                               const int* __restrict__ count,
+                                                               const float* __restrict__ orig,
+                                                               const float* __restrict__ zin, int k, float eps,
+                                                               int mode, float p, float* __restrict__ covs,
+                                                               int32_t* __restrict__ knn_out)
+{
+    const int n = *ix.n, B = ix.B, m = *count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int2 e = list[t];
+        const int qi = e.x;
+        const float4 q = make_float4(orig[3l * qi], orig[3l * qi + 1], orig[3l * qi + 2], __int_as_float(qi));
+        float bound = __int_as_float(e.y);
+        unsigned long long Lk[KMAX];
+        const unsigned long long lim = dkey(bound, 0x7fffffff);  // accepts every point within the bound
+#pragma unroll
+        for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : lim;
+        traverse(ix, q.x, q.y, q.z, bound, [&](int lf) {
+            const int beg = lf * B, end = min(beg + B, n);
+            for (int u0 = beg; u0 < end; u0 += 8) {
+                float4 pp[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    pp[j] = u0 + j < end ? ix.pts[u0 + j] : make_float4(GSICP_INF, GSICP_INF, GSICP_INF,
+                                                                        __int_as_float(0x7fffffff));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const unsigned long long key = dkey(point_d2(q.x, q.y, q.z, pp[j]), __float_as_int(pp[j].w));
+                    if (key < Lk[KMAX - 1]) key_insert(Lk, key);
+                }
+            }
+            bound = key_d2(Lk[KMAX - 1]);
+        });
+        finish_cov<KMAX>(Lk, k, q, ByIndex{orig}, SameIndex{}, zin, eps, mode, p, covs, knn_out, nullptr, 0);
+    }
+}
+
+template <int KMAX>
+static void launch_frame_knn_t(const IndexView& ix, const int* idx_img, int Ws, int Hs, int stride,
+                               const float intr[4], const float* pts, const float* z, int cap,
+                               const gsicp_cov_params& prm, float* covs, int32_t* knn, int2* fb_list, int* fb_count,
+                               cudaStream_t s)
+{
+    // fb_list holds the first pass's leftovers from the front and the second's from cap on;
+    // fb_count[0], fb_count[1] count them
+    const dim3 grid((Ws + WIN_TX - 1) / WIN_TX, (Hs + WIN_TY - 1) / WIN_TY);
+    knn_window_kernel<KMAX, 4><<<grid, WIN_TX * WIN_TY, 0, s>>>(idx_img, Ws, Hs, stride, intr[0], intr[1], intr[2],
+                                                                 intr[3], pts, z, prm.k, prm.eps, prm.reg_mode,
+                                                                 prm.p, covs, knn, fb_list, fb_count);
+    const int lgrid = std::max(1, std::min((cap + COV_THREADS - 1) / COV_THREADS, device_sm_count() * 8));
+    knn_wide_window_kernel<KMAX, 12><<<lgrid, COV_THREADS, 0, s>>>(
+        fb_list, fb_count, idx_img, Ws, Hs, stride, intr[0], intr[1], intr[2], intr[3], pts, z, prm.k, prm.eps,
+        prm.reg_mode, prm.p, covs, knn, fb_list + cap, fb_count + 1);
+    knn_list_kernel<KMAX><<<lgrid, COV_THREADS, 0, s>>>(ix, fb_list + cap, fb_count + 1, pts, z, prm.k, prm.eps,
+                                                         prm.reg_mode, prm.p, covs, knn);
+}
+
+gsicp_status launch_frame_knn_cov(const IndexView& ix, const int* idx_img, int Ws, int Hs, int stride,
+                                  const float intr[4], const float* pts, const float* z, int cap,
+                                  const gsicp_cov_params& prm, float* covs, int32_t* knn, int* fb_list,
+                                  int* fb_count, cudaStream_t s)
+{
+    if (cap <= 0) return GSICP_OK;
+    GSICP_CUDA(cudaMemsetAsync(fb_count, 0, 2 * sizeof(int), s));
+    const int k = prm.k;
+    int2* fl = reinterpret_cast<int2*>(fb_list);
+    if (k <= 8) launch_frame_knn_t<8>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
+    else if (k <= 16) launch_frame_knn_t<16>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
+    else if (k <= 20) launch_frame_knn_t<20>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
+    else launch_frame_knn_t<32>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

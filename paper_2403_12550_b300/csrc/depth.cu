@@ -36,7 +36,8 @@ __global__ void d2p_count_kernel(const float* __restrict__ depth, int W, int str
 __global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
                                  float z_min, float z_max, double fx, double fy, double cx, double cy,
                                  const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int nblocks,
-                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev)
+                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev,
+                                 int* __restrict__ idx_img)
 {
     __shared__ uint32_t wsum[D2P_THREADS / 32];
     const long idx = (long)blockIdx.x * D2P_THREADS + threadIdx.x;
@@ -57,6 +58,8 @@ __global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int str
         pts[3l * pos + 2] = d;
         if (z) z[pos] = d;
     }
+    // sample -> point index (-1: no point), for searches over the image grid
+    if (idx_img && idx < total) idx_img[idx] = ok && pos < (uint32_t)cap ? (int)pos : -1;
     if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
         const uint32_t all = offs[nblocks - 1] + counts[nblocks - 1];
         if (n_dev) *n_dev = (int)min(all, (uint32_t)cap);
@@ -66,7 +69,7 @@ __global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int str
 
 gsicp_status launch_depth_to_points(const float* depth, int W, int H, const float intr[4], int stride,
                                     float z_min, float z_max, float* pts, float* z, int cap, int* n_dev,
-                                    int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s)
+                                    int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s, int* idx_img)
 {
     const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
     const long total = (long)Ws * Hs;
@@ -78,7 +81,7 @@ gsicp_status launch_depth_to_points(const float* depth, int W, int H, const floa
     GSICP_CHECK(exclusive_scan_u32(cnt, off, nb, sums, s));
     d2p_write_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, Ws, total, z_min, z_max, (double)intr[0],
                                                 (double)intr[1], (double)intr[2], (double)intr[3], off, cnt, nb, pts,
-                                                z, cap, n_dev, total_dev);
+                                                z, cap, n_dev, total_dev, idx_img);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

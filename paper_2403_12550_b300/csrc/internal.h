@@ -70,13 +70,23 @@ gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf
 // a1: depth -> points (row-major compaction).  Writes *n_dev (clamped to cap) and *total_dev (unclamped).
 gsicp_status launch_depth_to_points(const float* depth, int W, int H, const float intr[4], int stride,
                                     float z_min, float z_max, float* pts, float* z, int cap, int* n_dev,
-                                    int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s);
+                                    int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s,
+                                    int* idx_img = nullptr);  // optional: sample -> point index (-1 none)
 
 // a2+a3: k-NN covariances of the points of `ix` (its pts hold the n points; orig gives the
 // unsorted xyz for neighbour gathering).
 gsicp_status launch_knn_cov(const IndexView& ix, const float* orig_pts, const float* z, int cap,
                             const gsicp_cov_params& prm, float* covs, int32_t* knn, float4* covs_sorted,
                             cudaStream_t s);
+
+// a2+a3 for the points of one depth frame (a1's output in row-major order, idx_img its
+// sample -> point map): image-window k-NN certified by the camera geometry, the uncertified
+// queries by the tree of `ix` (built over the same points).  fb_list (4 x cap ints) and fb_count
+// (2 ints) are scratch.  covs in original order.
+gsicp_status launch_frame_knn_cov(const IndexView& ix, const int* idx_img, int Ws, int Hs, int stride,
+                                  const float intr[4], const float* pts, const float* z, int cap,
+                                  const gsicp_cov_params& prm, float* covs, int32_t* knn, int* fb_list,
+                                  int* fb_count, cudaStream_t s);
 
 // Copy covariances (n x 6, original order) into the index's Morton order (2 float4 per point).
 gsicp_status launch_permute_covs(const IndexView& ix, const float* covs, int cap, float4* out, cudaStream_t s);
@@ -115,6 +125,7 @@ struct gsicp_ctx_s {
     gsicp::IndexBufs src_index;       // per-frame source index
     gsicp::DevBuf a1_counts, a1_sums, n_dev, total_dev;
     gsicp::DevBuf frame_pts, frame_z, frame_covs, frame_depth;
+    gsicp::DevBuf frame_idx, fb_list, fb_count;  // sample -> point map; tree-search list of the window k-NN
     gsicp::DevBuf covs_sorted;         // source covariances in the source index's order
     gsicp::RegMachine reg;
     int64_t* host_pinned = nullptr;   // small pinned scratch for counts

@@ -24,7 +24,8 @@ __global__ void d2p_count_kernel(const float* __restrict__ depth, int W, int str
 __global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
                                  float z_min, float z_max, double fx, double fy, double cx, double cy,
                                  const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int nblocks,
-                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev);
+                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev,
+                                 int* __restrict__ idx_img);
 __global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, int n, uint32_t* __restrict__ sums);
 __global__ void scan_sums_kernel(uint32_t* sums, int nb);
 __global__ void scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int n,
@@ -97,7 +98,7 @@ extern "C" gsicp_status gsicp_depth_to_points_noalloc(const float* depth_dev, in
     scan_apply_kernel<<<ns, 256, 0, s>>>(counts, offs, nb, sums);
     d2p_write_kernel<<<nb, 256, 0, s>>>(depth_dev, W, stride, Ws, total, z_min, z_max, (double)intr[0],
                                         (double)intr[1], (double)intr[2], (double)intr[3], offs, counts, nb, pts_dev,
-                                        z_dev, (int)cap, (int*)n_dev, (int*)total_dev);
+                                        z_dev, (int)cap, (int*)n_dev, (int*)total_dev, nullptr);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

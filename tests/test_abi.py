@@ -50,6 +50,13 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     lib.gsicp_source_covariances.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
     assert lib.gsicp_source_covariances(None, None, None, 10, None, None, None, None) == INVALID
+    lib.gsicp_frame_covariances.argtypes = [C.c_void_p] * 2 + [C.c_int] * 2 + [C.c_void_p, C.c_int, C.c_float,
+                                                                               C.c_float] + [C.c_void_p] * 4 + \
+        [C.c_int64, C.c_void_p, C.c_void_p]
+    assert lib.gsicp_frame_covariances(None, None, 8, 8, None, 1, 0.1, 10.0, None, None, None, None, 64, None,
+                                       None) == INVALID
+    lib.gsicp_ctx_frame_stats.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.gsicp_ctx_frame_stats(None, None) == INVALID
     lib.gsicp_map_size.restype = C.c_int64
     assert lib.gsicp_map_size(None) == 0
     lib.gsicp_map_destroy(None)

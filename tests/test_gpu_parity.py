@@ -418,6 +418,76 @@ def test_track_frame_empty_depth(g, ctx):
     assert r["status"] == g.ERR_DEGENERATE and r["n_points"] == 0
 
 
+# ----------------------------------------------------------------------------- a1+a2+a3 of a depth frame
+
+def _frame_cases():
+    scene = make_room(3)
+    rng = np.random.default_rng(55)
+    P = circle_poses(rng, scene, 1)[0]
+    vga = Intrinsics(640, 480, 525.0, 525.0, 319.5, 239.5)
+    small = Intrinsics(40, 30, 30.0, 30.0, 19.5, 14.5)
+    tiny = Intrinsics(7, 5, 6.0, 6.0, 3.0, 2.0)
+    return [(REPLICA_INTR, 2, 0.0), (vga, 1, 0.0), (vga, 2, 0.3), (vga, 3, 0.0), (small, 1, 0.1), (tiny, 1, 0.0)], \
+        scene, P
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_frame_covariances_equal_tree_path(g, ctx, case):
+    """The image-window k-NN (certified by the camera geometry, tree search for the rest) gives
+    bit-for-bit the points of gsicp_depth_to_points and the covariances of
+    gsicp_source_covariances on them: both are the exact float k-NN with the same ties."""
+    cases, scene, P = _frame_cases()
+    intr, stride, dropout = cases[case]
+    rng = np.random.default_rng(100 + case)
+    depth = add_depth_noise(raycast_depth(scene, P, intr), rng, 1e-3, dropout=dropout)
+    for p in (1.5, 0.0):
+        cp = g.CovParams(20, 1e-3, g.PLANE, p)
+        pf, zf, cf = g.gsicp_frame_covariances(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0, cp)
+        fs = g.gsicp_ctx_frame_stats(ctx)
+        pts, z = g.gsicp_depth_to_points(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0)
+        pts, z = pts.clone(), z.clone()
+        ct = g.gsicp_source_covariances(ctx, pts, z, cp)
+        assert torch.equal(pf, pts) and torch.equal(zf, z)
+        assert 0 <= fs["tree_queries"] <= fs["wide_window_queries"] <= len(pts)
+        bad = (cf != ct).any(dim=1).nonzero().flatten().cpu().numpy()
+        assert len(bad) == 0, (case, p, len(bad), fs, len(pts))
+
+
+def test_frame_covariances_match_oracle(g, ctx):
+    cases, scene, P = _frame_cases()
+    intr, stride, dropout = cases[2]
+    depth = add_depth_noise(raycast_depth(scene, P, intr), np.random.default_rng(7), 1e-3, dropout=dropout)
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    pf, zf, cf = g.gsicp_frame_covariances(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0, cp)
+    pts, z = oracle_frame_points(depth, intr, stride)
+    np.testing.assert_array_equal(pf.cpu().numpy(), pts)
+    ro = orc.source_covariances(pts, z, k=20, eps=1e-3, reg_mode=orc.PLANE, p=1.5)
+    keep = ro["gap"] >= PLANE_GAP_EXCLUDE
+    err = cov_rel_err(cf.cpu().numpy().astype(np.float64), ro["covs"])
+    assert np.all(err[keep] <= COV_REL_TOL), (err[keep].max(), int((~keep).sum()))
+    assert (~keep).mean() < 0.01
+
+
+def test_frame_covariances_capacity_and_empty(g, ctx):
+    intr = Intrinsics(16, 12, 12.0, 12.0, 7.5, 5.5)
+    d = np.full((12, 16), 2.0, np.float32)
+    cap = 10
+    pts = torch.empty((cap, 3), device="cuda")
+    z = torch.empty((cap,), device="cuda")
+    covs = torch.empty((cap, 6), device="cuda")
+    import ctypes as C
+    n = C.c_int64(0)
+    fi = (C.c_float * 4)(*intr.as_array().tolist())
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    st = g.lib.gsicp_frame_covariances(ctx.ptr, cu(d).data_ptr(), 16, 12, fi, 1, 0.1, 10.0, C.byref(cp),
+                                       pts.data_ptr(), z.data_ptr(), covs.data_ptr(), cap, C.byref(n), None)
+    torch.cuda.synchronize()
+    assert st == g.ERR_CAPACITY and n.value == cap
+    pf, zf, cf = g.gsicp_frame_covariances(ctx, cu(np.zeros((12, 16), np.float32)), intr.as_array(), 1, 0.1, 10.0,
+                                           cp)
+    assert len(pf) == 0 and len(cf) == 0
+
+
 # ----------------------------------------------------------------------------- TUM-shaped sequence
 
 def test_sequence_config3_matches_oracle(g, ctx):
