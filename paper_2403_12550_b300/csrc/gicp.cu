@@ -231,50 +231,19 @@ __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegSt
     pose_to_float(st);
 }
 
-__global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob* __restrict__ jp,
-                                                                cudaGraphConditionalHandle cond)
+// All the Gauss-Newton work for source point s of job J at the float pose (R, t) + (Rl, tl):
+// transform, exact nearest map point (cache / grid / tree), residual, weight and J^T W J, J^T W d,
+// d^T W d and the inlier count added to acc.  Returns 1 if the point's nearest-point search ran
+// (its cache was rebuilt).
+__device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], const float (&Rl)[9],
+                                        const float (&t)[3], const float (&tl)[3], int s, int nmap,
+                                        float (&acc)[NACC])
 {
-    const RegJob& J = *jp;
-    RegState* st = J.st;
-    if (st->status != REG_ST_RUNNING) {
-        // every block sees the same status here, so only this thread touches the condition
-        if (J.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-        return;
-    }
-    const int n = *J.n;
-    const int nmap = *J.map.n;
-    const int it_now = st->iter;
-    if (threadIdx.x == 0 && it_now < REG_STATS) {
-        unsigned long long t0;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-        atomicMin(&st->t_first[it_now], t0);
-    }
-    float R[9], t[3], Rl[9], tl[3];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        R[a] = st->Rf[a];
-        Rl[a] = st->Rlo[a];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        t[a] = st->tf[a];
-        tl[a] = st->tlo[a];
-    }
-    float acc[NACC];
-#pragma unroll
-    for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
-
-    // One source point per thread (the grid covers the context's capacity; the hardware block
-    // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
-    // the reduction order, hence the result, deterministic).
     int refreshed = 0;
     const float4 qq = *J.map.quant;
     const int B = J.map.B;
     const float max_d = sqrtf(J.max_d2);
     const float Rs = max_d + J.slack, Rs2 = Rs * Rs;
-    do {
-        const int s = blockIdx.x * blockDim.x + threadIdx.x;
-        if (s >= n) break;
         const float4 x = J.src[s];
         // y = R x + t as hi + lo: the searches run on hi; the final choice among the candidates
         // they return, the inlier test and the residual use hi + lo (distance differences at the
@@ -287,10 +256,11 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
             return sq3(__fsub_rn(__fsub_rn(p.x, y0), l0), __fsub_rn(__fsub_rn(p.y, y1), l1),
                        __fsub_rn(__fsub_rn(p.z, y2), l2));
         };
-        const int4 ca4 = reinterpret_cast<const int4*>(J.cand)[2l * s];
-        const int4 cb4 = reinterpret_cast<const int4*>(J.cand)[2l * s + 1];
+        // cache state through L2: in a persistent launch another SM wrote it in the last iteration
+        const int4 ca4 = __ldcg(reinterpret_cast<const int4*>(J.cand) + 2l * s);
+        const int4 cb4 = __ldcg(reinterpret_cast<const int4*>(J.cand) + 2l * s + 1);
         const int cp[KC] = {ca4.x, ca4.y, ca4.z, ca4.w, cb4.x, cb4.y, cb4.z, cb4.w};
-        const float4 anc = J.anchor[s];
+        const float4 anc = __ldcg(J.anchor + s);
         float best_d2 = J.max_d2;
         int best_oi = 0x7fffffff, best_pos = -1;
         bool resolved = false;
@@ -441,7 +411,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
             }
         }
         if (J.corr_out) J.corr_out[__float_as_int(x.w)] = best_pos >= 0 ? best_oi : -1;
-        if (best_pos < 0) break;
+        if (best_pos < 0) return refreshed;
 
         acc[28] += 1.f;
         const float4 mu = J.map.pts[best_pos];
@@ -463,7 +433,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         // W = Sigma^-1 (cofactors / determinant)
         const float c00 = s11 * s22 - s12 * s12, c01 = s02 * s12 - s01 * s22, c02 = s01 * s12 - s02 * s11;
         const float det = s00 * c00 + s01 * c01 + s02 * c02;
-        if (!(fabsf(det) > 0.f)) break;
+        if (!(fabsf(det) > 0.f)) return refreshed;
         const float id = 1.f / det;
         const float W00 = c00 * id, W01 = c01 * id, W02 = c02 * id;
         const float W11 = (s00 * s22 - s02 * s02) * id, W12 = (s01 * s02 - s00 * s12) * id;
@@ -511,11 +481,14 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         acc[25] -= Wd1;
         acc[26] -= Wd2;
         acc[27] += d0 * Wd0 + d1 * Wd1 + d2 * Wd2;
-    } while (false);
+        return refreshed;
+}
 
-    // ---- block reduction -> one partial per block
+// Block-wide sum of acc into row[0 .. NACC) (row[NACC ..32) zeroed; visible device-wide on return
+// to thread 0 after its __threadfence); returns the number of threads with refreshed != 0.
+__device__ __forceinline__ int block_partial(const float (&acc)[NACC], int refreshed, float* row)
+{
     __shared__ float red[REG_THREADS / 32][NACC];
-    __shared__ bool am_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < NACC; ++a) {
@@ -524,32 +497,28 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][a] = v;
     }
-    const int block_refreshed = __syncthreads_count(refreshed);
-    if (threadIdx.x == 0 && block_refreshed > 0 && st->iter < REG_STATS) atomicAdd(&st->refreshes[st->iter], block_refreshed);
+    const int count = __syncthreads_count(refreshed);
     if (threadIdx.x < 32) {
         float v = 0.f;
         if (threadIdx.x < NACC) {
 #pragma unroll
             for (int w = 0; w < REG_THREADS / 32; ++w) v += red[w][threadIdx.x];
         }
-        J.partials[32l * blockIdx.x + threadIdx.x] = v;
+        row[threadIdx.x] = v;
         __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (it_now < REG_STATS) {
-            unsigned long long t1;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-            atomicMax(&st->t_arrive[it_now], t1);
-        }
-        am_last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    unsigned long long t_start = 0;
-    if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    return count;
+}
 
+// The last block of a launch (or of a pair): compensated sum of the nb partial rows, then in its
+// first warp the H, b, cost and inliers of this linearisation and (solve mode) the FP64 solve,
+// the pose update and the stopping test.  Returns whether another iteration should run (on lane
+// 0 of warp 0; false elsewhere).  t_start: globaltimer when the block became the last.
+__device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const float* __restrict__ partials, int nb,
+                                         int it_now, unsigned long long t_start)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // ---- last block: compensated sum of all partials.  Thread t owns component group g = t % 8
     // (components 4g..4g+3, one float4 of a block's 32-float partial) and blocks t/8, t/8 + 32, ...;
     // all its loads are independent and issued in batches of 8.
@@ -558,8 +527,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
     {
         const int grp = threadIdx.x & 7, row = threadIdx.x >> 3;
         dfloat a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, a2 = {0.f, 0.f}, a3 = {0.f, 0.f};
-        const float4* P4 = reinterpret_cast<const float4*>(J.partials);
-        const int nb = (int)gridDim.x;
+        const float4* P4 = reinterpret_cast<const float4*>(partials);
         for (int b0 = row; b0 < nb; b0 += 8 * (REG_THREADS / 8)) {
             float4 v[8];
 #pragma unroll
@@ -598,7 +566,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
         tot[threadIdx.x] = sum;
     }
     __syncthreads();
-    if (warp != 0) return;
+    if (warp != 0) return false;
 
     // ---- warp 0: H, b, cost and inliers of this linearisation, then the lane-parallel FP64 solve
     const double tot_l = lane < NACC ? tot[lane] : 0.0;  // component `lane`
@@ -664,8 +632,68 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
             st->solve_ns[it] = (int)(t_end - t_solve);
         }
         __threadfence();
-        if (J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
     }
+    return more;
+}
+
+__global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob* __restrict__ jp,
+                                                                cudaGraphConditionalHandle cond)
+{
+    const RegJob& J = *jp;
+    RegState* st = J.st;
+    if (st->status != REG_ST_RUNNING) {
+        // every block sees the same status here, so only this thread touches the condition
+        if (J.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int n = *J.n;
+    const int nmap = *J.map.n;
+    const int it_now = st->iter;
+    if (threadIdx.x == 0 && it_now < REG_STATS) {
+        unsigned long long t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        atomicMin(&st->t_first[it_now], t0);
+    }
+    float R[9], t[3], Rl[9], tl[3];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        R[a] = st->Rf[a];
+        Rl[a] = st->Rlo[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        t[a] = st->tf[a];
+        tl[a] = st->tlo[a];
+    }
+    float acc[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
+    // One source point per thread (the grid covers the context's capacity; the hardware block
+    // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
+    // the reduction order, hence the result, deterministic).
+    int refreshed = 0;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) refreshed = gn_point(J, R, Rl, t, tl, s, nmap, acc);
+    const int block_refreshed = block_partial(acc, refreshed, J.partials + 32l * blockIdx.x);
+    __shared__ bool am_last;
+    if (threadIdx.x == 0) {
+        if (block_refreshed > 0 && it_now < REG_STATS) atomicAdd(&st->refreshes[it_now], block_refreshed);
+        if (it_now < REG_STATS) {
+            unsigned long long t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+            atomicMax(&st->t_arrive[it_now], t1);
+        }
+        am_last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    unsigned long long t_start = 0;
+    if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    // the rows of the blocks that held points (the rest are zero): the same rows, in the same
+    // order, as a batched registration of these points sums
+    const bool more = finalize(J, st, J.partials, (n + REG_THREADS - 1) / REG_THREADS, it_now, t_start);
+    if (threadIdx.x == 0 && J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------------------
