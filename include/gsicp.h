@@ -242,6 +242,26 @@ gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float
                             double b_out[6], int* iters_out, double* cost_out,
                             int64_t* inliers_out, void* stream);
 
+/* Batched registration (NEXT row of the hot path: many independent registrations at once; the
+ * paper registers one frame at a time).  B pairs, each exactly as gsicp_register would register
+ * it: source b (src_pts_dev[b], n[b] x 3, with covariances src_covs_dev[b], n[b] x 6) against map
+ * maps[b] from pose T0[16 b .. 16 b + 15], all with the same params.  The host arrays hold B
+ * device pointers / counts / handles.  All pairs run in one persistent launch that takes
+ * (pair, 256-point chunk) work items from a device queue: each pair advances through its own
+ * iterations, the pair's solve enqueueing its next iteration, and each pair's sums are taken in
+ * the same order as gsicp_register's, so each T_out equals what gsicp_register returns for that
+ * pair alone.  Outputs (host, B entries each, all but T_out nullable): T_out (B x 16), iters_out,
+ * cost_out, inliers_out, status_out (GSICP_OK, or GSICP_ERR_DEGENERATE for that pair: fewer than
+ * min_inliers correspondences, H not positive definite, or no points).  Returns GSICP_OK, an
+ * argument / CUDA error, or GSICP_ERR_TIMEOUT if a bounded wait of the work queue ran out.
+ * Synchronises the stream. */
+gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_pts_dev,
+                                  const float* const* src_covs_dev, const int64_t* n,
+                                  const gsicp_map* maps, const double* T0,
+                                  const gsicp_reg_params* params, double* T_out, int* iters_out,
+                                  double* cost_out, int64_t* inliers_out, int* status_out,
+                                  void* stream);
+
 /* One linearisation at pose T (no update): H (6x6), b, cost and inlier count as in
  * gsicp_register's first iteration.  corr_dev (n int32, nullable) receives each source point's
  * map index (-1 if none).  Synchronises the stream. */

@@ -21,7 +21,7 @@ __all__ = [
     "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
     "gsicp_build_map_index", "gsicp_map_append",
-    "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_linearise",
+    "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
 ]
 
@@ -104,6 +104,8 @@ _sig("gsicp_map_destroy", None, [_vp])
 _sig("gsicp_transform_gaussians", C.c_int, [_dp, _vp, _vp, C.c_int64, _vp, _vp, _vp])
 _sig("gsicp_register", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(RegParams), _dp, _dp, _dp,
                                  C.POINTER(C.c_int), _dp, _i64p, _vp])
+_sig("gsicp_register_batch", C.c_int, [_vp, C.c_int, _vp, _vp, _i64p, _vp, _dp, C.POINTER(RegParams), _dp,
+                                       C.POINTER(C.c_int), _dp, _i64p, C.POINTER(C.c_int), _vp])
 _sig("gsicp_linearise", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.c_float, _dp, _dp, _dp, _i64p, _vp, _vp])
 _sig("gsicp_map_nearest", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp])
 for _n in ("gsicp_track_frame", "gsicp_track_frame_host"):
@@ -351,6 +353,29 @@ def gsicp_register(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: Ma
     _check(st, "gsicp_register", allow=(ERR_DEGENERATE,))
     return dict(T=np.array(T).reshape(4, 4), H=np.array(H).reshape(6, 6), b=np.array(b), iters=it.value,
                 cost=cost.value, inliers=cnt.value, status=st)
+
+
+def gsicp_register_batch(ctx: Context, srcs: list, covs: list, maps: list, T0s, params: RegParams) -> dict:
+    """Batched a5-a7: pair b registers srcs[b] (n_b x 3) with covs[b] (n_b x 6) against maps[b]
+    from T0s[b].  Returns dict(T (B,4,4), iters, cost, inliers, status) as numpy arrays."""
+    B = len(srcs)
+    assert len(covs) == B and len(maps) == B
+    T0s = np.ascontiguousarray(np.asarray(T0s, dtype=np.float64).reshape(B, 16))
+    P = (C.c_void_p * max(B, 1))(*[_dev(t, cols=3).value if t.shape[0] else None for t in srcs])
+    Q = (C.c_void_p * max(B, 1))(*[_dev(t, cols=6).value if t.shape[0] else None for t in covs])
+    nn = (C.c_int64 * max(B, 1))(*[t.shape[0] for t in srcs])
+    M = (C.c_void_p * max(B, 1))(*[m.ptr for m in maps])
+    T = np.zeros((max(B, 1), 16))
+    it = (C.c_int * max(B, 1))()
+    cost = np.zeros(max(B, 1))
+    inl = (C.c_int64 * max(B, 1))()
+    stt = (C.c_int * max(B, 1))()
+    dp = C.POINTER(C.c_double)
+    _check(lib.gsicp_register_batch(ctx.ptr, B, P, Q, nn, M, T0s.ctypes.data_as(dp), C.byref(params),
+                                    T.ctypes.data_as(dp), it, cost.ctypes.data_as(dp), inl, stt, _stream()),
+           "gsicp_register_batch")
+    return dict(T=T[:B].reshape(B, 4, 4), iters=np.array(it[:B]), cost=cost[:B], inliers=np.array(inl[:B]),
+                status=np.array(stt[:B]))
 
 
 def gsicp_linearise(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: MapHandle, T,

@@ -9,6 +9,8 @@
 #include <new>
 #include <string>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace gsicp {
@@ -194,6 +196,7 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     if (!ctx) return;
     cudaDeviceSynchronize();
     ctx->reg.release();
+    ctx->batch.release();
     BuildScratch& b = ctx->build;
     b.k0.release(); b.k1.release(); b.v0.release(); b.v1.release(); b.hist.release(); b.sums.release();
     b.bbox.release();
@@ -423,6 +426,123 @@ gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float
                           map, params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, (int)n, true, s));
     return finish_registration(ctx, s, T_out, H_out, b_out, iters_out, cost_out, inliers_out);
+}
+
+gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_pts_dev,
+                                  const float* const* src_covs_dev, const int64_t* n, const gsicp_map* maps,
+                                  const double* T0, const gsicp_reg_params* params, double* T_out, int* iters_out,
+                                  double* cost_out, int64_t* inliers_out, int* status_out, void* stream)
+{
+    if (!ctx || B < 0 || B > 65535 || !valid_reg_params(params)) return GSICP_ERR_INVALID_ARG;
+    if (B == 0) return GSICP_OK;
+    if (!src_pts_dev || !src_covs_dev || !n || !maps || !T0 || !T_out) return GSICP_ERR_INVALID_ARG;
+    int64_t total = 0, chunks = 0;
+    for (int b = 0; b < B; ++b) {
+        if (n[b] < 0 || n[b] > (1 << 30) || !maps[b] || !valid_pose(T0 + 16l * b)) return GSICP_ERR_INVALID_ARG;
+        if (n[b] > 0 && (!src_pts_dev[b] || !src_covs_dev[b])) return GSICP_ERR_INVALID_ARG;
+        total += n[b];
+        chunks += (n[b] + 255) / 256;
+    }
+    const int64_t capacity = chunks * params->max_iters;
+    if (total > (1 << 30) || capacity > (int64_t)UINT32_MAX - 1) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchMachine& bm = ctx->batch;
+    const size_t N = (size_t)std::max<int64_t>(total, 1), C = (size_t)std::max<int64_t>(chunks, 1);
+    GSICP_CHECK(bm.src.ensure(sizeof(float4) * N));
+    GSICP_CHECK(bm.covs.ensure(sizeof(float4) * 2 * N));
+    GSICP_CHECK(bm.cand.ensure(sizeof(int) * KC * N));
+    GSICP_CHECK(bm.anchor.ensure(sizeof(float4) * N));
+    GSICP_CHECK(bm.partials.ensure(sizeof(float) * 32 * C));
+    GSICP_CHECK(bm.counts.ensure(sizeof(int) * B));
+    GSICP_CHECK(bm.jobs.ensure(sizeof(RegJob) * B));
+    GSICP_CHECK(bm.states.ensure(sizeof(RegState) * B));
+    GSICP_CHECK(bm.T0.ensure(sizeof(Pose16) * B));
+    GSICP_CHECK(bm.offsets.ensure(sizeof(unsigned) * B));
+    GSICP_CHECK(bm.queue.ensure(sizeof(BatchQueue)));
+    GSICP_CHECK(bm.items.ensure(sizeof(unsigned long long) * (size_t)std::max<int64_t>(capacity, 1)));
+    // pinned staging, laid out: jobs | states | poses | counts | offsets | queue
+    const size_t off_states = sizeof(RegJob) * B, off_T0 = off_states + sizeof(RegState) * B,
+                 off_counts = off_T0 + sizeof(Pose16) * B, off_offsets = off_counts + sizeof(int) * B,
+                 off_queue = (off_offsets + sizeof(unsigned) * B + 15) / 16 * 16,
+                 host_need = off_queue + sizeof(BatchQueue);
+    if (bm.host_bytes < host_need) {
+        if (bm.host) GSICP_CUDA(cudaFreeHost(bm.host));
+        bm.host = nullptr;
+        bm.host_bytes = 0;
+        GSICP_CUDA(cudaMallocHost(&bm.host, host_need));
+        bm.host_bytes = host_need;
+    }
+    GSICP_CUDA(cudaStreamSynchronize(s));  // the staging area may still feed an earlier batch's copies
+    char* hb = static_cast<char*>(bm.host);
+    RegJob* jobs_h = reinterpret_cast<RegJob*>(hb);
+    RegState* states_h = reinterpret_cast<RegState*>(hb + off_states);
+    Pose16* T0_h = reinterpret_cast<Pose16*>(hb + off_T0);
+    int* counts_h = reinterpret_cast<int*>(hb + off_counts);
+    unsigned* offsets_h = reinterpret_cast<unsigned*>(hb + off_offsets);
+    BatchQueue* queue_h = reinterpret_cast<BatchQueue*>(hb + off_queue);
+    int running = 0;
+    {
+        int64_t po = 0, co = 0;
+        for (int b = 0; b < B; ++b) {
+            counts_h[b] = (int)n[b];
+            offsets_h[b] = (unsigned)co;
+            for (int i = 0; i < 16; ++i) T0_h[b].v[i] = T0[16l * b + i];
+            RegJob j = make_job(bm.src.as<float4>() + po, bm.covs.as<float4>() + 2 * po, bm.counts.as<int>() + b,
+                                maps[b], params);
+            j.cand = bm.cand.as<int>() + KC * po;
+            j.anchor = bm.anchor.as<float4>() + po;
+            j.partials = bm.partials.as<float>() + 32 * co;
+            j.st = bm.states.as<RegState>() + b;
+            j.mode = REG_MODE_SOLVE;
+            j.use_cond = 0;
+            jobs_h[b] = j;
+            running += n[b] > 0;
+            po += n[b];
+            co += (n[b] + 255) / 256;
+        }
+        *queue_h = BatchQueue{0u, (unsigned)chunks, (unsigned)running, 0u};
+    }
+    GSICP_CUDA(cudaMemcpyAsync(bm.counts.ptr, counts_h, sizeof(int) * B, cudaMemcpyHostToDevice, s));
+    // Morton-ordered copy of every source and its covariances, and the first-iteration seeds; the
+    // largest first, so the shared scratch index is sized once
+    std::vector<int> order(B);
+    for (int b = 0; b < B; ++b) order[b] = b;
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return n[a] > n[c]; });
+    std::vector<int64_t> pofs(B);
+    {
+        int64_t po = 0;
+        for (int b = 0; b < B; ++b) { pofs[b] = po; po += n[b]; }
+    }
+    for (int b : order) {
+        if (n[b] == 0) continue;
+        const int* nd = bm.counts.as<int>() + b;
+        float4* src_b = bm.src.as<float4>() + pofs[b];
+        GSICP_CHECK(build_index(src_pts_dev[b], nullptr, (int)n[b], nd, 32, ctx->src_index, ctx->build, s));
+        GSICP_CUDA(cudaMemcpyAsync(src_b, ctx->src_index.pts.ptr, sizeof(float4) * n[b], cudaMemcpyDeviceToDevice, s));
+        GSICP_CHECK(launch_permute_covs(ctx->src_index.view(), src_covs_dev[b], (int)n[b],
+                                        bm.covs.as<float4>() + 2 * pofs[b], s));
+        GSICP_CHECK(launch_seed(maps[b]->index.view(), src_b, nd, (int)n[b], T0 + 16l * b,
+                                bm.cand.as<int>() + KC * pofs[b], bm.anchor.as<float4>() + pofs[b], s));
+    }
+    GSICP_CUDA(cudaMemcpyAsync(bm.jobs.ptr, jobs_h, sizeof(RegJob) * B, cudaMemcpyHostToDevice, s));
+    GSICP_CUDA(cudaMemcpyAsync(bm.T0.ptr, T0_h, sizeof(Pose16) * B, cudaMemcpyHostToDevice, s));
+    GSICP_CUDA(cudaMemcpyAsync(bm.offsets.ptr, offsets_h, sizeof(unsigned) * B, cudaMemcpyHostToDevice, s));
+    GSICP_CUDA(cudaMemcpyAsync(bm.queue.ptr, queue_h, sizeof(BatchQueue), cudaMemcpyHostToDevice, s));
+    GSICP_CHECK(batch_run(bm.jobs.as<const RegJob>(), B, bm.T0.as<const Pose16>(), bm.offsets.as<const unsigned>(),
+                          bm.queue.as<BatchQueue>(), bm.items.as<unsigned long long>(), (unsigned)capacity, s));
+    GSICP_CUDA(cudaMemcpyAsync(states_h, bm.states.ptr, sizeof(RegState) * B, cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaMemcpyAsync(queue_h, bm.queue.ptr, sizeof(BatchQueue), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b) {
+        const RegState& st = states_h[b];
+        memcpy(T_out + 16l * b, st.T, sizeof(double) * 16);
+        if (iters_out) iters_out[b] = st.iter;
+        if (cost_out) cost_out[b] = st.cost;
+        if (inliers_out) inliers_out[b] = st.inliers;
+        if (status_out) status_out[b] = st.status == REG_ST_DEGENERATE ? GSICP_ERR_DEGENERATE : GSICP_OK;
+    }
+    if (queue_h->error) return set_error(GSICP_ERR_TIMEOUT, "gsicp_register_batch: a work-queue wait ran out");
+    return GSICP_OK;
 }
 
 gsicp_status gsicp_linearise(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev, int64_t n,

@@ -260,6 +260,14 @@ constexpr int REG_STATS = 64;
 
 constexpr int KC = 8;  // map candidates cached per source point
 
+// Work queue of a batched registration (device memory, zeroed except as set by the host).
+struct BatchQueue {
+    unsigned int head;     // next slot to claim
+    unsigned int tail;     // slots reserved so far
+    unsigned int running;  // pairs not yet retired
+    unsigned int error;    // a wait exceeded its bound
+};
+
 struct RegJob {
     const float4* src;     // source points in Morton order (x, y, z, original index), n
     const float4* covs_s;  // their covariances in the same order, 2 float4 each (xx,xy,xz,yy | yz,zz,-,-)

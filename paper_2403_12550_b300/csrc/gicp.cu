@@ -697,6 +697,143 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
 }
 
 // ---------------------------------------------------------------------------------------------
+// Batched registration: many independent pairs in one persistent launch.
+//
+// Work items are (pair, 256-point chunk) of a pair's current iteration, taken from a device queue
+// (an append-only array of 64-bit items, empty slots all ones).  Resident blocks claim slots in
+// order (atomic head) and wait, with a bounded spin, for a claimed slot to be filled.  The block
+// that finishes a pair's last chunk of an iteration sums that pair's chunk partials in chunk order,
+// solves and updates its pose (finalize, as in the single registration) and, if the pair goes on,
+// appends the chunks of its next iteration; otherwise it retires the pair.  Pairs thus advance
+// independently (a small pair does not wait for a large one), there is no grid-wide barrier, and
+// every pair's sums are taken in the same order as gsicp_register's, so each pair's result is
+// bit-identical to registering it alone.  Blocks leave when every pair has retired, or when a
+// wait exceeds its bound (error flag: the host reports GSICP_ERR_TIMEOUT).
+constexpr unsigned long long BATCH_EMPTY = ~0ull;
+constexpr unsigned BATCH_SPIN_LIMIT = 1u << 22;  // polls of ~0.25 us each: ~1 s before giving up
+
+__global__ void __launch_bounds__(REG_THREADS, 3) gicp_batch_kernel(const RegJob* __restrict__ jobs,
+                                                                 BatchQueue* __restrict__ q,
+                                                                 unsigned long long* __restrict__ items,
+                                                                 unsigned capacity)
+{
+    __shared__ long long s_item;
+    __shared__ unsigned s_base;
+    __shared__ bool s_last;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long got = -1;
+            const unsigned idx = atomicAdd(&q->head, 1u);
+            if (idx < capacity) {
+                for (unsigned spin = 0;; ++spin) {
+                    const unsigned long long v = __ldcg(items + idx);
+                    if (v != BATCH_EMPTY) {
+                        got = (long long)v;
+                        break;
+                    }
+                    if (__ldcg(&q->running) == 0u) break;  // every pair has retired: nothing will come
+                    if (spin >= BATCH_SPIN_LIMIT) {
+                        atomicExch(&q->error, 1u);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            __threadfence();  // the pair's state was written before its item was published
+            s_item = got;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item < 0) return;
+        const int b = (int)(item >> 32), c = (int)(item & 0xffffffffll);
+        const RegJob& J = jobs[b];
+        RegState* st = J.st;
+        const int n = *J.n, nmap = *J.map.n;
+        const int nchunks = (n + REG_THREADS - 1) / REG_THREADS;
+        const int it_now = __ldcg(&st->iter);
+        float R[9], t[3], Rl[9], tl[3];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            R[a] = __ldcg(&st->Rf[a]);
+            Rl[a] = __ldcg(&st->Rlo[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t[a] = __ldcg(&st->tf[a]);
+            tl[a] = __ldcg(&st->tlo[a]);
+        }
+        float acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
+        const int s = c * REG_THREADS + threadIdx.x;
+        int refreshed = 0;
+        if (s < n) refreshed = gn_point(J, R, Rl, t, tl, s, nmap, acc);
+        block_partial(acc, refreshed, J.partials + 32l * c);
+        if (threadIdx.x == 0) s_last = atomicAdd(&st->counter, 1u) == (unsigned)nchunks - 1u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const bool more = finalize(J, st, J.partials, nchunks, it_now, 0ull);
+            __threadfence();  // the new pose and status before the next items
+            __syncthreads();
+            if (threadIdx.x == 0) s_base = more ? atomicAdd(&q->tail, (unsigned)nchunks) : 0xffffffffu;
+            __syncthreads();
+            if (s_base != 0xffffffffu) {
+                for (int j = threadIdx.x; j < nchunks; j += REG_THREADS)
+                    if (s_base + (unsigned)j < capacity) items[s_base + j] = ((unsigned long long)b << 32) | (unsigned)j;
+            } else if (threadIdx.x == 0) {
+                __threadfence();
+                atomicSub(&q->running, 1u);
+            }
+        }
+        __syncthreads();  // shared item slots are reused by the next claim
+    }
+}
+
+// Per pair: initial state (as reg_setup_kernel), and the iteration-0 items of every pair with
+// points, written at offsets[b]; block b handles pair b.
+__global__ void batch_setup_kernel(const RegJob* __restrict__ jobs, const Pose16* __restrict__ T0, int B,
+                                   const unsigned* __restrict__ offsets, unsigned long long* __restrict__ items)
+{
+    const int b = blockIdx.x;
+    if (b >= B) return;
+    const RegJob& J = jobs[b];
+    RegState* st = J.st;
+    const int n = *J.n;
+    const int nchunks = (n + REG_THREADS - 1) / REG_THREADS;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 16; ++i) st->T[i] = T0[b].v[i];
+        for (int i = 0; i < 36; ++i) st->H[i] = 0.0;
+        for (int i = 0; i < 6; ++i) st->b[i] = 0.0;
+        st->cost = 0.0;
+        st->inliers = 0;
+        st->iter = 0;
+        st->status = n > 0 ? REG_ST_RUNNING : REG_ST_DEGENERATE;
+        st->counter = 0u;
+        for (int i = 0; i < REG_STATS; ++i) {
+            st->refreshes[i] = st->tail_ns[i] = st->solve_ns[i] = 0;
+            st->t_first[i] = ~0ull;
+            st->t_arrive[i] = 0ull;
+        }
+        pose_to_float(st);
+    }
+    for (int j = threadIdx.x; j < nchunks; j += blockDim.x)
+        items[offsets[b] + j] = ((unsigned long long)b << 32) | (unsigned)j;
+}
+
+gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, const unsigned* offsets_dev,
+                       BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s)
+{
+    if (B <= 0) return GSICP_OK;
+    GSICP_CUDA(cudaMemsetAsync(items, 0xff, sizeof(unsigned long long) * (size_t)capacity, s));
+    batch_setup_kernel<<<B, 256, 0, s>>>(jobs_dev, T0_dev, B, offsets_dev, items);
+    const int grid = device_sm_count() * 3;  // resident blocks (launch bounds)
+    gicp_batch_kernel<<<grid, REG_THREADS, 0, s>>>(jobs_dev, q_dev, items, capacity);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
 
 gsicp_status RegMachine::init(int capacity)
 {
@@ -733,6 +870,15 @@ gsicp_status RegMachine::init(int capacity)
     GSICP_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
     GSICP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     return GSICP_OK;
+}
+
+void BatchMachine::release()
+{
+    src.release(); covs.release(); cand.release(); anchor.release(); partials.release(); counts.release();
+    jobs.release(); states.release(); T0.release(); offsets.release(); queue.release(); items.release();
+    if (host) cudaFreeHost(host);
+    host = nullptr;
+    host_bytes = 0;
 }
 
 void RegMachine::release()

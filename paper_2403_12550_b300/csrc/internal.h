@@ -107,6 +107,20 @@ struct RegMachine {
 gsicp_status reg_run(RegMachine& rm, const RegJob& job, const double T0[16], int n_cap, bool solve,
                      cudaStream_t s);
 
+// Batched registration (one persistent launch over B jobs; see gicp.cu).  items: capacity slots;
+// offsets_dev[b]: first slot of pair b's iteration-0 items; q_dev: head = 0, tail = total
+// iteration-0 items, running = pairs with points, error = 0.
+gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, const unsigned* offsets_dev,
+                       BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s);
+
+// Buffers of batched registrations (grown on demand, kept by the context).
+struct BatchMachine {
+    DevBuf src, covs, cand, anchor, partials, counts, jobs, states, T0, offsets, queue, items;
+    void* host = nullptr;  // pinned staging: jobs, poses, counts, offsets, queue, states
+    size_t host_bytes = 0;
+    void release();
+};
+
 gsicp_status launch_nearest(const IndexView& map, const float* q, int nq, float max_d2, int32_t* idx,
                             float* d2, cudaStream_t s);
 
@@ -128,6 +142,7 @@ struct gsicp_ctx_s {
     gsicp::DevBuf frame_idx, fb_list, fb_count;  // sample -> point map; tree-search list of the window k-NN
     gsicp::DevBuf covs_sorted;         // source covariances in the source index's order
     gsicp::RegMachine reg;
+    gsicp::BatchMachine batch;
     int64_t* host_pinned = nullptr;   // small pinned scratch for counts
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

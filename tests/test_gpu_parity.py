@@ -418,6 +418,49 @@ def test_track_frame_empty_depth(g, ctx):
     assert r["status"] == g.ERR_DEGENERATE and r["n_points"] == 0
 
 
+# ----------------------------------------------------------------------------- batched registration
+
+def test_register_batch_equals_single_and_oracle(g, ctx):
+    """Pairs of uneven sizes (incl. an empty source and one below a chunk) in one persistent
+    launch: each pair's result equals gsicp_register on it alone, bit for bit, and the oracle's
+    within the pose bar."""
+    sizes = [6000, 0, 150, 23000, 1200, 9000, 40]
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    pairs, maps = [], []
+    for b, n in enumerate(sizes):
+        src, cs, tgt, ct, T_gt = config1_inputs(b % 5, b % 3, n=max(n, 300))
+        src, cs = src[:n], cs[:n]
+        pairs.append((src, cs, tgt, ct))
+        maps.append(g.gsicp_build_map_index(ctx, cu(tgt), cu(ct)))
+    T0s = np.stack([random_offset(np.random.default_rng(50 + b), 1.0, 0.01) for b in range(len(sizes))])
+    rb = g.gsicp_register_batch(ctx, [cu(p[0]).reshape(-1, 3) for p in pairs], [cu(p[1]).reshape(-1, 6) for p in pairs],
+                                maps, T0s, rp)
+    for b, (src, cs, tgt, ct) in enumerate(pairs):
+        if len(src) == 0:
+            assert rb["status"][b] == g.ERR_DEGENERATE and rb["iters"][b] == 0
+            np.testing.assert_array_equal(rb["T"][b], T0s[b])
+            continue
+        rs = g.gsicp_register(ctx, cu(src), cu(cs), maps[b], T0s[b], rp)
+        assert rb["status"][b] == rs["status"], b
+        np.testing.assert_array_equal(rb["T"][b], rs["T"])
+        assert rb["iters"][b] == rs["iters"] and rb["inliers"][b] == rs["inliers"] and rb["cost"][b] == rs["cost"]
+        if rs["status"] == g.OK and len(src) >= 1000:
+            ro = orc.register(src, cs, orc.Map(tgt, ct), T0s[b], 0.1, 30, 1e-6, 1e-6, 6)
+            dr, dt = pose_diff(rb["T"][b], ro["T"])
+            assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (b, dr, dt)
+    # a second batch on the same context reuses its buffers and gives the same answer
+    rb2 = g.gsicp_register_batch(ctx, [cu(p[0]).reshape(-1, 3) for p in pairs], [cu(p[1]).reshape(-1, 6) for p in pairs],
+                                 maps, T0s, rp)
+    np.testing.assert_array_equal(rb2["T"], rb["T"])
+    for m in maps:
+        m.close()
+
+
+def test_register_batch_empty(g, ctx):
+    r = g.gsicp_register_batch(ctx, [], [], [], np.zeros((0, 4, 4)), g.RegParams())
+    assert r["T"].shape == (0, 4, 4)
+
+
 # ----------------------------------------------------------------------------- a1+a2+a3 of a depth frame
 
 def _frame_cases():
