@@ -29,6 +29,7 @@ __all__ = [
     "look_pose", "circle_poses", "random_offset", "rot_axis_angle", "inv_pose", "make_pose",
     "transform_points", "Intrinsics", "REPLICA_INTR", "TUM_INTR",
     "pair_config1", "frame_config2", "spline_trajectory", "sequence_config3", "const_velocity",
+    "batch_config4",
 ]
 
 
@@ -388,3 +389,23 @@ def const_velocity(T_prev: np.ndarray, T_prev2: np.ndarray | None) -> np.ndarray
     U, _, Vt = np.linalg.svd(T[:3, :3])
     T[:3, :3] = U @ Vt
     return T
+
+
+def batch_config4(seed: int, n_pairs: int = 64, n_min: int = 5_000, n_max: int = 300_000,
+                  max_deg: float = 5.0, max_m: float = 0.05, noise: float = 2e-3) -> list:
+    """Independent config-1-style registration pairs with point counts log-uniform in
+    [n_min, n_max] and offsets of uniform angle <= max_deg about a uniform axis and uniform
+    length <= max_m.  Each entry: dict(src, tgt float32 n x 3, T_gt), the source in the frame
+    T_gt^-1 (start from the identity)."""
+    rng = np.random.default_rng(31337 + seed)
+    out = []
+    for b in range(n_pairs):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        scene = make_room(int(rng.integers(0, 1 << 30)))
+        prng = np.random.default_rng(int(rng.integers(0, 1 << 62)))
+        src_w = sample_surface(scene, n, prng, noise)
+        tgt = sample_surface(scene, n, prng, noise)
+        T_gt = random_offset(prng, prng.uniform(0.0, max_deg), prng.uniform(0.0, max_m))
+        out.append(dict(src=transform_points(inv_pose(T_gt), src_w).astype(np.float32), tgt=tgt.astype(np.float32),
+                        T_gt=T_gt))
+    return out
