@@ -392,22 +392,10 @@ BATCH_METRIC = "batched G-ICP registrations/s (independent pairs, 5k-300k points
 
 
 def batch_launches(n_pts) -> int:
-    """Kernels one gsicp_register_batch call launches: per pair with points, its source index
-    (bbox 2, quantise 1, Morton keys 1, 4 radix passes x 5, gather 1, leaf boxes 1, box levels),
-    the covariance reorder and the seed; then the set-up and the persistent kernel."""
-    total = 2
-    for n in n_pts:
-        if n <= 0:
-            continue
-        leaves = 1
-        while leaves < (n + 31) // 32:
-            leaves *= 2
-        levels, count = 0, leaves
-        while count > 1:
-            count //= min(256, count)
-            levels += 1
-        total += 4 + (20 if n > 1 else 0) + 2 + levels + 2
-    return total
+    """Kernels one gsicp_register_batch call launches: the joint Morton order of all sources (bbox
+    2, quantise 1, keys 1, 4 radix passes x 5, cloud keys 1, 2 radix passes x 5, gather 1), the
+    seeds 1, the set-up 1 and the persistent kernel 1."""
+    return 39 if int(np.sum(n_pts)) > 1 else 3
 
 
 def run_batch(args, world, rank, local):

@@ -460,11 +460,15 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
     GSICP_CHECK(bm.offsets.ensure(sizeof(unsigned) * B));
     GSICP_CHECK(bm.queue.ensure(sizeof(BatchQueue)));
     GSICP_CHECK(bm.items.ensure(sizeof(unsigned long long) * (size_t)std::max<int64_t>(capacity, 1)));
-    // pinned staging, laid out: jobs | states | poses | counts | offsets | queue
+    GSICP_CHECK(bm.ptrs.ensure(sizeof(float*) * 2 * B));
+    GSICP_CHECK(bm.pofs.ensure(sizeof(int64_t) * (B + 1)));
+    // pinned staging, laid out: jobs | states | poses | counts | offsets | queue | pointers | point offsets
     const size_t off_states = sizeof(RegJob) * B, off_T0 = off_states + sizeof(RegState) * B,
                  off_counts = off_T0 + sizeof(Pose16) * B, off_offsets = off_counts + sizeof(int) * B,
                  off_queue = (off_offsets + sizeof(unsigned) * B + 15) / 16 * 16,
-                 host_need = off_queue + sizeof(BatchQueue);
+                 off_ptrs = off_queue + 16 * ((sizeof(BatchQueue) + 15) / 16),
+                 off_pofs = off_ptrs + sizeof(float*) * 2 * B,
+                 host_need = off_pofs + sizeof(int64_t) * (B + 1);
     if (bm.host_bytes < host_need) {
         if (bm.host) GSICP_CUDA(cudaFreeHost(bm.host));
         bm.host = nullptr;
@@ -502,32 +506,32 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
         }
         *queue_h = BatchQueue{0u, (unsigned)chunks, (unsigned)running, 0u};
     }
-    GSICP_CUDA(cudaMemcpyAsync(bm.counts.ptr, counts_h, sizeof(int) * B, cudaMemcpyHostToDevice, s));
-    // Morton-ordered copy of every source and its covariances, and the first-iteration seeds; the
-    // largest first, so the shared scratch index is sized once
-    std::vector<int> order(B);
-    for (int b = 0; b < B; ++b) order[b] = b;
-    std::sort(order.begin(), order.end(), [&](int a, int c) { return n[a] > n[c]; });
-    std::vector<int64_t> pofs(B);
+    // Morton-ordered copy of every source and its covariances (all clouds in one sort), then the
+    // first-iteration seeds of every pair
+    const float** ptr_h = reinterpret_cast<const float**>(hb + off_ptrs);
+    int64_t* pofs_h = reinterpret_cast<int64_t*>(hb + off_pofs);
     {
         int64_t po = 0;
-        for (int b = 0; b < B; ++b) { pofs[b] = po; po += n[b]; }
+        for (int b = 0; b < B; ++b) {
+            ptr_h[b] = n[b] > 0 ? src_pts_dev[b] : nullptr;
+            ptr_h[B + b] = n[b] > 0 ? src_covs_dev[b] : nullptr;
+            pofs_h[b] = po;
+            po += n[b];
+        }
+        pofs_h[B] = po;
     }
-    for (int b : order) {
-        if (n[b] == 0) continue;
-        const int* nd = bm.counts.as<int>() + b;
-        float4* src_b = bm.src.as<float4>() + pofs[b];
-        GSICP_CHECK(build_index(src_pts_dev[b], nullptr, (int)n[b], nd, 32, ctx->src_index, ctx->build, s));
-        GSICP_CUDA(cudaMemcpyAsync(src_b, ctx->src_index.pts.ptr, sizeof(float4) * n[b], cudaMemcpyDeviceToDevice, s));
-        GSICP_CHECK(launch_permute_covs(ctx->src_index.view(), src_covs_dev[b], (int)n[b],
-                                        bm.covs.as<float4>() + 2 * pofs[b], s));
-        GSICP_CHECK(launch_seed(maps[b]->index.view(), src_b, nd, (int)n[b], T0 + 16l * b,
-                                bm.cand.as<int>() + KC * pofs[b], bm.anchor.as<float4>() + pofs[b], s));
-    }
+    GSICP_CUDA(cudaMemcpyAsync(bm.counts.ptr, counts_h, sizeof(int) * B, cudaMemcpyHostToDevice, s));
+    GSICP_CUDA(cudaMemcpyAsync(bm.ptrs.ptr, ptr_h, sizeof(float*) * 2 * B, cudaMemcpyHostToDevice, s));
+    GSICP_CUDA(cudaMemcpyAsync(bm.pofs.ptr, pofs_h, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemcpyAsync(bm.jobs.ptr, jobs_h, sizeof(RegJob) * B, cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemcpyAsync(bm.T0.ptr, T0_h, sizeof(Pose16) * B, cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemcpyAsync(bm.offsets.ptr, offsets_h, sizeof(unsigned) * B, cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemcpyAsync(bm.queue.ptr, queue_h, sizeof(BatchQueue), cudaMemcpyHostToDevice, s));
+    const float* const* ptrs_dev = bm.ptrs.as<const float* const>();
+    GSICP_CHECK(batch_morton_order(ptrs_dev, ptrs_dev + B, bm.pofs.as<const int64_t>(), B, (long)total,
+                                   bm.src.as<float4>(), bm.covs.as<float4>(), ctx->build, bm.quant, s));
+    GSICP_CHECK(launch_batch_seed(bm.jobs.as<const RegJob>(), bm.T0.as<const Pose16>(), bm.pofs.as<const int64_t>(),
+                                  B, (long)total, s));
     GSICP_CHECK(batch_run(bm.jobs.as<const RegJob>(), B, bm.T0.as<const Pose16>(), bm.offsets.as<const unsigned>(),
                           bm.queue.as<BatchQueue>(), bm.items.as<unsigned long long>(), (unsigned)capacity, s));
     GSICP_CUDA(cudaMemcpyAsync(states_h, bm.states.ptr, sizeof(RegState) * B, cudaMemcpyDeviceToHost, s));

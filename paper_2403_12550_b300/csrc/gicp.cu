@@ -876,6 +876,7 @@ void BatchMachine::release()
 {
     src.release(); covs.release(); cand.release(); anchor.release(); partials.release(); counts.release();
     jobs.release(); states.release(); T0.release(); offsets.release(); queue.release(); items.release();
+    ptrs.release(); pofs.release(); quant.release();
     if (host) cudaFreeHost(host);
     host = nullptr;
     host_bytes = 0;
@@ -1016,35 +1017,71 @@ gsicp_status launch_transform(const double T[16], const float* pts, const float*
     return GSICP_OK;
 }
 
+// Morton-key seed of one source point (see seed_kernel); R, t: the start pose in float.
+__device__ __forceinline__ void seed_point(const IndexView& map, int m, float4 qz, const float (&Rt)[12],
+                                           const float4 x, long s, int* __restrict__ cand,
+                                           float4* __restrict__ anchor)
+{
+    int seed = -1;
+    if (m > 0 && map.keys && map.cell) {
+        const float y0 = fmaf(Rt[0], x.x, fmaf(Rt[1], x.y, fmaf(Rt[2], x.z, Rt[3])));
+        const float y1 = fmaf(Rt[4], x.x, fmaf(Rt[5], x.y, fmaf(Rt[6], x.z, Rt[7])));
+        const float y2 = fmaf(Rt[8], x.x, fmaf(Rt[9], x.y, fmaf(Rt[10], x.z, Rt[11])));
+        const uint32_t key = morton_of(qz, y0, y1, y2);
+        const uint32_t pre = key >> (30 - SEED_BITS);
+        int lo = map.cell[pre], hi = map.cell[pre + 1];
+        while (lo < hi) {  // Morton-nearest position within the query's cell
+            const int mid = (lo + hi) >> 1;
+            if (map.keys[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        seed = min(lo, m - 1);
+    }
+    reinterpret_cast<int4*>(cand)[2l * s] = make_int4(seed, -1, -1, -1);
+    reinterpret_cast<int4*>(cand)[2l * s + 1] = make_int4(-1, -1, -1, -1);
+    anchor[s] = make_float4(0.f, 0.f, 0.f, -2.f);  // no previous search
+}
+
+__global__ void batch_seed_kernel(const RegJob* __restrict__ jobs, const Pose16* __restrict__ T0,
+                                  const int64_t* __restrict__ ofs, int B, long N)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = B;  // job of point i (as cloud_of)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ofs[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const RegJob& J = jobs[lo];
+        const Pose16& T = T0[lo];
+        float Rt[12];
+#pragma unroll
+        for (int a = 0; a < 12; ++a) Rt[a] = (float)T.v[a];
+        const long s = i - ofs[lo];
+        seed_point(J.map, *J.map.n, *J.map.quant, Rt, J.src[s], s, J.cand, J.anchor);
+    }
+}
+
+gsicp_status launch_batch_seed(const RegJob* jobs_dev, const Pose16* T0_dev, const int64_t* ofs_dev, int B, long N,
+                               cudaStream_t s)
+{
+    if (N <= 0) return GSICP_OK;
+    const int grid = (int)std::max<long>(1, std::min<long>((N + 255) / 256, device_sm_count() * 8));
+    batch_seed_kernel<<<grid, 256, 0, s>>>(jobs_dev, T0_dev, ofs_dev, B, N);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
 __global__ void seed_kernel(IndexView map, const float4* __restrict__ src, const int* __restrict__ n_dev, Pose16 T,
                             int* __restrict__ cand, float4* __restrict__ anchor)
 {
     const int n = *n_dev, m = *map.n;
     const float4 qz = *map.quant;
-    const float R0 = (float)T.v[0], R1 = (float)T.v[1], R2 = (float)T.v[2], t0 = (float)T.v[3];
-    const float R3 = (float)T.v[4], R4 = (float)T.v[5], R5 = (float)T.v[6], t1 = (float)T.v[7];
-    const float R6 = (float)T.v[8], R7 = (float)T.v[9], R8 = (float)T.v[10], t2 = (float)T.v[11];
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        int seed = -1;
-        if (m > 0 && map.keys && map.cell) {
-            const float4 x = src[s];
-            const float y0 = fmaf(R0, x.x, fmaf(R1, x.y, fmaf(R2, x.z, t0)));
-            const float y1 = fmaf(R3, x.x, fmaf(R4, x.y, fmaf(R5, x.z, t1)));
-            const float y2 = fmaf(R6, x.x, fmaf(R7, x.y, fmaf(R8, x.z, t2)));
-            const uint32_t key = morton_of(qz, y0, y1, y2);
-            const uint32_t pre = key >> (30 - SEED_BITS);
-            int lo = map.cell[pre], hi = map.cell[pre + 1];
-            while (lo < hi) {  // Morton-nearest position within the query's cell
-                const int mid = (lo + hi) >> 1;
-                if (map.keys[mid] < key) lo = mid + 1;
-                else hi = mid;
-            }
-            seed = min(lo, m - 1);
-        }
-        reinterpret_cast<int4*>(cand)[2l * s] = make_int4(seed, -1, -1, -1);
-        reinterpret_cast<int4*>(cand)[2l * s + 1] = make_int4(-1, -1, -1, -1);
-        anchor[s] = make_float4(0.f, 0.f, 0.f, -2.f);  // no previous search
-    }
+    float Rt[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) Rt[a] = (float)T.v[a];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        seed_point(map, m, qz, Rt, src[s], s, cand, anchor);
 }
 
 gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_dev, int cap, const double T0[16],

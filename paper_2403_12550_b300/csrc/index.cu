@@ -495,6 +495,133 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
     return GSICP_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Batched Morton order of B clouds (batched registration).  Each cloud gets exactly the order
+// build_index gives it alone -- 30-bit Morton keys over its own bounding cube, stable sort, ties
+// in original order -- by sorting all clouds' keys together and then, stably, by cloud.
+
+// Cloud of global point i: the last b with ofs[b] <= i (empty clouds have equal offsets).
+__device__ __forceinline__ int cloud_of(const int64_t* __restrict__ ofs, int B, long i)
+{
+    int lo = 0, hi = B;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ofs[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void seg_bbox_init_kernel(uint32_t* __restrict__ bb, int B)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 6 * B; t += gridDim.x * blockDim.x)
+        bb[t] = (t % 6) < 3 ? 0xffffffffu : 0u;
+}
+
+__global__ void seg_bbox_kernel(const float* const* __restrict__ ptrs, const int64_t* __restrict__ ofs, int B,
+                                long N, uint32_t* __restrict__ bb)
+{
+    for (long i0 = (long)blockIdx.x * blockDim.x; i0 < N; i0 += (long)gridDim.x * blockDim.x) {
+        const long i = i0 + threadIdx.x;
+        const bool in = i < N;
+        const int b = in ? cloud_of(ofs, B, i) : -1;
+        float v[3] = {0.f, 0.f, 0.f};
+        if (in) {
+            const float* p = ptrs[b] + 3l * (i - ofs[b]);
+            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
+        }
+        // lanes of the same cloud combine first (order-preserving integer encoding), then one
+        // atomic per cloud and warp
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t lo = __reduce_min_sync(peers, f2ord(v[a]));
+            const uint32_t hi = __reduce_max_sync(peers, f2ord(v[a]));
+            if (in && lane == leader) {
+                atomicMin(&bb[6 * b + a], lo);
+                atomicMax(&bb[6 * b + 3 + a], hi);
+            }
+        }
+    }
+}
+
+__global__ void seg_quant_kernel(const uint32_t* __restrict__ bb, int B, float4* __restrict__ quant)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint32_t* q = bb + 6 * b;
+    const float lx = ord2f(q[0]), ly = ord2f(q[1]), lz = ord2f(q[2]);
+    const float ext = fmaxf(fmaxf(ord2f(q[3]) - lx, ord2f(q[4]) - ly), ord2f(q[5]) - lz);
+    quant[b] = make_float4(lx, ly, lz, ext > 0.f ? 1024.f / ext : 0.f);  // as quant_kernel with no cell
+}
+
+__global__ void seg_morton_kernel(const float* const* __restrict__ ptrs, const int64_t* __restrict__ ofs, int B,
+                                  long N, const float4* __restrict__ quant, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const int b = cloud_of(ofs, B, i);
+        const float* p = ptrs[b] + 3l * (i - ofs[b]);
+        keys[i] = morton_of(quant[b], p[0], p[1], p[2]);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void seg_cloud_keys_kernel(const uint32_t* __restrict__ vals, const int64_t* __restrict__ ofs, int B,
+                                      long N, uint32_t* __restrict__ keys)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+        keys[i] = (uint32_t)cloud_of(ofs, B, vals[i]);
+}
+
+__global__ void seg_gather_kernel(const float* const* __restrict__ pts, const float* const* __restrict__ covs,
+                                  const int64_t* __restrict__ ofs, int B, long N, const uint32_t* __restrict__ vals,
+                                  float4* __restrict__ src_out, float4* __restrict__ covs_out)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const long gi = vals[i];
+        const int b = cloud_of(ofs, B, gi);
+        const long li = gi - ofs[b];
+        const float* p = pts[b] + 3 * li;
+        src_out[i] = make_float4(p[0], p[1], p[2], __int_as_float((int)li));
+        const float* c = covs[b] + 6 * li;
+        covs_out[2 * i] = make_float4(c[0], c[1], c[2], c[3]);
+        covs_out[2 * i + 1] = make_float4(c[4], c[5], 0.f, 0.f);
+    }
+}
+
+gsicp_status batch_morton_order(const float* const* pts_dev, const float* const* covs_dev, const int64_t* ofs_dev,
+                                int B, long N, float4* src_out, float4* covs_out, BuildScratch& scr, DevBuf& quant,
+                                cudaStream_t s)
+{
+    if (N <= 0) return GSICP_OK;
+    if (N > INT32_MAX) return GSICP_ERR_INVALID_ARG;
+    GSICP_CHECK(scr.k0.ensure(sizeof(uint32_t) * N));
+    GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * N));
+    GSICP_CHECK(scr.v0.ensure(sizeof(uint32_t) * N));
+    GSICP_CHECK(scr.v1.ensure(sizeof(uint32_t) * N));
+    GSICP_CHECK(scr.bbox.ensure(sizeof(uint32_t) * 6 * (size_t)B));
+    GSICP_CHECK(quant.ensure(sizeof(float4) * (size_t)B));
+    const int sms = device_sm_count();
+    const int grid = (int)std::max<long>(1, std::min<long>((N + 255) / 256, sms * 8));
+    seg_bbox_init_kernel<<<(6 * B + 255) / 256, 256, 0, s>>>(scr.bbox.as<uint32_t>(), B);
+    seg_bbox_kernel<<<grid, 256, 0, s>>>(pts_dev, ofs_dev, B, N, scr.bbox.as<uint32_t>());
+    seg_quant_kernel<<<(B + 255) / 256, 256, 0, s>>>(scr.bbox.as<uint32_t>(), B, quant.as<float4>());
+    seg_morton_kernel<<<grid, 256, 0, s>>>(pts_dev, ofs_dev, B, N, quant.as<float4>(), scr.k0.as<uint32_t>(),
+                                           scr.v0.as<uint32_t>());
+    GSICP_CUDA(cudaGetLastError());
+    GSICP_CHECK(radix_sort_pairs(scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
+                                 scr.v1.as<uint32_t>(), (int)N, 30, scr.hist, scr.sums, s));
+    seg_cloud_keys_kernel<<<grid, 256, 0, s>>>(scr.v0.as<uint32_t>(), ofs_dev, B, N, scr.k0.as<uint32_t>());
+    GSICP_CHECK(radix_sort_pairs(scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
+                                 scr.v1.as<uint32_t>(), (int)N, B <= 256 ? 8 : 16, scr.hist, scr.sums, s));
+    seg_gather_kernel<<<grid, 256, 0, s>>>(pts_dev, covs_dev, ofs_dev, B, N, scr.v0.as<uint32_t>(), src_out,
+                                           covs_out);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
 IndexView IndexBufs::view() const
 {
     IndexView v;

@@ -107,6 +107,18 @@ struct RegMachine {
 gsicp_status reg_run(RegMachine& rm, const RegJob& job, const double T0[16], int n_cap, bool solve,
                      cudaStream_t s);
 
+// Morton order of B clouds at once (pts_dev / covs_dev: device arrays of B pointers; ofs_dev: B + 1
+// offsets of each cloud in the concatenated order, N = ofs[B]): src_out (N float4: x, y, z, index
+// within the cloud) and covs_out (2N float4) hold each cloud, in build_index's order for it alone,
+// at its offset.  quant: scratch.
+gsicp_status batch_morton_order(const float* const* pts_dev, const float* const* covs_dev, const int64_t* ofs_dev,
+                                int B, long N, float4* src_out, float4* covs_out, BuildScratch& scr, DevBuf& quant,
+                                cudaStream_t s);
+
+// First-iteration seeds of the B jobs' points at once (as launch_seed for each; ofs_dev as above).
+gsicp_status launch_batch_seed(const RegJob* jobs_dev, const Pose16* T0_dev, const int64_t* ofs_dev, int B, long N,
+                               cudaStream_t s);
+
 // Batched registration (one persistent launch over B jobs; see gicp.cu).  items: capacity slots;
 // offsets_dev[b]: first slot of pair b's iteration-0 items; q_dev: head = 0, tail = total
 // iteration-0 items, running = pairs with points, error = 0.
@@ -116,6 +128,7 @@ gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, cons
 // Buffers of batched registrations (grown on demand, kept by the context).
 struct BatchMachine {
     DevBuf src, covs, cand, anchor, partials, counts, jobs, states, T0, offsets, queue, items;
+    DevBuf ptrs, pofs, quant;  // cloud pointer tables, point offsets, per-cloud quantisation
     void* host = nullptr;  // pinned staging: jobs, poses, counts, offsets, queue, states
     size_t host_bytes = 0;
     void release();
