@@ -262,6 +262,12 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
                                   double* cost_out, int64_t* inliers_out, int* status_out,
                                   void* stream);
 
+/* Self-test of the batch queue's bounded wait (no counterpart in the paper): runs the batch
+ * kernel on a queue that claims one pair is running but never receives an item, so every
+ * block's wait runs out after about a second.  Returns GSICP_ERR_TIMEOUT when the bound works
+ * (the context stays usable), GSICP_OK if the waits somehow ended without it. */
+gsicp_status gsicp_selftest_batch_timeout(gsicp_ctx ctx, void* stream);
+
 /* One linearisation at pose T (no update): H (6x6), b, cost and inlier count as in
  * gsicp_register's first iteration.  corr_dev (n int32, nullable) receives each source point's
  * map index (-1 if none).  Synchronises the stream. */

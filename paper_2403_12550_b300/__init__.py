@@ -21,7 +21,7 @@ __all__ = [
     "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
     "gsicp_build_map_index", "gsicp_map_append",
-    "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_linearise",
+    "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_selftest_batch_timeout", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
 ]
 
@@ -106,6 +106,7 @@ _sig("gsicp_register", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(R
                                  C.POINTER(C.c_int), _dp, _i64p, _vp])
 _sig("gsicp_register_batch", C.c_int, [_vp, C.c_int, _vp, _vp, _i64p, _vp, _dp, C.POINTER(RegParams), _dp,
                                        C.POINTER(C.c_int), _dp, _i64p, C.POINTER(C.c_int), _vp])
+_sig("gsicp_selftest_batch_timeout", C.c_int, [_vp, _vp])
 _sig("gsicp_linearise", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.c_float, _dp, _dp, _dp, _i64p, _vp, _vp])
 _sig("gsicp_map_nearest", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp])
 for _n in ("gsicp_track_frame", "gsicp_track_frame_host"):
@@ -376,6 +377,11 @@ def gsicp_register_batch(ctx: Context, srcs: list, covs: list, maps: list, T0s, 
            "gsicp_register_batch")
     return dict(T=T[:B].reshape(B, 4, 4), iters=np.array(it[:B]), cost=cost[:B], inliers=np.array(inl[:B]),
                 status=np.array(stt[:B]))
+
+
+def gsicp_selftest_batch_timeout(ctx: Context) -> int:
+    """Status of the batch queue's bounded-wait self-test (ERR_TIMEOUT when the bound works)."""
+    return lib.gsicp_selftest_batch_timeout(ctx.ptr, _stream())
 
 
 def gsicp_linearise(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: MapHandle, T,

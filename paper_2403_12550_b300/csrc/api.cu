@@ -549,6 +549,22 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
     return GSICP_OK;
 }
 
+gsicp_status gsicp_selftest_batch_timeout(gsicp_ctx ctx, void* stream)
+{
+    if (!ctx) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchMachine& bm = ctx->batch;
+    const unsigned capacity = 4096;
+    GSICP_CHECK(bm.queue.ensure(sizeof(BatchQueue)));
+    GSICP_CHECK(bm.items.ensure(sizeof(unsigned long long) * capacity));
+    GSICP_CHECK(batch_wait_selftest(bm.queue.as<BatchQueue>(), bm.items.as<unsigned long long>(), capacity, s));
+    BatchQueue q;
+    GSICP_CUDA(cudaMemcpyAsync(&q, bm.queue.ptr, sizeof(q), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    if (q.error) return set_error(GSICP_ERR_TIMEOUT, "gsicp_selftest_batch_timeout: the queue waits ran out");
+    return GSICP_OK;
+}
+
 gsicp_status gsicp_linearise(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev, int64_t n,
                              gsicp_map map, const double T[16], float max_corr_dist, double H_out[36],
                              double b_out[6], double* cost_out, int64_t* inliers_out, int32_t* corr_dev, void* stream)

@@ -821,6 +821,18 @@ __global__ void batch_setup_kernel(const RegJob* __restrict__ jobs, const Pose16
         items[offsets[b] + j] = ((unsigned long long)b << 32) | (unsigned)j;
 }
 
+// The queue wait's bound, exercised: one pair "running" and no item will ever be published, so
+// every block's wait runs out, sets the error flag and leaves.  Takes about a second.
+gsicp_status batch_wait_selftest(BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s)
+{
+    GSICP_CUDA(cudaMemsetAsync(items, 0xff, sizeof(unsigned long long) * (size_t)capacity, s));
+    const BatchQueue q0 = {0u, 0u, 1u, 0u};
+    GSICP_CUDA(cudaMemcpyAsync(q_dev, &q0, sizeof(q0), cudaMemcpyHostToDevice, s));
+    gicp_batch_kernel<<<device_sm_count() * 3, REG_THREADS, 0, s>>>(nullptr, q_dev, items, capacity);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
 gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, const unsigned* offsets_dev,
                        BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s)
 {

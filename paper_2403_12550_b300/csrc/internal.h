@@ -125,6 +125,9 @@ gsicp_status launch_batch_seed(const RegJob* jobs_dev, const Pose16* T0_dev, con
 gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, const unsigned* offsets_dev,
                        BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s);
 
+// Runs the batch kernel on a queue whose one running pair never gets an item (its waits run out).
+gsicp_status batch_wait_selftest(BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s);
+
 // Buffers of batched registrations (grown on demand, kept by the context).
 struct BatchMachine {
     DevBuf src, covs, cand, anchor, partials, counts, jobs, states, T0, offsets, queue, items;

@@ -59,6 +59,8 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.gsicp_ctx_frame_stats(None, None) == INVALID
     lib.gsicp_register_batch.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 12
     assert lib.gsicp_register_batch(None, 2, *([None] * 12)) == INVALID
+    lib.gsicp_selftest_batch_timeout.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.gsicp_selftest_batch_timeout(None, None) == INVALID
     lib.gsicp_map_size.restype = C.c_int64
     assert lib.gsicp_map_size(None) == 0
     lib.gsicp_map_destroy(None)

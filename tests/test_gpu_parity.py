@@ -456,6 +456,21 @@ def test_register_batch_equals_single_and_oracle(g, ctx):
         m.close()
 
 
+def test_register_batch_queue_wait_is_bounded(g, ctx):
+    """A queue that claims a running pair but never gets an item: every wait runs out (about a
+    second), the call reports TIMEOUT, and the context keeps working."""
+    import time
+    t0 = time.time()
+    assert g.gsicp_selftest_batch_timeout(ctx) == g.ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    src, cs, tgt, ct, _ = config1_inputs(0, 0, n=3000)
+    m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    r = g.gsicp_register_batch(ctx, [cu(src)], [cu(cs)], [m], np.eye(4)[None], g.RegParams(0.1, 30, 1e-6, 1e-6, 6))
+    rs = g.gsicp_register(ctx, cu(src), cu(cs), m, np.eye(4), g.RegParams(0.1, 30, 1e-6, 1e-6, 6))
+    np.testing.assert_array_equal(r["T"][0], rs["T"])
+    m.close()
+
+
 def test_register_batch_empty(g, ctx):
     r = g.gsicp_register_batch(ctx, [], [], [], np.zeros((0, 4, 4)), g.RegParams())
     assert r["T"].shape == (0, 4, 4)
