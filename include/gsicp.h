@@ -304,6 +304,59 @@ gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int 
                                     double* cost_out, int64_t* inliers_out,
                                     int64_t* n_points_out, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Tracking loop with the paper's keyframe policy (NEXT row around the hot path).
+ *
+ * Sec. 3 Keyframe Selection: a frame whose proportion of correspondences with the map (inliers /
+ * points) falls below min_inlier_ratio becomes a keyframe; of its Gaussians only those that do not
+ * overlap the map (no map mean within overlap_radius) are added.  Sec. 3 Additional Keyframe
+ * Selection for Mapping: the force_every-th frame after a keyframe becomes one if none was
+ * selected before (30 in the paper), and every mapping_every-th frame after a keyframe (10) is a
+ * mapping-only keyframe: its new Gaussians go to the mapping map only.  Tracking registers against
+ * the tracking map (keyframes only); the mapping map holds keyframes and mapping-only keyframes.
+ * The paper gives no threshold values for the ratio or the overlap: min_inlier_ratio = 0.85 and
+ * overlap_radius = 0.01 m are this library's readings.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+    float min_inlier_ratio;  /* keyframe when inliers / points < this */
+    int force_every;         /* keyframe at this many frames after the last one at the latest */
+    int mapping_every;       /* mapping-only keyframe every this many frames after a keyframe (0: none) */
+    float overlap_radius;    /* m: a Gaussian with a map mean this close is not added */
+} gsicp_keyframe_params;
+
+typedef enum { GSICP_FRAME = 0, GSICP_KEYFRAME = 1, GSICP_MAPPING_KEYFRAME = 2 } gsicp_frame_kind;
+
+typedef struct {
+    int kind;               /* gsicp_frame_kind */
+    int status;             /* the frame's registration status (GSICP_OK or GSICP_ERR_DEGENERATE) */
+    int iters;              /* Gauss-Newton iterations (0 for the first frame) */
+    int64_t n_points;       /* points of the frame */
+    int64_t inliers;        /* correspondences of the last linearisation */
+    double inlier_ratio;    /* inliers / n_points */
+    int64_t added_tracking; /* Gaussians added to the tracking map */
+    int64_t added_mapping;  /* Gaussians added to the mapping map */
+} gsicp_frame_info;
+
+typedef struct gsicp_tracker_s* gsicp_tracker;
+
+/* A tracker on ctx (the ctx must outlive it); frames are taken with the given stride and depth
+ * range, covariances and registrations with cov / reg. */
+gsicp_status gsicp_tracker_create(gsicp_ctx ctx, int stride, float z_min, float z_max,
+                                  const gsicp_cov_params* cov, const gsicp_reg_params* reg,
+                                  const gsicp_keyframe_params* kf, gsicp_tracker* out);
+void gsicp_tracker_destroy(gsicp_tracker t);
+/* Tracks one depth frame (device, W x H float32 metres).  The first frame needs T_start (its
+ * pose) and becomes a keyframe; later frames start from T_start if given, else from the
+ * constant-velocity prediction T_{f-1} (T_{f-2}^-1 T_{f-1}) (T_{f-1} for the second frame).
+ * T_out (host) receives the frame's pose, *info (nullable) what happened.  Returns the
+ * registration's status (GSICP_ERR_DEGENERATE: the frame is not used and T_out holds the last
+ * valid pose of its registration).  Synchronises the stream. */
+gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_dev, int W, int H,
+                                 const float intr[4], const double* T_start, double T_out[16],
+                                 gsicp_frame_info* info, void* stream);
+/* The tracker's maps (owned by the tracker; NULL before the first frame). */
+gsicp_status gsicp_tracker_maps(gsicp_tracker t, gsicp_map* tracking_map, gsicp_map* mapping_map);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ __all__ = [
     "gsicp_build_map_index", "gsicp_map_append",
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_selftest_batch_timeout", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
+    "KeyframeParams", "FrameInfo", "Tracker", "FRAME", "KEYFRAME", "MAPPING_KEYFRAME",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgsicp.so")
@@ -59,6 +60,24 @@ class RegParams(C.Structure):
 
 class IndexParams(C.Structure):
     _fields_ = [("bucket", C.c_int), ("cell", C.c_float)]
+
+
+class KeyframeParams(C.Structure):
+    _fields_ = [("min_inlier_ratio", C.c_float), ("force_every", C.c_int), ("mapping_every", C.c_int),
+                ("overlap_radius", C.c_float)]
+
+    def __init__(self, min_inlier_ratio: float = 0.85, force_every: int = 30, mapping_every: int = 10,
+                 overlap_radius: float = 0.01):
+        super().__init__(min_inlier_ratio, force_every, mapping_every, overlap_radius)
+
+
+class FrameInfo(C.Structure):
+    _fields_ = [("kind", C.c_int), ("status", C.c_int), ("iters", C.c_int), ("n_points", C.c_int64),
+                ("inliers", C.c_int64), ("inlier_ratio", C.c_double), ("added_tracking", C.c_int64),
+                ("added_mapping", C.c_int64)]
+
+
+FRAME, KEYFRAME, MAPPING_KEYFRAME = 0, 1, 2
 
 
 if not os.path.exists(LIB_PATH):
@@ -107,6 +126,11 @@ _sig("gsicp_register", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(R
 _sig("gsicp_register_batch", C.c_int, [_vp, C.c_int, _vp, _vp, _i64p, _vp, _dp, C.POINTER(RegParams), _dp,
                                        C.POINTER(C.c_int), _dp, _i64p, C.POINTER(C.c_int), _vp])
 _sig("gsicp_selftest_batch_timeout", C.c_int, [_vp, _vp])
+_sig("gsicp_tracker_create", C.c_int, [_vp, C.c_int, C.c_float, C.c_float, C.POINTER(CovParams),
+                                       C.POINTER(RegParams), C.POINTER(KeyframeParams), C.POINTER(C.c_void_p)])
+_sig("gsicp_tracker_destroy", None, [_vp])
+_sig("gsicp_tracker_frame", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, _dp, _dp, C.POINTER(FrameInfo), _vp])
+_sig("gsicp_tracker_maps", C.c_int, [_vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)])
 _sig("gsicp_linearise", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.c_float, _dp, _dp, _dp, _i64p, _vp, _vp])
 _sig("gsicp_map_nearest", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp])
 for _n in ("gsicp_track_frame", "gsicp_track_frame_host"):
@@ -382,6 +406,47 @@ def gsicp_register_batch(ctx: Context, srcs: list, covs: list, maps: list, T0s, 
 def gsicp_selftest_batch_timeout(ctx: Context) -> int:
     """Status of the batch queue's bounded-wait self-test (ERR_TIMEOUT when the bound works)."""
     return lib.gsicp_selftest_batch_timeout(ctx.ptr, _stream())
+
+
+class Tracker:
+    """The tracking loop with the paper's keyframe policy (gsicp_tracker_*)."""
+
+    def __init__(self, ctx: Context, stride: int, z_min: float, z_max: float, cov: CovParams, reg: RegParams,
+                 kf: KeyframeParams | None = None):
+        self.ctx = ctx  # kept alive: the tracker uses it
+        self.ptr = C.c_void_p()
+        self.kf = kf if kf is not None else KeyframeParams()
+        _check(lib.gsicp_tracker_create(ctx.ptr, stride, z_min, z_max, C.byref(cov), C.byref(reg), C.byref(self.kf),
+                                        C.byref(self.ptr)), "gsicp_tracker_create")
+
+    def frame(self, depth: torch.Tensor, intr, T_start=None):
+        """Tracks one depth frame; returns (T 4x4, info dict)."""
+        H, W = depth.shape
+        fi = (C.c_float * 4)(*[float(v) for v in intr])
+        T = (C.c_double * 16)()
+        info = FrameInfo()
+        ts = _pose(T_start) if T_start is not None else None
+        st = lib.gsicp_tracker_frame(self.ptr, _dev(depth), W, H, fi, ts, T, C.byref(info), _stream())
+        _check(st, "gsicp_tracker_frame", allow=(ERR_DEGENERATE,))
+        d = {name: getattr(info, name) for name, _ in FrameInfo._fields_}
+        return np.array(T).reshape(4, 4), d
+
+    def map_sizes(self) -> tuple:
+        """(tracking map size, mapping map size)."""
+        a, b = C.c_void_p(), C.c_void_p()
+        _check(lib.gsicp_tracker_maps(self.ptr, C.byref(a), C.byref(b)), "gsicp_tracker_maps")
+        return (lib.gsicp_map_size(a) if a.value else 0), (lib.gsicp_map_size(b) if b.value else 0)
+
+    def close(self):
+        if self.ptr:
+            lib.gsicp_tracker_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gsicp_linearise(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: MapHandle, T,

@@ -594,7 +594,7 @@ gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* querie
 
 // a1 -> source index -> a2+a3 for one depth frame, into the context's frame buffers (points in
 // row-major order, their covariances in the same order and in the source index's order).
-static gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
+gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                       int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
                                       int cap, cudaStream_t s)
 {
@@ -652,7 +652,7 @@ gsicp_status gsicp_frame_covariances(gsicp_ctx ctx, const float* depth_dev, int 
     return n > cap ? GSICP_ERR_CAPACITY : GSICP_OK;
 }
 
-static gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
+gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                      int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
                                      gsicp_map map, const double T0[16], const gsicp_reg_params* reg_params,
                                      double T_out[16], double H_out[36], int* iters_out, double* cost_out,

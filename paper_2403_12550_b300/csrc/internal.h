@@ -173,3 +173,17 @@ struct gsicp_map_s {
     gsicp::DevBuf means, covs;        // unsorted copies (for appends)
     gsicp::DevBuf count;              // device int: number of Gaussians
 };
+
+// Frame helpers of api.cu used by the tracker (tracker.cu); defined in api.cu's C-linkage section.
+extern "C" {
+// a1 -> source index -> a2+a3 of one depth frame into the context's frame buffers.
+gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
+                               float z_min, float z_max, const gsicp_cov_params* cov_params, int cap,
+                               cudaStream_t s);
+// The whole a1..a7 step of gsicp_track_frame (arguments already checked).
+gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
+                              float z_min, float z_max, const gsicp_cov_params* cov_params, gsicp_map map,
+                              const double T0[16], const gsicp_reg_params* reg_params, double T_out[16],
+                              double H_out[36], int* iters_out, double* cost_out, int64_t* inliers_out,
+                              int64_t* n_points_out, cudaStream_t s);
+}  // extern "C"

@@ -61,6 +61,11 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.gsicp_register_batch(None, 2, *([None] * 12)) == INVALID
     lib.gsicp_selftest_batch_timeout.argtypes = [C.c_void_p, C.c_void_p]
     assert lib.gsicp_selftest_batch_timeout(None, None) == INVALID
+    lib.gsicp_tracker_create.argtypes = [C.c_void_p, C.c_int, C.c_float, C.c_float] + [C.c_void_p] * 4
+    assert lib.gsicp_tracker_create(None, 2, 0.1, 10.0, None, None, None, None) == INVALID
+    lib.gsicp_tracker_frame.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 5
+    assert lib.gsicp_tracker_frame(None, None, 8, 8, None, None, None, None, None) == INVALID
+    lib.gsicp_tracker_destroy(None)
     lib.gsicp_map_size.restype = C.c_int64
     assert lib.gsicp_map_size(None) == 0
     lib.gsicp_map_destroy(None)

@@ -546,6 +546,61 @@ def test_frame_covariances_capacity_and_empty(g, ctx):
     assert len(pf) == 0 and len(cf) == 0
 
 
+# ----------------------------------------------------------------------------- tracking loop with keyframes
+
+def test_tracker_policy_static_camera(g, ctx):
+    """The library's tracker follows the keyframe schedule and the non-overlap filter exactly as
+    the oracle's on a static camera (small frames)."""
+    from oracle.tracker import Tracker as OTracker
+    from synth import look_pose
+    intr = Intrinsics(48, 36, 40.0, 40.0, 23.5, 17.5)
+    scene = make_room(2)
+    P = look_pose(scene.centre + np.array([0.3, -0.2, 0.0]), 0.7, 0.2)
+    depth = raycast_depth(scene, P, intr)
+    trk = g.Tracker(ctx, 1, 0.1, 10.0, g.CovParams(20, 1e-3, g.PLANE, 0.0), g.RegParams(0.1, 30, 1e-6, 1e-6, 6))
+    otrk = OTracker(intr.as_array(), stride=1, p=0.0)
+    d = cu(depth)
+    for f in range(41):
+        T, info = trk.frame(d, intr.as_array(), P if f == 0 else None)
+        To, io = otrk.frame(depth, P if f == 0 else None)
+        assert info["kind"] == io["kind"], f
+        assert (info["added_tracking"], info["added_mapping"]) == (io["added_tracking"], io["added_mapping"]), f
+        dr, dt = pose_diff(T, To)
+        assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL
+    assert trk.map_sizes() == (len(otrk.track_means), len(otrk.map_means))
+    trk.close()
+
+
+def test_tracker_sequence_matches_oracle(g, ctx):
+    """TUM-shaped sequence, 45 frames: the library's tracker and the oracle's take the same
+    keyframe decisions, grow maps of the same size (up to points at the overlap radius) and track
+    with the same ATE."""
+    from oracle.tracker import Tracker as OTracker
+    F = 45
+    seq = sequence_config3(1, n_frames=F)
+    io_ = seq["intr"]
+    trk = g.Tracker(ctx, 2, 0.1, 10.0, g.CovParams(20, 1e-3, g.PLANE, 1.5), g.RegParams(0.1, 30, 1e-6, 1e-6, 6))
+    otrk = OTracker(io_.as_array(), stride=2, p=1.5)
+    est_g, est_o, kinds_g, kinds_o = [], [], [], []
+    for f in range(F):
+        depth = seq["depth"](f)
+        T, info = trk.frame(cu(depth), io_.as_array(), seq["poses"][0] if f == 0 else None)
+        To, io = otrk.frame(depth, seq["poses"][0] if f == 0 else None)
+        est_g.append(T)
+        est_o.append(To)
+        kinds_g.append(info["kind"])
+        kinds_o.append(io["kind"])
+    assert kinds_g == kinds_o, (kinds_g, kinds_o)
+    assert 1 in kinds_g[1:] and 2 in kinds_g  # the sequence exercises both kinds
+    sg, so = trk.map_sizes(), (len(otrk.track_means), len(otrk.map_means))
+    assert all(abs(a - b) <= 1e-3 * b for a, b in zip(sg, so)), (sg, so)
+
+    def ate(est):
+        return float(np.sqrt(np.mean([np.sum((est[f][:3, 3] - seq["poses"][f][:3, 3]) ** 2) for f in range(F)])))
+    assert ate(est_o) < 0.01 and abs(ate(est_g) - ate(est_o)) < 1e-4, (ate(est_g), ate(est_o))
+    trk.close()
+
+
 # ----------------------------------------------------------------------------- TUM-shaped sequence
 
 def test_sequence_config3_matches_oracle(g, ctx):

@@ -1,0 +1,44 @@
+"""The keyframe policy of the tracking loop on the oracle (CPU): forced and mapping-only
+keyframes on schedule, and the non-overlap filter, on a small static scene."""
+import numpy as np
+
+from oracle.tracker import Tracker
+from synth import Intrinsics, look_pose, make_room, raycast_depth
+
+SMALL = Intrinsics(48, 36, 40.0, 40.0, 23.5, 17.5)
+
+
+def _static_frames():
+    scene = make_room(2)
+    P = look_pose(scene.centre + np.array([0.3, -0.2, 0.0]), 0.7, 0.2)
+    return raycast_depth(scene, P, SMALL), P
+
+
+def test_schedule_and_overlap_on_a_static_camera():
+    depth, P = _static_frames()
+    trk = Tracker(SMALL.as_array(), stride=1, p=0.0, force_every=30, mapping_every=10)
+    kinds, added = [], []
+    for f in range(41):
+        T, info = trk.frame(depth, P if f == 0 else None)
+        kinds.append(info["kind"])
+        added.append((info["added_tracking"], info["added_mapping"]))
+        if f > 0:
+            assert info["inlier_ratio"] == 1.0  # every point sees its own copy in the map
+            assert np.abs(T - P).max() < 1e-6  # the map holds the points rounded to float
+    expect = [1 if f in (0, 30) else (2 if f in (10, 20, 40) else 0) for f in range(41)]
+    assert kinds == expect
+    # the first keyframe adds every point; later ones add nothing (everything overlaps)
+    assert added[0][0] == added[0][1] == int(np.isfinite(depth).sum())
+    assert all(a == (0, 0) for f, a in enumerate(added) if f > 0)
+
+
+def test_low_inlier_ratio_makes_a_keyframe():
+    depth, P = _static_frames()
+    trk = Tracker(SMALL.as_array(), stride=1, p=0.0, min_inlier_ratio=0.85)
+    trk.frame(depth, P)
+    # a frame whose right third sees nothing the map holds (pushed 0.5 m back): under 85 % inliers
+    d2 = depth.copy()
+    d2[:, 32:] += 0.5
+    _, info = trk.frame(d2, P)
+    assert info["inlier_ratio"] < 0.85 and info["kind"] == 1
+    assert 0 < info["added_tracking"] <= (d2[:, 32:] > 0).sum()
