@@ -327,48 +327,69 @@ def frame_config2(seed: int, n_views: int = 10, intr: Intrinsics = REPLICA_INTR,
 
 
 def spline_trajectory(seed: int, scene: Scene, n_frames: int = 500, fps: float = 30.0,
-                      vmax: float = 1.0, wmax_deg: float = 60.0, n_knots: int = 12) -> list:
+                      vmax: float = 1.0, wmax_deg: float = 60.0, n_knots: int = 12,
+                      clearance: float = 0.6) -> list:
     """A smooth camera trajectory: positions and headings follow clamped
     natural cubic splines through seeded knots near the room centre, sampled
     at ``fps``; speeds are capped at ``vmax`` m/s and ``wmax_deg`` deg/s by
-    slowing the time parameterisation."""
+    slowing the time parameterisation.  The camera keeps ``clearance`` from
+    the walls, the ceiling and every sphere, and stays above the boxes (the
+    knots are drawn again, from the same seeded stream, until it does)."""
     from scipy.interpolate import CubicSpline
 
     rng = np.random.default_rng(4242 + seed)
     c = scene.centre
     span = 0.35 * (scene.room_hi - scene.room_lo)
-    knots_p = c + rng.uniform(-1, 1, size=(n_knots, 3)) * np.array([span[0], span[1], 0.0])
-    knots_p[:, 2] = rng.uniform(1.2, 1.8, n_knots)
-    knots_yaw = np.cumsum(rng.uniform(-1.2, 1.2, n_knots))
-    knots_pitch = np.deg2rad(rng.uniform(5, 25, n_knots))
-    s = np.arange(n_knots, dtype=np.float64)
-    sp_p = CubicSpline(s, knots_p, bc_type="clamped")
-    sp_y = CubicSpline(s, knots_yaw, bc_type="clamped")
-    sp_pt = CubicSpline(s, knots_pitch, bc_type="clamped")
-    # dense arc-parameter march with speed caps
+    box_top = float(np.max(2.0 * scene.box_half[:, 2])) if len(scene.box_half) else 0.0
     dt = 1.0 / fps
-    poses, u = [], 0.0
-    for _ in range(n_frames):
-        poses.append(look_pose(sp_p(u), float(sp_y(u)), float(sp_pt(u))))
-        v = np.linalg.norm(sp_p(u, 1))
-        w = abs(float(sp_y(u, 1)))
-        du = min(vmax * dt / max(v, 1e-9), np.deg2rad(wmax_deg) * dt / max(w, 1e-9), 0.05)
-        # the rates change along the step: shrink it until the step itself keeps both caps
-        while du > 1e-9 and (np.linalg.norm(sp_p(min(u + du, n_knots - 1.0)) - sp_p(u)) > vmax * dt or
-                             abs(float(sp_y(min(u + du, n_knots - 1.0)) - sp_y(u))) > np.deg2rad(wmax_deg) * dt):
-            du *= 0.9
-        u = min(u + du, n_knots - 1.0)
-    return poses
+
+    def clear(pos) -> bool:
+        if np.any(pos - scene.room_lo < clearance) or np.any(scene.room_hi - pos < clearance):
+            return False
+        if pos[2] < box_top + 0.2:
+            return False
+        return all(np.linalg.norm(pos - sc) > r + clearance for sc, r in zip(scene.sph_center, scene.sph_radius))
+
+    for _attempt in range(200):
+        knots_p = c + rng.uniform(-1, 1, size=(n_knots, 3)) * np.array([span[0], span[1], 0.0])
+        knots_p[:, 2] = rng.uniform(1.2, 1.8, n_knots)
+        knots_yaw = np.cumsum(rng.uniform(-1.2, 1.2, n_knots))
+        knots_pitch = np.deg2rad(rng.uniform(5, 25, n_knots))
+        s = np.arange(n_knots, dtype=np.float64)
+        sp_p = CubicSpline(s, knots_p, bc_type="clamped")
+        sp_y = CubicSpline(s, knots_yaw, bc_type="clamped")
+        sp_pt = CubicSpline(s, knots_pitch, bc_type="clamped")
+        # dense arc-parameter march with speed caps
+        poses, u, ok = [], 0.0, True
+        for _ in range(n_frames):
+            pos = sp_p(u)
+            if not clear(pos):
+                ok = False
+                break
+            poses.append(look_pose(pos, float(sp_y(u)), float(sp_pt(u))))
+            v = np.linalg.norm(sp_p(u, 1))
+            w = abs(float(sp_y(u, 1)))
+            du = min(vmax * dt / max(v, 1e-9), np.deg2rad(wmax_deg) * dt / max(w, 1e-9), 0.05)
+            # the rates change along the step: shrink it until the step itself keeps both caps
+            while du > 1e-9 and (np.linalg.norm(sp_p(min(u + du, n_knots - 1.0)) - sp_p(u)) > vmax * dt or
+                                 abs(float(sp_y(min(u + du, n_knots - 1.0)) - sp_y(u))) > np.deg2rad(wmax_deg) * dt):
+                du *= 0.9
+            u = min(u + du, n_knots - 1.0)
+        if ok:
+            return poses
+    raise RuntimeError("no clear trajectory in this scene")
 
 
 def sequence_config3(seed: int, n_frames: int = 500, intr: Intrinsics = TUM_INTR, noise_coeff: float = 1e-3):
-    """TUM-shaped tracking sequence: a 6 x 5 x 3 m room with boxes and spheres,
+    """TUM-shaped tracking sequence: a 6 x 5 x 3 m room with 24 boxes and 12 spheres,
     ``n_frames`` poses at 30 Hz along :func:`spline_trajectory` (<= 1 m/s,
     <= 60 deg/s), and ``depth(f)``, the noisy 640x480 depth image of frame f
     (ray-cast on demand; its noise is seeded by (seed, f)).
 
     Returns a dict with keys ``scene, intr, poses, depth``."""
-    scene = make_room(seed + 100, size=(6.0, 5.0, 3.0))
+    # a 6 x 5 m room needs more furniture than the 4 x 3 m one for most views to constrain all six
+    # degrees of freedom (a view of bare wall and floor leaves a translation along them free)
+    scene = make_room(seed + 100, size=(6.0, 5.0, 3.0), n_boxes=24, n_spheres=12)
     poses = spline_trajectory(seed, scene, n_frames=n_frames)
 
     def depth(f: int) -> np.ndarray:
