@@ -63,8 +63,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["frame", "batch"], default="frame",
-                    help="frame: the tracking step (default); batch: batched registration of independent pairs")
+    ap.add_argument("--workload", choices=["frame", "batch", "sequence"], default="frame",
+                    help="frame: the tracking step (default); batch: batched registration of independent pairs; "
+                         "sequence: the tracking loop with keyframes over a TUM-shaped sequence (latency p50/p99)")
+    ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--pairs", type=int, default=64)
     return ap.parse_args()
 
@@ -476,6 +478,65 @@ def run_batch(args, world, rank, local):
     ctx.close()
 
 
+# ----------------------------------------------------------------------------- tracking sequence
+
+SEQ_METRIC = "tracked frames/s and per-frame latency (640x480 sequence, keyframe appends, tracking loop)"
+
+
+def run_sequence(args, world, rank, local):
+    """The tracking loop (gsicp_tracker_frame: a1..a7, keyframe decision, non-overlap appends with
+    map-index rebuilds) over a TUM-shaped sequence; per-frame latency is host wall time of each
+    call (it synchronises), depth images resident on the device."""
+    import torch
+
+    import paper_2403_12550_b300 as g
+    from synth import sequence_config3
+
+    torch.cuda.set_device(local)
+    seed = 1 + args.seed
+    seq = sequence_config3(seed, n_frames=args.frames)
+    depths = [torch.from_numpy(seq["depth"](f)).cuda() for f in range(args.frames)]
+    intr = seq["intr"].as_array()
+    ctx = g.Context()
+    cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
+    rp = g.RegParams(MAX_DIST, MAX_ITERS, TOL, TOL, 6)
+
+    def one_pass():
+        trk = g.Tracker(ctx, 2, Z_MIN, Z_MAX, cp, rp)
+        lat, est, kinds = [], [], []
+        for f, d in enumerate(depths):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            T, info = trk.frame(d, intr, seq["poses"][0] if f == 0 else None)
+            lat.append(time.perf_counter() - t0)
+            est.append(T)
+            kinds.append(info["kind"])
+        sizes = trk.map_sizes()
+        trk.close()
+        return lat, est, kinds, sizes
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        one_pass()
+    lat, est, kinds, sizes = one_pass()
+    lat_ms = np.array(lat[1:]) * 1e3  # frame 0 only builds the first map
+    ate = float(np.sqrt(np.mean([np.sum((a[:3, 3] - b[:3, 3]) ** 2) for a, b in zip(est, seq["poses"])])))
+    out = {
+        "metric": SEQ_METRIC, "value": world * len(lat_ms) / (lat_ms.sum() / 1e3), "unit": "frames/s",
+        "n_gpus": world, "steps": len(lat_ms), "warmup": args.warmup, "ms_per_step": float(lat_ms.mean()),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"TUM-shaped sequence seed {seed}: {args.frames} frames 640x480 at 30 Hz, stride 2, "
+                               f"keyframes by inlier ratio < 0.85, forced every 30, mapping-only every 10",
+                   "k": K_NN, "reg": "plane", "p": P_ALIGN},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "max": float(lat_ms.max())},
+        "ate_m": ate, "keyframes": kinds.count(g.KEYFRAME), "mapping_keyframes": kinds.count(g.MAPPING_KEYFRAME),
+        "map_sizes": list(sizes),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -483,6 +544,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batch":
         run_batch(args, world, rank, local)
+    elif args.workload == "sequence":
+        run_sequence(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 
