@@ -43,9 +43,9 @@ BYTES_PER_MAP_GAUSSIAN = 84 + 48  # read mean 12 + cov 24 (x2: bbox/morton and g
 REGSTATE_BYTES = 544 + 4       # pose/H/b/cost/iters/status record + point count read back per frame
 L2_FLUSH_BYTES = 256 << 20
 # kernels launched per timed step (counted from the ncu launch list of this workload):
-LAUNCHES_MAP_REBUILD = 33  # count reset 1, bbox 2, quantise 1, Morton keys 1, 4 radix passes x 5, gather 1,
-                           # leaf boxes 1, box levels 3, grid insert/end 2, seed table 1
-LAUNCHES_FRAME = 39        # a1 5 (count, 3 scan, write), source index 28, k-NN covariances 4 (9x9 window,
+LAUNCHES_MAP_REBUILD = 18  # count reset 1, bbox 2, quantise 1, Morton keys 1, radix sort 5 (digit counts + 4
+                           # passes), gather 1, leaf boxes 1, box levels 3, grid insert/end 2, seed table 1
+LAUNCHES_FRAME = 24        # a1 5 (count, 3 scan, write), source index 13, k-NN covariances 4 (9x9 window,
                            # 25x25 window, tree, reorder), GN seed 1, GN set-up 1; plus one Gauss-Newton
                            # launch per iteration
 # DRAM bytes per gicp_iter_kernel launch (read + write, mean over the iterations of one frame of this
@@ -395,9 +395,9 @@ BATCH_METRIC = "batched G-ICP registrations/s (independent pairs, 5k-300k points
 
 def batch_launches(n_pts) -> int:
     """Kernels one gsicp_register_batch call launches: the joint Morton order of all sources (bbox
-    2, quantise 1, keys 1, 4 radix passes x 5, cloud keys 1, 2 radix passes x 5, gather 1), the
+    2, quantise 1, keys 1, radix sort by key 5, cloud keys 1, radix sort by cloud 3, gather 1), the
     seeds 1, the set-up 1 and the persistent kernel 1."""
-    return 39 if int(np.sum(n_pts)) > 1 else 3
+    return 17 if int(np.sum(n_pts)) > 1 else 3
 
 
 def run_batch(args, world, rank, local):

@@ -112,62 +112,130 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 8;                      // 32-key rounds per warp
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 2048 keys per block
 
-__global__ void rs_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* __restrict__ hist,
-                               int tiles)
+// One kernel per 8-bit pass (digit counts of all passes first): each block takes the next tile
+// of RS_TILE keys (tile numbers handed out in the order blocks start), counts its digits, publishes
+// them, and finds its tile's offset per digit by looking back over the earlier tiles' published
+// counts until one whose offset is already complete (decoupled look-back); then it scatters its
+// keys (each warp ranks a contiguous run of 256 keys in order, 32 at a time, peers found with
+// match.any, so equal digits keep their input order: stable).  A tile only waits on tiles claimed before it, by blocks that
+// are running or done and never wait on it, so every wait ends; the spin is bounded all the same
+// (err set if a bound ever ran out).
+constexpr uint32_t OS_FLAG_AGG = 1u << 30;   // the tile's own counts are published
+constexpr uint32_t OS_FLAG_INC = 2u << 30;   // the tile's counts including all earlier tiles
+constexpr uint32_t OS_VALUE = (1u << 30) - 1u;
+constexpr unsigned OS_SPIN_LIMIT = 1u << 21;
+
+// Digit counts of every pass (hist[p][256]), then in the last block their exclusive scans
+// (offs[p][256]); hist and *done must be zero on entry.
+__global__ void os_hist_kernel(const uint32_t* __restrict__ keys, int n, int passes, uint32_t* __restrict__ hist,
+                               uint32_t* __restrict__ offs, uint32_t* __restrict__ done)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[4][256];
+    __shared__ uint32_t ws[32];
+    __shared__ bool last;
+    for (int j = threadIdx.x; j < 4 * 256; j += RS_THREADS) (&h[0][0])[j] = 0u;
     __syncthreads();
-    const long base = (long)blockIdx.x * RS_TILE;
-#pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        long i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    for (long i = (long)blockIdx.x * RS_THREADS + threadIdx.x; i < n; i += (long)gridDim.x * RS_THREADS) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
-    hist[(long)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+    for (int j = threadIdx.x; j < passes * 256; j += RS_THREADS) {
+        const uint32_t v = (&h[0][0])[j];
+        if (v) atomicAdd(&hist[j], v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int p = 0; p < passes; ++p) {
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(__ldcg(&hist[p * 256 + threadIdx.x]), ws, total);
+        offs[p * 256 + threadIdx.x] = ex;
+    }
 }
 
-// Each warp ranks a contiguous run of 256 keys in order (32 at a time, peers
-// found with match.any), so equal digits keep their input order: stable.
-__global__ void rs_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int n, int shift,
-                                  const uint32_t* __restrict__ offs, int tiles)
+__global__ void __launch_bounds__(RS_THREADS) os_pass_kernel(const uint32_t* __restrict__ kin,
+                                                             const uint32_t* __restrict__ vin,
+                                                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                             int n, int shift, const uint32_t* __restrict__ offs,
+                                                             uint32_t* __restrict__ status,
+                                                             uint32_t* __restrict__ tile_ctr,
+                                                             uint32_t* __restrict__ err)
 {
     __shared__ uint32_t wc[RS_WARPS][256];
+    __shared__ uint32_t base[256];
+    __shared__ int s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < RS_WARPS * 256; j += RS_THREADS) (&wc[0][0])[j] = 0;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+    for (int j = threadIdx.x; j < RS_WARPS * 256; j += RS_THREADS) (&wc[0][0])[j] = 0u;
     __syncthreads();
-    const long sub = (long)blockIdx.x * RS_TILE + (long)warp * (32 * RS_ROUNDS);
+    const int tile = s_tile;
+    const long sub = (long)tile * RS_TILE + (long)warp * (32 * RS_ROUNDS);
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t key[RS_ROUNDS], dig[RS_ROUNDS];
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        long i = sub + r * 32 + lane;
+        const long i = sub + r * 32 + lane;
         key[r] = i < n ? kin[i] : 0u;
         dig[r] = i < n ? ((key[r] >> shift) & 255u) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
         if (dig[r] < 256u && lane == __ffs(peers) - 1) wc[warp][dig[r]] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    {   // per digit: exclusive prefix over warps, offset by this tile's global base
+    {   // per digit: the tile's count, prefix over its warps, then the offset over earlier tiles
         const int d = threadIdx.x;
-        uint32_t run = offs[(long)d * tiles + blockIdx.x];
+        uint32_t cnt = 0u;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = wc[w][d];
-            wc[w][d] = run;
-            run += c;
+            const uint32_t c = wc[w][d];
+            wc[w][d] = cnt;
+            cnt += c;
         }
+        uint32_t* my = status + (long)tile * 256 + d;
+        uint32_t excl = 0u;
+        if (tile > 0) {
+            atomicExch(my, OS_FLAG_AGG | cnt);
+            // eight predecessors per step, read together (the walk is a chain of dependent loads)
+            unsigned spins = 0;
+            for (int t = tile - 1; t >= 0;) {
+                uint32_t v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = t - j >= 0 ? *reinterpret_cast<volatile uint32_t*>(status + (long)(t - j) * 256 + d)
+                                      : (2u << 30);  // before tile 0: nothing (complete, 0)
+                int used = 0;
+                bool stop = false;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (stop || used < j) continue;  // a gap: that tile had not published yet
+                    const uint32_t f = v[j] & ~OS_VALUE;
+                    if (f == 0u) continue;
+                    excl += v[j] & OS_VALUE;
+                    ++used;
+                    if (f == OS_FLAG_INC) stop = true;
+                }
+                if (stop) break;
+                t -= used;
+                if (used == 0 && ++spins > OS_SPIN_LIMIT) {
+                    atomicExch(err, 1u);
+                    break;
+                }
+            }
+        }
+        atomicExch(my, OS_FLAG_INC | (excl + cnt));
+        base[d] = offs[d] + excl;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        long i = sub + r * 32 + lane;
-        uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        const long i = sub + r * 32 + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
         if (dig[r] < 256u) {
-            uint32_t pos = wc[warp][dig[r]] + __popc(peers & lt_mask);
+            const uint32_t pos = base[dig[r]] + wc[warp][dig[r]] + __popc(peers & lt_mask);
             kout[pos] = key[r];
             vout[pos] = vin[i];
         }
@@ -181,11 +249,25 @@ __global__ void rs_scatter_kernel(const uint32_t* __restrict__ kin, const uint32
 static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int bits,
                                      DevBuf& hist, DevBuf& sums, cudaStream_t s)
 {
+    (void)sums;
     if (n <= 1) return GSICP_OK;
+    if (n > (int)OS_VALUE) return GSICP_ERR_INVALID_ARG;
     const int tiles = (n + RS_TILE - 1) / RS_TILE;
-    GSICP_CHECK(hist.ensure(sizeof(uint32_t) * 256 * (size_t)tiles));
     int passes = (bits + 7) / 8;
     if (passes & 1) ++passes;  // even count: the result lands back in (k0, v0)
+    const int real = std::min(passes, 4);
+    // layout: counts [4][256] | offsets [4][256] | done | error | - | tile counter | status [tiles][256]
+    const size_t status_off = 2 * 4 * 256 + 4;
+    GSICP_CHECK(hist.ensure(sizeof(uint32_t) * (status_off + 256 * (size_t)tiles)));
+    uint32_t* H = hist.as<uint32_t>();
+    uint32_t* O = H + 4 * 256;
+    uint32_t* done = H + 2 * 4 * 256;
+    uint32_t* err = done + 1;
+    uint32_t* status = H + status_off;
+    uint32_t* tile_ctr = status - 1;  // cleared with the status words before each pass
+    GSICP_CUDA(cudaMemsetAsync(H, 0, sizeof(uint32_t) * (status_off), s));
+    const int hgrid = std::max(1, std::min(tiles, device_sm_count() * 4));
+    os_hist_kernel<<<hgrid, RS_THREADS, 0, s>>>(k0, n, real, H, O, done);
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         uint32_t* ki = (p & 1) ? k1 : k0;
@@ -197,9 +279,8 @@ static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, u
             GSICP_CUDA(cudaMemcpyAsync(vo, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
             continue;
         }
-        rs_hist_kernel<<<tiles, RS_THREADS, 0, s>>>(ki, n, shift, hist.as<uint32_t>(), tiles);
-        GSICP_CHECK(exclusive_scan_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), 256 * tiles, sums, s));
-        rs_scatter_kernel<<<tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist.as<uint32_t>(), tiles);
+        GSICP_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * (1 + 256 * (size_t)tiles), s));
+        os_pass_kernel<<<tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, O + 256 * p, status, tile_ctr, err);
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
