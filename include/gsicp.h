@@ -103,6 +103,13 @@ const char* gsicp_version(void);
  * covariances, out[3] Gauss-Newton loop, out[4] whole frame; out[5] = Gauss-Newton iterations.
  * Disabled by default (no events are recorded). */
 gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable);
+/* Search tuning of this context's registrations (gsicp_register, gsicp_linearise,
+ * gsicp_register_batch, gsicp_track_frame*): in each warp of 32 source points, when at most
+ * max_per_warp of them need a walk of the map's tree in an iteration, the warp's 32 lanes walk for
+ * each of them in turn (one query at a time, 32 boxes or points per step); otherwise each point
+ * walks alone.  0 = always alone, 32 = always together.  Results do not depend on it (both walks
+ * are exact); only time does.  Default 4.  GSICP_ERR_INVALID_ARG outside 0..32 or for a null ctx. */
+gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp);
 gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6]);
 
 /* Telemetry of the last frame whose covariances this context computed (gsicp_frame_covariances,

@@ -101,11 +101,12 @@ constexpr float CACHE_SLACK = 0.01f;  // m beyond max_corr_dist kept in the cand
 constexpr float CACHE_STEP = 0.002f;  // m: points that moved more since their last search skip the cache
 constexpr float MAP_CELL = 0.008f;    // m: default map grid cell
 
-static RegJob make_job(const float4* src, const float4* covs_s, const int* n_dev, gsicp_map map,
+static RegJob make_job(gsicp_ctx ctx, const float4* src, const float4* covs_s, const int* n_dev, gsicp_map map,
                        const gsicp_reg_params* prm)
 {
     RegJob job;
     memset(&job, 0, sizeof(job));
+    job.coop_max = ctx->coop_walks;
     job.src = src;
     job.covs_s = covs_s;
     job.slack = CACHE_SLACK;
@@ -218,6 +219,13 @@ gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable)
     if (enable && !ctx->ev[0])
         for (cudaEvent_t& e : ctx->ev) GSICP_CUDA(cudaEventCreate(&e));
     ctx->timing = enable != 0;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp)
+{
+    if (!ctx || max_per_warp < 0 || max_per_warp > 32) return GSICP_ERR_INVALID_ARG;
+    ctx->coop_walks = max_per_warp;
     return GSICP_OK;
 }
 
@@ -422,7 +430,7 @@ gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float
     if (n > 0 && (!src_pts_dev || !src_covs_dev)) return GSICP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     GSICP_CHECK(prepare_source(ctx, src_pts_dev, src_covs_dev, (int)n, s));
-    RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
+    RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
                           map, params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, (int)n, true, s));
     return finish_registration(ctx, s, T_out, H_out, b_out, iters_out, cost_out, inliers_out);
@@ -491,7 +499,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
             counts_h[b] = (int)n[b];
             offsets_h[b] = (unsigned)co;
             for (int i = 0; i < 16; ++i) T0_h[b].v[i] = T0[16l * b + i];
-            RegJob j = make_job(bm.src.as<float4>() + po, bm.covs.as<float4>() + 2 * po, bm.counts.as<int>() + b,
+            RegJob j = make_job(ctx, bm.src.as<float4>() + po, bm.covs.as<float4>() + 2 * po, bm.counts.as<int>() + b,
                                 maps[b], params);
             j.cand = bm.cand.as<int>() + KC * po;
             j.anchor = bm.anchor.as<float4>() + po;
@@ -575,7 +583,7 @@ gsicp_status gsicp_linearise(gsicp_ctx ctx, const float* src_pts_dev, const floa
     cudaStream_t s = (cudaStream_t)stream;
     gsicp_reg_params prm = {max_corr_dist, 1, 0.0, 0.0, 0};
     GSICP_CHECK(prepare_source(ctx, src_pts_dev, src_covs_dev, (int)n, s));
-    RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
+    RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
                           map, &prm);
     job.corr_out = corr_dev;
     GSICP_CHECK(reg_run(ctx->reg, job, T, (int)n, false, s));
@@ -664,7 +672,7 @@ gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int 
     int* nd = ctx->n_dev.as<int>();
     const bool tm = ctx->timing;
     GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s));
-    RegJob job = make_job(ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
+    RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));
     if (n_points_out) GSICP_CUDA(cudaMemcpyAsync(ctx->host_pinned, nd, sizeof(int), cudaMemcpyDeviceToHost, s));

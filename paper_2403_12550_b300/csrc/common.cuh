@@ -288,6 +288,9 @@ struct RegJob {
     int min_inliers;
     int mode;              // REG_MODE_*
     int use_cond;          // 1 when launched inside the conditional-while graph
+    int coop_max;          // warps with at most this many tree walks do them together (0: never)
 };
+
+constexpr int COOP_WALKS_DEFAULT = 4;  // default RegJob::coop_max
 
 }  // namespace gsicp

@@ -233,36 +233,68 @@ __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegSt
 
 // All the Gauss-Newton work for source point s of job J at the float pose (R, t) + (Rl, tl):
 // transform, exact nearest map point (cache / grid / tree), residual, weight and J^T W J, J^T W d,
-// d^T W d and the inlier count added to acc.  Returns 1 if the point's nearest-point search ran
-// (its cache was rebuilt).
+// d^T W d and the inlier count added to acc.  Called by all 32 lanes of a warp, converged (lanes
+// with active == false hold no point); wstack is the warp's stack for cooperative walks.
+// Returns 1 if the point's nearest-point search ran (its cache was rebuilt).
+//
+// Tree walks: in a warp where at most J.coop_max points need one, the whole warp walks for each of
+// them in turn (warp_knn); in busier warps each point walks alone.  A lone walk of a point far from
+// the map is a long chain of dependent loads, and in the late iterations, where a handful of points
+// per launch still search, that chain sets the launch's duration.  Both walks are exact, so every
+// choice returns the same nearest point and leaves the same cache state.
 __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], const float (&Rl)[9],
-                                        const float (&t)[3], const float (&tl)[3], int s, int nmap,
-                                        float (&acc)[NACC])
+                                        const float (&t)[3], const float (&tl)[3], int s, bool active, int nmap,
+                                        float (&acc)[NACC], int2* wstack)
 {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     int refreshed = 0;
     const float4 qq = *J.map.quant;
     const int B = J.map.B;
     const float max_d = sqrtf(J.max_d2);
     const float Rs = max_d + J.slack, Rs2 = Rs * Rs;
-        const float4 x = J.src[s];
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;
+    float best_d2 = J.max_d2;
+    int best_oi = 0x7fffffff, best_pos = -1;
+    int walk = 0;     // a tree walk is still needed: 1 nearest point only, 2 the KC nearest within lim
+    float lim = 0.f;  // walk 2: squared search radius
+    int h0 = -1, h1 = -1;  // leaves of the previous candidates, scanned first by a walk
+    auto exact_d2 = [&](const float4& p) {
+        return sq3(__fsub_rn(__fsub_rn(p.x, y0), l0), __fsub_rn(__fsub_rn(p.y, y1), l1),
+                   __fsub_rn(__fsub_rn(p.z, y2), l2));
+    };
+    // the nearest by hi + lo among a sorted KC list (positions P, -1 = none)
+    auto pick_exact = [&](const int (&P)[KC]) {
+        best_d2 = J.max_d2;
+        best_oi = 0x7fffffff;
+        best_pos = -1;
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            if (P[j] < 0) continue;
+            const float4 p = J.map.pts[P[j]];
+            const float ed2 = exact_d2(p);
+            const int oi = __float_as_int(p.w);
+            if (before(ed2, oi, best_d2, best_oi)) {
+                best_d2 = ed2;
+                best_oi = oi;
+                best_pos = P[j];
+            }
+        }
+    };
+    if (active) {
+        x = J.src[s];
         // y = R x + t as hi + lo: the searches run on hi; the final choice among the candidates
         // they return, the inlier test and the residual use hi + lo (distance differences at the
         // level of float rounding of y would otherwise flip near-equidistant correspondences)
-        float y0, y1, y2, l0, l1, l2;
         transform_df(R, Rl, t[0], tl[0], x.x, x.y, x.z, y0, l0);
         transform_df(R + 3, Rl + 3, t[1], tl[1], x.x, x.y, x.z, y1, l1);
         transform_df(R + 6, Rl + 6, t[2], tl[2], x.x, x.y, x.z, y2, l2);
-        auto exact_d2 = [&](const float4& p) {
-            return sq3(__fsub_rn(__fsub_rn(p.x, y0), l0), __fsub_rn(__fsub_rn(p.y, y1), l1),
-                       __fsub_rn(__fsub_rn(p.z, y2), l2));
-        };
         // cache state through L2: in a persistent launch another SM wrote it in the last iteration
         const int4 ca4 = __ldcg(reinterpret_cast<const int4*>(J.cand) + 2l * s);
         const int4 cb4 = __ldcg(reinterpret_cast<const int4*>(J.cand) + 2l * s + 1);
         const int cp[KC] = {ca4.x, ca4.y, ca4.z, ca4.w, cb4.x, cb4.y, cb4.z, cb4.w};
         const float4 anc = __ldcg(J.anchor + s);
-        float best_d2 = J.max_d2;
-        int best_oi = 0x7fffffff, best_pos = -1;
         bool resolved = false;
         if (anc.w > 0.f) {
             // Cached candidates were complete within radius anc.w of the anchor; the query has
@@ -310,6 +342,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
             int2 rng[8];
             const float cert = grid_block8(J.map, qq, y0, y1, y2, rng);
             const float cert2 = cert > 0.f ? cert * cert * (1.f - 2e-5f) : -1.f;
+            h0 = cp[0] >= 0 ? cp[0] / B : -1;
             if (one_nn) {
                 // the pose is still moving a lot: only the nearest point, no cache
                 if (cert2 > 0.f) {
@@ -327,161 +360,238 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                         }
                 }
                 if (!(best_pos >= 0 && best_d2 <= cert2)) {
-                    auto scan1 = [&](int lf) {
-                        scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), [&](int u, const float4& p) {
-                            const float d2 = point_d2(y0, y1, y2, p);
-                            const int oi = __float_as_int(p.w);
-                            if (before(d2, oi, best_d2, best_oi)) {
-                                best_d2 = d2;
-                                best_oi = oi;
-                                best_pos = u;
-                            }
-                        });
-                    };
-                    const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
-                    if (h0 >= 0) scan1(h0);
-                    traverse8(J.map, y0, y1, y2, best_d2, [&](int lf) {
-                        if (lf != h0) scan1(lf);
-                    });
+                    walk = 1;
+                } else {
+                    reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+                    J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
                 }
-                reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
-                J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
             } else {
                 // exact KC nearest map points, grid block first, else a tree walk within Rs
                 unsigned long long Lk[KC];  // ascending (squared distance, index) keys
                 int P[KC];                  // their sorted map positions
-                auto reset = [&](float lim) {
 #pragma unroll
-                    for (int j = 0; j < KC; ++j) {
-                        Lk[j] = dkey(lim, 0x7fffffff);
-                        P[j] = -1;
-                    }
-                };
-                auto offer = [&](int u, const float4& p) {
-                    const unsigned long long key = dkey(point_d2(y0, y1, y2, p), __float_as_int(p.w));
-                    if (key < Lk[KC - 1]) key_insert(Lk, P, key, u);
-                };
-                float rc;
-                reset(GSICP_INF);
+                for (int j = 0; j < KC; ++j) {
+                    Lk[j] = dkey(GSICP_INF, 0x7fffffff);
+                    P[j] = -1;
+                }
                 if (cert2 > 0.f) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
-                        for (int u = rng[c].x; u < rng[c].y; ++u) offer(u, J.map.pts[u]);
+                        for (int u = rng[c].x; u < rng[c].y; ++u) {
+                            const float4 p = J.map.pts[u];
+                            const unsigned long long key = dkey(point_d2(y0, y1, y2, p), __float_as_int(p.w));
+                            if (key < Lk[KC - 1]) key_insert(Lk, P, key, u);
+                        }
                 }
                 if (key_idx(Lk[0]) != 0x7fffffff && key_d2(Lk[0]) <= cert2) {
                     // points outside the list: outside the block (>= cert) or beaten by the KC-th
-                    rc = fminf(cert, key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : GSICP_INF) *
-                         (1.f - 1e-6f);
+                    const float rc =
+                        fminf(cert, key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : GSICP_INF) *
+                        (1.f - 1e-6f);
+                    reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
+                    reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
+                    J.anchor[s] = make_float4(y0, y1, y2, rc);
+                    pick_exact(P);
                 } else {
-                    const float lim = key_idx(Lk[KC - 1]) != 0x7fffffff ? fminf(key_d2(Lk[KC - 1]), Rs2) : Rs2;
-                    reset(lim);
-                    float bound = lim;
-                    auto scan_leaf = [&](int lf) {
-                        scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), offer);
-                        bound = key_d2(Lk[KC - 1]);
-                    };
-                    const int h0 = cp[0] >= 0 ? cp[0] / B : -1;
-                    const int h1 = (cp[KC - 1] >= 0 && cp[KC - 1] / B != h0) ? cp[KC - 1] / B : -1;
-                    if (h0 >= 0) scan_leaf(h0);
-                    if (h1 >= 0) scan_leaf(h1);
-                    traverse8(J.map, y0, y1, y2, bound, [&](int lf) {
-                        if (lf != h0 && lf != h1) scan_leaf(lf);
-                    });
-                    rc = (key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : Rs) * (1.f - 1e-6f);
+                    walk = 2;
+                    lim = key_idx(Lk[KC - 1]) != 0x7fffffff ? fminf(key_d2(Lk[KC - 1]), Rs2) : Rs2;
+                    h1 = (cp[KC - 1] >= 0 && cp[KC - 1] / B != h0) ? cp[KC - 1] / B : -1;
                 }
-                reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
-                reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
-                J.anchor[s] = make_float4(y0, y1, y2, rc);
-                // the nearest by hi + lo among the list
-                best_d2 = J.max_d2;
-                best_oi = 0x7fffffff;
-                best_pos = -1;
-#pragma unroll
-                for (int j = 0; j < KC; ++j) {
-                    if (P[j] < 0) continue;
-                    const float4 p = J.map.pts[P[j]];
-                    const float ed2 = exact_d2(p);
+            }
+        }
+    }
+    // Tree walks.  Few in this warp: all lanes walk for each of them in turn.
+    unsigned pend = __ballot_sync(FULL, walk != 0);
+    if (pend != 0u && __popc(pend) <= J.coop_max) {
+        while (pend != 0u) {
+            const int o = __ffs(pend) - 1;
+            pend &= pend - 1u;
+            const int mode = __shfl_sync(FULL, walk, o);
+            const float q0 = __shfl_sync(FULL, y0, o), q1 = __shfl_sync(FULL, y1, o),
+                        q2 = __shfl_sync(FULL, y2, o);
+            const unsigned long long lk =
+                __shfl_sync(FULL, walk == 1 ? dkey(best_d2, best_oi) : dkey(lim, 0x7fffffff), o);
+            const int ip = __shfl_sync(FULL, best_pos, o);
+            const int k0 = __shfl_sync(FULL, h0, o), k1 = __shfl_sync(FULL, h1, o);
+            const int so = __shfl_sync(FULL, s, o);
+            unsigned long long key;
+            int pos;
+            if (!warp_knn(J.map, nmap, q0, q1, q2, mode == 1 ? 1 : KC, lk, mode == 1 ? ip : -1, k0, k1, wstack, key,
+                          pos))
+                continue;  // stack overflow: lane o walks alone below
+            if (mode == 1) {
+                const unsigned long long k = __shfl_sync(FULL, key, 0);
+                const int p = __shfl_sync(FULL, pos, 0);
+                if (lane == o) {
+                    best_d2 = key_d2(k);
+                    best_oi = key_idx(k);
+                    best_pos = p;
+                    walk = 0;
+                    reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+                    J.anchor[s] = make_float4(y0, y1, y2, -1.f);
+                }
+            } else {
+                const unsigned long long klast = __shfl_sync(FULL, key, KC - 1);
+                const float rc = (key_idx(klast) != 0x7fffffff ? sqrtf(key_d2(klast)) : Rs) * (1.f - 1e-6f);
+                if (lane < KC) J.cand[(long)KC * so + lane] = pos;
+                if (lane == 0) J.anchor[so] = make_float4(q0, q1, q2, rc);
+                // the nearest by hi + lo among the list: lane j < KC tests entry j
+                const float m0 = __shfl_sync(FULL, l0, o), m1 = __shfl_sync(FULL, l1, o),
+                            m2 = __shfl_sync(FULL, l2, o);
+                unsigned long long ek = ~0ull;
+                if (lane < KC && pos >= 0) {
+                    const float4 p = J.map.pts[pos];
+                    const float ed2 = sq3(__fsub_rn(__fsub_rn(p.x, q0), m0), __fsub_rn(__fsub_rn(p.y, q1), m1),
+                                          __fsub_rn(__fsub_rn(p.z, q2), m2));
                     const int oi = __float_as_int(p.w);
-                    if (before(ed2, oi, best_d2, best_oi)) {
-                        best_d2 = ed2;
-                        best_oi = oi;
-                        best_pos = P[j];
+                    if (before(ed2, oi, J.max_d2, 0x7fffffff)) ek = dkey(ed2, oi);
+                }
+                int ep = pos;
+#pragma unroll
+                for (int off = 1; off < KC; off <<= 1) {
+                    const unsigned long long ok = __shfl_xor_sync(FULL, ek, off);
+                    const int op = __shfl_xor_sync(FULL, ep, off);
+                    if (ok < ek) {
+                        ek = ok;
+                        ep = op;
+                    }
+                }
+                ek = __shfl_sync(FULL, ek, 0);
+                ep = __shfl_sync(FULL, ep, 0);
+                if (lane == o) {
+                    walk = 0;
+                    if (ek != ~0ull) {
+                        best_d2 = key_d2(ek);
+                        best_oi = key_idx(ek);
+                        best_pos = ep;
+                    } else {
+                        best_d2 = J.max_d2;
+                        best_oi = 0x7fffffff;
+                        best_pos = -1;
                     }
                 }
             }
         }
-        if (J.corr_out) J.corr_out[__float_as_int(x.w)] = best_pos >= 0 ? best_oi : -1;
-        if (best_pos < 0) return refreshed;
-
-        acc[28] += 1.f;
-        const float4 mu = J.map.pts[best_pos];
-        const float4 ca = J.map.covs[2 * best_pos], cb = J.map.covs[2 * best_pos + 1];
-        const float4 sa = J.covs_s[2l * s], sb = J.covs_s[2l * s + 1];
-        const float S[9] = {sa.x, sa.y, sa.z, sa.y, sa.w, sb.x, sa.z, sb.x, sb.y};
-        float RS[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                RS[3 * r + c] = fmaf(R[3 * r], S[c], fmaf(R[3 * r + 1], S[3 + c], R[3 * r + 2] * S[6 + c]));
-        auto rcr = [&](int r, int c) {
-            return fmaf(RS[3 * r], R[3 * c], fmaf(RS[3 * r + 1], R[3 * c + 1], RS[3 * r + 2] * R[3 * c + 2]));
+    }
+    // Many in this warp (or a cooperative walk ran out of stack): each point walks alone.
+    if (walk == 1) {
+        auto scan1 = [&](int lf) {
+            scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), [&](int u, const float4& p) {
+                const float d2 = point_d2(y0, y1, y2, p);
+                const int oi = __float_as_int(p.w);
+                if (before(d2, oi, best_d2, best_oi)) {
+                    best_d2 = d2;
+                    best_oi = oi;
+                    best_pos = u;
+                }
+            });
         };
-        // Sigma = C^t + R C^s R^T
-        const float s00 = ca.x + rcr(0, 0), s01 = ca.y + rcr(0, 1), s02 = ca.z + rcr(0, 2);
-        const float s11 = ca.w + rcr(1, 1), s12 = cb.x + rcr(1, 2), s22 = cb.y + rcr(2, 2);
-        // W = Sigma^-1 (cofactors / determinant)
-        const float c00 = s11 * s22 - s12 * s12, c01 = s02 * s12 - s01 * s22, c02 = s01 * s12 - s02 * s11;
-        const float det = s00 * c00 + s01 * c01 + s02 * c02;
-        if (!(fabsf(det) > 0.f)) return refreshed;
-        const float id = 1.f / det;
-        const float W00 = c00 * id, W01 = c01 * id, W02 = c02 * id;
-        const float W11 = (s00 * s22 - s02 * s02) * id, W12 = (s01 * s02 - s00 * s12) * id;
-        const float W22 = (s00 * s11 - s01 * s01) * id;
-        const float W[9] = {W00, W01, W02, W01, W11, W12, W02, W12, W22};
-        const float d0 = __fsub_rn(__fsub_rn(mu.x, y0), l0), d1 = __fsub_rn(__fsub_rn(mu.y, y1), l1),
-                    d2 = __fsub_rn(__fsub_rn(mu.z, y2), l2);
-        const float Wd0 = W00 * d0 + W01 * d1 + W02 * d2;
-        const float Wd1 = W01 * d0 + W11 * d1 + W12 * d2;
-        const float Wd2 = W02 * d0 + W12 * d1 + W22 * d2;
-        // A = [y]x ; WA = W A
-        const float A[9] = {0.f, -y2, y1, y2, 0.f, -y0, -y1, y0, 0.f};
-        float WA[9];
+        if (h0 >= 0) scan1(h0);
+        traverse8(J.map, y0, y1, y2, best_d2, [&](int lf) {
+            if (lf != h0) scan1(lf);
+        });
+        reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+        J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
+    } else if (walk == 2) {
+        unsigned long long Lk[KC];
+        int P[KC];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                WA[3 * r + c] = W[3 * r] * A[c] + W[3 * r + 1] * A[3 + c] + W[3 * r + 2] * A[6 + c];
-        // A^T W A = -A (W A): column c is -(y x WA[:, c])
-        float AWA[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float m0 = WA[c], m1 = WA[3 + c], m2 = WA[6 + c];
-            AWA[c] = -(y1 * m2 - y2 * m1);
-            AWA[3 + c] = -(y2 * m0 - y0 * m2);
-            AWA[6 + c] = -(y0 * m1 - y1 * m0);
+        for (int j = 0; j < KC; ++j) {
+            Lk[j] = dkey(lim, 0x7fffffff);
+            P[j] = -1;
         }
+        float bound = lim;
+        auto scan_leaf = [&](int lf) {
+            scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), [&](int u, const float4& p) {
+                const unsigned long long key = dkey(point_d2(y0, y1, y2, p), __float_as_int(p.w));
+                if (key < Lk[KC - 1]) key_insert(Lk, P, key, u);
+            });
+            bound = key_d2(Lk[KC - 1]);
+        };
+        if (h0 >= 0) scan_leaf(h0);
+        if (h1 >= 0) scan_leaf(h1);
+        traverse8(J.map, y0, y1, y2, bound, [&](int lf) {
+            if (lf != h0 && lf != h1) scan_leaf(lf);
+        });
+        const float rc = (key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : Rs) * (1.f - 1e-6f);
+        reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
+        reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
+        J.anchor[s] = make_float4(y0, y1, y2, rc);
+        pick_exact(P);
+    }
+    if (!active) return 0;
+    if (J.corr_out) J.corr_out[__float_as_int(x.w)] = best_pos >= 0 ? best_oi : -1;
+    if (best_pos < 0) return refreshed;
+
+    acc[28] += 1.f;
+    const float4 mu = J.map.pts[best_pos];
+    const float4 ca = J.map.covs[2 * best_pos], cb = J.map.covs[2 * best_pos + 1];
+    const float4 sa = J.covs_s[2l * s], sb = J.covs_s[2l * s + 1];
+    const float S[9] = {sa.x, sa.y, sa.z, sa.y, sa.w, sb.x, sa.z, sb.x, sb.y};
+    float RS[9];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = r; c < 3; ++c) acc[ut(r, c)] += AWA[3 * r + c];
+        for (int c = 0; c < 3; ++c)
+            RS[3 * r + c] = fmaf(R[3 * r], S[c], fmaf(R[3 * r + 1], S[3 + c], R[3 * r + 2] * S[6 + c]));
+    auto rcr = [&](int r, int c) {
+        return fmaf(RS[3 * r], R[3 * c], fmaf(RS[3 * r + 1], R[3 * c + 1], RS[3 * r + 2] * R[3 * c + 2]));
+    };
+    // Sigma = C^t + R C^s R^T
+    const float s00 = ca.x + rcr(0, 0), s01 = ca.y + rcr(0, 1), s02 = ca.z + rcr(0, 2);
+    const float s11 = ca.w + rcr(1, 1), s12 = cb.x + rcr(1, 2), s22 = cb.y + rcr(2, 2);
+    // W = Sigma^-1 (cofactors / determinant)
+    const float c00 = s11 * s22 - s12 * s12, c01 = s02 * s12 - s01 * s22, c02 = s01 * s12 - s02 * s11;
+    const float det = s00 * c00 + s01 * c01 + s02 * c02;
+    if (!(fabsf(det) > 0.f)) return refreshed;
+    const float id = 1.f / det;
+    const float W00 = c00 * id, W01 = c01 * id, W02 = c02 * id;
+    const float W11 = (s00 * s22 - s02 * s02) * id, W12 = (s01 * s02 - s00 * s12) * id;
+    const float W22 = (s00 * s11 - s01 * s01) * id;
+    const float W[9] = {W00, W01, W02, W01, W11, W12, W02, W12, W22};
+    const float d0 = __fsub_rn(__fsub_rn(mu.x, y0), l0), d1 = __fsub_rn(__fsub_rn(mu.y, y1), l1),
+                d2 = __fsub_rn(__fsub_rn(mu.z, y2), l2);
+    const float Wd0 = W00 * d0 + W01 * d1 + W02 * d2;
+    const float Wd1 = W01 * d0 + W11 * d1 + W12 * d2;
+    const float Wd2 = W02 * d0 + W12 * d1 + W22 * d2;
+    // A = [y]x ; WA = W A
+    const float A[9] = {0.f, -y2, y1, y2, 0.f, -y0, -y1, y0, 0.f};
+    float WA[9];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[ut(r, 3 + c)] -= WA[3 * c + r];
+        for (int c = 0; c < 3; ++c)
+            WA[3 * r + c] = W[3 * r] * A[c] + W[3 * r + 1] * A[3 + c] + W[3 * r + 2] * A[6 + c];
+    // A^T W A = -A (W A): column c is -(y x WA[:, c])
+    float AWA[9];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+        const float m0 = WA[c], m1 = WA[3 + c], m2 = WA[6 + c];
+        AWA[c] = -(y1 * m2 - y2 * m1);
+        AWA[3 + c] = -(y2 * m0 - y0 * m2);
+        AWA[6 + c] = -(y0 * m1 - y1 * m0);
+    }
 #pragma unroll
-            for (int c = r; c < 3; ++c) acc[ut(3 + r, 3 + c)] += W[3 * r + c];
-        // b = [A^T W d ; -W d],  A^T u = u x y
-        acc[21] += Wd1 * y2 - Wd2 * y1;
-        acc[22] += Wd2 * y0 - Wd0 * y2;
-        acc[23] += Wd0 * y1 - Wd1 * y0;
-        acc[24] -= Wd0;
-        acc[25] -= Wd1;
-        acc[26] -= Wd2;
-        acc[27] += d0 * Wd0 + d1 * Wd1 + d2 * Wd2;
-        return refreshed;
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) acc[ut(r, c)] += AWA[3 * r + c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[ut(r, 3 + c)] -= WA[3 * c + r];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) acc[ut(3 + r, 3 + c)] += W[3 * r + c];
+    // b = [A^T W d ; -W d],  A^T u = u x y
+    acc[21] += Wd1 * y2 - Wd2 * y1;
+    acc[22] += Wd2 * y0 - Wd0 * y2;
+    acc[23] += Wd0 * y1 - Wd1 * y0;
+    acc[24] -= Wd0;
+    acc[25] -= Wd1;
+    acc[26] -= Wd2;
+    acc[27] += d0 * Wd0 + d1 * Wd1 + d2 * Wd2;
+    return refreshed;
 }
 
 // Block-wide sum of acc into row[0 .. NACC) (row[NACC ..32) zeroed; visible device-wide on return
@@ -671,9 +781,9 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
     // One source point per thread (the grid covers the context's capacity; the hardware block
     // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
     // the reduction order, hence the result, deterministic).
-    int refreshed = 0;
+    __shared__ int2 wstack[REG_THREADS / 32][WARP_STACK];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) refreshed = gn_point(J, R, Rl, t, tl, s, nmap, acc);
+    const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
     const int block_refreshed = block_partial(acc, refreshed, J.partials + 32l * blockIdx.x);
     __shared__ bool am_last;
     if (threadIdx.x == 0) {
@@ -720,6 +830,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_batch_kernel(const RegJob
     __shared__ long long s_item;
     __shared__ unsigned s_base;
     __shared__ bool s_last;
+    __shared__ int2 wstack[REG_THREADS / 32][WARP_STACK];
     for (;;) {
         if (threadIdx.x == 0) {
             long long got = -1;
@@ -766,8 +877,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_batch_kernel(const RegJob
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
         const int s = c * REG_THREADS + threadIdx.x;
-        int refreshed = 0;
-        if (s < n) refreshed = gn_point(J, R, Rl, t, tl, s, nmap, acc);
+        const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
         block_partial(acc, refreshed, J.partials + 32l * c);
         if (threadIdx.x == 0) s_last = atomicAdd(&st->counter, 1u) == (unsigned)nchunks - 1u;
         __syncthreads();

@@ -161,6 +161,7 @@ struct gsicp_ctx_s {
     gsicp::BatchMachine batch;
     int64_t* host_pinned = nullptr;   // small pinned scratch for counts
     bool timing = false;
+    int coop_walks = gsicp::COOP_WALKS_DEFAULT;  // RegJob::coop_max of this context's registrations
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double phase_ms[6] = {0, 0, 0, 0, 0, 0};
 };

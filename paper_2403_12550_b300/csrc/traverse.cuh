@@ -208,6 +208,121 @@ __device__ __forceinline__ void packet_traverse(const IndexView& ix, bool active
     }
 }
 
+// Warp-cooperative exact search for the kk (1 <= kk <= 32) nearest points of ONE query: all 32
+// lanes call it, converged, with the same arguments.  The list of the kk smallest (squared
+// distance, index) keys below lim_key is kept ascending in lanes 0 .. kk-1 (lane 0 may start with
+// a known point at init_pos; the other entries start empty).  Leaves skip0 / skip1 (or -1) are
+// scanned first and skipped by the walk.  The walk keeps its stack in shared memory (stk, WARP_STACK
+// entries of (node, box distance bits)); each step takes up to four of the top entries whose box
+// is still within the bound and gives each eight lanes: an internal node's eight descendants
+// three levels down are box-tested and pushed, a leaf's points are read eight at a time and
+// offered to the list.  A step thus costs one dependent memory round trip for up to 32 boxes or
+// 32 points, where a single-thread walk pays one per node and one per four points.  Exactness is
+// the argument of traverse(): a box is dropped only when its lower bound exceeds the current bound,
+// which only shrinks.  Returns false, list incomplete, if the stack would overflow; the caller
+// then searches this query alone.
+constexpr int WARP_STACK = 256;
+
+__device__ __forceinline__ bool warp_knn(const IndexView& ix, int nmap, float qx, float qy, float qz, int kk,
+                                         unsigned long long lim_key, int init_pos, int skip0, int skip1,
+                                         int2* __restrict__ stk, unsigned long long& lkey, int& lpos)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned long long NONE = ~0ull;
+    const int lane = threadIdx.x & 31, slot = lane >> 3, sub = lane & 7;
+    const unsigned below = (1u << lane) - 1u;
+    const int L = ix.L, B = ix.B;
+    lkey = lim_key;
+    lpos = lane == 0 ? init_pos : -1;
+    unsigned long long kth = lim_key;  // list entry kk-1 (every lane)
+    // offer one candidate key per lane (NONE: none) to the list, one accepted key at a time
+    auto offer = [&](unsigned long long ck, int cpos) {
+        unsigned m = __ballot_sync(FULL, ck < kth);
+        while (m != 0u) {
+            const int src = __ffs(m) - 1;
+            const unsigned long long k = __shfl_sync(FULL, ck, src);
+            const int p = __shfl_sync(FULL, cpos, src);
+            const unsigned long long up = __shfl_up_sync(FULL, lkey, 1);
+            const int upp = __shfl_up_sync(FULL, lpos, 1);
+            if (lane < kk && k < lkey) {
+                const bool here = lane == 0 || up < k;
+                lkey = here ? k : up;
+                lpos = here ? p : upp;
+            }
+            kth = __shfl_sync(FULL, lkey, kk - 1);
+            if (lane == src) ck = NONE;
+            m = __ballot_sync(FULL, ck < kth);
+        }
+    };
+    // the points of leaf lf (or none for lf < 0) handled by this lane: sub, sub + 8, ... < B
+    auto scan_leaf = [&](int lf) {
+        unsigned long long ck[4];
+        int cu[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int u = lf * B + sub + 8 * r;
+            const bool ok = lf >= 0 && 8 * r < B && u < nmap;
+            const float4 p = ok ? __ldg(ix.pts + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ck[r] = ok ? dkey(point_d2(qx, qy, qz, p), __float_as_int(p.w)) : NONE;
+            cu[r] = u;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) offer(ck[r], cu[r]);
+    };
+    scan_leaf(slot == 0 ? skip0 : (slot == 1 ? skip1 : -1));
+    // entry nodes: the 1, 2 or 4 nodes at depth (log2 L) mod 3, from which 8-way steps reach the leaves
+    int sp;
+    {
+        const int first = 1 << ((31 - __clz(L)) % 3);
+        float d = GSICP_INF;
+        if (lane < first) d = box_d2(qx, qy, qz, ix.boxes[2 * (first + lane)], ix.boxes[2 * (first + lane) + 1]);
+        const bool push = lane < first && d <= key_d2(kth);
+        const unsigned pm = __ballot_sync(FULL, push);
+        if (push) stk[__popc(pm & below)] = make_int2(first + lane, __float_as_int(d));
+        sp = __popc(pm);
+        __syncwarp();
+    }
+    while (sp > 0) {
+        const float bound = key_d2(kth);
+        // the top eight entries (lane 0 = top); live ones are still within the bound
+        const int rd = min(8, sp);
+        const int2 e = lane < rd ? stk[sp - 1 - lane] : make_int2(0, __float_as_int(GSICP_INF));
+        const unsigned live = __ballot_sync(FULL, lane < rd && __int_as_float(e.y) <= bound);
+        // take the first four live entries; entries above the last one taken are consumed
+        unsigned rest = live;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rest &= rest - 1u;
+        const unsigned take = live & ~rest;
+        sp -= rest != 0u ? 32 - __clz(take) : rd;
+        unsigned mine = take;  // this slot's entry: the slot-th set bit of take
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < slot) mine &= mine - 1u;
+        int node = __shfl_sync(FULL, e.x, mine != 0u ? __ffs(mine) - 1 : 0);
+        if (mine == 0u) node = 0;
+        __syncwarp();  // reads of the popped entries before the pushes below overwrite them
+        bool push = false;
+        int child = 0;
+        float d = GSICP_INF;
+        int lf = -1;
+        if (node != 0 && node < L) {
+            child = 8 * node + sub;
+            d = box_d2(qx, qy, qz, __ldg(ix.boxes + 2 * child), __ldg(ix.boxes + 2 * child + 1));
+            push = d <= bound;
+        } else if (node >= L) {
+            lf = node - L;
+            if (lf == skip0 || lf == skip1) lf = -1;
+        }
+        const unsigned pm = __ballot_sync(FULL, push);
+        if (sp + __popc(pm) > WARP_STACK) return false;
+        if (push) stk[sp + __popc(pm & below)] = make_int2(child, __float_as_int(d));
+        sp += __popc(pm);
+        if (__any_sync(FULL, lf >= 0)) scan_leaf(lf);
+        __syncwarp();  // pushes visible to the next step's reads
+    }
+    return true;
+}
+
 // Grid fast path.  Looks up the 2x2x2 block of grid cells around q (the octant of q's cell it
 // lies in) and returns their point ranges in rng and the radius `cert` within which the block is
 // exhaustive: every point outside it is at least cert from q (the distance from q to the block's

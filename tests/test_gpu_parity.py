@@ -409,6 +409,43 @@ def test_track_frame_config2_matches_oracle(g, ctx):
     m.close()
 
 
+def test_coop_walks_do_not_change_results(g, ctx):
+    """The cooperative tree walk (a whole warp per query) and the per-point walk are both exact:
+    the full-size frame and a config-1 registration give bit-identical poses, systems, iteration
+    counts and refresh counts whichever is used (0 = never together, 32 = always)."""
+    f, means, covs = _cfg2()
+    m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    src, cs, tgt, ct, _ = config1_inputs(1, 2)
+    m1 = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    T1 = random_offset(np.random.default_rng(7), 5.0, 0.05)
+    out = {}
+    try:
+        for c in (0, 4, 32):
+            g.gsicp_ctx_set_coop_walks(ctx, c)
+            r = g.gsicp_track_frame(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
+            st = g.gsicp_ctx_reg_stats(ctx, r["iters"])
+            r1 = g.gsicp_register(ctx, cu(src), cu(cs), m1, T1, rp)
+            out[c] = (r, st["refreshes"], r1)
+    finally:
+        g.gsicp_ctx_set_coop_walks(ctx, 4)
+    r0, ref0, r10 = out[0]
+    assert r0["status"] == g.OK and r10["status"] == g.OK
+    for c in (4, 32):
+        r, ref, r1 = out[c]
+        for key in ("T", "H"):
+            np.testing.assert_array_equal(r[key], r0[key])
+            np.testing.assert_array_equal(r1[key], r10[key])
+        assert (r["iters"], r["cost"], r["inliers"]) == (r0["iters"], r0["cost"], r0["inliers"])
+        assert (r1["iters"], r1["cost"], r1["inliers"]) == (r10["iters"], r10["cost"], r10["inliers"])
+        assert list(ref) == list(ref0)
+    with pytest.raises(RuntimeError):
+        g.gsicp_ctx_set_coop_walks(ctx, 33)
+    m.close()
+    m1.close()
+
+
 def test_track_frame_empty_depth(g, ctx):
     src, cs, tgt, ct, _ = config1_inputs(0, 0, n=2000)
     m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
