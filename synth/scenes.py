@@ -29,7 +29,7 @@ __all__ = [
     "look_pose", "circle_poses", "random_offset", "rot_axis_angle", "inv_pose", "make_pose",
     "transform_points", "Intrinsics", "REPLICA_INTR", "TUM_INTR",
     "pair_config1", "frame_config2", "spline_trajectory", "sequence_config3", "const_velocity",
-    "batch_config4",
+    "batch_config4", "HALF_TUM_INTR", "surrogate_train_config5", "sequence_config5",
 ]
 
 
@@ -430,3 +430,50 @@ def batch_config4(seed: int, n_pairs: int = 64, n_min: int = 5_000, n_max: int =
         out.append(dict(src=transform_points(inv_pose(T_gt), src_w).astype(np.float32), tgt=tgt.astype(np.float32),
                         T_gt=T_gt))
     return out
+
+
+# --------------------------------------------------------------------------- learned-covariance configuration
+
+# TUM_INTR's stride-2 sample grid as an image of its own: pixel (j, i) here looks along the same ray
+# as pixel (2j, 2i) of a 640 x 480 TUM_INTR image, so a 320 x 240 render at stride 1 yields the
+# points a 640 x 480 render yields at stride 2, at a quarter of the ray-casting cost.
+HALF_TUM_INTR = Intrinsics(320, 240, 262.5, 262.5, 159.75, 119.75)
+
+
+def surrogate_train_config5(seed: int = 0, n_frames: int = 2000, n_scenes: int = 20,
+                            intr: Intrinsics = HALF_TUM_INTR, noise_coeff: float = 1e-3):
+    """Training frames of the covariance surrogate: ``n_scenes`` config-2-style rooms (4 x 3 x 2.5 m,
+    8 boxes, 4 spheres; room seeds 1000 (seed + 1) + s, disjoint from :func:`sequence_config5`'s)
+    seen from ``n_frames`` random poses (frame f in room f mod n_scenes): positions within 0.45 m
+    of the room centre (horizontally) at heights 1.0-1.8 m, any heading, 0-40 degrees down.
+    ``depth(f)`` ray-casts frame f on demand with noise N(0, (noise_coeff z^2)^2) seeded by
+    (seed, f).  Returns a dict with keys ``scenes, intr, poses, depth``."""
+    scenes = [make_room(1000 * (seed + 1) + s) for s in range(n_scenes)]
+    rng = np.random.default_rng(555_001 + seed)
+    poses = []
+    for f in range(n_frames):
+        sc = scenes[f % n_scenes]
+        r, phi = 0.45 * np.sqrt(rng.uniform()), rng.uniform(0, 2 * np.pi)
+        pos = np.array([sc.centre[0] + r * np.cos(phi), sc.centre[1] + r * np.sin(phi), rng.uniform(1.0, 1.8)])
+        poses.append(look_pose(pos, rng.uniform(0, 2 * np.pi), np.deg2rad(rng.uniform(0.0, 40.0))))
+
+    def depth(f: int) -> np.ndarray:
+        frng = np.random.default_rng(3_000_017 * (seed + 1) + f)
+        return add_depth_noise(raycast_depth(scenes[f % n_scenes], poses[f], intr), frng, noise_coeff)
+
+    return dict(scenes=scenes, intr=intr, poses=poses, depth=depth)
+
+
+def sequence_config5(seed: int = 0, n_frames: int = 500, intr: Intrinsics = TUM_INTR, noise_coeff: float = 1e-3):
+    """Held-out sequence of the covariance surrogate: a config-2-style room (seed 500 + seed, none of
+    the training rooms), ``n_frames`` poses at 30 Hz along :func:`spline_trajectory` (<= 1 m/s,
+    <= 60 deg/s, 0.35 m clearance: the room is small), 640 x 480 depth frames ``depth(f)`` with
+    noise seeded by (seed, f).  Returns a dict with keys ``scene, intr, poses, depth``."""
+    scene = make_room(500 + seed)
+    poses = spline_trajectory(seed, scene, n_frames=n_frames, clearance=0.35)
+
+    def depth(f: int) -> np.ndarray:
+        rng = np.random.default_rng(8_000_009 * (seed + 1) + f)
+        return add_depth_noise(raycast_depth(scene, poses[f], intr), rng, noise_coeff)
+
+    return dict(scene=scene, intr=intr, poses=poses, depth=depth)

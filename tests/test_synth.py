@@ -33,3 +33,19 @@ def test_rot_angle_reads_angles_and_ignores_scale():
         R = rot_axis_angle(np.array([0.2, -0.7, 0.4]), a)
         assert abs(rot_angle(R) - a) < 1e-12
         assert abs(rot_angle(R * (1 - 3e-9)) - a) < 1e-8  # not sqrt(6 * 3e-9) = 1.3e-4
+
+
+def test_config5_half_res_grid_and_held_out_rooms():
+    """A HALF_TUM_INTR render is the stride-2 sample grid of the TUM_INTR render from the same
+    pose; the training rooms exclude the held-out sequence's room; frames are deterministic."""
+    from synth import HALF_TUM_INTR, TUM_INTR, raycast_depth, sequence_config5, surrogate_train_config5
+    tr = surrogate_train_config5(0, n_frames=6, n_scenes=3)
+    full = raycast_depth(tr["scenes"][1], tr["poses"][1], TUM_INTR)
+    half = raycast_depth(tr["scenes"][1], tr["poses"][1], HALF_TUM_INTR)
+    np.testing.assert_allclose(half, full[::2, ::2], rtol=1e-6)
+    np.testing.assert_array_equal(tr["depth"](4), tr["depth"](4))
+    seq = sequence_config5(0, n_frames=10)
+    held = seq["scene"]
+    for sc in tr["scenes"]:
+        assert not (np.array_equal(sc.box_center, held.box_center) and np.array_equal(sc.sph_center, held.sph_center))
+    assert seq["depth"](3).shape == (480, 640)
