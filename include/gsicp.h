@@ -364,6 +364,65 @@ gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_dev, int W,
 /* The tracker's maps (owned by the tracker; NULL before the first frame). */
 gsicp_status gsicp_tracker_maps(gsicp_tracker t, gsicp_map* tracking_map, gsicp_map* mapping_map);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned covariance surrogate.  A small convolutional network over the stride-sampled point map
+ * of a depth frame predicts each point's surface normal n; the point's Gaussian is then the
+ * plane-regularised, scale-aligned covariance of Sec. 3 built on it, (I - (1 - eps) n n^T)
+ * z^(-2p), in place of the k-NN covariance (a2 + a3).  Network: layer 1 maps the centred
+ * differences M(u+d) (P(u+d) - P(u)) of the 5 x 5 samples around u (P the back-projected sample,
+ * M its validity) to 32 channels, layer 2 is a 5 x 5 convolution 32 -> 32, layer 3 a 5 x 5
+ * convolution 32 -> 3 giving v, n = v / |v| (|v| = 0: isotropic z^(-2p) I); no biases; ReLU and
+ * bfloat16 rounding after layers 1 and 2, zero at invalid samples; taps read (i + dy - 2,
+ * j + dx - 2), zero outside the image.  Weights are bfloat16 (the float weights rounded to
+ * nearest even); every sum is float.  Weight vector layout (GSICP_SURROGATE_WEIGHTS floats):
+ * W1[32][3][5][5], W2[32][32][5][5], W3[3][32][5][5] ([out][in][dy][dx]).
+ * ------------------------------------------------------------------------------------------- */
+#define GSICP_SURROGATE_WEIGHTS 30400
+typedef struct gsicp_surrogate_s* gsicp_surrogate;
+
+/* A surrogate with the given weights (host, GSICP_SURROGATE_WEIGHTS floats) on the current
+ * device; Adam state zero.  Synchronises the device's default stream. */
+gsicp_status gsicp_surrogate_create(const float* weights, gsicp_surrogate* out);
+void gsicp_surrogate_destroy(gsicp_surrogate sg);
+/* Copy the current float weights out (host) / replace them (host; resets the Adam state). */
+gsicp_status gsicp_surrogate_get_weights(gsicp_surrogate sg, float* weights);
+gsicp_status gsicp_surrogate_set_weights(gsicp_surrogate sg, const float* weights);
+
+/* a1 + the surrogate's covariances of one depth frame: points as gsicp_depth_to_points writes
+ * them (pts_dev cap x 3, z_dev nullable) and their covariances (covs_dev cap x 6, same order)
+ * from params->eps and params->p (k and reg_mode unused).  v_dev (nullable, device,
+ * ceil(H/stride) x ceil(W/stride) x 3 floats): the network's raw output per sample, zero at
+ * invalid samples.  *n_out as gsicp_frame_covariances (synchronises; GSICP_ERR_CAPACITY when the
+ * frame has more than cap points). */
+gsicp_status gsicp_surrogate_covariances(gsicp_ctx ctx, gsicp_surrogate sg, const float* depth_dev, int W, int H,
+                                         const float intr[4], int stride, float z_min, float z_max,
+                                         const gsicp_cov_params* params, float* pts_dev, float* z_dev,
+                                         float* covs_dev, float* v_dev, int64_t cap, int64_t* n_out, void* stream);
+
+/* One training step on one depth frame.  Targets: target_covs_dev (device, the frame's points'
+ * plane-regularised covariances in a1 order, cap x 6) or, when null, the frame's own k-NN
+ * covariances from params (reg_mode must then be GSICP_REG_PLANE).  Loss: the mean over points
+ * whose target is a plane covariance (T = (I - C z^(2p)) / (1 - eps) with trace within 0.01 of
+ * 1) of 1 - n^T T n.  Gradients by back-propagation, the bfloat16 roundings taken as the
+ * identity.  apply = 1: one Adam step (b1 0.9, b2 0.999, eps 1e-8, learning rate lr) on the
+ * float weights; apply = 0: weights and Adam state untouched.  loss_out, count_out (targets used)
+ * and grad_out (host, GSICP_SURROGATE_WEIGHTS floats: the gradient of the mean) are nullable.
+ * Synchronises the stream. */
+gsicp_status gsicp_surrogate_train_step(gsicp_ctx ctx, gsicp_surrogate sg, const float* depth_dev, int W, int H,
+                                        const float intr[4], int stride, float z_min, float z_max,
+                                        const gsicp_cov_params* params, const float* target_covs_dev, float lr,
+                                        int apply, double* loss_out, int64_t* count_out, float* grad_out,
+                                        void* stream);
+
+/* gsicp_track_frame with the surrogate's covariances in place of the k-NN ones (cov_params
+ * supplies eps and p). */
+gsicp_status gsicp_track_frame_surrogate(gsicp_ctx ctx, gsicp_surrogate sg, const float* depth_dev, int W, int H,
+                                         const float intr[4], int stride, float z_min, float z_max,
+                                         const gsicp_cov_params* cov_params, gsicp_map map, const double T0[16],
+                                         const gsicp_reg_params* reg_params, double T_out[16], double H_out[36],
+                                         int* iters_out, double* cost_out, int64_t* inliers_out,
+                                         int64_t* n_points_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,8 @@ __all__ = [
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_selftest_batch_timeout", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
     "KeyframeParams", "FrameInfo", "Tracker", "FRAME", "KEYFRAME", "MAPPING_KEYFRAME",
+    "Surrogate", "SURROGATE_WEIGHTS", "gsicp_surrogate_covariances", "gsicp_surrogate_train_step",
+    "gsicp_track_frame_surrogate",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgsicp.so")
@@ -137,6 +139,18 @@ _sig("gsicp_map_nearest", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp, _v
 for _n in ("gsicp_track_frame", "gsicp_track_frame_host"):
     _sig(_n, C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float, C.POINTER(CovParams), _vp,
                        _dp, C.POINTER(RegParams), _dp, _dp, C.POINTER(C.c_int), _dp, _i64p, _i64p, _vp])
+_sig("gsicp_track_frame_surrogate", C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float,
+                                              C.POINTER(CovParams), _vp, _dp, C.POINTER(RegParams), _dp, _dp,
+                                              C.POINTER(C.c_int), _dp, _i64p, _i64p, _vp])
+_sig("gsicp_surrogate_create", C.c_int, [_fp, C.POINTER(C.c_void_p)])
+_sig("gsicp_surrogate_destroy", None, [_vp])
+_sig("gsicp_surrogate_get_weights", C.c_int, [_vp, _fp])
+_sig("gsicp_surrogate_set_weights", C.c_int, [_vp, _fp])
+_sig("gsicp_surrogate_covariances", C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float,
+                                              C.POINTER(CovParams), _vp, _vp, _vp, _vp, C.c_int64, _i64p, _vp])
+_sig("gsicp_surrogate_train_step", C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float,
+                                             C.POINTER(CovParams), _vp, C.c_float, C.c_int, _dp, _i64p, _fp, _vp])
+SURROGATE_WEIGHTS = 30400
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -492,6 +506,99 @@ def gsicp_track_frame(ctx: Context, depth: torch.Tensor, intr, stride: int, z_mi
     H, W = depth.shape
     return _frame(lib.gsicp_track_frame, ctx, _dev(depth), W, H, intr, stride, z_min, z_max, cov_params, map_, T0,
                   reg_params)
+
+
+def gsicp_track_frame_surrogate(ctx: Context, sg: "Surrogate", depth: torch.Tensor, intr, stride: int, z_min: float,
+                                z_max: float, cov_params: CovParams, map_: MapHandle, T0, reg_params: RegParams) -> dict:
+    """gsicp_track_frame with the surrogate's covariances (cov_params gives eps and p)."""
+    H, W = depth.shape
+    fn = lib.gsicp_track_frame_surrogate
+    T, Hm, _, it, cost, cnt = _reg_outputs()
+    npts = C.c_int64(0)
+    fi = (C.c_float * 4)(*[float(v) for v in intr])
+    st = fn(ctx.ptr, sg.ptr, _dev(depth), W, H, fi, stride, z_min, z_max, C.byref(cov_params), map_.ptr, _pose(T0),
+            C.byref(reg_params), T, Hm, C.byref(it), C.byref(cost), C.byref(cnt), C.byref(npts), _stream())
+    _check(st, "gsicp_track_frame_surrogate", allow=(ERR_DEGENERATE,))
+    return dict(T=np.array(T).reshape(4, 4), H=np.array(Hm).reshape(6, 6), iters=it.value, cost=cost.value,
+                inliers=cnt.value, n_points=npts.value, status=st)
+
+
+class Surrogate:
+    """Owns a ``gsicp_surrogate``: the covariance network's weights (float master copy, bfloat16
+    kernel copies) and its Adam state on the current device."""
+
+    def __init__(self, weights):
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        if w.size != SURROGATE_WEIGHTS:
+            raise ValueError(f"expected {SURROGATE_WEIGHTS} weights")
+        h = C.c_void_p()
+        _check(lib.gsicp_surrogate_create(w.ctypes.data_as(_fp), C.byref(h)), "gsicp_surrogate_create")
+        self.ptr = h
+
+    def weights(self) -> np.ndarray:
+        out = np.empty(SURROGATE_WEIGHTS, np.float32)
+        _check(lib.gsicp_surrogate_get_weights(self.ptr, out.ctypes.data_as(_fp)), "gsicp_surrogate_get_weights")
+        return out
+
+    def set_weights(self, weights):
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        if w.size != SURROGATE_WEIGHTS:
+            raise ValueError(f"expected {SURROGATE_WEIGHTS} weights")
+        _check(lib.gsicp_surrogate_set_weights(self.ptr, w.ctypes.data_as(_fp)), "gsicp_surrogate_set_weights")
+
+    def close(self):
+        if self.ptr:
+            lib.gsicp_surrogate_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gsicp_surrogate_covariances(ctx: Context, sg: Surrogate, depth: torch.Tensor, intr, stride: int, z_min: float,
+                                z_max: float, params: CovParams, want_v: bool = False):
+    """a1 + surrogate covariances of one device depth frame.  Returns (pts[:n], z[:n], covs[:n])
+    and, with want_v, the raw network output per sample (h, w, 3)."""
+    H, W = depth.shape
+    hs, ws = (H + stride - 1) // stride, (W + stride - 1) // stride
+    cap = hs * ws
+    pts = torch.empty((cap, 3), device=depth.device, dtype=torch.float32)
+    z = torch.empty((cap,), device=depth.device, dtype=torch.float32)
+    covs = torch.empty((cap, 6), device=depth.device, dtype=torch.float32)
+    v = torch.empty((hs, ws, 3), device=depth.device, dtype=torch.float32) if want_v else None
+    fi = (C.c_float * 4)(*[float(a) for a in intr])
+    n = C.c_int64(0)
+    _check(lib.gsicp_surrogate_covariances(ctx.ptr, sg.ptr, _dev(depth), W, H, fi, stride, z_min, z_max,
+                                           C.byref(params), _dev(pts, cols=3), _dev(z), _dev(covs, cols=6),
+                                           _dev(v) if v is not None else None, cap, C.byref(n), _stream()),
+           "gsicp_surrogate_covariances")
+    m = n.value
+    out = (pts[:m], z[:m], covs[:m])
+    return out + (v,) if want_v else out
+
+
+def gsicp_surrogate_train_step(ctx: Context, sg: Surrogate, depth: torch.Tensor, intr, stride: int, z_min: float,
+                               z_max: float, params: CovParams, target_covs: torch.Tensor | None = None,
+                               lr: float = 1e-3, apply: bool = True, want_grad: bool = False) -> dict:
+    """One training step (targets: target_covs in a1 order, or the frame's own k-NN covariances).
+    Returns dict(loss, count[, grad])."""
+    H, W = depth.shape
+    fi = (C.c_float * 4)(*[float(a) for a in intr])
+    loss = C.c_double(0.0)
+    cnt = C.c_int64(0)
+    grad = np.empty(SURROGATE_WEIGHTS, np.float32) if want_grad else None
+    _check(lib.gsicp_surrogate_train_step(ctx.ptr, sg.ptr, _dev(depth), W, H, fi, stride, z_min, z_max,
+                                          C.byref(params), _dev(target_covs, cols=6) if target_covs is not None else None,
+                                          float(lr), int(bool(apply)), C.byref(loss), C.byref(cnt),
+                                          grad.ctypes.data_as(_fp) if grad is not None else None, _stream()),
+           "gsicp_surrogate_train_step")
+    out = dict(loss=loss.value, count=cnt.value)
+    if want_grad:
+        out["grad"] = grad
+    return out
 
 
 def gsicp_track_frame_host(ctx: Context, depth_host, intr, stride: int, z_min: float, z_max: float,

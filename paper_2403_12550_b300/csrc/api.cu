@@ -604,7 +604,7 @@ gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* querie
 // row-major order, their covariances in the same order and in the source index's order).
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                       int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
-                                      int cap, cudaStream_t s)
+                                      int cap, cudaStream_t s, gsicp_surrogate sg)
 {
     const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
     GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)cap));
@@ -623,10 +623,14 @@ gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
     GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
-    GSICP_CHECK(launch_frame_knn_cov(ctx->src_index.view(), ctx->frame_idx.as<int>(), Ws, Hs, stride, intr,
-                                     ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap, *cov_params,
-                                     ctx->frame_covs.as<float>(), nullptr, ctx->fb_list.as<int>(),
-                                     ctx->fb_count.as<int>(), s));
+    if (sg)
+        GSICP_CHECK(surrogate_forward(sg, ctx->frame_pts.as<float>(), ctx->frame_idx.as<int>(), Ws, Hs,
+                                      cov_params->eps, cov_params->p, ctx->frame_covs.as<float>(), nullptr, s));
+    else
+        GSICP_CHECK(launch_frame_knn_cov(ctx->src_index.view(), ctx->frame_idx.as<int>(), Ws, Hs, stride, intr,
+                                         ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap, *cov_params,
+                                         ctx->frame_covs.as<float>(), nullptr, ctx->fb_list.as<int>(),
+                                         ctx->fb_count.as<int>(), s));
     GSICP_CHECK(launch_permute_covs(ctx->src_index.view(), ctx->frame_covs.as<float>(), cap,
                                     ctx->covs_sorted.as<float4>(), s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], s));
@@ -645,7 +649,7 @@ gsicp_status gsicp_frame_covariances(gsicp_ctx ctx, const float* depth_dev, int 
     const int64_t frame_cap = (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride);
     if (frame_cap > (1 << 30)) return GSICP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, params, (int)frame_cap, s));
+    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, params, (int)frame_cap, s, nullptr));
     int* h = (int*)ctx->host_pinned;
     GSICP_CUDA(cudaMemcpyAsync(h, ctx->n_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GSICP_CUDA(cudaStreamSynchronize(s));
@@ -664,14 +668,15 @@ gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int 
                                      int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
                                      gsicp_map map, const double T0[16], const gsicp_reg_params* reg_params,
                                      double T_out[16], double H_out[36], int* iters_out, double* cost_out,
-                                     int64_t* inliers_out, int64_t* n_points_out, cudaStream_t s)
+                                     int64_t* inliers_out, int64_t* n_points_out, cudaStream_t s,
+                                     gsicp_surrogate sg)
 {
     const int64_t cap64 = (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride);
     if (cap64 > (1 << 30)) return GSICP_ERR_INVALID_ARG;
     const int cap = (int)cap64;
     int* nd = ctx->n_dev.as<int>();
     const bool tm = ctx->timing;
-    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s));
+    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s, sg));
     RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));
@@ -708,7 +713,20 @@ gsicp_status gsicp_track_frame(gsicp_ctx ctx, const float* depth_dev, int W, int
     if (!valid_frame_args(ctx, depth_dev, W, H, intr, stride, cov_params, map, T0, reg_params, T_out))
         return GSICP_ERR_INVALID_ARG;
     return track_frame_impl(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, map, T0, reg_params, T_out,
-                            H_out, iters_out, cost_out, inliers_out, n_points_out, (cudaStream_t)stream);
+                            H_out, iters_out, cost_out, inliers_out, n_points_out, (cudaStream_t)stream, nullptr);
+}
+
+gsicp_status gsicp_track_frame_surrogate(gsicp_ctx ctx, gsicp_surrogate sg, const float* depth_dev, int W, int H,
+                                         const float intr[4], int stride, float z_min, float z_max,
+                                         const gsicp_cov_params* cov_params, gsicp_map map, const double T0[16],
+                                         const gsicp_reg_params* reg_params, double T_out[16], double H_out[36],
+                                         int* iters_out, double* cost_out, int64_t* inliers_out,
+                                         int64_t* n_points_out, void* stream)
+{
+    if (!sg || !valid_frame_args(ctx, depth_dev, W, H, intr, stride, cov_params, map, T0, reg_params, T_out))
+        return GSICP_ERR_INVALID_ARG;
+    return track_frame_impl(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, map, T0, reg_params, T_out,
+                            H_out, iters_out, cost_out, inliers_out, n_points_out, (cudaStream_t)stream, sg);
 }
 
 gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int W, int H, const float intr[4],
@@ -724,7 +742,7 @@ gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int 
     GSICP_CHECK(ctx->frame_depth.ensure(bytes));
     GSICP_CUDA(cudaMemcpyAsync(ctx->frame_depth.ptr, depth_host, bytes, cudaMemcpyHostToDevice, s));
     return track_frame_impl(ctx, ctx->frame_depth.as<float>(), W, H, intr, stride, z_min, z_max, cov_params, map, T0,
-                            reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out, s);
+                            reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out, s, nullptr);
 }
 
 }  // extern "C"

@@ -147,6 +147,12 @@ gsicp_status launch_set_int(int* dst, int value, cudaStream_t s);
 
 int device_sm_count();
 
+// The surrogate's layers 1-3 over a frame's a1 output (pts in a1 order, idx_img the sample ->
+// point map of the ws x hs sample grid): covariances (a1 order, nullable) and v per sample
+// (nullable).  Defined in surrogate.cu.
+gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const int* idx_img, int ws, int hs, float eps,
+                               float p, float* covs, float* v_out, cudaStream_t s);
+
 }  // namespace gsicp
 
 struct gsicp_ctx_s {
@@ -177,14 +183,15 @@ struct gsicp_map_s {
 
 // Frame helpers of api.cu used by the tracker (tracker.cu); defined in api.cu's C-linkage section.
 extern "C" {
-// a1 -> source index -> a2+a3 of one depth frame into the context's frame buffers.
+// a1 -> source index -> a2+a3 of one depth frame into the context's frame buffers; with a
+// surrogate (non-null sg) the covariances are its predictions instead of the k-NN ones.
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
                                float z_min, float z_max, const gsicp_cov_params* cov_params, int cap,
-                               cudaStream_t s);
-// The whole a1..a7 step of gsicp_track_frame (arguments already checked).
+                               cudaStream_t s, gsicp_surrogate sg);
+// The whole a1..a7 step of gsicp_track_frame (arguments already checked), covariances as above.
 gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
                               float z_min, float z_max, const gsicp_cov_params* cov_params, gsicp_map map,
                               const double T0[16], const gsicp_reg_params* reg_params, double T_out[16],
                               double H_out[36], int* iters_out, double* cost_out, int64_t* inliers_out,
-                              int64_t* n_points_out, cudaStream_t s);
+                              int64_t* n_points_out, cudaStream_t s, gsicp_surrogate sg);
 }  // extern "C"

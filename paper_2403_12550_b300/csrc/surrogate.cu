@@ -1,0 +1,823 @@
+// surrogate.cu -- the learned covariance surrogate: a 3-layer 5x5 convolutional network over the
+// point map of a depth frame that predicts each point's surface normal, from which the point's
+// plane-regularised, scale-aligned covariance (Sec. 3) is built in place of the k-NN step.
+//
+// Network (bias-free, ReLU; weights bfloat16, activations bfloat16 between layers, every sum in
+// float):
+//   a1(u)[o] = sum_{d, c} W1[o][c][d] M(u+d) (P_c(u+d) - P_c(u))      3 -> 32 channels
+//   h1 = bf16(relu(a1)) M,   a2 = W2 * h1,   h2 = bf16(relu(a2)) M       32 -> 32
+//   v = W3 * h2,   n = v / |v|,   C = (I - (1 - eps) n n^T) z^(-2p)      32 -> 3
+// over the stride-sampled grid (P the back-projected samples, M their validity), 5 x 5 taps read
+// (i + dy - 2, j + dx - 2), zero outside the image.  Centred differences make layer 1 blind to
+// the patch's position; without biases every layer is positively homogeneous, so n does not
+// depend on the distance to the surface.
+//
+// Training minimises the mean over points with a k-NN target of 1 - n^T T n, T = (I - C_knn
+// z^(2p)) / (1 - eps) the projector on the k-NN normal (points whose k-NN covariance is not a plane
+// one, trace(T) off 1, are skipped); back-propagation treats the bfloat16 roundings as the
+// identity; Adam (Kingma & Ba) updates float master weights.
+//
+// Layout: per-pixel tensors channels-last over the sample grid (h1, h2: 32 bfloat16 = 64 B per
+// pixel; gradients float).  Every kernel works on 16 x 16 output tiles with a 2-pixel halo staged
+// in shared memory, channel-major ([c][20 * 20 + 1]) so that lanes that differ in pixel or in
+// channel hit distinct banks; weights are staged in shared memory and read as broadcasts.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "internal.h"
+
+namespace gsicp {
+
+constexpr int SG_T = 16;               // output tile side
+constexpr int SG_HS = SG_T + 4;        // halo tile side
+constexpr int SG_HP = SG_HS * SG_HS;   // halo positions (400)
+constexpr int SG_HPAD = SG_HP + 1;     // channel stride in shared memory
+constexpr int SG_C = 32;               // hidden channels
+constexpr int SG_TAPS = 25;
+constexpr int SG_NW1 = SG_C * 3 * SG_TAPS, SG_NW2 = SG_C * SG_C * SG_TAPS, SG_NW3 = 3 * SG_C * SG_TAPS;
+constexpr int SG_NW = SG_NW1 + SG_NW2 + SG_NW3;
+static_assert(SG_NW == GSICP_SURROGATE_WEIGHTS, "weight count");
+
+// Kernel layouts of the bfloat16-rounded weights (float values), in one buffer:
+constexpr int WK_W1 = 0;                           // float4 [25 t][32 o]: (W1[o][0..2][t], 0)
+constexpr int WK_W2 = WK_W1 + 4 * SG_TAPS * SG_C;  // float  [32 c][25 t][32 o]: W2[o][c][t]
+constexpr int WK_W2T = WK_W2 + SG_NW2;             // float  [32 o][25 t][32 c]: W2[o][c][24 - t]
+constexpr int WK_W3 = WK_W2T + SG_NW2;             // float4 [32 c][25 t]: (W3[0..2][c][t], 0)
+constexpr int WK_W3T = WK_W3 + 4 * SG_C * SG_TAPS; // float4 [25 t][32 c]: (W3[0..2][c][24 - t], 0)
+constexpr int WK_TOTAL = WK_W3T + 4 * SG_TAPS * SG_C;
+
+}  // namespace gsicp
+
+struct gsicp_surrogate_s {
+    int device = 0;
+    gsicp::DevBuf w, m, s, g;      // float [SG_NW]: master weights, Adam moments, gradient sums
+    gsicp::DevBuf wk;              // kernel layouts (WK_TOTAL floats)
+    gsicp::DevBuf grid, h1, h2, v, dv, da2, da1;  // per-pixel buffers
+    gsicp::DevBuf scal;            // double loss sum | unsigned long long target count
+    int64_t pix_cap = 0;
+    int steps = 0;                 // Adam steps taken
+};
+
+namespace gsicp {
+
+namespace {
+
+__device__ __forceinline__ int halo_of(int t, int tx, int ty) { return (ty + t / 5) * SG_HS + tx + t % 5; }
+
+// ---------------------------------------------------------------------------------------------
+// grid and weight preparation
+
+__global__ void sg_grid_kernel(const float* __restrict__ pts, const int* __restrict__ idx_img, int npix,
+                               float4* __restrict__ grid)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    const int id = idx_img[i];
+    grid[i] = id >= 0 ? make_float4(pts[3l * id], pts[3l * id + 1], pts[3l * id + 2], 1.f)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void sg_layout_kernel(const float* __restrict__ w, float* __restrict__ wk)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < SG_NW1) {  // W1[o][c][t]
+        const int o = i / 75, c = (i / 25) % 3, t = i % 25;
+        wk[WK_W1 + 4 * (t * SG_C + o) + c] = bf16r(w[i]);
+        if (c == 0) wk[WK_W1 + 4 * (t * SG_C + o) + 3] = 0.f;
+    } else if (i < SG_NW1 + SG_NW2) {  // W2[o][c][t]
+        const int j = i - SG_NW1, o = j / 800, c = (j / 25) % 32, t = j % 25;
+        const float v = bf16r(w[i]);
+        wk[WK_W2 + (c * SG_TAPS + t) * SG_C + o] = v;
+        wk[WK_W2T + (o * SG_TAPS + (24 - t)) * SG_C + c] = v;
+    } else if (i < SG_NW) {  // W3[o][c][t]
+        const int j = i - SG_NW1 - SG_NW2, o = j / 800, c = (j / 25) % 32, t = j % 25;
+        const float v = bf16r(w[i]);
+        wk[WK_W3 + 4 * (c * SG_TAPS + t) + o] = v;
+        wk[WK_W3T + 4 * ((24 - t) * SG_C + c) + o] = v;
+        if (o == 0) {
+            wk[WK_W3 + 4 * (c * SG_TAPS + t) + 3] = 0.f;
+            wk[WK_W3T + 4 * ((24 - t) * SG_C + c) + 3] = 0.f;
+        }
+    }
+}
+
+// Stage a channels-last 32-channel tensor's halo tile into shared memory as float [c][SG_HPAD].
+template <bool kBf16>
+__device__ __forceinline__ void stage32(const void* __restrict__ in, int w, int h, int x0, int y0, float* tile)
+{
+    for (int q = threadIdx.x; q < SG_HP * 4; q += blockDim.x) {
+        const int pos = q >> 2, part = q & 3;
+        const int yy = y0 + pos / SG_HS - 2, xx = x0 + pos % SG_HS - 2;
+        float v[8];
+        if (yy >= 0 && yy < h && xx >= 0 && xx < w) {
+            const long pix = (long)yy * w + xx;
+            if (kBf16) {
+                const uint4 raw = reinterpret_cast<const uint4*>(in)[pix * 4 + part];
+                const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(b[k]);
+                    v[2 * k] = f.x;
+                    v[2 * k + 1] = f.y;
+                }
+            } else {
+                const float4 a = reinterpret_cast<const float4*>(in)[pix * 8 + 2 * part];
+                const float4 b = reinterpret_cast<const float4*>(in)[pix * 8 + 2 * part + 1];
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tile[(part * 8 + k) * SG_HPAD + pos] = v[k];
+    }
+}
+
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float* v)
+{
+    uint4 out[2];
+    __nv_bfloat162* b = reinterpret_cast<__nv_bfloat162*>(out);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    reinterpret_cast<uint4*>(dst)[0] = out[0];
+    reinterpret_cast<uint4*>(dst)[1] = out[1];
+}
+
+// ---------------------------------------------------------------------------------------------
+// forward
+
+// Layer 1 (centred differences, 3 -> 32) + ReLU + bfloat16, zero at invalid pixels.
+__global__ void __launch_bounds__(256) sg_l1_kernel(const float4* __restrict__ grid, int w, int h,
+                                                    const float4* __restrict__ w1k, __nv_bfloat16* __restrict__ h1)
+{
+    __shared__ float4 tile[SG_HP];
+    __shared__ float4 ws[SG_TAPS * SG_C];
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    for (int i = threadIdx.x; i < SG_TAPS * SG_C; i += blockDim.x) ws[i] = w1k[i];
+    for (int q = threadIdx.x; q < SG_HP; q += blockDim.x) {
+        const int yy = y0 + q / SG_HS - 2, xx = x0 + q % SG_HS - 2;
+        tile[q] = (yy >= 0 && yy < h && xx >= 0 && xx < w) ? grid[(long)yy * w + xx] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= w || y >= h) return;
+    const float4 c = tile[(ty + 2) * SG_HS + tx + 2];
+    float acc[SG_C];
+#pragma unroll
+    for (int o = 0; o < SG_C; ++o) acc[o] = 0.f;
+    if (c.w != 0.f) {
+        for (int t = 0; t < SG_TAPS; ++t) {
+            const float4 nb = tile[halo_of(t, tx, ty)];
+            if (nb.w == 0.f) continue;
+            const float dx = nb.x - c.x, dy = nb.y - c.y, dz = nb.z - c.z;
+#pragma unroll
+            for (int o = 0; o < SG_C; ++o) {
+                const float4 wv = ws[t * SG_C + o];
+                acc[o] = fmaf(wv.x, dx, fmaf(wv.y, dy, fmaf(wv.z, dz, acc[o])));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < SG_C; ++o) acc[o] = c.w != 0.f ? fmaxf(acc[o], 0.f) : 0.f;
+    __nv_bfloat16* dst = h1 + ((long)y * w + x) * SG_C;
+    store_bf16x16(dst, acc);
+    store_bf16x16(dst + 16, acc + 16);
+}
+
+enum { SG_EPI_RELU_BF16 = 0, SG_EPI_GATE_F32 = 1 };
+
+// 32 -> 32 channel 5 x 5 convolution for output channels [16 half, 16 half + 16).
+//   kEpi = SG_EPI_RELU_BF16: out (bfloat16) = bf16(relu(acc)) at valid pixels, else 0   (layer 2)
+//   kEpi = SG_EPI_GATE_F32 : out (float) = acc where gate (bfloat16) > 0, else 0        (d layer 1)
+// wk: [32 c][25 t][32 o] float.  Dynamic shared memory: SG_C * SG_HPAD + 32 * 25 * 16 floats.
+template <bool kBf16In, int kEpi>
+__global__ void __launch_bounds__(256) sg_conv32_kernel(const void* __restrict__ in, int w, int h,
+                                                        const float* __restrict__ wk,
+                                                        const float4* __restrict__ grid,
+                                                        const __nv_bfloat16* __restrict__ gate,
+                                                        void* __restrict__ out)
+{
+    extern __shared__ float sm[];
+    float* tile = sm;                       // [32][SG_HPAD]
+    float* ws = sm + SG_C * SG_HPAD;        // [32 c][25 t][16 o]
+    const int half = blockIdx.z;
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    for (int i = threadIdx.x; i < SG_C * SG_TAPS * 16; i += blockDim.x) {
+        const int ct = i >> 4, o = i & 15;
+        ws[i] = wk[ct * SG_C + 16 * half + o];
+    }
+    stage32<kBf16In>(in, w, h, x0, y0, tile);
+    __syncthreads();
+    const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= w || y >= h) return;
+    float acc[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) acc[o] = 0.f;
+    for (int c = 0; c < SG_C; ++c) {
+        const float* tc = tile + c * SG_HPAD;
+        const float4* wc = reinterpret_cast<const float4*>(ws + c * SG_TAPS * 16);
+#pragma unroll 5
+        for (int t = 0; t < SG_TAPS; ++t) {
+            const float xv = tc[halo_of(t, tx, ty)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 wv = wc[t * 4 + q];
+                acc[4 * q + 0] = fmaf(wv.x, xv, acc[4 * q + 0]);
+                acc[4 * q + 1] = fmaf(wv.y, xv, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(wv.z, xv, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(wv.w, xv, acc[4 * q + 3]);
+            }
+        }
+    }
+    const long pix = (long)y * w + x;
+    if (kEpi == SG_EPI_RELU_BF16) {
+        const bool valid = grid[pix].w != 0.f;
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[o] = valid ? fmaxf(acc[o], 0.f) : 0.f;
+        store_bf16x16(static_cast<__nv_bfloat16*>(out) + pix * SG_C + 16 * half, acc);
+    } else {
+        const __nv_bfloat16* gp = gate + pix * SG_C + 16 * half;
+        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + pix * SG_C + 16 * half);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float r[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[k] = __bfloat162float(gp[4 * q + k]) > 0.f ? acc[4 * q + k] : 0.f;
+            dst[q] = make_float4(r[0], r[1], r[2], r[3]);
+        }
+    }
+}
+
+// Layer 3 (32 -> 3), then per valid pixel: the normal n = v / |v| and the plane covariance
+// (I - (1 - eps) n n^T) z^(-2p) written at the point's index (a1 order); |v| = 0 gives the
+// isotropic z^(-2p) I.  v_out (optional): v per pixel (zero at invalid pixels).
+__global__ void __launch_bounds__(256) sg_l3_kernel(const __nv_bfloat16* __restrict__ h2, int w, int h,
+                                                    const float4* __restrict__ w3k,
+                                                    const float4* __restrict__ grid,
+                                                    const int* __restrict__ idx_img, float eps, float p,
+                                                    float* __restrict__ covs, float* __restrict__ v_out)
+{
+    extern __shared__ float sm[];
+    float* tile = sm;                                          // [32][SG_HPAD]
+    float4* ws = reinterpret_cast<float4*>(sm + SG_C * SG_HPAD);  // [32 c][25 t] (32 * 401 floats: 16-byte aligned)
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    for (int i = threadIdx.x; i < SG_C * SG_TAPS; i += blockDim.x) ws[i] = w3k[i];
+    stage32<true>(h2, w, h, x0, y0, tile);
+    __syncthreads();
+    const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= w || y >= h) return;
+    const long pix = (long)y * w + x;
+    const float4 g = grid[pix];
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    if (g.w != 0.f) {
+        for (int c = 0; c < SG_C; ++c) {
+            const float* tc = tile + c * SG_HPAD;
+            const float4* wc = ws + c * SG_TAPS;
+#pragma unroll 5
+            for (int t = 0; t < SG_TAPS; ++t) {
+                const float xv = tc[halo_of(t, tx, ty)];
+                const float4 wv = wc[t];
+                v0 = fmaf(wv.x, xv, v0);
+                v1 = fmaf(wv.y, xv, v1);
+                v2 = fmaf(wv.z, xv, v2);
+            }
+        }
+    }
+    if (v_out) {
+        v_out[3 * pix] = v0;
+        v_out[3 * pix + 1] = v1;
+        v_out[3 * pix + 2] = v2;
+    }
+    if (!covs || g.w == 0.f) return;
+    const int id = idx_img[pix];
+    if (id < 0) return;
+    const float s = powf(g.z, -2.f * p);
+    const float nn = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+    float* C = covs + 6l * id;
+    if (!(nn > 0.f)) {
+        C[0] = s; C[1] = 0.f; C[2] = 0.f; C[3] = s; C[4] = 0.f; C[5] = s;
+        return;
+    }
+    const float n0 = v0 / nn, n1 = v1 / nn, n2 = v2 / nn, k = 1.f - eps;
+    C[0] = (1.f - k * n0 * n0) * s;
+    C[1] = (-k * n0 * n1) * s;
+    C[2] = (-k * n0 * n2) * s;
+    C[3] = (1.f - k * n1 * n1) * s;
+    C[4] = (-k * n1 * n2) * s;
+    C[5] = (1.f - k * n2 * n2) * s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// training
+
+// Loss and dL/dv (without the 1/N of the mean: the gradient sums are scaled when applied).
+__global__ void sg_loss_kernel(const float* __restrict__ v, const float4* __restrict__ grid,
+                               const int* __restrict__ idx_img, const float* __restrict__ covs_knn, int npix,
+                               float eps, float p, float* __restrict__ dv, double* __restrict__ loss_sum,
+                               unsigned long long* __restrict__ count)
+{
+    __shared__ double sl[8];
+    __shared__ unsigned sc[8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    unsigned cnt = 0u;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (i < npix && grid[i].w != 0.f && idx_img[i] >= 0) {
+        const float* C = covs_knn + 6l * idx_img[i];
+        const float s = powf(grid[i].z, 2.f * p), inv = 1.f / (1.f - eps);
+        const float T00 = (1.f - C[0] * s) * inv, T01 = (-C[1] * s) * inv, T02 = (-C[2] * s) * inv;
+        const float T11 = (1.f - C[3] * s) * inv, T12 = (-C[4] * s) * inv, T22 = (1.f - C[5] * s) * inv;
+        if (fabsf(T00 + T11 + T22 - 1.f) < 0.01f) {
+            cnt = 1u;
+            const float a = v[3l * i], b = v[3l * i + 1], c = v[3l * i + 2];
+            const float nn = sqrtf(fmaf(a, a, fmaf(b, b, c * c)));
+            if (nn > 0.f) {
+                const float n0 = a / nn, n1 = b / nn, n2 = c / nn;
+                const float t0 = T00 * n0 + T01 * n1 + T02 * n2;
+                const float t1 = T01 * n0 + T11 * n1 + T12 * n2;
+                const float t2 = T02 * n0 + T12 * n1 + T22 * n2;
+                const float q = n0 * t0 + n1 * t1 + n2 * t2;
+                l = 1.0 - (double)q;
+                // dL/dn = -2 T n; dL/dv = (I - n n^T) dL/dn / |v|
+                const float e0 = -2.f * t0, e1 = -2.f * t1, e2 = -2.f * t2;
+                const float ne = n0 * e0 + n1 * e1 + n2 * e2;
+                g0 = (e0 - n0 * ne) / nn;
+                g1 = (e1 - n1 * ne) / nn;
+                g2 = (e2 - n2 * ne) / nn;
+            } else {
+                l = 1.0;
+            }
+        }
+    }
+    if (i < npix) {
+        dv[3l * i] = g0;
+        dv[3l * i + 1] = g1;
+        dv[3l * i + 2] = g2;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        sl[warp] = l;
+        sc[warp] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L = 0.0;
+        unsigned long long N = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            L += sl[k];
+            N += sc[k];
+        }
+        if (N) {
+            atomicAdd(loss_sum, L);
+            atomicAdd(count, N);
+        }
+    }
+}
+
+// dW3[o][c][t] += sum over the tile's pixels of dv[o](u) h2[c](u + d_t).
+__global__ void __launch_bounds__(256) sg_gw3_kernel(const float* __restrict__ dv, const __nv_bfloat16* __restrict__ h2,
+                                                     int w, int h, float* __restrict__ gw3)
+{
+    extern __shared__ float sm[];
+    float* tile = sm;                         // h2 halo [32][SG_HPAD]
+    float* dt = sm + SG_C * SG_HPAD;          // dv [3][256]
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    stage32<true>(h2, w, h, x0, y0, tile);
+    {
+        const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T, x = x0 + tx, y = y0 + ty;
+        const bool in = x < w && y < h;
+        const long pix = (long)y * w + x;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) dt[o * 256 + threadIdx.x] = in ? dv[3 * pix + o] : 0.f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < SG_NW3; j += blockDim.x) {
+        const int o = j / 800, c = (j / 25) % 32, t = j % 25;
+        const float* tc = tile + c * SG_HPAD;
+        const float* d = dt + o * 256;
+        float acc = 0.f;
+        for (int q = 0; q < 256; ++q) acc = fmaf(d[q], tc[halo_of(t, q % SG_T, q / SG_T)], acc);
+        if (acc != 0.f) atomicAdd(gw3 + j, acc);
+    }
+}
+
+// da2[c](u) = [h2[c](u) > 0] sum_{t, o} W3[o][c][24 - t] dv[o](u + d_t)  (layer 3 transposed).
+__global__ void __launch_bounds__(256) sg_dl3_kernel(const float* __restrict__ dv, int w, int h,
+                                                     const float4* __restrict__ w3t,
+                                                     const __nv_bfloat16* __restrict__ h2, float* __restrict__ da2)
+{
+    __shared__ float4 tile[SG_HP];
+    __shared__ float4 ws[SG_TAPS * SG_C];
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    for (int i = threadIdx.x; i < SG_TAPS * SG_C; i += blockDim.x) ws[i] = w3t[i];
+    for (int q = threadIdx.x; q < SG_HP; q += blockDim.x) {
+        const int yy = y0 + q / SG_HS - 2, xx = x0 + q % SG_HS - 2;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (yy >= 0 && yy < h && xx >= 0 && xx < w) {
+            const long pix = (long)yy * w + xx;
+            v = make_float4(dv[3 * pix], dv[3 * pix + 1], dv[3 * pix + 2], 0.f);
+        }
+        tile[q] = v;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= w || y >= h) return;
+    float acc[SG_C];
+#pragma unroll
+    for (int c = 0; c < SG_C; ++c) acc[c] = 0.f;
+    for (int t = 0; t < SG_TAPS; ++t) {
+        const float4 d = tile[halo_of(t, tx, ty)];
+        if (d.x == 0.f && d.y == 0.f && d.z == 0.f) continue;
+#pragma unroll
+        for (int c = 0; c < SG_C; ++c) {
+            const float4 wv = ws[t * SG_C + c];
+            acc[c] = fmaf(wv.x, d.x, fmaf(wv.y, d.y, fmaf(wv.z, d.z, acc[c])));
+        }
+    }
+    const long pix = (long)y * w + x;
+    const __nv_bfloat16* gp = h2 + pix * SG_C;
+    float4* dst = reinterpret_cast<float4*>(da2 + pix * SG_C);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[k] = __bfloat162float(gp[4 * q + k]) > 0.f ? acc[4 * q + k] : 0.f;
+        dst[q] = make_float4(r[0], r[1], r[2], r[3]);
+    }
+}
+
+// dW2[o][c][t] += sum over the tile's pixels of da2[o](u) h1[c](u + d_t).  Thread (c = lane,
+// o-group = warp) holds 4 outputs x 5 taps of one tap row at a time.
+__global__ void __launch_bounds__(256) sg_gw2_kernel(const float* __restrict__ da2, const __nv_bfloat16* __restrict__ h1,
+                                                     int w, int h, float* __restrict__ gw2)
+{
+    extern __shared__ float sm[];
+    float* tile = sm;                      // h1 halo [32][SG_HPAD]
+    float* dt = sm + SG_C * SG_HPAD;       // da2 [32 o][256]
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    stage32<true>(h1, w, h, x0, y0, tile);
+    {
+        const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T, x = x0 + tx, y = y0 + ty;
+        const bool in = x < w && y < h;
+        const long pix = (long)y * w + x;
+        for (int o = 0; o < SG_C; ++o) dt[o * 256 + threadIdx.x] = in ? da2[pix * SG_C + o] : 0.f;
+    }
+    __syncthreads();
+    const int c = threadIdx.x & 31, og = threadIdx.x >> 5;
+    const float* tc = tile + c * SG_HPAD;
+    for (int dy = 0; dy < 5; ++dy) {
+        float acc[4][5];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 5; ++b) acc[a][b] = 0.f;
+        for (int q = 0; q < 256; ++q) {
+            const int qx = q % SG_T, qy = q / SG_T;
+            float d[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) d[a] = dt[(4 * og + a) * 256 + q];
+            const float* row = tc + (qy + dy) * SG_HS + qx;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+                const float xv = row[b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a][b] = fmaf(d[a], xv, acc[a][b]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                if (acc[a][b] != 0.f) atomicAdd(gw2 + (4 * og + a) * 800 + c * 25 + dy * 5 + b, acc[a][b]);
+    }
+}
+
+// dW1[o][c][t] += sum over the tile's pixels of da1[o](u) M(u + d_t) (P_c(u + d_t) - P_c(u)).
+__global__ void __launch_bounds__(256) sg_gw1_kernel(const float* __restrict__ da1, const float4* __restrict__ grid,
+                                                     int w, int h, float* __restrict__ gw1)
+{
+    extern __shared__ float sm[];
+    float4* tile = reinterpret_cast<float4*>(sm);   // grid halo [SG_HP]
+    float* dt = sm + 4 * SG_HP;                      // da1 [32 o][256]
+    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    for (int q = threadIdx.x; q < SG_HP; q += blockDim.x) {
+        const int yy = y0 + q / SG_HS - 2, xx = x0 + q % SG_HS - 2;
+        tile[q] = (yy >= 0 && yy < h && xx >= 0 && xx < w) ? grid[(long)yy * w + xx] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    {
+        const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T, x = x0 + tx, y = y0 + ty;
+        const bool in = x < w && y < h;
+        const long pix = (long)y * w + x;
+        for (int o = 0; o < SG_C; ++o) dt[o * 256 + threadIdx.x] = in ? da1[pix * SG_C + o] : 0.f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < SG_NW1; j += blockDim.x) {
+        const int o = j / 75, c = (j / 25) % 3, t = j % 25;
+        const float* d = dt + o * 256;
+        float acc = 0.f;
+        for (int q = 0; q < 256; ++q) {
+            const float dq = d[q];
+            if (dq == 0.f) continue;
+            const int qx = q % SG_T, qy = q / SG_T;
+            const float4 nb = tile[halo_of(t, qx, qy)];
+            if (nb.w == 0.f) continue;
+            const float4 ce = tile[(qy + 2) * SG_HS + qx + 2];
+            const float diff = c == 0 ? nb.x - ce.x : (c == 1 ? nb.y - ce.y : nb.z - ce.z);
+            acc = fmaf(dq, diff, acc);
+        }
+        if (acc != 0.f) atomicAdd(gw1 + j, acc);
+    }
+}
+
+// Adam on the float master weights with the gradient sums scaled by inv_n; bc1, bc2 = 1 - b^t.
+__global__ void sg_adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ s,
+                               const float* __restrict__ g, float inv_n, float lr, float b1, float b2, float eps,
+                               float bc1, float bc2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= SG_NW) return;
+    const float gi = g[i] * inv_n;
+    const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+    const float si = fmaf(b2, s[i], (1.f - b2) * gi * gi);
+    m[i] = mi;
+    s[i] = si;
+    w[i] -= lr * (mi / bc1) / (sqrtf(si / bc2) + eps);
+}
+
+constexpr size_t SMEM_CONV = sizeof(float) * (SG_C * SG_HPAD + SG_C * SG_TAPS * 16);
+constexpr size_t SMEM_L3 = sizeof(float) * SG_C * SG_HPAD + sizeof(float4) * SG_C * SG_TAPS;
+static_assert((SG_C * SG_HPAD) % 4 == 0, "float4 weights after the tile must stay 16-byte aligned");
+constexpr size_t SMEM_GW3 = sizeof(float) * (SG_C * SG_HPAD + 3 * 256);
+constexpr size_t SMEM_GW2 = sizeof(float) * (SG_C * SG_HPAD + SG_C * 256);
+constexpr size_t SMEM_GW1 = sizeof(float) * (4 * SG_HP + SG_C * 256);
+
+gsicp_status sg_set_smem()
+{
+    static bool done = false;
+    if (done) return GSICP_OK;
+    GSICP_CUDA(cudaFuncSetAttribute(sg_conv32_kernel<true, SG_EPI_RELU_BF16>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_conv32_kernel<false, SG_EPI_GATE_F32>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_l3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_L3));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_gw3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW3));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_gw2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW2));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_gw1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW1));
+    done = true;
+    return GSICP_OK;
+}
+
+gsicp_status sg_ensure(gsicp_surrogate_s* sg, int64_t npix)
+{
+    if (npix <= sg->pix_cap) return GSICP_OK;
+    const size_t n = (size_t)npix;
+    GSICP_CHECK(sg->grid.ensure(sizeof(float4) * n));
+    GSICP_CHECK(sg->h1.ensure(sizeof(__nv_bfloat16) * SG_C * n));
+    GSICP_CHECK(sg->h2.ensure(sizeof(__nv_bfloat16) * SG_C * n));
+    GSICP_CHECK(sg->v.ensure(sizeof(float) * 3 * n));
+    GSICP_CHECK(sg->dv.ensure(sizeof(float) * 3 * n));
+    GSICP_CHECK(sg->da2.ensure(sizeof(float) * SG_C * n));
+    GSICP_CHECK(sg->da1.ensure(sizeof(float) * SG_C * n));
+    sg->pix_cap = npix;
+    return GSICP_OK;
+}
+
+}  // namespace
+
+// Grid + layers 1-3 over the frame's a1 output (pts in a1 order, idx_img the sample -> point map).
+gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const int* idx_img, int ws, int hs, float eps,
+                        float p, float* covs, float* v_out, cudaStream_t s)
+{
+    const int64_t npix = (int64_t)ws * hs;
+    if (npix <= 0) return GSICP_OK;
+    GSICP_CHECK(sg_set_smem());
+    GSICP_CHECK(sg_ensure(sg, npix));
+    const float* wk = sg->wk.as<float>();
+    float4* grid = sg->grid.as<float4>();
+    sg_grid_kernel<<<(int)((npix + 255) / 256), 256, 0, s>>>(pts, idx_img, (int)npix, grid);
+    const dim3 tiles((ws + SG_T - 1) / SG_T, (hs + SG_T - 1) / SG_T);
+    sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, reinterpret_cast<const float4*>(wk + WK_W1),
+                                       sg->h1.as<__nv_bfloat16>());
+    sg_conv32_kernel<true, SG_EPI_RELU_BF16><<<dim3(tiles.x, tiles.y, 2), 256, SMEM_CONV, s>>>(
+        sg->h1.ptr, ws, hs, wk + WK_W2, grid, nullptr, sg->h2.ptr);
+    sg_l3_kernel<<<tiles, 256, SMEM_L3, s>>>(sg->h2.as<__nv_bfloat16>(), ws, hs,
+                                             reinterpret_cast<const float4*>(wk + WK_W3), grid, idx_img, eps, p,
+                                             covs, v_out);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+namespace {
+
+// Back-propagation of the loss against covs_knn (a1 order) into sg->g (sums, not means).
+gsicp_status sg_backward(gsicp_surrogate_s* sg, const int* idx_img, const float* covs_knn, int ws, int hs,
+                         float eps, float p, cudaStream_t s)
+{
+    const int64_t npix = (int64_t)ws * hs;
+    const float* wk = sg->wk.as<float>();
+    const float4* grid = sg->grid.as<const float4>();
+    double* loss_sum = sg->scal.as<double>();
+    unsigned long long* count = reinterpret_cast<unsigned long long*>(loss_sum + 1);
+    GSICP_CUDA(cudaMemsetAsync(sg->g.ptr, 0, sizeof(float) * SG_NW, s));
+    GSICP_CUDA(cudaMemsetAsync(sg->scal.ptr, 0, 16, s));
+    if (npix <= 0) return GSICP_OK;
+    const dim3 tiles((ws + SG_T - 1) / SG_T, (hs + SG_T - 1) / SG_T);
+    float* g = sg->g.as<float>();
+    sg_loss_kernel<<<(int)((npix + 255) / 256), 256, 0, s>>>(sg->v.as<float>(), grid, idx_img, covs_knn, (int)npix,
+                                                             eps, p, sg->dv.as<float>(), loss_sum, count);
+    sg_gw3_kernel<<<tiles, 256, SMEM_GW3, s>>>(sg->dv.as<float>(), sg->h2.as<__nv_bfloat16>(), ws, hs,
+                                               g + SG_NW1 + SG_NW2);
+    float* da2 = sg->da2.as<float>();
+    float* da1 = sg->da1.as<float>();
+    sg_dl3_kernel<<<tiles, 256, 0, s>>>(sg->dv.as<float>(), ws, hs, reinterpret_cast<const float4*>(wk + WK_W3T),
+                                        sg->h2.as<__nv_bfloat16>(), da2);
+    sg_gw2_kernel<<<tiles, 256, SMEM_GW2, s>>>(da2, sg->h1.as<__nv_bfloat16>(), ws, hs, g + SG_NW1);
+    // da1 = [h1 > 0] (layer 2 transposed: W2 with flipped taps, channels swapped) * da2
+    sg_conv32_kernel<false, SG_EPI_GATE_F32><<<dim3(tiles.x, tiles.y, 2), 256, SMEM_CONV, s>>>(
+        da2, ws, hs, wk + WK_W2T, grid, sg->h1.as<__nv_bfloat16>(), da1);
+    sg_gw1_kernel<<<tiles, 256, SMEM_GW1, s>>>(da1, grid, ws, hs, g);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+gsicp_status sg_upload(gsicp_surrogate_s* sg, const float* w_host, cudaStream_t s)
+{
+    GSICP_CUDA(cudaMemcpyAsync(sg->w.ptr, w_host, sizeof(float) * SG_NW, cudaMemcpyHostToDevice, s));
+    GSICP_CUDA(cudaMemsetAsync(sg->m.ptr, 0, sizeof(float) * SG_NW, s));
+    GSICP_CUDA(cudaMemsetAsync(sg->s.ptr, 0, sizeof(float) * SG_NW, s));
+    sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>());
+    GSICP_CUDA(cudaGetLastError());
+    sg->steps = 0;
+    return GSICP_OK;
+}
+
+}  // namespace
+}  // namespace gsicp
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+
+using namespace gsicp;
+
+extern "C" {
+
+gsicp_status gsicp_surrogate_create(const float* weights, gsicp_surrogate* out)
+{
+    if (!weights || !out) return GSICP_ERR_INVALID_ARG;
+    *out = nullptr;
+    gsicp_surrogate_s* sg = new (std::nothrow) gsicp_surrogate_s;
+    if (!sg) return GSICP_ERR_OOM;
+    cudaGetDevice(&sg->device);
+    gsicp_status st = GSICP_OK;
+    if ((st = sg->w.ensure(sizeof(float) * SG_NW)) != GSICP_OK || (st = sg->m.ensure(sizeof(float) * SG_NW)) != GSICP_OK ||
+        (st = sg->s.ensure(sizeof(float) * SG_NW)) != GSICP_OK || (st = sg->g.ensure(sizeof(float) * SG_NW)) != GSICP_OK ||
+        (st = sg->wk.ensure(sizeof(float) * WK_TOTAL)) != GSICP_OK || (st = sg->scal.ensure(16)) != GSICP_OK ||
+        (st = sg_upload(sg, weights, nullptr)) != GSICP_OK) {
+        gsicp_surrogate_destroy(sg);
+        return st;
+    }
+    cudaError_t e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        gsicp_surrogate_destroy(sg);
+        return cuda_status(e, "gsicp_surrogate_create");
+    }
+    *out = sg;
+    return GSICP_OK;
+}
+
+void gsicp_surrogate_destroy(gsicp_surrogate sg)
+{
+    if (!sg) return;
+    for (DevBuf* b : {&sg->w, &sg->m, &sg->s, &sg->g, &sg->wk, &sg->grid, &sg->h1, &sg->h2, &sg->v, &sg->dv, &sg->da2,
+                      &sg->da1, &sg->scal})
+        b->release();
+    delete sg;
+}
+
+gsicp_status gsicp_surrogate_get_weights(gsicp_surrogate sg, float* weights)
+{
+    if (!sg || !weights) return GSICP_ERR_INVALID_ARG;
+    GSICP_CUDA(cudaMemcpy(weights, sg->w.ptr, sizeof(float) * SG_NW, cudaMemcpyDeviceToHost));
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_surrogate_set_weights(gsicp_surrogate sg, const float* weights)
+{
+    if (!sg || !weights) return GSICP_ERR_INVALID_ARG;
+    GSICP_CHECK(sg_upload(sg, weights, nullptr));
+    GSICP_CUDA(cudaStreamSynchronize(nullptr));
+    return GSICP_OK;
+}
+
+static bool valid_sg_frame(gsicp_ctx ctx, gsicp_surrogate sg, const void* depth, int W, int H, const float intr[4],
+                           int stride, const gsicp_cov_params* params)
+{
+    return ctx && sg && depth && intr && W > 0 && H > 0 && stride > 0 && params && params->eps > 0.f &&
+           params->eps < 1.f && params->p >= 0.f && intr[0] != 0.f && intr[1] != 0.f &&
+           (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride) <= (1 << 30);
+}
+
+gsicp_status gsicp_surrogate_covariances(gsicp_ctx ctx, gsicp_surrogate sg, const float* depth_dev, int W, int H,
+                                         const float intr[4], int stride, float z_min, float z_max,
+                                         const gsicp_cov_params* params, float* pts_dev, float* z_dev,
+                                         float* covs_dev, float* v_dev, int64_t cap, int64_t* n_out, void* stream)
+{
+    if (!valid_sg_frame(ctx, sg, depth_dev, W, H, intr, stride, params) || !pts_dev || !covs_dev || !n_out || cap < 0 ||
+        cap > INT32_MAX)
+        return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ws = (W + stride - 1) / stride, hs = (H + stride - 1) / stride;
+    const int fcap = ws * hs;
+    GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)fcap));
+    GSICP_CHECK(ctx->frame_z.ensure(sizeof(float) * (size_t)fcap));
+    GSICP_CHECK(ctx->frame_covs.ensure(sizeof(float) * 6 * (size_t)fcap));
+    GSICP_CHECK(ctx->frame_idx.ensure(sizeof(int) * (size_t)fcap));
+    GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, ctx->frame_pts.as<float>(),
+                                       ctx->frame_z.as<float>(), fcap, ctx->n_dev.as<int>(), ctx->total_dev.as<int>(),
+                                       ctx->a1_counts, ctx->a1_sums, s, ctx->frame_idx.as<int>()));
+    GSICP_CHECK(surrogate_forward(sg, ctx->frame_pts.as<float>(), ctx->frame_idx.as<int>(), ws, hs, params->eps,
+                                  params->p, ctx->frame_covs.as<float>(), v_dev, s));
+    int* h = (int*)ctx->host_pinned;
+    GSICP_CUDA(cudaMemcpyAsync(h, ctx->n_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    const int64_t n = h[0], m = std::min<int64_t>(n, cap);
+    if (m > 0) {
+        GSICP_CUDA(cudaMemcpyAsync(pts_dev, ctx->frame_pts.ptr, sizeof(float) * 3 * m, cudaMemcpyDeviceToDevice, s));
+        GSICP_CUDA(cudaMemcpyAsync(covs_dev, ctx->frame_covs.ptr, sizeof(float) * 6 * m, cudaMemcpyDeviceToDevice, s));
+        if (z_dev) GSICP_CUDA(cudaMemcpyAsync(z_dev, ctx->frame_z.ptr, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
+    }
+    *n_out = m;
+    return n > cap ? GSICP_ERR_CAPACITY : GSICP_OK;
+}
+
+gsicp_status gsicp_surrogate_train_step(gsicp_ctx ctx, gsicp_surrogate sg, const float* depth_dev, int W, int H,
+                                        const float intr[4], int stride, float z_min, float z_max,
+                                        const gsicp_cov_params* params, const float* target_covs_dev, float lr,
+                                        int apply, double* loss_out, int64_t* count_out, float* grad_out,
+                                        void* stream)
+{
+    if (!valid_sg_frame(ctx, sg, depth_dev, W, H, intr, stride, params) || !(lr >= 0.f) || (apply != 0 && apply != 1))
+        return GSICP_ERR_INVALID_ARG;
+    if (!target_covs_dev && params->reg_mode != GSICP_REG_PLANE) return GSICP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ws = (W + stride - 1) / stride, hs = (H + stride - 1) / stride;
+    const int fcap = ws * hs;
+    if (target_covs_dev) {  // a1 only; the caller's targets are in a1 order
+        GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)fcap));
+        GSICP_CHECK(ctx->frame_z.ensure(sizeof(float) * (size_t)fcap));
+        GSICP_CHECK(ctx->frame_idx.ensure(sizeof(int) * (size_t)fcap));
+        GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, ctx->frame_pts.as<float>(),
+                                           ctx->frame_z.as<float>(), fcap, ctx->n_dev.as<int>(),
+                                           ctx->total_dev.as<int>(), ctx->a1_counts, ctx->a1_sums, s,
+                                           ctx->frame_idx.as<int>()));
+    } else {  // the plain k-NN covariances of the frame are the targets
+        GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, params, fcap, s, nullptr));
+    }
+    const float* targets = target_covs_dev ? target_covs_dev : ctx->frame_covs.as<float>();
+    GSICP_CHECK(sg_ensure(sg, (int64_t)fcap));  // sg->v must exist before its address is taken
+    GSICP_CHECK(surrogate_forward(sg, ctx->frame_pts.as<float>(), ctx->frame_idx.as<int>(), ws, hs, params->eps,
+                                  params->p, nullptr, sg->v.as<float>(), s));
+    GSICP_CHECK(sg_backward(sg, ctx->frame_idx.as<int>(), targets, ws, hs, params->eps, params->p, s));
+    double* hs_ = reinterpret_cast<double*>(ctx->host_pinned);
+    GSICP_CUDA(cudaMemcpyAsync(hs_, sg->scal.ptr, 16, cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    const double loss_sum = hs_[0];
+    const unsigned long long cnt = reinterpret_cast<unsigned long long*>(hs_)[1];
+    if (loss_out) *loss_out = cnt ? loss_sum / (double)cnt : 0.0;
+    if (count_out) *count_out = (int64_t)cnt;
+    if (grad_out) {
+        GSICP_CUDA(cudaMemcpy(grad_out, sg->g.ptr, sizeof(float) * SG_NW, cudaMemcpyDeviceToHost));
+        if (cnt)
+            for (int i = 0; i < SG_NW; ++i) grad_out[i] = (float)((double)grad_out[i] / (double)cnt);
+    }
+    if (apply && cnt) {
+        const int t = sg->steps + 1;
+        const double b1 = 0.9, b2 = 0.999;
+        sg_adam_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->m.as<float>(), sg->s.as<float>(),
+                                                            sg->g.as<float>(), (float)(1.0 / (double)cnt), lr,
+                                                            (float)b1, (float)b2, 1e-8f, (float)(1.0 - pow(b1, t)),
+                                                            (float)(1.0 - pow(b2, t)));
+        sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>());
+        GSICP_CUDA(cudaGetLastError());
+        sg->steps = t;
+    }
+    return GSICP_OK;
+}
+
+}  // extern "C"

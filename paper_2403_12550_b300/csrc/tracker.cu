@@ -206,7 +206,8 @@ extern "C" gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_
     int64_t n = 0;
     if (t->frames == 0) {
         memcpy(T, T_start, sizeof(T));
-        GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, cap, s));
+        GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, cap, s,
+                                      nullptr));
         int h = 0;
         GSICP_CUDA(cudaMemcpyAsync(&h, ctx->n_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         GSICP_CUDA(cudaStreamSynchronize(s));
@@ -220,7 +221,7 @@ extern "C" gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_
         int iters = 0;
         int64_t inl = 0;
         st = track_frame_impl(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, t->track_map, T0,
-                              &t->reg, T, nullptr, &iters, nullptr, &inl, &n, s);
+                              &t->reg, T, nullptr, &iters, nullptr, &inl, &n, s, nullptr);
         if (st != GSICP_OK && st != GSICP_ERR_DEGENERATE) return st;
         fi.iters = iters;
         fi.inliers = inl;

@@ -68,6 +68,26 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     lib.gsicp_tracker_destroy(None)
     lib.gsicp_ctx_set_coop_walks.argtypes = [C.c_void_p, C.c_int]
     assert lib.gsicp_ctx_set_coop_walks(None, 4) == INVALID
+    lib.gsicp_surrogate_create.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.gsicp_surrogate_create(None, None) == INVALID
+    lib.gsicp_surrogate_destroy(None)
+    lib.gsicp_surrogate_get_weights.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.gsicp_surrogate_get_weights(None, None) == INVALID
+    lib.gsicp_surrogate_set_weights.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.gsicp_surrogate_set_weights(None, None) == INVALID
+    lib.gsicp_surrogate_covariances.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                                C.c_int, C.c_float, C.c_float] + [C.c_void_p] * 5 + \
+        [C.c_int64, C.c_void_p, C.c_void_p]
+    assert lib.gsicp_surrogate_covariances(None, None, None, 8, 8, None, 1, 0.1, 10.0, None, None, None, None, None,
+                                           64, None, None) == INVALID
+    lib.gsicp_surrogate_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                               C.c_int, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_float,
+                                               C.c_int] + [C.c_void_p] * 4
+    assert lib.gsicp_surrogate_train_step(None, None, None, 8, 8, None, 1, 0.1, 10.0, None, None, 1e-3, 1,
+                                          None, None, None, None) == INVALID
+    lib.gsicp_track_frame_surrogate.argtypes = [C.c_void_p] * 3 + [C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                                                   C.c_float, C.c_float] + [C.c_void_p] * 11
+    assert lib.gsicp_track_frame_surrogate(None, None, None, 8, 8, None, 1, 0.1, 10.0, *([None] * 11)) == INVALID
     lib.gsicp_map_size.restype = C.c_int64
     assert lib.gsicp_map_size(None) == 0
     lib.gsicp_map_destroy(None)
