@@ -342,9 +342,13 @@ typedef struct {
     double inlier_ratio;    /* inliers / n_points */
     int64_t added_tracking; /* Gaussians added to the tracking map */
     int64_t added_mapping;  /* Gaussians added to the mapping map */
+    int cov_source;         /* covariances of the accepted registration: 0 k-NN, 1 the surrogate's */
+    int fell_back;          /* 1: the surrogate's registration was rejected, the frame re-tracked with k-NN */
+    double residual;        /* RMS distance (m) of the accepted registration's inlier correspondences */
 } gsicp_frame_info;
 
 typedef struct gsicp_tracker_s* gsicp_tracker;
+typedef struct gsicp_surrogate_s* gsicp_surrogate;  /* see "Learned covariance surrogate" below */
 
 /* A tracker on ctx (the ctx must outlive it); frames are taken with the given stride and depth
  * range, covariances and registrations with cov / reg. */
@@ -361,6 +365,18 @@ void gsicp_tracker_destroy(gsicp_tracker t);
 gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_dev, int W, int H,
                                  const float intr[4], const double* T_start, double T_out[16],
                                  gsicp_frame_info* info, void* stream);
+/* Track with a learned surrogate's covariances (sg null: k-NN covariances only, the default).
+ * The first tracked frame and then every calib_every-th (>= 1) are calibration frames, tracked
+ * with k-NN covariances; their residual (RMS distance of the inlier correspondences at the final
+ * pose, a measure that does not depend on the covariances) is the reference.  Every other frame is
+ * tracked with the surrogate's covariances, and when that registration fails or its residual
+ * exceeds fallback_ratio times the reference, the frame is tracked again from the same start with
+ * k-NN covariances (and becomes the new reference).  A keyframe adds to the maps the covariances of
+ * its accepted registration (keyframe_knn = 0) or, when that was the surrogate's, its k-NN
+ * covariances computed then (keyframe_knn = 1: the maps hold k-NN covariances only).  sg must
+ * outlive its use by the tracker. */
+gsicp_status gsicp_tracker_set_surrogate(gsicp_tracker t, gsicp_surrogate sg, float fallback_ratio,
+                                         int calib_every, int keyframe_knn);
 /* The tracker's maps (owned by the tracker; NULL before the first frame). */
 gsicp_status gsicp_tracker_maps(gsicp_tracker t, gsicp_map* tracking_map, gsicp_map* mapping_map);
 
@@ -378,7 +394,6 @@ gsicp_status gsicp_tracker_maps(gsicp_tracker t, gsicp_map* tracking_map, gsicp_
  * W1[32][3][5][5], W2[32][32][5][5], W3[3][32][5][5] ([out][in][dy][dx]).
  * ------------------------------------------------------------------------------------------- */
 #define GSICP_SURROGATE_WEIGHTS 30400
-typedef struct gsicp_surrogate_s* gsicp_surrogate;
 
 /* A surrogate with the given weights (host, GSICP_SURROGATE_WEIGHTS floats) on the current
  * device; Adam state zero.  Synchronises the device's default stream. */

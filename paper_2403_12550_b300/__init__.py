@@ -76,7 +76,8 @@ class KeyframeParams(C.Structure):
 class FrameInfo(C.Structure):
     _fields_ = [("kind", C.c_int), ("status", C.c_int), ("iters", C.c_int), ("n_points", C.c_int64),
                 ("inliers", C.c_int64), ("inlier_ratio", C.c_double), ("added_tracking", C.c_int64),
-                ("added_mapping", C.c_int64)]
+                ("added_mapping", C.c_int64), ("cov_source", C.c_int), ("fell_back", C.c_int),
+                ("residual", C.c_double)]
 
 
 FRAME, KEYFRAME, MAPPING_KEYFRAME = 0, 1, 2
@@ -134,6 +135,7 @@ _sig("gsicp_tracker_create", C.c_int, [_vp, C.c_int, C.c_float, C.c_float, C.POI
 _sig("gsicp_tracker_destroy", None, [_vp])
 _sig("gsicp_tracker_frame", C.c_int, [_vp, _vp, C.c_int, C.c_int, _fp, _dp, _dp, C.POINTER(FrameInfo), _vp])
 _sig("gsicp_tracker_maps", C.c_int, [_vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)])
+_sig("gsicp_tracker_set_surrogate", C.c_int, [_vp, _vp, C.c_float, C.c_int, C.c_int])
 _sig("gsicp_linearise", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.c_float, _dp, _dp, _dp, _i64p, _vp, _vp])
 _sig("gsicp_map_nearest", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp])
 for _n in ("gsicp_track_frame", "gsicp_track_frame_host"):
@@ -451,6 +453,15 @@ class Tracker:
         _check(st, "gsicp_tracker_frame", allow=(ERR_DEGENERATE,))
         d = {name: getattr(info, name) for name, _ in FrameInfo._fields_}
         return np.array(T).reshape(4, 4), d
+
+    def set_surrogate(self, sg, fallback_ratio: float = 1.1, calib_every: int = 30, keyframe_knn: bool = True):
+        """Track with the surrogate's covariances (None: k-NN only), falling back to k-NN per frame
+        when the residual (RMS correspondence distance) exceeds fallback_ratio times the last k-NN
+        frame's; keyframe_knn: the maps receive k-NN covariances only."""
+        self.sg = sg  # kept alive: the tracker uses it
+        _check(lib.gsicp_tracker_set_surrogate(self.ptr, sg.ptr if sg is not None else None, float(fallback_ratio),
+                                               int(calib_every), int(bool(keyframe_knn))),
+               "gsicp_tracker_set_surrogate")
 
     def map_sizes(self) -> tuple:
         """(tracking map size, mapping map size)."""

@@ -725,8 +725,11 @@ gsicp_status gsicp_track_frame_surrogate(gsicp_ctx ctx, gsicp_surrogate sg, cons
 {
     if (!sg || !valid_frame_args(ctx, depth_dev, W, H, intr, stride, cov_params, map, T0, reg_params, T_out))
         return GSICP_ERR_INVALID_ARG;
-    return track_frame_impl(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, map, T0, reg_params, T_out,
-                            H_out, iters_out, cost_out, inliers_out, n_points_out, (cudaStream_t)stream, sg);
+    const gsicp_status st = track_frame_impl(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, map, T0,
+                                             reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out,
+                                             (cudaStream_t)stream, sg);
+    GSICP_CHECK(surrogate_status(sg));  // the stream is synchronised by now
+    return st;
 }
 
 gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int W, int H, const float intr[4],

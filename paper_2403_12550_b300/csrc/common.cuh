@@ -234,7 +234,7 @@ struct Pose16 {
 enum { REG_MODE_SOLVE = 0, REG_MODE_LINEARISE = 1 };
 enum { REG_ST_RUNNING = 0, REG_ST_CONVERGED = 1, REG_ST_MAXITER = 2, REG_ST_DEGENERATE = 3 };
 
-constexpr int NACC = 29;  // 21 (upper triangle of H) + 6 (b) + cost + count
+constexpr int NACC = 30;  // 21 (upper triangle of H) + 6 (b) + cost + count + squared distances
 
 struct RegState {
     double T[16];      // current pose
@@ -242,6 +242,7 @@ struct RegState {
     double b[6];
     double cost;
     long long inliers;
+    double sqdist;     // sum of the inliers' squared Euclidean residuals |mu - y|^2 (last linearisation)
     float Rf[9], tf[3];  // float copy of the current pose for the per-point work
     float Rlo[9], tlo[3];  // remainders: Rf + Rlo and tf + tlo carry the pose to ~48 bits
     int iter;          // completed iterations

@@ -219,6 +219,7 @@ __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegSt
     for (int i = 0; i < 36; ++i) st->H[i] = 0.0;
     for (int i = 0; i < 6; ++i) st->b[i] = 0.0;
     st->cost = 0.0;
+    st->sqdist = 0.0;
     st->inliers = 0;
     st->iter = 0;
     st->status = REG_ST_RUNNING;
@@ -591,6 +592,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
     acc[25] -= Wd1;
     acc[26] -= Wd2;
     acc[27] += d0 * Wd0 + d1 * Wd1 + d2 * Wd2;
+    acc[29] += d0 * d0 + d1 * d1 + d2 * d2;
     return refreshed;
 }
 
@@ -694,6 +696,8 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
         st->cost = tot_l;
     } else if (lane == 28) {
         st->inliers = (long long)llrint(tot_l);
+    } else if (lane == 29) {
+        st->sqdist = tot_l;
     }
     if (lane == 0) st->counter = 0u;
     const long long inliers = (long long)llrint(tot[28]);
@@ -916,6 +920,7 @@ __global__ void batch_setup_kernel(const RegJob* __restrict__ jobs, const Pose16
         for (int i = 0; i < 36; ++i) st->H[i] = 0.0;
         for (int i = 0; i < 6; ++i) st->b[i] = 0.0;
         st->cost = 0.0;
+        st->sqdist = 0.0;
         st->inliers = 0;
         st->iter = 0;
         st->status = n > 0 ? REG_ST_RUNNING : REG_ST_DEGENERATE;

@@ -152,6 +152,9 @@ int device_sm_count();
 // (nullable).  Defined in surrogate.cu.
 gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const int* idx_img, int ws, int hs, float eps,
                                float p, float* covs, float* v_out, cudaStream_t s);
+// GSICP_ERR_TIMEOUT (and the flag cleared) if a bounded wait of the surrogate's kernels ran out
+// since the last call; read after the stream has been synchronised.
+gsicp_status surrogate_status(gsicp_surrogate_s* sg);
 
 }  // namespace gsicp
 

@@ -55,6 +55,8 @@ struct gsicp_surrogate_s {
     int device = 0;
     gsicp::DevBuf w, m, s, g;      // float [SG_NW]: master weights, Adam moments, gradient sums
     gsicp::DevBuf wk;              // kernel layouts (WK_TOTAL floats)
+    gsicp::DevBuf wmma;            // layer-2 weights as the tensor-core B operand (bfloat16, see sg_conv2_tc_kernel)
+    unsigned* err = nullptr;       // pinned, device-visible: a bounded wait of a kernel ran out
     gsicp::DevBuf grid, h1, h2, v, dv, da2, da1;  // per-pixel buffers
     gsicp::DevBuf scal;            // double loss sum | unsigned long long target count
     int64_t pix_cap = 0;
@@ -82,7 +84,7 @@ __global__ void sg_grid_kernel(const float* __restrict__ pts, const int* __restr
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__global__ void sg_layout_kernel(const float* __restrict__ w, float* __restrict__ wk)
+__global__ void sg_layout_kernel(const float* __restrict__ w, float* __restrict__ wk, __nv_bfloat16* __restrict__ w2mma)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < SG_NW1) {  // W1[o][c][t]
@@ -94,6 +96,8 @@ __global__ void sg_layout_kernel(const float* __restrict__ w, float* __restrict_
         const float v = bf16r(w[i]);
         wk[WK_W2 + (c * SG_TAPS + t) * SG_C + o] = v;
         wk[WK_W2T + (o * SG_TAPS + (24 - t)) * SG_C + c] = v;
+        // tensor-core B operand: [tap t][channel group c / 8][output o][c % 8]
+        w2mma[((t * 4 + c / 8) * SG_C + o) * 8 + c % 8] = __float2bfloat16_rn(v);
     } else if (i < SG_NW) {  // W3[o][c][t]
         const int j = i - SG_NW1 - SG_NW2, o = j / 800, c = (j / 25) % 32, t = j % 25;
         const float v = bf16r(w[i]);
@@ -254,6 +258,141 @@ __global__ void __launch_bounds__(256) sg_conv32_kernel(const void* __restrict__
             for (int k = 0; k < 4; ++k) r[k] = __bfloat162float(gp[4 * q + k]) > 0.f ? acc[4 * q + k] : 0.f;
             dst[q] = make_float4(r[0], r[1], r[2], r[3]);
         }
+    }
+}
+
+// Layer 2 on the tensor cores (tcgen05, an implicit GEMM).  A CTA of 4 warps takes output tiles of
+// 8 x 16 pixels = the 128 rows of one MMA (M = 128, N = 32 output channels, K = 16 per instruction,
+// bfloat16 operands, float accumulator in tensor memory).  The h1 halo of the tile (12 x 20 pixels)
+// is staged once in shared memory as four 8-channel planes [group][halo row][halo column][16 B],
+// which is the canonical K-major layout without swizzle: a core matrix (8 rows x 16 B) is one output
+// row's 8 pixels, shifted by the tap, so the A operand of every tap is the same staged tile seen
+// through a descriptor with its own start address (row stride SBO = one halo row, K stride LBO =
+// one channel plane).  The weights (B, [tap][group][output][8 channels]) are staged once per CTA.
+// 25 taps x 2 channel halves = 50 MMAs per tile, issued by one thread and committed to an
+// mbarrier; the epilogue reads the accumulator (warp w: rows 32w..32w+31) with tcgen05.ld, applies
+// ReLU, the validity mask and bfloat16 rounding and writes h2.  Every wait is bounded: when one runs
+// out the CTA records it in err, stops taking tiles, frees its tensor memory and returns.
+constexpr int TC_TW = 8, TC_TH = 16;                  // output tile (128 pixels)
+constexpr int TC_HW = TC_TW + 4, TC_HH = TC_TH + 4;   // halo tile 12 x 20
+constexpr int TC_PLANE = TC_HW * TC_HH * 16;          // one 8-channel plane of the halo: 3840 B
+constexpr int TC_A_BYTES = 4 * TC_PLANE;              // 15360 B
+constexpr int TC_B_BYTES = SG_TAPS * 4 * SG_C * 16;   // 51200 B
+constexpr int TC_PAD = 4096;  // slack after B: every descriptor's reach stays inside the allocation
+constexpr size_t SMEM_TC = TC_A_BYTES + TC_B_BYTES + TC_PAD;
+constexpr unsigned TC_SPIN_LIMIT = 1u << 22;
+// instruction descriptor, kind::f16: D float (bit 4), A and B bfloat16 (bits 7, 10), both K-major,
+// N / 8 at bit 17, M / 16 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, canonical layout without swizzle: start address, the byte
+// distance between core matrices along K (lbo) and along M or N (sbo), all in 16-byte units;
+// descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+__global__ void __launch_bounds__(128) sg_conv2_tc_kernel(const __nv_bfloat16* __restrict__ h1, int w, int h,
+                                                          const uint4* __restrict__ wb,
+                                                          const float4* __restrict__ grid,
+                                                          __nv_bfloat16* __restrict__ h2, unsigned* __restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    uint8_t* sA = tc_smem;
+    uint8_t* sB = tc_smem + TC_A_BYTES;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (w + TC_TW - 1) / TC_TW, tiles_y = (h + TC_TH - 1) / TC_TH;
+    const int ntiles = tiles_x * tiles_y;
+    for (int i = tid; i < TC_B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = wb[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");  // the weights, for the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB), barp = smem_u32(&bar);
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TC_TW, y0 = (tile / tiles_x) * TC_TH;
+        for (int q = tid; q < 4 * TC_HW * TC_HH; q += 128) {
+            const int g = q / (TC_HW * TC_HH), r = q % (TC_HW * TC_HH);
+            const int y = y0 + r / TC_HW - 2, x = x0 + r % TC_HW - 2;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (y >= 0 && y < h && x >= 0 && x < w) v = reinterpret_cast<const uint4*>(h1)[((long)y * w + x) * 4 + g];
+            reinterpret_cast<uint4*>(sA)[q] = v;  // byte 16 q = g * TC_PLANE + 16 (row * TC_HW + col)
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+            for (int t = 0; t < SG_TAPS; ++t) {
+                const uint32_t shift = (uint32_t)(((t / 5) * TC_HW + t % 5) * 16);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint64_t da = tc_desc(a0 + 2 * j * TC_PLANE + shift, TC_PLANE, TC_HW * 16);
+                    const uint64_t db = tc_desc(b0 + (t * 4 + 2 * j) * (SG_C * 16), SG_C * 16, 128);
+                    const uint32_t accumulate = (t | j) != 0;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                 ::"r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barp));
+        }
+        uint32_t ok = 0;
+        for (unsigned it = 0; it < TC_SPIN_LIMIT && !ok; ++it)
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         "selp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(ok) : "r"(barp), "r"(phase));
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) *reinterpret_cast<volatile unsigned*>(err) = 1u;  // pinned host word
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        uint32_t r[32];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                     "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                       "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                       "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
+        if (x < w && y < h) {
+            const long pix = (long)y * w + x;
+            const bool valid = grid[pix].w != 0.f;
+            float v[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] = valid ? fmaxf(__uint_as_float(r[k]), 0.f) : 0.f;
+            store_bf16x16(h2 + pix * SG_C, v);
+            store_bf16x16(h2 + pix * SG_C + 16, v + 16);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();  // accumulator read and staged tile used before the next tile overwrites them
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
     }
 }
 
@@ -571,11 +710,10 @@ gsicp_status sg_set_smem()
 {
     static bool done = false;
     if (done) return GSICP_OK;
-    GSICP_CUDA(cudaFuncSetAttribute(sg_conv32_kernel<true, SG_EPI_RELU_BF16>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
     GSICP_CUDA(cudaFuncSetAttribute(sg_conv32_kernel<false, SG_EPI_GATE_F32>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
     GSICP_CUDA(cudaFuncSetAttribute(sg_l3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_L3));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_conv2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC));
     GSICP_CUDA(cudaFuncSetAttribute(sg_gw3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW3));
     GSICP_CUDA(cudaFuncSetAttribute(sg_gw2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW2));
     GSICP_CUDA(cudaFuncSetAttribute(sg_gw1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW1));
@@ -601,6 +739,17 @@ gsicp_status sg_ensure(gsicp_surrogate_s* sg, int64_t npix)
 }  // namespace
 
 // Grid + layers 1-3 over the frame's a1 output (pts in a1 order, idx_img the sample -> point map).
+gsicp_status set_error(gsicp_status st, const char* msg);
+
+gsicp_status surrogate_status(gsicp_surrogate_s* sg)
+{
+    if (sg && sg->err && *reinterpret_cast<volatile unsigned*>(sg->err)) {
+        *sg->err = 0u;
+        return set_error(GSICP_ERR_TIMEOUT, "surrogate: a tensor-core wait ran out");
+    }
+    return GSICP_OK;
+}
+
 gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const int* idx_img, int ws, int hs, float eps,
                         float p, float* covs, float* v_out, cudaStream_t s)
 {
@@ -614,8 +763,12 @@ gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const in
     const dim3 tiles((ws + SG_T - 1) / SG_T, (hs + SG_T - 1) / SG_T);
     sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, reinterpret_cast<const float4*>(wk + WK_W1),
                                        sg->h1.as<__nv_bfloat16>());
-    sg_conv32_kernel<true, SG_EPI_RELU_BF16><<<dim3(tiles.x, tiles.y, 2), 256, SMEM_CONV, s>>>(
-        sg->h1.ptr, ws, hs, wk + WK_W2, grid, nullptr, sg->h2.ptr);
+    {
+        const int ntc = ((ws + TC_TW - 1) / TC_TW) * ((hs + TC_TH - 1) / TC_TH);
+        const int gtc = std::max(1, std::min(ntc, 3 * device_sm_count()));
+        sg_conv2_tc_kernel<<<gtc, 128, SMEM_TC, s>>>(sg->h1.as<__nv_bfloat16>(), ws, hs, sg->wmma.as<const uint4>(),
+                                                    grid, sg->h2.as<__nv_bfloat16>(), sg->err);
+    }
     sg_l3_kernel<<<tiles, 256, SMEM_L3, s>>>(sg->h2.as<__nv_bfloat16>(), ws, hs,
                                              reinterpret_cast<const float4*>(wk + WK_W3), grid, idx_img, eps, p,
                                              covs, v_out);
@@ -661,7 +814,8 @@ gsicp_status sg_upload(gsicp_surrogate_s* sg, const float* w_host, cudaStream_t 
     GSICP_CUDA(cudaMemcpyAsync(sg->w.ptr, w_host, sizeof(float) * SG_NW, cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemsetAsync(sg->m.ptr, 0, sizeof(float) * SG_NW, s));
     GSICP_CUDA(cudaMemsetAsync(sg->s.ptr, 0, sizeof(float) * SG_NW, s));
-    sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>());
+    sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>(),
+                                                         sg->wmma.as<__nv_bfloat16>());
     GSICP_CUDA(cudaGetLastError());
     sg->steps = 0;
     return GSICP_OK;
@@ -688,10 +842,13 @@ gsicp_status gsicp_surrogate_create(const float* weights, gsicp_surrogate* out)
     if ((st = sg->w.ensure(sizeof(float) * SG_NW)) != GSICP_OK || (st = sg->m.ensure(sizeof(float) * SG_NW)) != GSICP_OK ||
         (st = sg->s.ensure(sizeof(float) * SG_NW)) != GSICP_OK || (st = sg->g.ensure(sizeof(float) * SG_NW)) != GSICP_OK ||
         (st = sg->wk.ensure(sizeof(float) * WK_TOTAL)) != GSICP_OK || (st = sg->scal.ensure(16)) != GSICP_OK ||
+        (st = sg->wmma.ensure(sizeof(__nv_bfloat16) * SG_NW2)) != GSICP_OK ||
+        (st = (cudaMallocHost((void**)&sg->err, sizeof(unsigned)) == cudaSuccess ? GSICP_OK : GSICP_ERR_OOM)) != GSICP_OK ||
         (st = sg_upload(sg, weights, nullptr)) != GSICP_OK) {
         gsicp_surrogate_destroy(sg);
         return st;
     }
+    *sg->err = 0u;
     cudaError_t e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
         gsicp_surrogate_destroy(sg);
@@ -704,9 +861,10 @@ gsicp_status gsicp_surrogate_create(const float* weights, gsicp_surrogate* out)
 void gsicp_surrogate_destroy(gsicp_surrogate sg)
 {
     if (!sg) return;
-    for (DevBuf* b : {&sg->w, &sg->m, &sg->s, &sg->g, &sg->wk, &sg->grid, &sg->h1, &sg->h2, &sg->v, &sg->dv, &sg->da2,
-                      &sg->da1, &sg->scal})
+    for (DevBuf* b : {&sg->w, &sg->m, &sg->s, &sg->g, &sg->wk, &sg->wmma, &sg->grid, &sg->h1, &sg->h2, &sg->v, &sg->dv,
+                      &sg->da2, &sg->da1, &sg->scal})
         b->release();
+    if (sg->err) cudaFreeHost(sg->err);
     delete sg;
 }
 
@@ -756,6 +914,7 @@ gsicp_status gsicp_surrogate_covariances(gsicp_ctx ctx, gsicp_surrogate sg, cons
     int* h = (int*)ctx->host_pinned;
     GSICP_CUDA(cudaMemcpyAsync(h, ctx->n_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GSICP_CUDA(cudaStreamSynchronize(s));
+    GSICP_CHECK(surrogate_status(sg));
     const int64_t n = h[0], m = std::min<int64_t>(n, cap);
     if (m > 0) {
         GSICP_CUDA(cudaMemcpyAsync(pts_dev, ctx->frame_pts.ptr, sizeof(float) * 3 * m, cudaMemcpyDeviceToDevice, s));
@@ -797,6 +956,7 @@ gsicp_status gsicp_surrogate_train_step(gsicp_ctx ctx, gsicp_surrogate sg, const
     double* hs_ = reinterpret_cast<double*>(ctx->host_pinned);
     GSICP_CUDA(cudaMemcpyAsync(hs_, sg->scal.ptr, 16, cudaMemcpyDeviceToHost, s));
     GSICP_CUDA(cudaStreamSynchronize(s));
+    GSICP_CHECK(surrogate_status(sg));
     const double loss_sum = hs_[0];
     const unsigned long long cnt = reinterpret_cast<unsigned long long*>(hs_)[1];
     if (loss_out) *loss_out = cnt ? loss_sum / (double)cnt : 0.0;
@@ -813,7 +973,8 @@ gsicp_status gsicp_surrogate_train_step(gsicp_ctx ctx, gsicp_surrogate sg, const
                                                             sg->g.as<float>(), (float)(1.0 / (double)cnt), lr,
                                                             (float)b1, (float)b2, 1e-8f, (float)(1.0 - pow(b1, t)),
                                                             (float)(1.0 - pow(b2, t)));
-        sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>());
+        sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>(),
+                                                             sg->wmma.as<__nv_bfloat16>());
         GSICP_CUDA(cudaGetLastError());
         sg->steps = t;
     }

@@ -8,6 +8,9 @@
 // used for mapping but not to the one tracking registers against.  Tracking keyframes add to
 // both.  The next frame starts from the constant-velocity prediction of the last two poses.
 //
+// Optionally the frames are tracked with a learned surrogate's covariances, with a per-frame
+// fallback to the k-NN ones (gsicp_tracker_set_surrogate).
+//
 // Per frame on the device: gsicp_track_frame's kernels (a1..a7), then, for a keyframe, the
 // frame's Gaussians moved into the world frame, the exact nearest map mean of each (a
 // non-overlap test: none within the overlap radius), an order-preserving compaction of the new
@@ -71,6 +74,13 @@ struct gsicp_tracker_s {
     int since_kf = 0;
     double T1[16], T2[16];  // the last two poses (T1 the latest)
     DevBuf wpts, wcovs, idx, kpts, kcovs, counts, sums, nk;
+    // learned covariances (gsicp_tracker_set_surrogate)
+    gsicp_surrogate sg = nullptr;
+    float fallback_ratio = 1.1f;
+    int calib_every = 30;
+    double ref_residual = 0.0;  // residual of the last frame tracked with k-NN covariances
+    int since_calib = 0;        // frames tracked with the surrogate since then
+    int keyframe_knn = 1;       // keyframes tracked with the surrogate add k-NN covariances to the maps
 };
 
 static void mat_mul(const double* A, const double* B, double* C)
@@ -110,6 +120,14 @@ static void predict(const double* T1, const double* T2, double* T)
         for (int c = 0; c < 3; ++c) T[4 * r + c] = R[3 * r + c];
     T[12] = T[13] = T[14] = 0.0;
     T[15] = 1.0;
+}
+
+// RMS Euclidean distance of the last registration's inlier correspondences: a residual that does
+// not depend on the covariances used, so registrations with different ones compare on one scale.
+static double rms_residual(gsicp_ctx ctx, int64_t inliers)
+{
+    const RegState* st = ctx->reg.state_host;
+    return inliers > 0 && st ? sqrt(st->sqdist / (double)inliers) : 0.0;
 }
 
 // Gaussians (world frame, n) not within the overlap radius of any mean of `map` (all of them if
@@ -220,9 +238,37 @@ extern "C" gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_
         else memcpy(T0, t->T1, sizeof(T0));
         int iters = 0;
         int64_t inl = 0;
-        st = track_frame_impl(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, t->track_map, T0,
-                              &t->reg, T, nullptr, &iters, nullptr, &inl, &n, s, nullptr);
-        if (st != GSICP_OK && st != GSICP_ERR_DEGENERATE) return st;
+        double cost = 0.0;
+        // Learned covariances: a frame is tracked with the surrogate's covariances unless it is a
+        // calibration frame (the first tracked one, then every calib_every-th); the result stands
+        // if its residual (RMS correspondence distance) is within fallback_ratio of the last
+        // k-NN-tracked frame's, else the frame is tracked again, from the same start, with k-NN
+        // covariances.
+        const bool use_sg = t->sg && t->ref_residual > 0.0 && t->since_calib < t->calib_every - 1;
+        if (use_sg) {
+            st = track_frame_impl(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, t->track_map,
+                                  T0, &t->reg, T, nullptr, &iters, &cost, &inl, &n, s, t->sg);
+            if (st != GSICP_OK && st != GSICP_ERR_DEGENERATE) return st;
+            GSICP_CHECK(surrogate_status(t->sg));
+            fi.residual = rms_residual(ctx, inl);
+            fi.cov_source = 1;
+            if (st == GSICP_OK && inl > 0 && fi.residual <= (double)t->fallback_ratio * t->ref_residual) {
+                t->since_calib += 1;
+            } else {
+                fi.fell_back = 1;
+            }
+        }
+        if (!use_sg || fi.fell_back) {
+            st = track_frame_impl(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, t->track_map,
+                                  T0, &t->reg, T, nullptr, &iters, &cost, &inl, &n, s, nullptr);
+            if (st != GSICP_OK && st != GSICP_ERR_DEGENERATE) return st;
+            fi.residual = rms_residual(ctx, inl);
+            fi.cov_source = 0;
+            if (t->sg && st == GSICP_OK && inl > 0) {
+                t->ref_residual = fi.residual;
+                t->since_calib = 0;
+            }
+        }
         fi.iters = iters;
         fi.inliers = inl;
         fi.inlier_ratio = n > 0 ? (double)inl / (double)n : 0.0;
@@ -236,6 +282,11 @@ extern "C" gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_
     }
     fi.n_points = n;
     fi.status = st;
+    if (fi.kind != GSICP_FRAME && n > 0 && fi.cov_source == 1 && t->keyframe_knn) {
+        // the maps keep k-NN covariances: recompute them for this keyframe (same points)
+        GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, t->stride, t->z_min, t->z_max, &t->cov, cap, s,
+                                      nullptr));
+    }
     if (fi.kind != GSICP_FRAME && n > 0) {
         // the frame's Gaussians (row-major, as a1 wrote them) moved into the world frame
         GSICP_CHECK(t->wpts.ensure(sizeof(float) * 3 * n));
@@ -255,6 +306,20 @@ extern "C" gsicp_status gsicp_tracker_frame(gsicp_tracker t, const float* depth_
     memcpy(T_out, T, sizeof(T));
     if (info) *info = fi;
     return st;
+}
+
+extern "C" gsicp_status gsicp_tracker_set_surrogate(gsicp_tracker t, gsicp_surrogate sg, float fallback_ratio,
+                                                    int calib_every, int keyframe_knn)
+{
+    if (!t || (sg && (!(fallback_ratio >= 0.f) || calib_every < 1 || (keyframe_knn != 0 && keyframe_knn != 1))))
+        return GSICP_ERR_INVALID_ARG;
+    t->keyframe_knn = keyframe_knn;
+    t->sg = sg;
+    t->fallback_ratio = fallback_ratio;
+    t->calib_every = calib_every;
+    t->ref_residual = 0.0;
+    t->since_calib = 0;
+    return GSICP_OK;
 }
 
 extern "C" gsicp_status gsicp_tracker_maps(gsicp_tracker t, gsicp_map* tracking_map, gsicp_map* mapping_map)

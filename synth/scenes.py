@@ -29,7 +29,7 @@ __all__ = [
     "look_pose", "circle_poses", "random_offset", "rot_axis_angle", "inv_pose", "make_pose",
     "transform_points", "Intrinsics", "REPLICA_INTR", "TUM_INTR",
     "pair_config1", "frame_config2", "spline_trajectory", "sequence_config3", "const_velocity",
-    "batch_config4", "HALF_TUM_INTR", "surrogate_train_config5", "sequence_config5",
+    "batch_config4", "HALF_TUM_INTR", "surrogate_train_config5", "sequence_config5", "orbit_trajectory",
 ]
 
 
@@ -464,13 +464,40 @@ def surrogate_train_config5(seed: int = 0, n_frames: int = 2000, n_scenes: int =
     return dict(scenes=scenes, intr=intr, poses=poses, depth=depth)
 
 
+def orbit_trajectory(seed: int, scene: Scene, n_frames: int = 500, fps: float = 30.0, turns: float = 1.0) -> list:
+    """A camera orbiting the room centre while looking inwards: position on an ellipse with semi-axes
+    0.3 of the room's length and width (radius and height wobbling smoothly), heading towards the
+    centre plus a smooth swing of up to 25 degrees, 15-30 degrees down; ``turns`` orbits over the
+    sequence.  Views keep the middle of the room (the furniture) in sight, where a free-roaming
+    camera in a small room keeps facing bare walls and floor, which leave translations along them
+    unconstrained."""
+    rng = np.random.default_rng(6161 + seed)
+    c = scene.centre
+    ax, ay = 0.3 * (scene.room_hi - scene.room_lo)[:2]
+    ph = rng.uniform(0, 2 * np.pi, size=4)
+    phi0 = rng.uniform(0, 2 * np.pi)
+    poses = []
+    for f in range(n_frames):
+        s = f / max(1, n_frames - 1)
+        phi = phi0 + 2 * np.pi * turns * s
+        rad = 1.0 + 0.12 * np.sin(2 * np.pi * 2 * s + ph[0])
+        pos = np.array([c[0] + ax * rad * np.cos(phi), c[1] + ay * rad * np.sin(phi),
+                        1.5 + 0.2 * np.sin(2 * np.pi * 1.5 * s + ph[1])])
+        to_c = c[:2] - pos[:2]
+        yaw = np.arctan2(to_c[1], to_c[0]) + np.deg2rad(25.0) * np.sin(2 * np.pi * 2.5 * s + ph[2])
+        pitch = np.deg2rad(22.5 + 7.5 * np.sin(2 * np.pi * 1.7 * s + ph[3]))
+        poses.append(look_pose(pos, yaw, pitch))
+    return poses
+
+
 def sequence_config5(seed: int = 0, n_frames: int = 500, intr: Intrinsics = TUM_INTR, noise_coeff: float = 1e-3):
-    """Held-out sequence of the covariance surrogate: a config-2-style room (seed 500 + seed, none of
-    the training rooms), ``n_frames`` poses at 30 Hz along :func:`spline_trajectory` (<= 1 m/s,
-    <= 60 deg/s, 0.35 m clearance: the room is small), 640 x 480 depth frames ``depth(f)`` with
-    noise seeded by (seed, f).  Returns a dict with keys ``scene, intr, poses, depth``."""
+    """Held-out sequence of the covariance surrogate: a config-2-style room (4 x 3 x 2.5 m, 8 boxes,
+    4 spheres; seed 500 + seed, none of the training rooms) seen along :func:`orbit_trajectory` at
+    30 Hz (one orbit in ``n_frames`` frames: ~0.4 m/s, ~25 deg/s), 640 x 480 depth frames
+    ``depth(f)`` with noise seeded by (seed, f).  Returns a dict with keys ``scene, intr, poses,
+    depth``."""
     scene = make_room(500 + seed)
-    poses = spline_trajectory(seed, scene, n_frames=n_frames, clearance=0.35)
+    poses = orbit_trajectory(seed, scene, n_frames=n_frames)
 
     def depth(f: int) -> np.ndarray:
         rng = np.random.default_rng(8_000_009 * (seed + 1) + f)

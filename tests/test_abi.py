@@ -88,6 +88,8 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     lib.gsicp_track_frame_surrogate.argtypes = [C.c_void_p] * 3 + [C.c_int, C.c_int, C.c_void_p, C.c_int,
                                                                    C.c_float, C.c_float] + [C.c_void_p] * 11
     assert lib.gsicp_track_frame_surrogate(None, None, None, 8, 8, None, 1, 0.1, 10.0, *([None] * 11)) == INVALID
+    lib.gsicp_tracker_set_surrogate.argtypes = [C.c_void_p, C.c_void_p, C.c_float, C.c_int, C.c_int]
+    assert lib.gsicp_tracker_set_surrogate(None, None, 1.1, 30, 1) == INVALID
     lib.gsicp_map_size.restype = C.c_int64
     assert lib.gsicp_map_size(None) == 0
     lib.gsicp_map_destroy(None)

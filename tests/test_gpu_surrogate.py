@@ -189,3 +189,38 @@ def test_surrogate_entry_points_reject_bad_input(g, ctx):
     with pytest.raises(ValueError):
         g.Surrogate(np.zeros(10, np.float32))
     sg.close()
+
+
+def test_tracker_fallback_policy(g, ctx):
+    """A tracker with a surrogate and fallback ratio 0 rejects every surrogate registration and
+    re-tracks with k-NN covariances: poses bit-identical to the k-NN tracker's.  With an infinite
+    ratio every non-calibration frame keeps the surrogate's registration."""
+    from synth import TUM_INTR, sequence_config5
+    seq = sequence_config5(0, n_frames=12)
+    intr = TUM_INTR.as_array()
+    frames = [cu(seq["depth"](f)) for f in range(12)]
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    sg = g.Surrogate(_weights(9))
+
+    def run(ratio, calib, use):
+        tr = g.Tracker(ctx, 2, 0.1, 10.0, cp, rp)
+        if use:
+            tr.set_surrogate(sg, ratio, calib)
+        out = [tr.frame(fr, intr, seq["poses"][0] if i == 0 else None) for i, fr in enumerate(frames)]
+        tr.close()
+        return out
+
+    plain = run(0.0, 30, False)
+    never = run(0.0, 30, True)
+    for (Tp, ip), (Tn, inn) in zip(plain, never):
+        np.testing.assert_array_equal(Tn, Tp)
+        assert inn["cov_source"] == 0 and ip["cov_source"] == 0
+    assert sum(i["fell_back"] for _, i in never) == 12 - 2  # all but the keyframe and the calibration frame
+    always = run(float("inf"), 5, True)
+    kinds = [(i["cov_source"], i["fell_back"]) for _, i in always]
+    # frame 0: keyframe (k-NN); frame 1 and every 5th after it: calibration (k-NN); the rest surrogate
+    assert kinds[0] == (0, 0) and kinds[1] == (0, 0)
+    assert all(fb == 0 for _, fb in kinds)
+    assert [src for src, _ in kinds[2:]] == [1, 1, 1, 1, 0, 1, 1, 1, 1, 0]
+    sg.close()
