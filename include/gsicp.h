@@ -399,6 +399,12 @@ gsicp_status gsicp_tracker_maps(gsicp_tracker t, gsicp_map* tracking_map, gsicp_
  * device; Adam state zero.  Synchronises the device's default stream. */
 gsicp_status gsicp_surrogate_create(const float* weights, gsicp_surrogate* out);
 void gsicp_surrogate_destroy(gsicp_surrogate sg);
+/* Profiling: with timing enabled, every forward of the network records CUDA events on its stream
+ * between its layers; gsicp_surrogate_layer_times returns the device time (ms) of the last one
+ * (after a synchronisation): out[0] grid + layer 1, out[1] layer 2, out[2] layer 3 + covariances.
+ * GSICP_ERR_INVALID_ARG before timing was ever enabled. */
+gsicp_status gsicp_surrogate_set_timing(gsicp_surrogate sg, int enable);
+gsicp_status gsicp_surrogate_layer_times(gsicp_surrogate sg, double out[3]);
 /* Copy the current float weights out (host) / replace them (host; resets the Adam state). */
 gsicp_status gsicp_surrogate_get_weights(gsicp_surrogate sg, float* weights);
 gsicp_status gsicp_surrogate_set_weights(gsicp_surrogate sg, const float* weights);

@@ -148,6 +148,8 @@ _sig("gsicp_surrogate_create", C.c_int, [_fp, C.POINTER(C.c_void_p)])
 _sig("gsicp_surrogate_destroy", None, [_vp])
 _sig("gsicp_surrogate_get_weights", C.c_int, [_vp, _fp])
 _sig("gsicp_surrogate_set_weights", C.c_int, [_vp, _fp])
+_sig("gsicp_surrogate_set_timing", C.c_int, [_vp, C.c_int])
+_sig("gsicp_surrogate_layer_times", C.c_int, [_vp, _dp])
 _sig("gsicp_surrogate_covariances", C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float,
                                               C.POINTER(CovParams), _vp, _vp, _vp, _vp, C.c_int64, _i64p, _vp])
 _sig("gsicp_surrogate_train_step", C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _fp, C.c_int, C.c_float, C.c_float,
@@ -556,6 +558,15 @@ class Surrogate:
         if w.size != SURROGATE_WEIGHTS:
             raise ValueError(f"expected {SURROGATE_WEIGHTS} weights")
         _check(lib.gsicp_surrogate_set_weights(self.ptr, w.ctypes.data_as(_fp)), "gsicp_surrogate_set_weights")
+
+    def set_timing(self, enable: bool):
+        _check(lib.gsicp_surrogate_set_timing(self.ptr, int(bool(enable))), "gsicp_surrogate_set_timing")
+
+    def layer_times(self) -> tuple:
+        """Device ms of the last forward: (grid + layer 1, layer 2, layer 3 + covariances)."""
+        out = (C.c_double * 3)()
+        _check(lib.gsicp_surrogate_layer_times(self.ptr, out), "gsicp_surrogate_layer_times")
+        return tuple(out)
 
     def close(self):
         if self.ptr:

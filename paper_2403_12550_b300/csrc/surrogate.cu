@@ -55,8 +55,10 @@ struct gsicp_surrogate_s {
     int device = 0;
     gsicp::DevBuf w, m, s, g;      // float [SG_NW]: master weights, Adam moments, gradient sums
     gsicp::DevBuf wk;              // kernel layouts (WK_TOTAL floats)
-    gsicp::DevBuf wmma;            // layer-2 weights as the tensor-core B operand (bfloat16, see sg_conv2_tc_kernel)
+    gsicp::DevBuf wmma;            // layers 2 and 3 as tensor-core B operands (bfloat16, see sg_conv_tc_kernel)
     unsigned* err = nullptr;       // pinned, device-visible: a bounded wait of a kernel ran out
+    bool timing = false;           // record events around the layers of every forward
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     gsicp::DevBuf grid, h1, h2, v, dv, da2, da1;  // per-pixel buffers
     gsicp::DevBuf scal;            // double loss sum | unsigned long long target count
     int64_t pix_cap = 0;
@@ -107,6 +109,8 @@ __global__ void sg_layout_kernel(const float* __restrict__ w, float* __restrict_
             wk[WK_W3 + 4 * (c * SG_TAPS + t) + 3] = 0.f;
             wk[WK_W3T + 4 * ((24 - t) * SG_C + c) + 3] = 0.f;
         }
+        // tensor-core B operand of layer 3 (after layer 2's): [tap][group][16 outputs, 3 used][8]
+        w2mma[SG_NW2 + ((t * 4 + c / 8) * 16 + o) * 8 + c % 8] = __float2bfloat16_rn(v);
     }
 }
 
@@ -261,29 +265,53 @@ __global__ void __launch_bounds__(256) sg_conv32_kernel(const void* __restrict__
     }
 }
 
-// Layer 2 on the tensor cores (tcgen05, an implicit GEMM).  A CTA of 4 warps takes output tiles of
-// 8 x 16 pixels = the 128 rows of one MMA (M = 128, N = 32 output channels, K = 16 per instruction,
-// bfloat16 operands, float accumulator in tensor memory).  The h1 halo of the tile (12 x 20 pixels)
-// is staged once in shared memory as four 8-channel planes [group][halo row][halo column][16 B],
-// which is the canonical K-major layout without swizzle: a core matrix (8 rows x 16 B) is one output
-// row's 8 pixels, shifted by the tap, so the A operand of every tap is the same staged tile seen
-// through a descriptor with its own start address (row stride SBO = one halo row, K stride LBO =
-// one channel plane).  The weights (B, [tap][group][output][8 channels]) are staged once per CTA.
-// 25 taps x 2 channel halves = 50 MMAs per tile, issued by one thread and committed to an
-// mbarrier; the epilogue reads the accumulator (warp w: rows 32w..32w+31) with tcgen05.ld, applies
-// ReLU, the validity mask and bfloat16 rounding and writes h2.  Every wait is bounded: when one runs
-// out the CTA records it in err, stops taking tiles, frees its tensor memory and returns.
+// The plane covariance on n = v / |v| with the scale aligning factor z^(-2p): (I - (1 - eps) n n^T)
+// z^(-2p) as (xx, xy, xz, yy, yz, zz); |v| = 0 gives the isotropic z^(-2p) I.
+__device__ __forceinline__ void plane_cov_from_v(float v0, float v1, float v2, float z, float eps, float p, float* C)
+{
+    const float s = powf(z, -2.f * p);
+    const float nn = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+    if (!(nn > 0.f)) {
+        C[0] = s; C[1] = 0.f; C[2] = 0.f; C[3] = s; C[4] = 0.f; C[5] = s;
+        return;
+    }
+    const float n0 = v0 / nn, n1 = v1 / nn, n2 = v2 / nn, k = 1.f - eps;
+    C[0] = (1.f - k * n0 * n0) * s;
+    C[1] = (-k * n0 * n1) * s;
+    C[2] = (-k * n0 * n2) * s;
+    C[3] = (1.f - k * n1 * n1) * s;
+    C[4] = (-k * n1 * n2) * s;
+    C[5] = (1.f - k * n2 * n2) * s;
+}
+
+// Layers 2 and 3 on the tensor cores (tcgen05, an implicit GEMM).  A CTA of 4 warps takes output
+// tiles of 8 x 16 pixels = the 128 rows of one MMA (M = 128, K = 16 per instruction, bfloat16
+// operands, float accumulator in tensor memory; N = 32 output channels for layer 2, 16 for layer
+// 3, whose 3 outputs are padded with zero weights).  The 32-channel input's halo of the tile (12 x
+// 20 pixels) is staged once in shared memory as four 8-channel planes [group][halo row][halo
+// column][16 B], which is the canonical K-major layout without swizzle: a core matrix (8 rows x
+// 16 B) is one output row's 8 pixels, shifted by the tap, so the A operand of every tap is the same
+// staged tile seen through a descriptor with its own start address (row stride SBO = one halo row,
+// K stride LBO = one channel plane).  The weights (B, [tap][group][output][8 channels]) are staged
+// once per CTA.  25 taps x 2 channel halves = 50 MMAs per tile, issued by one thread and committed
+// to an mbarrier; the epilogue reads the accumulator (warp w: rows 32w..32w+31) with tcgen05.ld.
+// Layer 2's epilogue applies ReLU, the validity mask and bfloat16 rounding and writes h2; layer 3's
+// writes v and the point's plane covariance.  Every wait is bounded: when one runs out the CTA
+// records it in err, stops taking tiles, frees its tensor memory and returns.
 constexpr int TC_TW = 8, TC_TH = 16;                  // output tile (128 pixels)
 constexpr int TC_HW = TC_TW + 4, TC_HH = TC_TH + 4;   // halo tile 12 x 20
 constexpr int TC_PLANE = TC_HW * TC_HH * 16;          // one 8-channel plane of the halo: 3840 B
 constexpr int TC_A_BYTES = 4 * TC_PLANE;              // 15360 B
-constexpr int TC_B_BYTES = SG_TAPS * 4 * SG_C * 16;   // 51200 B
 constexpr int TC_PAD = 4096;  // slack after B: every descriptor's reach stays inside the allocation
-constexpr size_t SMEM_TC = TC_A_BYTES + TC_B_BYTES + TC_PAD;
+template <int kN>
+constexpr int tc_b_bytes() { return SG_TAPS * 4 * kN * 16; }
+template <int kN>
+constexpr size_t tc_smem() { return TC_A_BYTES + tc_b_bytes<kN>() + TC_PAD; }
 constexpr unsigned TC_SPIN_LIMIT = 1u << 22;
 // instruction descriptor, kind::f16: D float (bit 4), A and B bfloat16 (bits 7, 10), both K-major,
 // N / 8 at bit 17, M / 16 at bit 24
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+template <int kN>
+constexpr uint32_t tc_idesc() { return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -296,20 +324,24 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
            ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
 }
 
-__global__ void __launch_bounds__(128) sg_conv2_tc_kernel(const __nv_bfloat16* __restrict__ h1, int w, int h,
-                                                          const uint4* __restrict__ wb,
-                                                          const float4* __restrict__ grid,
-                                                          __nv_bfloat16* __restrict__ h2, unsigned* __restrict__ err)
+template <int kN>
+__global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __nv_bfloat16* __restrict__ in, int w, int h,
+                                                         const uint4* __restrict__ wb,
+                                                         const float4* __restrict__ grid,
+                                                         __nv_bfloat16* __restrict__ h2, const int* __restrict__ idx_img,
+                                                         float eps, float p, float* __restrict__ covs,
+                                                         float* __restrict__ v_out, unsigned* __restrict__ err)
 {
-    extern __shared__ __align__(1024) uint8_t tc_smem[];
-    uint8_t* sA = tc_smem;
-    uint8_t* sB = tc_smem + TC_A_BYTES;
+    static_assert(kN == 32 || kN == 16, "layer 2 (N = 32) or layer 3 (N = 16)");
+    extern __shared__ __align__(1024) uint8_t tc_smem_[];
+    uint8_t* sA = tc_smem_;
+    uint8_t* sB = tc_smem_ + TC_A_BYTES;
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (w + TC_TW - 1) / TC_TW, tiles_y = (h + TC_TH - 1) / TC_TH;
     const int ntiles = tiles_x * tiles_y;
-    for (int i = tid; i < TC_B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = wb[i];
+    for (int i = tid; i < tc_b_bytes<kN>() / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = wb[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -331,7 +363,7 @@ __global__ void __launch_bounds__(128) sg_conv2_tc_kernel(const __nv_bfloat16* _
             const int g = q / (TC_HW * TC_HH), r = q % (TC_HW * TC_HH);
             const int y = y0 + r / TC_HW - 2, x = x0 + r % TC_HW - 2;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (y >= 0 && y < h && x >= 0 && x < w) v = reinterpret_cast<const uint4*>(h1)[((long)y * w + x) * 4 + g];
+            if (y >= 0 && y < h && x >= 0 && x < w) v = reinterpret_cast<const uint4*>(in)[((long)y * w + x) * 4 + g];
             reinterpret_cast<uint4*>(sA)[q] = v;  // byte 16 q = g * TC_PLANE + 16 (row * TC_HW + col)
         }
         asm volatile("fence.proxy.async.shared::cta;");
@@ -345,11 +377,11 @@ __global__ void __launch_bounds__(128) sg_conv2_tc_kernel(const __nv_bfloat16* _
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const uint64_t da = tc_desc(a0 + 2 * j * TC_PLANE + shift, TC_PLANE, TC_HW * 16);
-                    const uint64_t db = tc_desc(b0 + (t * 4 + 2 * j) * (SG_C * 16), SG_C * 16, 128);
+                    const uint64_t db = tc_desc(b0 + (t * 4 + 2 * j) * (kN * 16), kN * 16, 128);
                     const uint32_t accumulate = (t | j) != 0;
                     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                 ::"r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate));
+                                 ::"r"(tmem), "l"(da), "l"(db), "r"(tc_idesc<kN>()), "r"(accumulate));
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barp));
@@ -365,26 +397,48 @@ __global__ void __launch_bounds__(128) sg_conv2_tc_kernel(const __nv_bfloat16* _
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        uint32_t r[32];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                     "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                     "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                       "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                       "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                     : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
         const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
-        if (x < w && y < h) {
-            const long pix = (long)y * w + x;
-            const bool valid = grid[pix].w != 0.f;
-            float v[32];
+        const bool inside = x < w && y < h;
+        const long pix = (long)y * w + x;
+        if (kN == 32) {
+            uint32_t r[32];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (inside) {
+                const bool valid = grid[pix].w != 0.f;
+                float v[32];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) v[k] = valid ? fmaxf(__uint_as_float(r[k]), 0.f) : 0.f;
-            store_bf16x16(h2 + pix * SG_C, v);
-            store_bf16x16(h2 + pix * SG_C + 16, v + 16);
+                for (int k = 0; k < 32; ++k) v[k] = valid ? fmaxf(__uint_as_float(r[k]), 0.f) : 0.f;
+                store_bf16x16(h2 + pix * SG_C, v);
+                store_bf16x16(h2 + pix * SG_C + 16, v + 16);
+            }
+        } else {
+            uint32_t r[4];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (inside) {
+                const float4 g = grid[pix];
+                const bool valid = g.w != 0.f;
+                const float v0 = valid ? __uint_as_float(r[0]) : 0.f, v1 = valid ? __uint_as_float(r[1]) : 0.f,
+                            v2 = valid ? __uint_as_float(r[2]) : 0.f;
+                if (v_out) {
+                    v_out[3 * pix] = v0;
+                    v_out[3 * pix + 1] = v1;
+                    v_out[3 * pix + 2] = v2;
+                }
+                const int id = valid && covs ? idx_img[pix] : -1;
+                if (id >= 0) plane_cov_from_v(v0, v1, v2, g.z, eps, p, covs + 6l * id);
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();  // accumulator read and staged tile used before the next tile overwrites them
@@ -394,66 +448,6 @@ __global__ void __launch_bounds__(128) sg_conv2_tc_kernel(const __nv_bfloat16* _
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
     }
-}
-
-// Layer 3 (32 -> 3), then per valid pixel: the normal n = v / |v| and the plane covariance
-// (I - (1 - eps) n n^T) z^(-2p) written at the point's index (a1 order); |v| = 0 gives the
-// isotropic z^(-2p) I.  v_out (optional): v per pixel (zero at invalid pixels).
-__global__ void __launch_bounds__(256) sg_l3_kernel(const __nv_bfloat16* __restrict__ h2, int w, int h,
-                                                    const float4* __restrict__ w3k,
-                                                    const float4* __restrict__ grid,
-                                                    const int* __restrict__ idx_img, float eps, float p,
-                                                    float* __restrict__ covs, float* __restrict__ v_out)
-{
-    extern __shared__ float sm[];
-    float* tile = sm;                                          // [32][SG_HPAD]
-    float4* ws = reinterpret_cast<float4*>(sm + SG_C * SG_HPAD);  // [32 c][25 t] (32 * 401 floats: 16-byte aligned)
-    const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
-    for (int i = threadIdx.x; i < SG_C * SG_TAPS; i += blockDim.x) ws[i] = w3k[i];
-    stage32<true>(h2, w, h, x0, y0, tile);
-    __syncthreads();
-    const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= w || y >= h) return;
-    const long pix = (long)y * w + x;
-    const float4 g = grid[pix];
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    if (g.w != 0.f) {
-        for (int c = 0; c < SG_C; ++c) {
-            const float* tc = tile + c * SG_HPAD;
-            const float4* wc = ws + c * SG_TAPS;
-#pragma unroll 5
-            for (int t = 0; t < SG_TAPS; ++t) {
-                const float xv = tc[halo_of(t, tx, ty)];
-                const float4 wv = wc[t];
-                v0 = fmaf(wv.x, xv, v0);
-                v1 = fmaf(wv.y, xv, v1);
-                v2 = fmaf(wv.z, xv, v2);
-            }
-        }
-    }
-    if (v_out) {
-        v_out[3 * pix] = v0;
-        v_out[3 * pix + 1] = v1;
-        v_out[3 * pix + 2] = v2;
-    }
-    if (!covs || g.w == 0.f) return;
-    const int id = idx_img[pix];
-    if (id < 0) return;
-    const float s = powf(g.z, -2.f * p);
-    const float nn = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
-    float* C = covs + 6l * id;
-    if (!(nn > 0.f)) {
-        C[0] = s; C[1] = 0.f; C[2] = 0.f; C[3] = s; C[4] = 0.f; C[5] = s;
-        return;
-    }
-    const float n0 = v0 / nn, n1 = v1 / nn, n2 = v2 / nn, k = 1.f - eps;
-    C[0] = (1.f - k * n0 * n0) * s;
-    C[1] = (-k * n0 * n1) * s;
-    C[2] = (-k * n0 * n2) * s;
-    C[3] = (1.f - k * n1 * n1) * s;
-    C[4] = (-k * n1 * n2) * s;
-    C[5] = (1.f - k * n2 * n2) * s;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -700,8 +694,6 @@ __global__ void sg_adam_kernel(float* __restrict__ w, float* __restrict__ m, flo
 }
 
 constexpr size_t SMEM_CONV = sizeof(float) * (SG_C * SG_HPAD + SG_C * SG_TAPS * 16);
-constexpr size_t SMEM_L3 = sizeof(float) * SG_C * SG_HPAD + sizeof(float4) * SG_C * SG_TAPS;
-static_assert((SG_C * SG_HPAD) % 4 == 0, "float4 weights after the tile must stay 16-byte aligned");
 constexpr size_t SMEM_GW3 = sizeof(float) * (SG_C * SG_HPAD + 3 * 256);
 constexpr size_t SMEM_GW2 = sizeof(float) * (SG_C * SG_HPAD + SG_C * 256);
 constexpr size_t SMEM_GW1 = sizeof(float) * (4 * SG_HP + SG_C * 256);
@@ -712,8 +704,10 @@ gsicp_status sg_set_smem()
     if (done) return GSICP_OK;
     GSICP_CUDA(cudaFuncSetAttribute(sg_conv32_kernel<false, SG_EPI_GATE_F32>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
-    GSICP_CUDA(cudaFuncSetAttribute(sg_l3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_L3));
-    GSICP_CUDA(cudaFuncSetAttribute(sg_conv2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tc_smem<32>()));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tc_smem<16>()));
     GSICP_CUDA(cudaFuncSetAttribute(sg_gw3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW3));
     GSICP_CUDA(cudaFuncSetAttribute(sg_gw2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW2));
     GSICP_CUDA(cudaFuncSetAttribute(sg_gw1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GW1));
@@ -759,19 +753,22 @@ gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const in
     GSICP_CHECK(sg_ensure(sg, npix));
     const float* wk = sg->wk.as<float>();
     float4* grid = sg->grid.as<float4>();
+    if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[0], s));
     sg_grid_kernel<<<(int)((npix + 255) / 256), 256, 0, s>>>(pts, idx_img, (int)npix, grid);
     const dim3 tiles((ws + SG_T - 1) / SG_T, (hs + SG_T - 1) / SG_T);
     sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, reinterpret_cast<const float4*>(wk + WK_W1),
                                        sg->h1.as<__nv_bfloat16>());
-    {
-        const int ntc = ((ws + TC_TW - 1) / TC_TW) * ((hs + TC_TH - 1) / TC_TH);
-        const int gtc = std::max(1, std::min(ntc, 3 * device_sm_count()));
-        sg_conv2_tc_kernel<<<gtc, 128, SMEM_TC, s>>>(sg->h1.as<__nv_bfloat16>(), ws, hs, sg->wmma.as<const uint4>(),
-                                                    grid, sg->h2.as<__nv_bfloat16>(), sg->err);
-    }
-    sg_l3_kernel<<<tiles, 256, SMEM_L3, s>>>(sg->h2.as<__nv_bfloat16>(), ws, hs,
-                                             reinterpret_cast<const float4*>(wk + WK_W3), grid, idx_img, eps, p,
-                                             covs, v_out);
+    if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[1], s));
+    const int ntc = ((ws + TC_TW - 1) / TC_TW) * ((hs + TC_TH - 1) / TC_TH);
+    const int gtc = std::max(1, std::min(ntc, 3 * device_sm_count()));
+    sg_conv_tc_kernel<32><<<gtc, 128, tc_smem<32>(), s>>>(sg->h1.as<__nv_bfloat16>(), ws, hs,
+                                                          sg->wmma.as<const uint4>(), grid, sg->h2.as<__nv_bfloat16>(),
+                                                          nullptr, 0.f, 0.f, nullptr, nullptr, sg->err);
+    if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[2], s));
+    sg_conv_tc_kernel<16><<<gtc, 128, tc_smem<16>(), s>>>(sg->h2.as<__nv_bfloat16>(), ws, hs,
+                                                          sg->wmma.as<const uint4>() + tc_b_bytes<32>() / 16, grid,
+                                                          nullptr, idx_img, eps, p, covs, v_out, sg->err);
+    if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[3], s));
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }
@@ -842,7 +839,9 @@ gsicp_status gsicp_surrogate_create(const float* weights, gsicp_surrogate* out)
     if ((st = sg->w.ensure(sizeof(float) * SG_NW)) != GSICP_OK || (st = sg->m.ensure(sizeof(float) * SG_NW)) != GSICP_OK ||
         (st = sg->s.ensure(sizeof(float) * SG_NW)) != GSICP_OK || (st = sg->g.ensure(sizeof(float) * SG_NW)) != GSICP_OK ||
         (st = sg->wk.ensure(sizeof(float) * WK_TOTAL)) != GSICP_OK || (st = sg->scal.ensure(16)) != GSICP_OK ||
-        (st = sg->wmma.ensure(sizeof(__nv_bfloat16) * SG_NW2)) != GSICP_OK ||
+        (st = sg->wmma.ensure(sizeof(__nv_bfloat16) * (SG_NW2 + SG_TAPS * SG_C * 16))) != GSICP_OK ||
+        (st = (cudaMemset(sg->wmma.ptr, 0, sizeof(__nv_bfloat16) * (SG_NW2 + SG_TAPS * SG_C * 16)) == cudaSuccess
+                   ? GSICP_OK : GSICP_ERR_CUDA)) != GSICP_OK ||
         (st = (cudaMallocHost((void**)&sg->err, sizeof(unsigned)) == cudaSuccess ? GSICP_OK : GSICP_ERR_OOM)) != GSICP_OK ||
         (st = sg_upload(sg, weights, nullptr)) != GSICP_OK) {
         gsicp_surrogate_destroy(sg);
@@ -865,7 +864,27 @@ void gsicp_surrogate_destroy(gsicp_surrogate sg)
                       &sg->da2, &sg->da1, &sg->scal})
         b->release();
     if (sg->err) cudaFreeHost(sg->err);
+    for (cudaEvent_t& e : sg->ev)
+        if (e) cudaEventDestroy(e);
     delete sg;
+}
+
+gsicp_status gsicp_surrogate_set_timing(gsicp_surrogate sg, int enable)
+{
+    if (!sg) return GSICP_ERR_INVALID_ARG;
+    if (enable && !sg->ev[0])
+        for (cudaEvent_t& e : sg->ev) GSICP_CUDA(cudaEventCreate(&e));
+    sg->timing = enable != 0;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_surrogate_layer_times(gsicp_surrogate sg, double out[3])
+{
+    if (!sg || !out || !sg->ev[0]) return GSICP_ERR_INVALID_ARG;
+    float ms[3];
+    for (int i = 0; i < 3; ++i) GSICP_CUDA(cudaEventElapsedTime(&ms[i], sg->ev[i], sg->ev[i + 1]));
+    for (int i = 0; i < 3; ++i) out[i] = ms[i];
+    return GSICP_OK;
 }
 
 gsicp_status gsicp_surrogate_get_weights(gsicp_surrogate sg, float* weights)

@@ -71,6 +71,10 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     lib.gsicp_surrogate_create.argtypes = [C.c_void_p, C.c_void_p]
     assert lib.gsicp_surrogate_create(None, None) == INVALID
     lib.gsicp_surrogate_destroy(None)
+    lib.gsicp_surrogate_set_timing.argtypes = [C.c_void_p, C.c_int]
+    assert lib.gsicp_surrogate_set_timing(None, 1) == INVALID
+    lib.gsicp_surrogate_layer_times.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.gsicp_surrogate_layer_times(None, None) == INVALID
     lib.gsicp_surrogate_get_weights.argtypes = [C.c_void_p, C.c_void_p]
     assert lib.gsicp_surrogate_get_weights(None, None) == INVALID
     lib.gsicp_surrogate_set_weights.argtypes = [C.c_void_p, C.c_void_p]
