@@ -49,6 +49,13 @@ constexpr int WK_W3 = WK_W2T + SG_NW2;             // float4 [32 c][25 t]: (W3[0
 constexpr int WK_W3T = WK_W3 + 4 * SG_C * SG_TAPS; // float4 [25 t][32 c]: (W3[0..2][c][24 - t], 0)
 constexpr int WK_TOTAL = WK_W3T + 4 * SG_TAPS * SG_C;
 
+// Layer 1's weights as a kernel parameter ([tap][output][coordinate], bfloat16 values): every thread
+// reads the same weight at the same time, so they are constant-bank operands of the multiply-adds
+// rather than shared-memory loads.
+struct SgW1 {
+    float w[SG_TAPS * SG_C * 3];
+};
+
 }  // namespace gsicp
 
 struct gsicp_surrogate_s {
@@ -57,6 +64,7 @@ struct gsicp_surrogate_s {
     gsicp::DevBuf wk;              // kernel layouts (WK_TOTAL floats)
     gsicp::DevBuf wmma;            // layers 2 and 3 as tensor-core B operands (bfloat16, see sg_conv_tc_kernel)
     unsigned* err = nullptr;       // pinned, device-visible: a bounded wait of a kernel ran out
+    gsicp::SgW1 w1;                // host copy of layer 1's kernel weights (passed by value)
     bool timing = false;           // record events around the layers of every forward
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     gsicp::DevBuf grid, h1, h2, v, dv, da2, da1;  // per-pixel buffers
@@ -161,14 +169,14 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float* v
 // ---------------------------------------------------------------------------------------------
 // forward
 
-// Layer 1 (centred differences, 3 -> 32) + ReLU + bfloat16, zero at invalid pixels.
+// Layer 1 (centred differences, 3 -> 32) + ReLU + bfloat16, zero at invalid pixels.  One pixel per
+// thread, the 16 x 16 tile's 20 x 20 halo of points in shared memory; an invalid neighbour
+// contributes its difference times 0.
 __global__ void __launch_bounds__(256) sg_l1_kernel(const float4* __restrict__ grid, int w, int h,
-                                                    const float4* __restrict__ w1k, __nv_bfloat16* __restrict__ h1)
+                                                    const __grid_constant__ SgW1 W1, __nv_bfloat16* __restrict__ h1)
 {
     __shared__ float4 tile[SG_HP];
-    __shared__ float4 ws[SG_TAPS * SG_C];
     const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
-    for (int i = threadIdx.x; i < SG_TAPS * SG_C; i += blockDim.x) ws[i] = w1k[i];
     for (int q = threadIdx.x; q < SG_HP; q += blockDim.x) {
         const int yy = y0 + q / SG_HS - 2, xx = x0 + q % SG_HS - 2;
         tile[q] = (yy >= 0 && yy < h && xx >= 0 && xx < w) ? grid[(long)yy * w + xx] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -181,17 +189,14 @@ __global__ void __launch_bounds__(256) sg_l1_kernel(const float4* __restrict__ g
     float acc[SG_C];
 #pragma unroll
     for (int o = 0; o < SG_C; ++o) acc[o] = 0.f;
-    if (c.w != 0.f) {
-        for (int t = 0; t < SG_TAPS; ++t) {
-            const float4 nb = tile[halo_of(t, tx, ty)];
-            if (nb.w == 0.f) continue;
-            const float dx = nb.x - c.x, dy = nb.y - c.y, dz = nb.z - c.z;
 #pragma unroll
-            for (int o = 0; o < SG_C; ++o) {
-                const float4 wv = ws[t * SG_C + o];
-                acc[o] = fmaf(wv.x, dx, fmaf(wv.y, dy, fmaf(wv.z, dz, acc[o])));
-            }
-        }
+    for (int t = 0; t < SG_TAPS; ++t) {
+        const float4 nb = tile[halo_of(t, tx, ty)];
+        const float dx = (nb.x - c.x) * nb.w, dy = (nb.y - c.y) * nb.w, dz = (nb.z - c.z) * nb.w;
+#pragma unroll
+        for (int o = 0; o < SG_C; ++o)
+            acc[o] = fmaf(W1.w[(t * SG_C + o) * 3], dx,
+                          fmaf(W1.w[(t * SG_C + o) * 3 + 1], dy, fmaf(W1.w[(t * SG_C + o) * 3 + 2], dz, acc[o])));
     }
 #pragma unroll
     for (int o = 0; o < SG_C; ++o) acc[o] = c.w != 0.f ? fmaxf(acc[o], 0.f) : 0.f;
@@ -756,8 +761,7 @@ gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const in
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[0], s));
     sg_grid_kernel<<<(int)((npix + 255) / 256), 256, 0, s>>>(pts, idx_img, (int)npix, grid);
     const dim3 tiles((ws + SG_T - 1) / SG_T, (hs + SG_T - 1) / SG_T);
-    sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, reinterpret_cast<const float4*>(wk + WK_W1),
-                                       sg->h1.as<__nv_bfloat16>());
+    sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, sg->w1, sg->h1.as<__nv_bfloat16>());
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[1], s));
     const int ntc = ((ws + TC_TW - 1) / TC_TW) * ((hs + TC_TH - 1) / TC_TH);
     const int gtc = std::max(1, std::min(ntc, 3 * device_sm_count()));
@@ -806,6 +810,20 @@ gsicp_status sg_backward(gsicp_surrogate_s* sg, const int* idx_img, const float*
     return GSICP_OK;
 }
 
+// Refresh the host copy of layer 1's kernel weights from the device layout (synchronises s).
+gsicp_status sg_fetch_w1(gsicp_surrogate_s* sg, cudaStream_t s)
+{
+    float4 tmp[SG_TAPS * SG_C];
+    GSICP_CUDA(cudaMemcpyAsync(tmp, sg->wk.as<float>() + WK_W1, sizeof(tmp), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < SG_TAPS * SG_C; ++i) {
+        sg->w1.w[3 * i] = tmp[i].x;
+        sg->w1.w[3 * i + 1] = tmp[i].y;
+        sg->w1.w[3 * i + 2] = tmp[i].z;
+    }
+    return GSICP_OK;
+}
+
 gsicp_status sg_upload(gsicp_surrogate_s* sg, const float* w_host, cudaStream_t s)
 {
     GSICP_CUDA(cudaMemcpyAsync(sg->w.ptr, w_host, sizeof(float) * SG_NW, cudaMemcpyHostToDevice, s));
@@ -814,6 +832,7 @@ gsicp_status sg_upload(gsicp_surrogate_s* sg, const float* w_host, cudaStream_t 
     sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>(),
                                                          sg->wmma.as<__nv_bfloat16>());
     GSICP_CUDA(cudaGetLastError());
+    GSICP_CHECK(sg_fetch_w1(sg, s));
     sg->steps = 0;
     return GSICP_OK;
 }
@@ -995,6 +1014,7 @@ gsicp_status gsicp_surrogate_train_step(gsicp_ctx ctx, gsicp_surrogate sg, const
         sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>(),
                                                              sg->wmma.as<__nv_bfloat16>());
         GSICP_CUDA(cudaGetLastError());
+        GSICP_CHECK(sg_fetch_w1(sg, s));
         sg->steps = t;
     }
     return GSICP_OK;

@@ -4,8 +4,8 @@ small convolutional network; gsicp_surrogate_* in the C ABI).
 Training (``python -m paper_2403_12550_b300.surrogate train``): the config-5 training frames
 (synthetic config-2-style rooms, seeded, ray-cast in worker processes), each frame's own k-NN
 plane covariances from the plain GPU path as targets, one Adam step per frame
-(gsicp_surrogate_train_step), 10 epochs in a seeded shuffled order, the learning rate 2e-3
-decaying by 0.75 per epoch.  The trained weights are
+(gsicp_surrogate_train_step), 20 epochs in a seeded shuffled order, the learning rate 2e-3
+decaying by 0.85 per epoch.  The trained weights are
 written to ``data/cov_surrogate.npy`` beside this file, which :func:`load_weights` reads.
 
 Evaluation (``... evaluate``): the held-out config-5 sequence (640 x 480 frames of a room none of
@@ -90,8 +90,8 @@ def render_sequence(seed: int, n_frames: int, workers: int) -> np.ndarray:
 
 # ----------------------------------------------------------------------------- training
 
-def train(seed: int = 0, n_frames: int = 2000, n_scenes: int = 20, epochs: int = 10, lr: float = 2e-3,
-          decay: float = 0.75, workers: int | None = None, out: str = WEIGHTS_PATH, log=print, frames=None) -> dict:
+def train(seed: int = 0, n_frames: int = 2000, n_scenes: int = 20, epochs: int = 20, lr: float = 2e-3,
+          decay: float = 0.85, workers: int | None = None, out: str = WEIGHTS_PATH, log=print, frames=None) -> dict:
     import torch
     import paper_2403_12550_b300 as g
     from synth import HALF_TUM_INTR
@@ -198,7 +198,7 @@ def main(argv=None):
     ap.add_argument("cmd", choices=("train", "evaluate"))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--frames", type=int, default=None)
-    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=WEIGHTS_PATH)
     ap.add_argument("--weights", default=None)
