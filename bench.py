@@ -67,9 +67,13 @@ def parse():
                     help="frame: the tracking step (default); batch: batched registration of independent pairs; "
                          "sequence: the tracking loop with keyframes over a TUM-shaped sequence (latency p50/p99); "
                          "surrogate: the tracking loop with learned covariances on their held-out sequence")
-    ap.add_argument("--frames", type=int, default=300)
+    ap.add_argument("--frames", type=int, default=None,
+                    help="sequence length (default 300 for sequence, 500 for surrogate)")
     ap.add_argument("--pairs", type=int, default=64)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.frames is None:
+        args.frames = 500 if args.workload == "surrogate" else 300
+    return args
 
 
 def load_peaks():

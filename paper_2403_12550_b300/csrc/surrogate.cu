@@ -21,7 +21,9 @@
 // pixel; gradients float).  Every kernel works on 16 x 16 output tiles with a 2-pixel halo staged
 // in shared memory, channel-major ([c][20 * 20 + 1]) so that lanes that differ in pixel or in
 // channel hit distinct banks; weights are staged in shared memory and read as broadcasts.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -30,6 +32,8 @@
 #include "internal.h"
 
 namespace gsicp {
+
+gsicp_status set_error(gsicp_status st, const char* msg);
 
 constexpr int SG_T = 16;               // output tile side
 constexpr int SG_HS = SG_T + 4;        // halo tile side
@@ -293,25 +297,33 @@ __device__ __forceinline__ void plane_cov_from_v(float v0, float v1, float v2, f
 // tiles of 8 x 16 pixels = the 128 rows of one MMA (M = 128, K = 16 per instruction, bfloat16
 // operands, float accumulator in tensor memory; N = 32 output channels for layer 2, 16 for layer
 // 3, whose 3 outputs are padded with zero weights).  The 32-channel input's halo of the tile (12 x
-// 20 pixels) is staged once in shared memory as four 8-channel planes [group][halo row][halo
-// column][16 B], which is the canonical K-major layout without swizzle: a core matrix (8 rows x
-// 16 B) is one output row's 8 pixels, shifted by the tap, so the A operand of every tap is the same
-// staged tile seen through a descriptor with its own start address (row stride SBO = one halo row,
-// K stride LBO = one channel plane).  The weights (B, [tap][group][output][8 channels]) are staged
-// once per CTA.  25 taps x 2 channel halves = 50 MMAs per tile, issued by one thread and committed
-// to an mbarrier; the epilogue reads the accumulator (warp w: rows 32w..32w+31) with tcgen05.ld.
-// Layer 2's epilogue applies ReLU, the validity mask and bfloat16 rounding and writes h2; layer 3's
-// writes v and the point's plane covariance.  Every wait is bounded: when one runs out the CTA
-// records it in err, stops taking tiles, frees its tensor memory and returns.
+// 20 pixels) is brought into shared memory by the tensor-memory-access unit as four 8-channel
+// boxes (one 3-D tiled copy each: 8 channels x 12 columns x 20 rows, zero outside the image) that
+// land as [group][halo row][halo column][16 B]: the canonical K-major layout without swizzle, in
+// which a core matrix (8 rows x 16 B) is one output row's 8 pixels shifted by the tap, so the A
+// operand of every tap is the same staged tile seen through a descriptor with its own start address
+// (row stride SBO = one halo row, K stride LBO = one channel plane).  The weights (B,
+// [tap][group][output][8 channels]) arrive once per CTA by one bulk copy.  Two tile buffers: the
+// copy of the next tile is issued right after the current tile's 50 MMAs (25 taps x 2 channel
+// halves), so it runs under the MMAs and the epilogue.  One thread issues copies and MMAs; the
+// MMAs are committed to an mbarrier; the epilogue reads the accumulator (warp w: rows
+// 32w..32w+31) with tcgen05.ld.  Layer 2's epilogue applies ReLU, the validity mask and bfloat16
+// rounding and writes h2; layer 3's writes v and the point's plane covariance.  Every wait is
+// bounded: when one runs out the CTA records it in err, waits (bounded) for its copies in flight,
+// frees its tensor memory and returns.
 constexpr int TC_TW = 8, TC_TH = 16;                  // output tile (128 pixels)
 constexpr int TC_HW = TC_TW + 4, TC_HH = TC_TH + 4;   // halo tile 12 x 20
-constexpr int TC_PLANE = TC_HW * TC_HH * 16;          // one 8-channel plane of the halo: 3840 B
-constexpr int TC_A_BYTES = 4 * TC_PLANE;              // 15360 B
-constexpr int TC_PAD = 4096;  // slack after B: every descriptor's reach stays inside the allocation
+constexpr int TC_PLANE = TC_HW * TC_HH * 16;          // one 8-channel plane of the halo: 3840 B (30 x 128)
+constexpr int TC_A_BYTES = 4 * TC_PLANE;              // 15360 B per tile buffer
 template <int kN>
 constexpr int tc_b_bytes() { return SG_TAPS * 4 * kN * 16; }
+// slack after B, so that every descriptor's reach, read with LBO and SBO either way round, stays
+// inside the allocation (at most 23872 + 15 x 3840 + 319 = 81791 bytes from the base)
 template <int kN>
-constexpr size_t tc_smem() { return TC_A_BYTES + tc_b_bytes<kN>() + TC_PAD; }
+constexpr int tc_pad() { return kN == 16 ? 28672 : 4096; }
+template <int kN>
+constexpr size_t tc_smem() { return 2 * TC_A_BYTES + tc_b_bytes<kN>() + tc_pad<kN>(); }
+static_assert(2 * TC_A_BYTES + 25600 + 28672 > 81791 && 2 * TC_A_BYTES + 51200 + 4096 > 81791, "descriptor slack");
 constexpr unsigned TC_SPIN_LIMIT = 1u << 22;
 // instruction descriptor, kind::f16: D float (bit 4), A and B bfloat16 (bits 7, 10), both K-major,
 // N / 8 at bit 17, M / 16 at bit 24
@@ -322,15 +334,45 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 
 // Shared-memory matrix descriptor, canonical layout without swizzle: start address, the byte
 // distance between core matrices along K (lbo) and along M or N (sbo), all in 16-byte units;
-// descriptor version 1 (bit 46).
+// descriptor version 1 (bit 46).  Shared-memory addresses are below 2^18, so start addresses fit
+// the 14-bit field and adding a 16-byte-unit offset to a descriptor moves only its start address.
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
 }
 
+// Bounded wait for the completion of the mbarrier phase with this parity; true if it completed.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok = 0;
+    for (unsigned it = 0; it < TC_SPIN_LIMIT && !ok; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tc_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// The four 8-channel boxes of the halo of the tile at (x0, y0) into tile buffer dst.
+__device__ __forceinline__ void tc_load_tile(const CUtensorMap* tmap, uint32_t dst, int x0, int y0, uint32_t bar)
+{
+    tc_expect(bar, TC_A_BYTES);
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                     "[%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(dst + g * TC_PLANE), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(8 * g), "r"(x0 - 2),
+                       "r"(y0 - 2), "r"(bar)
+                     : "memory");
+}
+
 template <int kN>
-__global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __nv_bfloat16* __restrict__ in, int w, int h,
+__global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, int w, int h,
                                                          const uint4* __restrict__ wb,
                                                          const float4* __restrict__ grid,
                                                          __nv_bfloat16* __restrict__ h2, const int* __restrict__ idx_img,
@@ -339,114 +381,137 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __nv_bfloat16* __
 {
     static_assert(kN == 32 || kN == 16, "layer 2 (N = 32) or layer 3 (N = 16)");
     extern __shared__ __align__(1024) uint8_t tc_smem_[];
-    uint8_t* sA = tc_smem_;
-    uint8_t* sB = tc_smem_ + TC_A_BYTES;
-    __shared__ __align__(8) uint64_t bar;
+    uint8_t* sB = tc_smem_ + 2 * TC_A_BYTES;
+    __shared__ __align__(8) uint64_t bars[4];  // B copy, tile buffer 0, tile buffer 1, MMA done
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (w + TC_TW - 1) / TC_TW, tiles_y = (h + TC_TH - 1) / TC_TH;
     const int ntiles = tiles_x * tiles_y;
-    for (int i = tid; i < tc_b_bytes<kN>() / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = wb[i];
+    const uint32_t a0 = smem_u32(tc_smem_), b0 = smem_u32(sB);
+    const uint32_t bar_b = smem_u32(&bars[0]), bar_m = smem_u32(&bars[3]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        // the weights: one bulk copy; the first tile: four box copies
+        tc_expect(bar_b, tc_b_bytes<kN>());
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(b0), "l"(reinterpret_cast<uint64_t>(wb)), "r"(tc_b_bytes<kN>()), "r"(bar_b)
+                     : "memory");
+        if ((int)blockIdx.x < ntiles)
+            tc_load_tile(&tmap, a0, (blockIdx.x % tiles_x) * TC_TW, (blockIdx.x / tiles_x) * TC_TH,
+                         smem_u32(&bars[1]));
     }
-    asm volatile("fence.proxy.async.shared::cta;");  // the weights, for the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB), barp = smem_u32(&bar);
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % tiles_x) * TC_TW, y0 = (tile / tiles_x) * TC_TH;
-        for (int q = tid; q < 4 * TC_HW * TC_HH; q += 128) {
-            const int g = q / (TC_HW * TC_HH), r = q % (TC_HW * TC_HH);
-            const int y = y0 + r / TC_HW - 2, x = x0 + r % TC_HW - 2;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (y >= 0 && y < h && x >= 0 && x < w) v = reinterpret_cast<const uint4*>(in)[((long)y * w + x) * 4 + g];
-            reinterpret_cast<uint4*>(sA)[q] = v;  // byte 16 q = g * TC_PLANE + 16 (row * TC_HW + col)
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (tid == 0) {
+    bool failed = false, prefetched = false;
+    uint32_t pending_bar = 0, pending_parity = 0;
+    if (tid == 0) failed = !tc_wait(bar_b, 0);
+    int k = 0;
+    if (!__syncthreads_or(failed)) {
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+            const int buf = k & 1;
+            const int x0 = (tile % tiles_x) * TC_TW, y0 = (tile / tiles_x) * TC_TH;
+            const uint32_t abuf = a0 + buf * TC_A_BYTES;
+            bool bad = false;
+            if (tid == 0) {
+                bad = !tc_wait(smem_u32(&bars[1 + buf]), (k >> 1) & 1);
+                prefetched = false;
+                if (!bad) {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    // the 50 descriptors differ only in their start address (the low 14 bits, in
+                    // 16-byte units, which no offset here carries out of): base + constant
+                    const uint64_t da0 = tc_desc(abuf, TC_PLANE, TC_HW * 16), db0 = tc_desc(b0, kN * 16, 128);
+#pragma unroll
+                    for (int t = 0; t < SG_TAPS; ++t) {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const uint64_t da = da0 + (uint64_t)((2 * j * TC_PLANE + ((t / 5) * TC_HW + t % 5) * 16) >> 4);
+                            const uint64_t db = db0 + (uint64_t)(((t * 4 + 2 * j) * (kN * 16)) >> 4);
+                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                         ::"r"(tmem), "l"(da), "l"(db), "r"(tc_idesc<kN>()), "r"((t | j) != 0 ? 1u : 0u));
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(bar_m) : "memory");
+                    // the next tile's copy into the other buffer (its last reader, the previous
+                    // tile's MMAs, has completed)
+                    const int next = tile + gridDim.x;
+                    if (next < ntiles) {
+                        pending_bar = smem_u32(&bars[1 + (buf ^ 1)]);
+                        pending_parity = ((k + 1) >> 1) & 1;
+                        tc_load_tile(&tmap, a0 + (buf ^ 1) * TC_A_BYTES, (next % tiles_x) * TC_TW,
+                                     (next / tiles_x) * TC_TH, pending_bar);
+                        prefetched = true;
+                    }
+                }
+            }
+            if (__syncthreads_or(bad)) {
+                failed = true;
+                break;
+            }
+            if (__syncthreads_or(!tc_wait(bar_m, k & 1))) {
+                failed = true;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll 1
-            for (int t = 0; t < SG_TAPS; ++t) {
-                const uint32_t shift = (uint32_t)(((t / 5) * TC_HW + t % 5) * 16);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
+            const bool inside = x < w && y < h;
+            const long pix = (long)y * w + x;
+            if (kN == 32) {
+                uint32_t r[32];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                             "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                               "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                               "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                               "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                               "=r"(r[31])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (inside) {
+                    const bool valid = grid[pix].w != 0.f;
+                    float v[32];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const uint64_t da = tc_desc(a0 + 2 * j * TC_PLANE + shift, TC_PLANE, TC_HW * 16);
-                    const uint64_t db = tc_desc(b0 + (t * 4 + 2 * j) * (kN * 16), kN * 16, 128);
-                    const uint32_t accumulate = (t | j) != 0;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                 ::"r"(tmem), "l"(da), "l"(db), "r"(tc_idesc<kN>()), "r"(accumulate));
+                    for (int q = 0; q < 32; ++q) v[q] = valid ? fmaxf(__uint_as_float(r[q]), 0.f) : 0.f;
+                    store_bf16x16(h2 + pix * SG_C, v);
+                    store_bf16x16(h2 + pix * SG_C + 16, v + 16);
+                }
+            } else {
+                uint32_t r[4];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (inside) {
+                    const float4 g = grid[pix];
+                    const bool valid = g.w != 0.f;
+                    const float v0 = valid ? __uint_as_float(r[0]) : 0.f, v1 = valid ? __uint_as_float(r[1]) : 0.f,
+                                v2 = valid ? __uint_as_float(r[2]) : 0.f;
+                    if (v_out) {
+                        v_out[3 * pix] = v0;
+                        v_out[3 * pix + 1] = v1;
+                        v_out[3 * pix + 2] = v2;
+                    }
+                    const int id = valid && covs ? idx_img[pix] : -1;
+                    if (id >= 0) plane_cov_from_v(v0, v1, v2, g.z, eps, p, covs + 6l * id);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barp));
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();  // accumulator read before the next tile's MMAs overwrite it
         }
-        uint32_t ok = 0;
-        for (unsigned it = 0; it < TC_SPIN_LIMIT && !ok; ++it)
-            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                         "selp.u32 %0, 1, 0, p;\n}\n"
-                         : "=r"(ok) : "r"(barp), "r"(phase));
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) *reinterpret_cast<volatile unsigned*>(err) = 1u;  // pinned host word
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
-        const bool inside = x < w && y < h;
-        const long pix = (long)y * w + x;
-        if (kN == 32) {
-            uint32_t r[32];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-                           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-                           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (inside) {
-                const bool valid = grid[pix].w != 0.f;
-                float v[32];
-#pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = valid ? fmaxf(__uint_as_float(r[k]), 0.f) : 0.f;
-                store_bf16x16(h2 + pix * SG_C, v);
-                store_bf16x16(h2 + pix * SG_C + 16, v + 16);
-            }
-        } else {
-            uint32_t r[4];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (inside) {
-                const float4 g = grid[pix];
-                const bool valid = g.w != 0.f;
-                const float v0 = valid ? __uint_as_float(r[0]) : 0.f, v1 = valid ? __uint_as_float(r[1]) : 0.f,
-                            v2 = valid ? __uint_as_float(r[2]) : 0.f;
-                if (v_out) {
-                    v_out[3 * pix] = v0;
-                    v_out[3 * pix + 1] = v1;
-                    v_out[3 * pix + 2] = v2;
-                }
-                const int id = valid && covs ? idx_img[pix] : -1;
-                if (id >= 0) plane_cov_from_v(v0, v1, v2, g.z, eps, p, covs + 6l * id);
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();  // accumulator read and staged tile used before the next tile overwrites them
+    }
+    if (failed && tid == 0) {
+        *reinterpret_cast<volatile unsigned*>(err) = 1u;  // pinned host word
+        if (prefetched) tc_wait(pending_bar, pending_parity);  // no copy may land after the CTA is gone
     }
     __syncthreads();
     if (warp == 0) {
@@ -735,11 +800,32 @@ gsicp_status sg_ensure(gsicp_surrogate_s* sg, int64_t npix)
     return GSICP_OK;
 }
 
+// Tensor map of a channels-last 32-channel bfloat16 activation (w x h pixels): boxes of 8 channels
+// x 12 columns x 20 rows (a tile's halo, one channel group), no swizzle, zero fill outside.
+gsicp_status act_tensor_map(CUtensorMap* m, void* base, int w, int h)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        GSICP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return set_error(GSICP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)SG_C, (cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[2] = {(cuuint64_t)SG_C * 2, (cuuint64_t)SG_C * 2 * (cuuint64_t)w};
+    const cuuint32_t box[3] = {8, (cuuint32_t)TC_HW, (cuuint32_t)TC_HH};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(GSICP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return GSICP_OK;
+}
+
 }  // namespace
 
 // Grid + layers 1-3 over the frame's a1 output (pts in a1 order, idx_img the sample -> point map).
-gsicp_status set_error(gsicp_status st, const char* msg);
-
 gsicp_status surrogate_status(gsicp_surrogate_s* sg)
 {
     if (sg && sg->err && *reinterpret_cast<volatile unsigned*>(sg->err)) {
@@ -764,14 +850,16 @@ gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const in
     sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, sg->w1, sg->h1.as<__nv_bfloat16>());
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[1], s));
     const int ntc = ((ws + TC_TW - 1) / TC_TW) * ((hs + TC_TH - 1) / TC_TH);
-    const int gtc = std::max(1, std::min(ntc, 3 * device_sm_count()));
-    sg_conv_tc_kernel<32><<<gtc, 128, tc_smem<32>(), s>>>(sg->h1.as<__nv_bfloat16>(), ws, hs,
-                                                          sg->wmma.as<const uint4>(), grid, sg->h2.as<__nv_bfloat16>(),
-                                                          nullptr, 0.f, 0.f, nullptr, nullptr, sg->err);
+    const int gtc = std::max(1, std::min(ntc, 2 * device_sm_count()));
+    CUtensorMap m1, m2;
+    GSICP_CHECK(act_tensor_map(&m1, sg->h1.ptr, ws, hs));
+    GSICP_CHECK(act_tensor_map(&m2, sg->h2.ptr, ws, hs));
+    sg_conv_tc_kernel<32><<<gtc, 128, tc_smem<32>(), s>>>(m1, ws, hs, sg->wmma.as<const uint4>(), grid,
+                                                          sg->h2.as<__nv_bfloat16>(), nullptr, 0.f, 0.f, nullptr,
+                                                          nullptr, sg->err);
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[2], s));
-    sg_conv_tc_kernel<16><<<gtc, 128, tc_smem<16>(), s>>>(sg->h2.as<__nv_bfloat16>(), ws, hs,
-                                                          sg->wmma.as<const uint4>() + tc_b_bytes<32>() / 16, grid,
-                                                          nullptr, idx_img, eps, p, covs, v_out, sg->err);
+    sg_conv_tc_kernel<16><<<gtc, 128, tc_smem<16>(), s>>>(m2, ws, hs, sg->wmma.as<const uint4>() + tc_b_bytes<32>() / 16,
+                                                          grid, nullptr, idx_img, eps, p, covs, v_out, sg->err);
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[3], s));
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;

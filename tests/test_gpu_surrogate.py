@@ -59,9 +59,13 @@ def _weights(seed, scale=1.0):
     return (sgo.init_weights(seed) * scale).astype(np.float32)
 
 
-@pytest.mark.parametrize("shape,stride", [((90, 121), 1), ((240, 320), 2), ((37, 50), 1)])
+@pytest.mark.parametrize("shape,stride", [((90, 121), 1), ((240, 320), 2), ((37, 50), 1), ("full", 2)])
 def test_forward_matches_oracle(g, ctx, shape, stride):
-    d, intr = _frame(1, crop=shape)
+    if shape == "full":  # the benchmark's frame: 640 x 480 at stride 2 (a 320 x 240 grid, 600 tiles)
+        from synth import TUM_INTR, sequence_config5
+        d, intr = sequence_config5(0, n_frames=3)["depth"](1), TUM_INTR.as_array()
+    else:
+        d, intr = _frame(1, crop=shape)
     w = _weights(3)
     sg = g.Surrogate(w)
     cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
