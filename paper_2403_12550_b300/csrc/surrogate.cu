@@ -53,13 +53,6 @@ constexpr int WK_W3 = WK_W2T + SG_NW2;             // float4 [32 c][25 t]: (W3[0
 constexpr int WK_W3T = WK_W3 + 4 * SG_C * SG_TAPS; // float4 [25 t][32 c]: (W3[0..2][c][24 - t], 0)
 constexpr int WK_TOTAL = WK_W3T + 4 * SG_TAPS * SG_C;
 
-// Layer 1's weights as a kernel parameter ([tap][output][coordinate], bfloat16 values): every thread
-// reads the same weight at the same time, so they are constant-bank operands of the multiply-adds
-// rather than shared-memory loads.
-struct SgW1 {
-    float w[SG_TAPS * SG_C * 3];
-};
-
 }  // namespace gsicp
 
 struct gsicp_surrogate_s {
@@ -68,7 +61,6 @@ struct gsicp_surrogate_s {
     gsicp::DevBuf wk;              // kernel layouts (WK_TOTAL floats)
     gsicp::DevBuf wmma;            // layers 2 and 3 as tensor-core B operands (bfloat16, see sg_conv_tc_kernel)
     unsigned* err = nullptr;       // pinned, device-visible: a bounded wait of a kernel ran out
-    gsicp::SgW1 w1;                // host copy of layer 1's kernel weights (passed by value)
     bool timing = false;           // record events around the layers of every forward
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     gsicp::DevBuf grid, h1, h2, v, dv, da2, da1;  // per-pixel buffers
@@ -173,40 +165,59 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float* v
 // ---------------------------------------------------------------------------------------------
 // forward
 
-// Layer 1 (centred differences, 3 -> 32) + ReLU + bfloat16, zero at invalid pixels.  One pixel per
-// thread, the 16 x 16 tile's 20 x 20 halo of points in shared memory; an invalid neighbour
-// contributes its difference times 0.
-__global__ void __launch_bounds__(256) sg_l1_kernel(const float4* __restrict__ grid, int w, int h,
-                                                    const __grid_constant__ SgW1 W1, __nv_bfloat16* __restrict__ h1)
+// Layer 1 (centred differences, 3 -> 32) + ReLU + bfloat16, zero at invalid pixels.  The 16 x 16
+// tile's 20 x 20 halo of points and the weights sit in shared memory; each thread computes two
+// vertically adjacent pixels, so every weight read (a broadcast) feeds both; an invalid neighbour
+// contributes its difference times 0.  The tap loop stays rolled: unrolled, the 4800 multiply-adds
+// overflow the instruction cache.
+constexpr int SG_L1_THREADS = SG_T * SG_T / 2;
+
+__global__ void __launch_bounds__(SG_L1_THREADS) sg_l1_kernel(const float4* __restrict__ grid, int w, int h,
+                                                              const float4* __restrict__ w1k,
+                                                              __nv_bfloat16* __restrict__ h1)
 {
     __shared__ float4 tile[SG_HP];
+    __shared__ float4 ws[SG_TAPS * SG_C];
     const int x0 = blockIdx.x * SG_T, y0 = blockIdx.y * SG_T;
+    for (int i = threadIdx.x; i < SG_TAPS * SG_C; i += blockDim.x) ws[i] = w1k[i];
     for (int q = threadIdx.x; q < SG_HP; q += blockDim.x) {
         const int yy = y0 + q / SG_HS - 2, xx = x0 + q % SG_HS - 2;
         tile[q] = (yy >= 0 && yy < h && xx >= 0 && xx < w) ? grid[(long)yy * w + xx] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
+    const int tx = threadIdx.x % SG_T, ty = 2 * (threadIdx.x / SG_T);  // pixels (tx, ty) and (tx, ty + 1)
     const int x = x0 + tx, y = y0 + ty;
     if (x >= w || y >= h) return;
-    const float4 c = tile[(ty + 2) * SG_HS + tx + 2];
-    float acc[SG_C];
+    const float4 c0 = tile[(ty + 2) * SG_HS + tx + 2], c1 = tile[(ty + 3) * SG_HS + tx + 2];
+    float a0[SG_C], a1[SG_C];
 #pragma unroll
-    for (int o = 0; o < SG_C; ++o) acc[o] = 0.f;
-#pragma unroll
+    for (int o = 0; o < SG_C; ++o) a0[o] = a1[o] = 0.f;
+#pragma unroll 1
     for (int t = 0; t < SG_TAPS; ++t) {
-        const float4 nb = tile[halo_of(t, tx, ty)];
-        const float dx = (nb.x - c.x) * nb.w, dy = (nb.y - c.y) * nb.w, dz = (nb.z - c.z) * nb.w;
+        const float4 n0 = tile[halo_of(t, tx, ty)], n1 = tile[halo_of(t, tx, ty + 1)];
+        const float dx0 = (n0.x - c0.x) * n0.w, dy0 = (n0.y - c0.y) * n0.w, dz0 = (n0.z - c0.z) * n0.w;
+        const float dx1 = (n1.x - c1.x) * n1.w, dy1 = (n1.y - c1.y) * n1.w, dz1 = (n1.z - c1.z) * n1.w;
+        const float4* wt = ws + t * SG_C;
 #pragma unroll
-        for (int o = 0; o < SG_C; ++o)
-            acc[o] = fmaf(W1.w[(t * SG_C + o) * 3], dx,
-                          fmaf(W1.w[(t * SG_C + o) * 3 + 1], dy, fmaf(W1.w[(t * SG_C + o) * 3 + 2], dz, acc[o])));
+        for (int o = 0; o < SG_C; ++o) {
+            const float4 wv = wt[o];
+            a0[o] = fmaf(wv.x, dx0, fmaf(wv.y, dy0, fmaf(wv.z, dz0, a0[o])));
+            a1[o] = fmaf(wv.x, dx1, fmaf(wv.y, dy1, fmaf(wv.z, dz1, a1[o])));
+        }
     }
 #pragma unroll
-    for (int o = 0; o < SG_C; ++o) acc[o] = c.w != 0.f ? fmaxf(acc[o], 0.f) : 0.f;
+    for (int o = 0; o < SG_C; ++o) {
+        a0[o] = c0.w != 0.f ? fmaxf(a0[o], 0.f) : 0.f;
+        a1[o] = c1.w != 0.f ? fmaxf(a1[o], 0.f) : 0.f;
+    }
     __nv_bfloat16* dst = h1 + ((long)y * w + x) * SG_C;
-    store_bf16x16(dst, acc);
-    store_bf16x16(dst + 16, acc + 16);
+    store_bf16x16(dst, a0);
+    store_bf16x16(dst + 16, a0 + 16);
+    if (y + 1 < h) {
+        dst += (long)w * SG_C;
+        store_bf16x16(dst, a1);
+        store_bf16x16(dst + 16, a1 + 16);
+    }
 }
 
 enum { SG_EPI_RELU_BF16 = 0, SG_EPI_GATE_F32 = 1 };
@@ -847,7 +858,8 @@ gsicp_status surrogate_forward(gsicp_surrogate_s* sg, const float* pts, const in
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[0], s));
     sg_grid_kernel<<<(int)((npix + 255) / 256), 256, 0, s>>>(pts, idx_img, (int)npix, grid);
     const dim3 tiles((ws + SG_T - 1) / SG_T, (hs + SG_T - 1) / SG_T);
-    sg_l1_kernel<<<tiles, 256, 0, s>>>(grid, ws, hs, sg->w1, sg->h1.as<__nv_bfloat16>());
+    sg_l1_kernel<<<tiles, SG_L1_THREADS, 0, s>>>(grid, ws, hs, reinterpret_cast<const float4*>(wk + WK_W1),
+                                                 sg->h1.as<__nv_bfloat16>());
     if (sg->timing) GSICP_CUDA(cudaEventRecord(sg->ev[1], s));
     const int ntc = ((ws + TC_TW - 1) / TC_TW) * ((hs + TC_TH - 1) / TC_TH);
     const int gtc = std::max(1, std::min(ntc, 2 * device_sm_count()));
@@ -898,20 +910,6 @@ gsicp_status sg_backward(gsicp_surrogate_s* sg, const int* idx_img, const float*
     return GSICP_OK;
 }
 
-// Refresh the host copy of layer 1's kernel weights from the device layout (synchronises s).
-gsicp_status sg_fetch_w1(gsicp_surrogate_s* sg, cudaStream_t s)
-{
-    float4 tmp[SG_TAPS * SG_C];
-    GSICP_CUDA(cudaMemcpyAsync(tmp, sg->wk.as<float>() + WK_W1, sizeof(tmp), cudaMemcpyDeviceToHost, s));
-    GSICP_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < SG_TAPS * SG_C; ++i) {
-        sg->w1.w[3 * i] = tmp[i].x;
-        sg->w1.w[3 * i + 1] = tmp[i].y;
-        sg->w1.w[3 * i + 2] = tmp[i].z;
-    }
-    return GSICP_OK;
-}
-
 gsicp_status sg_upload(gsicp_surrogate_s* sg, const float* w_host, cudaStream_t s)
 {
     GSICP_CUDA(cudaMemcpyAsync(sg->w.ptr, w_host, sizeof(float) * SG_NW, cudaMemcpyHostToDevice, s));
@@ -920,7 +918,6 @@ gsicp_status sg_upload(gsicp_surrogate_s* sg, const float* w_host, cudaStream_t 
     sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>(),
                                                          sg->wmma.as<__nv_bfloat16>());
     GSICP_CUDA(cudaGetLastError());
-    GSICP_CHECK(sg_fetch_w1(sg, s));
     sg->steps = 0;
     return GSICP_OK;
 }
@@ -1102,7 +1099,6 @@ gsicp_status gsicp_surrogate_train_step(gsicp_ctx ctx, gsicp_surrogate sg, const
         sg_layout_kernel<<<(SG_NW + 255) / 256, 256, 0, s>>>(sg->w.as<float>(), sg->wk.as<float>(),
                                                              sg->wmma.as<__nv_bfloat16>());
         GSICP_CUDA(cudaGetLastError());
-        GSICP_CHECK(sg_fetch_w1(sg, s));
         sg->steps = t;
     }
     return GSICP_OK;
