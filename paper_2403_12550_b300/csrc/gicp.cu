@@ -7,7 +7,8 @@
 // minimised by Gauss-Newton with left perturbations T <- exp(xi^) T,
 // xi = (omega, v): J_i = dd_i/dxi = [[y_i]x, -I] with y_i = R x_i + t.
 //
-// One kernel launch per iteration.  One thread per source point, points in
+// One kernel launch per iteration (chained by programmatic dependent launch, four per pass of a
+// conditional-while CUDA graph).  One thread per source point, points in
 // the source index's Morton order: transform, exact nearest map mean, then the
 // residual, weight, J^T W J (21 unique), J^T W d (6), d^T W d and the inlier
 // count -> warp shuffles -> one FP32 partial per block.  The last block to
@@ -35,6 +36,7 @@
 namespace gsicp {
 
 constexpr int REG_THREADS = 256;
+constexpr int GN_BODY_ITERS = 4;  // iteration launches per pass of the conditional-while graph
 
 // Exact nearest point of `ix` to q with (d2, original index) lexicographically
 // smallest among points with d2 <= the incoming (best_d2, best_oi): an 8-wide walk (a third of the
@@ -751,6 +753,9 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
 __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob* __restrict__ jp,
                                                                 cudaGraphConditionalHandle cond)
 {
+    // launched as a programmatic dependent of the previous iteration (plain-launch mode): wait for
+    // it to complete (a no-op otherwise) before reading the pose and status it wrote
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const RegJob& J = *jp;
     RegState* st = J.st;
     if (st->status != REG_ST_RUNNING) {
@@ -787,6 +792,9 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
     const int block_refreshed = block_partial(acc, refreshed, J.partials + 32l * blockIdx.x);
+    // this block's share is written: the next iteration's launch may begin (its blocks wait in
+    // griddepcontrol.wait until this grid, the last block's solve included, has completed)
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ bool am_last;
     if (threadIdx.x == 0) {
         if (block_refreshed > 0 && it_now < REG_STATS) atomicAdd(&st->refreshes[it_now], block_refreshed);
@@ -982,6 +990,10 @@ gsicp_status RegMachine::init(int capacity)
     cp.conditional.size = 1;
     cudaGraphNode_t cnode;
     GSICP_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+    // The loop body: GN_BODY_ITERS iteration launches in a chain of programmatic edges, so that each
+    // launch begins (and its blocks wait in griddepcontrol.wait) while the one before finishes its
+    // solve, and the condition is re-evaluated once per GN_BODY_ITERS iterations (launches after
+    // convergence exit at once).
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     const RegJob* jptr = job.as<const RegJob>();
     void* args[] = {(void*)&jptr, (void*)&cond};
@@ -991,8 +1003,17 @@ gsicp_status RegMachine::init(int capacity)
     kp.blockDim = dim3(REG_THREADS);
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
-    cudaGraphNode_t knode;
-    GSICP_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
+    cudaGraphNode_t knode[GN_BODY_ITERS];
+    for (int k = 0; k < GN_BODY_ITERS; ++k) {
+        GSICP_CUDA(cudaGraphAddKernelNode(&knode[k], body, nullptr, 0, &kp));
+        if (k > 0) {
+            cudaGraphEdgeData ed = {};
+            ed.from_port = cudaGraphKernelNodePortProgrammatic;
+            ed.to_port = 0;
+            ed.type = cudaGraphDependencyTypeProgrammatic;
+            GSICP_CUDA(cudaGraphAddDependencies(body, &knode[k - 1], &knode[k], &ed, 1));
+        }
+    }
     GSICP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     return GSICP_OK;
 }
@@ -1041,11 +1062,23 @@ gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], 
     reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
     GSICP_CUDA(cudaGetLastError());
     if (solve && rm.unrolled) {
-        // profiling mode: one plain launch per iteration (finished launches exit at once)
+        // plain-launch mode: one launch per iteration, each a programmatic dependent of the one
+        // before (finished launches exit at once)
         job.use_cond = 0;
         reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr.val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(rm.grid);
+        cfg.blockDim = dim3(REG_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        const RegJob* jp = rm.job.as<const RegJob>();
         for (int i = 0; i < job.max_iters; ++i)
-            gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
+            GSICP_CUDA(cudaLaunchKernelEx(&cfg, gicp_iter_kernel, jp, rm.cond));
         GSICP_CUDA(cudaGetLastError());
     } else if (solve) {
         GSICP_CUDA(cudaGraphLaunch(rm.exec, s));
