@@ -460,7 +460,9 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
     GSICP_CHECK(bm.covs.ensure(sizeof(float4) * 2 * N));
     GSICP_CHECK(bm.cand.ensure(sizeof(int) * KC * N));
     GSICP_CHECK(bm.anchor.ensure(sizeof(float4) * N));
-    GSICP_CHECK(bm.partials.ensure(sizeof(float) * 32 * C));
+    size_t red_floats = 0;
+    for (int b = 0; b < B; ++b) red_floats += reduction_floats((int)((n[b] + 255) / 256));
+    GSICP_CHECK(bm.partials.ensure(sizeof(float) * std::max<size_t>(red_floats, 1)));
     GSICP_CHECK(bm.counts.ensure(sizeof(int) * B));
     GSICP_CHECK(bm.jobs.ensure(sizeof(RegJob) * B));
     GSICP_CHECK(bm.states.ensure(sizeof(RegState) * B));
@@ -495,6 +497,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
     int running = 0;
     {
         int64_t po = 0, co = 0;
+        size_t red_off = 0;
         for (int b = 0; b < B; ++b) {
             counts_h[b] = (int)n[b];
             offsets_h[b] = (unsigned)co;
@@ -503,7 +506,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
                                 maps[b], params);
             j.cand = bm.cand.as<int>() + KC * po;
             j.anchor = bm.anchor.as<float4>() + po;
-            j.partials = bm.partials.as<float>() + 32 * co;
+            j.partials = bm.partials.as<float>() + red_off;
             j.st = bm.states.as<RegState>() + b;
             j.mode = REG_MODE_SOLVE;
             j.use_cond = 0;
@@ -511,6 +514,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
             running += n[b] > 0;
             po += n[b];
             co += (n[b] + 255) / 256;
+            red_off += reduction_floats((int)((n[b] + 255) / 256));
         }
         *queue_h = BatchQueue{0u, (unsigned)chunks, (unsigned)running, 0u};
     }
@@ -528,6 +532,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
         }
         pofs_h[B] = po;
     }
+    GSICP_CUDA(cudaMemsetAsync(bm.partials.ptr, 0, sizeof(float) * std::max<size_t>(red_floats, 1), s));
     GSICP_CUDA(cudaMemcpyAsync(bm.counts.ptr, counts_h, sizeof(int) * B, cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemcpyAsync(bm.ptrs.ptr, ptr_h, sizeof(float*) * 2 * B, cudaMemcpyHostToDevice, s));
     GSICP_CUDA(cudaMemcpyAsync(bm.pofs.ptr, pofs_h, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, s));

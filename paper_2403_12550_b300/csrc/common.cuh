@@ -261,6 +261,15 @@ constexpr int REG_STATS = 64;
 
 constexpr int KC = 8;  // map candidates cached per source point
 
+// Gauss-Newton reduction (gicp.cu): block partial rows are summed in groups of GN_GROUP; a
+// registration's reduction area holds its nrows rows (32 floats), the group rows (64 floats: hi,
+// lo) and the group counters (one word each, zero between iterations).
+constexpr int GN_GROUP = 32;
+__host__ __device__ constexpr size_t reduction_floats(int nrows)
+{
+    return 32 * (size_t)nrows + 65 * (size_t)((nrows + GN_GROUP - 1) / GN_GROUP);
+}
+
 // Work queue of a batched registration (device memory, zeroed except as set by the host).
 struct BatchQueue {
     unsigned int head;     // next slot to claim

@@ -623,59 +623,59 @@ __device__ __forceinline__ int block_partial(const float (&acc)[NACC], int refre
     return count;
 }
 
-// The last block of a launch (or of a pair): compensated sum of the nb partial rows, then in its
-// first warp the H, b, cost and inliers of this linearisation and (solve mode) the FP64 solve,
-// the pose update and the stopping test.  Returns whether another iteration should run (on lane
-// 0 of warp 0; false elsewhere).  t_start: globaltimer when the block became the last.
-__device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const float* __restrict__ partials, int nb,
+// Reduction of the per-block partial rows, in two levels so that the part left to the last block is
+// short: blocks are grouped by index in runs of GN_GROUP; the block that completes a group sums its
+// group's rows (in row order, compensated float) into a group row of (hi, lo) pairs, and the block
+// that completes the last group sums the group rows (in group order) and solves.  The order of every
+// sum is fixed by the row indices alone, so a registration's result does not depend on which block
+// finished when, and the batched kernel (same rows, same groups) gets the same bits.
+// Layout after the nrows block rows (32 floats each) of a reduction area: G group rows (hi[32],
+// lo[32]) and G group counters.
+__device__ __forceinline__ float* group_rows(float* partials, int nrows) { return partials + 32l * nrows; }
+__device__ __forceinline__ unsigned* group_counters(float* partials, int nrows, int ngroups)
+{
+    return reinterpret_cast<unsigned*>(partials + 32l * nrows + 64l * ngroups);
+}
+
+// Warp 0 of the block that completed group g: the compensated sum, in row order, of the group's rows
+// below nb into its group row.
+__device__ __forceinline__ void group_sum(const float* __restrict__ partials, int g, int nb, float* __restrict__ grow)
+{
+    const int c = threadIdx.x;  // component (lane of warp 0)
+    const int r0 = g * GN_GROUP, r1 = min(r0 + GN_GROUP, nb);
+    float v[GN_GROUP];
+#pragma unroll
+    for (int j = 0; j < GN_GROUP; ++j) v[j] = r0 + j < r1 ? __ldcg(partials + 32l * (r0 + j) + c) : 0.f;
+    dfloat a = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < GN_GROUP; ++j) df_add(a, v[j]);
+    grow[64l * g + c] = a.hi;
+    grow[64l * g + 32 + c] = a.lo;
+}
+
+// The block that completed the last group: the compensated sum of the ng group rows, then in its
+// first warp the H, b, cost and inliers of this linearisation and (solve mode) the FP64 solve, the
+// pose update and the stopping test.  Returns whether another iteration should run (on lane 0 of
+// warp 0; false elsewhere).  t_start: globaltimer when the block became the last.
+__device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const float* __restrict__ grow, int ng,
                                          int it_now, unsigned long long t_start)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // ---- last block: compensated sum of all partials.  Thread t owns component group g = t % 8
-    // (components 4g..4g+3, one float4 of a block's 32-float partial) and blocks t/8, t/8 + 32, ...;
-    // all its loads are independent and issued in batches of 8.
-    __shared__ float shi[REG_THREADS / 32][32], slo[REG_THREADS / 32][32];
-    __shared__ double tot[NACC];
-    {
-        const int grp = threadIdx.x & 7, row = threadIdx.x >> 3;
-        dfloat a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, a2 = {0.f, 0.f}, a3 = {0.f, 0.f};
-        const float4* P4 = reinterpret_cast<const float4*>(partials);
-        for (int b0 = row; b0 < nb; b0 += 8 * (REG_THREADS / 8)) {
-            float4 v[8];
+    __shared__ double tot[32];
+    if (warp == 0) {
+        dfloat a = {0.f, 0.f};
+        for (int g0 = 0; g0 < ng; g0 += 8) {
+            float hi[8], lo[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int b = b0 + j * (REG_THREADS / 8);
-                v[j] = b < nb ? __ldcg(P4 + 8l * b + grp) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool in = g0 + j < ng;
+                hi[j] = in ? __ldcg(grow + 64l * (g0 + j) + lane) : 0.f;
+                lo[j] = in ? __ldcg(grow + 64l * (g0 + j) + 32 + lane) : 0.f;
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                df_add(a0, v[j].x);
-                df_add(a1, v[j].y);
-                df_add(a2, v[j].z);
-                df_add(a3, v[j].w);
-            }
+            for (int j = 0; j < 8; ++j) df_merge(a, hi[j], lo[j]);
         }
-        // lanes l, l^8, l^16, l^24 hold the same group: combine them
-#pragma unroll
-        for (int o = 8; o < 32; o <<= 1) {
-            df_merge(a0, __shfl_xor_sync(0xffffffffu, a0.hi, o), __shfl_xor_sync(0xffffffffu, a0.lo, o));
-            df_merge(a1, __shfl_xor_sync(0xffffffffu, a1.hi, o), __shfl_xor_sync(0xffffffffu, a1.lo, o));
-            df_merge(a2, __shfl_xor_sync(0xffffffffu, a2.hi, o), __shfl_xor_sync(0xffffffffu, a2.lo, o));
-            df_merge(a3, __shfl_xor_sync(0xffffffffu, a3.hi, o), __shfl_xor_sync(0xffffffffu, a3.lo, o));
-        }
-        if (lane < 8) {
-            shi[warp][4 * lane + 0] = a0.hi; slo[warp][4 * lane + 0] = a0.lo;
-            shi[warp][4 * lane + 1] = a1.hi; slo[warp][4 * lane + 1] = a1.lo;
-            shi[warp][4 * lane + 2] = a2.hi; slo[warp][4 * lane + 2] = a2.lo;
-            shi[warp][4 * lane + 3] = a3.hi; slo[warp][4 * lane + 3] = a3.lo;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < NACC) {
-        double sum = 0.0;
-#pragma unroll
-        for (int w = 0; w < REG_THREADS / 32; ++w) sum += (double)shi[w][threadIdx.x] + (double)slo[w][threadIdx.x];
-        tot[threadIdx.x] = sum;
+        tot[lane] = (double)a.hi + (double)a.lo;
     }
     __syncthreads();
     if (warp != 0) return false;
@@ -795,6 +795,10 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
     // this block's share is written: the next iteration's launch may begin (its blocks wait in
     // griddepcontrol.wait until this grid, the last block's solve included, has completed)
     asm volatile("griddepcontrol.launch_dependents;");
+    const int nrows = gridDim.x, ngroups = (nrows + GN_GROUP - 1) / GN_GROUP, g = blockIdx.x / GN_GROUP;
+    const int nb = (n + REG_THREADS - 1) / REG_THREADS;  // rows of blocks that held points (the rest are zero)
+    unsigned* gctr = group_counters(J.partials, nrows, ngroups);
+    float* grow = group_rows(J.partials, nrows);
     __shared__ bool am_last;
     if (threadIdx.x == 0) {
         if (block_refreshed > 0 && it_now < REG_STATS) atomicAdd(&st->refreshes[it_now], block_refreshed);
@@ -803,16 +807,29 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
             atomicMax(&st->t_arrive[it_now], t1);
         }
-        am_last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+        am_last = atomicAdd(&gctr[g], 1u) == (unsigned)(min(nrows - g * GN_GROUP, GN_GROUP) - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        group_sum(J.partials, g, nb, grow);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gctr[g] = 0u;  // every block of the group has counted: ready for the next iteration
+        __threadfence();
+        am_last = atomicAdd(&st->counter, 1u) == (unsigned)(ngroups - 1);
     }
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     unsigned long long t_start = 0;
     if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
-    // the rows of the blocks that held points (the rest are zero): the same rows, in the same
-    // order, as a batched registration of these points sums
-    const bool more = finalize(J, st, J.partials, (n + REG_THREADS - 1) / REG_THREADS, it_now, t_start);
+    // the groups of the blocks that held points: the same rows, groups and order as a batched
+    // registration of these points sums
+    const bool more = finalize(J, st, grow, (nb + GN_GROUP - 1) / GN_GROUP, it_now, t_start);
     if (threadIdx.x == 0 && J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 
@@ -889,11 +906,29 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_batch_kernel(const RegJob
         const int s = c * REG_THREADS + threadIdx.x;
         const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
         block_partial(acc, refreshed, J.partials + 32l * c);
-        if (threadIdx.x == 0) s_last = atomicAdd(&st->counter, 1u) == (unsigned)nchunks - 1u;
+        const int ngroups = (nchunks + GN_GROUP - 1) / GN_GROUP, g = c / GN_GROUP;
+        unsigned* gctr = group_counters(J.partials, nchunks, ngroups);
+        float* grow = group_rows(J.partials, nchunks);
+        if (threadIdx.x == 0)
+            s_last = atomicAdd(&gctr[g], 1u) == (unsigned)(min(nchunks - g * GN_GROUP, GN_GROUP) - 1);
         __syncthreads();
         if (s_last) {
             __threadfence();
-            const bool more = finalize(J, st, J.partials, nchunks, it_now, 0ull);
+            if (threadIdx.x < 32) {
+                group_sum(J.partials, g, nchunks, grow);
+                __threadfence();
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                gctr[g] = 0u;  // reset before the pair's next iteration can be queued
+                __threadfence();
+                s_last = atomicAdd(&st->counter, 1u) == (unsigned)(ngroups - 1);
+            }
+            __syncthreads();
+        }
+        if (s_last) {
+            __threadfence();
+            const bool more = finalize(J, st, grow, ngroups, it_now, 0ull);
             __threadfence();  // the new pose and status before the next items
             __syncthreads();
             if (threadIdx.x == 0) s_base = more ? atomicAdd(&q->tail, (unsigned)nchunks) : 0xffffffffu;
@@ -977,7 +1012,8 @@ gsicp_status RegMachine::init(int capacity)
     exec = nullptr;
     graph = nullptr;
     grid = std::max(want, grid);
-    GSICP_CHECK(partials.ensure(sizeof(float) * 32 * (size_t)grid));
+    GSICP_CHECK(partials.ensure(sizeof(float) * reduction_floats(grid)));
+    GSICP_CUDA(cudaMemset(partials.ptr, 0, sizeof(float) * reduction_floats(grid)));  // group counters start at 0
     GSICP_CHECK(job.ensure(sizeof(RegJob)));
     GSICP_CHECK(state.ensure(sizeof(RegState)));
     if (!state_host) GSICP_CUDA(cudaMallocHost((void**)&state_host, sizeof(RegState)));
