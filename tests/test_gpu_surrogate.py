@@ -228,3 +228,39 @@ def test_tracker_fallback_policy(g, ctx):
     assert all(fb == 0 for _, fb in kinds)
     assert [src for src, _ in kinds[2:]] == [1, 1, 1, 1, 0, 1, 1, 1, 1, 0]
     sg.close()
+
+
+def test_track_frame_surrogate_equals_register_on_its_covariances(g, ctx):
+    """gsicp_track_frame_surrogate is a1 + the network + the registration: the same pose, system and
+    counts as gsicp_register on the points and covariances gsicp_surrogate_covariances returns."""
+    from paper_2403_12550_b300 import surrogate as S
+    from synth import TUM_INTR, sequence_config5
+    seq = sequence_config5(0, n_frames=500)  # frames 0 and 3 of the held-out sequence (~4 cm apart)
+    intr = TUM_INTR.as_array()
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    # map: frame 0's k-NN Gaussians in the world frame
+    d0 = cu(seq["depth"](0))
+    p0, z0, c0 = g.gsicp_frame_covariances(ctx, d0, intr, 2, 0.1, 10.0, cp)
+    T = seq["poses"][0]
+    R = torch.from_numpy(T[:3, :3]).float().cuda()
+    pw = (p0 @ R.T + torch.from_numpy(T[:3, 3]).float().cuda()).contiguous()
+    C = torch.stack([c0[:, 0], c0[:, 1], c0[:, 2], c0[:, 1], c0[:, 3], c0[:, 4], c0[:, 2], c0[:, 4], c0[:, 5]],
+                    1).reshape(-1, 3, 3)
+    Cw = R @ C @ R.T
+    cw = torch.stack([Cw[:, 0, 0], Cw[:, 0, 1], Cw[:, 0, 2], Cw[:, 1, 1], Cw[:, 1, 2], Cw[:, 2, 2]], 1).contiguous()
+    m = g.gsicp_build_map_index(ctx, pw, cw)
+    sg = g.Surrogate(S.load_weights())
+    d = cu(seq["depth"](3))
+    rt = g.gsicp_track_frame_surrogate(ctx, sg, d, intr, 2, 0.1, 10.0, cp, m, T, rp)
+    pts, z, covs = g.gsicp_surrogate_covariances(ctx, sg, d, intr, 2, 0.1, 10.0, cp)
+    rr = g.gsicp_register(ctx, pts.contiguous(), covs.contiguous(), m, T, rp)
+    assert rt["status"] == rr["status"] == g.OK and rt["n_points"] == len(pts)
+    np.testing.assert_array_equal(rt["T"], rr["T"])
+    np.testing.assert_array_equal(rt["H"], rr["H"])
+    assert (rt["iters"], rt["inliers"], rt["cost"]) == (rr["iters"], rr["inliers"], rr["cost"])
+    # and the result is a sensible pose: within 5 mm of the ground truth (started 4 cm away)
+    Tg = seq["poses"][3]
+    assert np.linalg.norm(rt["T"][:3, 3] - Tg[:3, 3]) < 0.005
+    sg.close()
+    m.close()
