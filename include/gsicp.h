@@ -103,6 +103,11 @@ const char* gsicp_version(void);
  * covariances, out[3] Gauss-Newton loop, out[4] whole frame; out[5] = Gauss-Newton iterations.
  * Disabled by default (no events are recorded). */
 gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable);
+/* The last registration's (or linearisation's) final linearisation: *sqdist_out = the sum over its
+ * inlier correspondences of |mu - T x|^2 (squared Euclidean residuals, m^2), *inliers_out
+ * (nullable) their count.  The tracker's fallback test uses sqrt(sqdist / inliers).  Valid after
+ * the call that registered has returned; GSICP_ERR_INVALID_ARG before any registration. */
+gsicp_status gsicp_ctx_last_residual(gsicp_ctx ctx, double* sqdist_out, int64_t* inliers_out);
 /* Search tuning of this context's registrations (gsicp_register, gsicp_linearise,
  * gsicp_register_batch, gsicp_track_frame*): in each warp of 32 source points, when at most
  * max_per_warp of them need a walk of the map's tree in an iteration, the warp's 32 lanes walk for

@@ -18,7 +18,7 @@ import torch
 __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
-    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_set_coop_walks", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
     "gsicp_build_map_index", "gsicp_map_append",
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_selftest_batch_timeout", "gsicp_linearise",
@@ -106,6 +106,7 @@ _sig("gsicp_status_string", C.c_char_p, [C.c_int])
 _sig("gsicp_last_error", C.c_char_p, [])
 _sig("gsicp_version", C.c_char_p, [])
 _sig("gsicp_ctx_set_timing", C.c_int, [_vp, C.c_int])
+_sig("gsicp_ctx_last_residual", C.c_int, [_vp, _dp, _i64p])
 _sig("gsicp_ctx_set_coop_walks", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
 _sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
@@ -256,6 +257,15 @@ def gsicp_ctx_set_coop_walks(ctx: Context, max_per_warp: int):
     """Warps with at most max_per_warp tree walks in an iteration walk together (0..32; results
     do not depend on it)."""
     _check(lib.gsicp_ctx_set_coop_walks(ctx.ptr, int(max_per_warp)), "gsicp_ctx_set_coop_walks")
+
+
+def gsicp_ctx_last_residual(ctx: Context) -> tuple:
+    """(sum of squared Euclidean residuals over the inliers, inlier count) of the last registration's
+    final linearisation."""
+    sq = C.c_double(0.0)
+    n = C.c_int64(0)
+    _check(lib.gsicp_ctx_last_residual(ctx.ptr, C.byref(sq), C.byref(n)), "gsicp_ctx_last_residual")
+    return sq.value, n.value
 
 
 def gsicp_ctx_phase_times(ctx: Context) -> dict:

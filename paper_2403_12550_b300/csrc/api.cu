@@ -246,6 +246,14 @@ gsicp_status gsicp_ctx_frame_stats(gsicp_ctx ctx, int64_t out[2])
     return GSICP_OK;
 }
 
+gsicp_status gsicp_ctx_last_residual(gsicp_ctx ctx, double* sqdist_out, int64_t* inliers_out)
+{
+    if (!ctx || !sqdist_out || !ctx->reg.state_host) return GSICP_ERR_INVALID_ARG;
+    *sqdist_out = ctx->reg.state_host->sqdist;
+    if (inliers_out) *inliers_out = ctx->reg.state_host->inliers;
+    return GSICP_OK;
+}
+
 gsicp_status gsicp_ctx_reg_stats(gsicp_ctx ctx, int n, int32_t* refreshes_out, int32_t* tail_ns_out,
                                  int32_t* solve_ns_out, int32_t* main_ns_out)
 {

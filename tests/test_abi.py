@@ -66,6 +66,8 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     lib.gsicp_tracker_frame.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 5
     assert lib.gsicp_tracker_frame(None, None, 8, 8, None, None, None, None, None) == INVALID
     lib.gsicp_tracker_destroy(None)
+    lib.gsicp_ctx_last_residual.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    assert lib.gsicp_ctx_last_residual(None, None, None) == INVALID
     lib.gsicp_ctx_set_coop_walks.argtypes = [C.c_void_p, C.c_int]
     assert lib.gsicp_ctx_set_coop_walks(None, 4) == INVALID
     lib.gsicp_surrogate_create.argtypes = [C.c_void_p, C.c_void_p]

@@ -290,6 +290,12 @@ def test_linearise_matches_oracle(g, ctx):
         cerr = abs(lg["cost"] - lo["cost"]) / max(lo["cost"], 1e-12)
         assert herr < 1e-3 and cerr < 1e-3 and (berr < 1e-2 or np.linalg.norm(lo["b"]) < 1e-3 * np.linalg.norm(lo["H"])), \
             (herr, berr, cerr, mism)
+        # the squared Euclidean residuals of the inliers (the tracker's fallback residual), against
+        # the sum over the oracle's own correspondences (near-ties differ by ~1e-6 m each)
+        sq, ninl = g.gsicp_ctx_last_residual(ctx)
+        sel = lo["corr"] >= 0
+        sq_o = float(np.sum((tgt[lo["corr"][sel]].astype(np.float64) - y[sel]) ** 2))
+        assert ninl == lg["inliers"] and abs(sq - sq_o) <= 1e-5 * sq_o + mism * 1e-3 * 0.01, (sq, sq_o)
     m.close()
 
 
