@@ -18,9 +18,11 @@
 // identity; Adam (Kingma & Ba) updates float master weights.
 //
 // Layout: per-pixel tensors channels-last over the sample grid (h1, h2: 32 bfloat16 = 64 B per
-// pixel; gradients float).  Every kernel works on 16 x 16 output tiles with a 2-pixel halo staged
-// in shared memory, channel-major ([c][20 * 20 + 1]) so that lanes that differ in pixel or in
-// channel hit distinct banks; weights are staged in shared memory and read as broadcasts.
+// pixel; gradients float).  Forward: layer 1 on CUDA cores (float: the centred differences need
+// it), layers 2 and 3 as tcgen05 implicit GEMMs fed by TMA (sg_conv_tc_kernel).  Training kernels
+// (CUDA cores, float) work on 16 x 16 output tiles with a 2-pixel halo staged in shared memory,
+// channel-major ([c][20 * 20 + 1]) so that lanes that differ in pixel or in channel hit distinct
+// banks, weights staged in shared memory and read as broadcasts.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -45,12 +47,11 @@ constexpr int SG_NW1 = SG_C * 3 * SG_TAPS, SG_NW2 = SG_C * SG_C * SG_TAPS, SG_NW
 constexpr int SG_NW = SG_NW1 + SG_NW2 + SG_NW3;
 static_assert(SG_NW == GSICP_SURROGATE_WEIGHTS, "weight count");
 
-// Kernel layouts of the bfloat16-rounded weights (float values), in one buffer:
+// CUDA-core layouts of the bfloat16-rounded weights (float values), in one buffer (layers 2 and 3
+// run forward on the tensor cores from their own bfloat16 layouts):
 constexpr int WK_W1 = 0;                           // float4 [25 t][32 o]: (W1[o][0..2][t], 0)
-constexpr int WK_W2 = WK_W1 + 4 * SG_TAPS * SG_C;  // float  [32 c][25 t][32 o]: W2[o][c][t]
-constexpr int WK_W2T = WK_W2 + SG_NW2;             // float  [32 o][25 t][32 c]: W2[o][c][24 - t]
-constexpr int WK_W3 = WK_W2T + SG_NW2;             // float4 [32 c][25 t]: (W3[0..2][c][t], 0)
-constexpr int WK_W3T = WK_W3 + 4 * SG_C * SG_TAPS; // float4 [25 t][32 c]: (W3[0..2][c][24 - t], 0)
+constexpr int WK_W2T = WK_W1 + 4 * SG_TAPS * SG_C; // float  [32 o][25 t][32 c]: W2[o][c][24 - t] (backward)
+constexpr int WK_W3T = WK_W2T + SG_NW2;            // float4 [25 t][32 c]: (W3[0..2][c][24 - t], 0) (backward)
 constexpr int WK_TOTAL = WK_W3T + 4 * SG_TAPS * SG_C;
 
 }  // namespace gsicp
@@ -100,19 +101,14 @@ __global__ void sg_layout_kernel(const float* __restrict__ w, float* __restrict_
     } else if (i < SG_NW1 + SG_NW2) {  // W2[o][c][t]
         const int j = i - SG_NW1, o = j / 800, c = (j / 25) % 32, t = j % 25;
         const float v = bf16r(w[i]);
-        wk[WK_W2 + (c * SG_TAPS + t) * SG_C + o] = v;
         wk[WK_W2T + (o * SG_TAPS + (24 - t)) * SG_C + c] = v;
         // tensor-core B operand: [tap t][channel group c / 8][output o][c % 8]
         w2mma[((t * 4 + c / 8) * SG_C + o) * 8 + c % 8] = __float2bfloat16_rn(v);
     } else if (i < SG_NW) {  // W3[o][c][t]
         const int j = i - SG_NW1 - SG_NW2, o = j / 800, c = (j / 25) % 32, t = j % 25;
         const float v = bf16r(w[i]);
-        wk[WK_W3 + 4 * (c * SG_TAPS + t) + o] = v;
         wk[WK_W3T + 4 * ((24 - t) * SG_C + c) + o] = v;
-        if (o == 0) {
-            wk[WK_W3 + 4 * (c * SG_TAPS + t) + 3] = 0.f;
-            wk[WK_W3T + 4 * ((24 - t) * SG_C + c) + 3] = 0.f;
-        }
+        if (o == 0) wk[WK_W3T + 4 * ((24 - t) * SG_C + c) + 3] = 0.f;
         // tensor-core B operand of layer 3 (after layer 2's): [tap][group][16 outputs, 3 used][8]
         w2mma[SG_NW2 + ((t * 4 + c / 8) * 16 + o) * 8 + c % 8] = __float2bfloat16_rn(v);
     }
@@ -220,18 +216,13 @@ __global__ void __launch_bounds__(SG_L1_THREADS) sg_l1_kernel(const float4* __re
     }
 }
 
-enum { SG_EPI_RELU_BF16 = 0, SG_EPI_GATE_F32 = 1 };
-
-// 32 -> 32 channel 5 x 5 convolution for output channels [16 half, 16 half + 16).
-//   kEpi = SG_EPI_RELU_BF16: out (bfloat16) = bf16(relu(acc)) at valid pixels, else 0   (layer 2)
-//   kEpi = SG_EPI_GATE_F32 : out (float) = acc where gate (bfloat16) > 0, else 0        (d layer 1)
-// wk: [32 c][25 t][32 o] float.  Dynamic shared memory: SG_C * SG_HPAD + 32 * 25 * 16 floats.
-template <bool kBf16In, int kEpi>
-__global__ void __launch_bounds__(256) sg_conv32_kernel(const void* __restrict__ in, int w, int h,
-                                                        const float* __restrict__ wk,
-                                                        const float4* __restrict__ grid,
-                                                        const __nv_bfloat16* __restrict__ gate,
-                                                        void* __restrict__ out)
+// Back-propagation through layer 2: da1 = [h1 > 0] (W2 transposed * da2), a 32 -> 32 channel 5 x 5
+// convolution of the float da2 with the flipped, channel-swapped weights wk ([32 in][25 t][32 out]),
+// output channels [16 half, 16 half + 16), gated by h1 > 0.  Float on CUDA cores (training only).
+// Dynamic shared memory: SG_C * SG_HPAD + 32 * 25 * 16 floats.
+__global__ void __launch_bounds__(256) sg_dl2_kernel(const float* __restrict__ da2, int w, int h,
+                                                     const float* __restrict__ wk,
+                                                     const __nv_bfloat16* __restrict__ h1, float* __restrict__ da1)
 {
     extern __shared__ float sm[];
     float* tile = sm;                       // [32][SG_HPAD]
@@ -242,7 +233,7 @@ __global__ void __launch_bounds__(256) sg_conv32_kernel(const void* __restrict__
         const int ct = i >> 4, o = i & 15;
         ws[i] = wk[ct * SG_C + 16 * half + o];
     }
-    stage32<kBf16In>(in, w, h, x0, y0, tile);
+    stage32<false>(da2, w, h, x0, y0, tile);
     __syncthreads();
     const int tx = threadIdx.x % SG_T, ty = threadIdx.x / SG_T;
     const int x = x0 + tx, y = y0 + ty;
@@ -267,21 +258,14 @@ __global__ void __launch_bounds__(256) sg_conv32_kernel(const void* __restrict__
         }
     }
     const long pix = (long)y * w + x;
-    if (kEpi == SG_EPI_RELU_BF16) {
-        const bool valid = grid[pix].w != 0.f;
+    const __nv_bfloat16* gp = h1 + pix * SG_C + 16 * half;
+    float4* dst = reinterpret_cast<float4*>(da1 + pix * SG_C + 16 * half);
 #pragma unroll
-        for (int o = 0; o < 16; ++o) acc[o] = valid ? fmaxf(acc[o], 0.f) : 0.f;
-        store_bf16x16(static_cast<__nv_bfloat16*>(out) + pix * SG_C + 16 * half, acc);
-    } else {
-        const __nv_bfloat16* gp = gate + pix * SG_C + 16 * half;
-        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + pix * SG_C + 16 * half);
+    for (int q = 0; q < 4; ++q) {
+        float r[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float r[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) r[k] = __bfloat162float(gp[4 * q + k]) > 0.f ? acc[4 * q + k] : 0.f;
-            dst[q] = make_float4(r[0], r[1], r[2], r[3]);
-        }
+        for (int k = 0; k < 4; ++k) r[k] = __bfloat162float(gp[4 * q + k]) > 0.f ? acc[4 * q + k] : 0.f;
+        dst[q] = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
@@ -783,8 +767,7 @@ gsicp_status sg_set_smem()
 {
     static bool done = false;
     if (done) return GSICP_OK;
-    GSICP_CUDA(cudaFuncSetAttribute(sg_conv32_kernel<false, SG_EPI_GATE_F32>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
+    GSICP_CUDA(cudaFuncSetAttribute(sg_dl2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV));
     GSICP_CUDA(cudaFuncSetAttribute(sg_conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)tc_smem<32>()));
     GSICP_CUDA(cudaFuncSetAttribute(sg_conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -903,8 +886,8 @@ gsicp_status sg_backward(gsicp_surrogate_s* sg, const int* idx_img, const float*
                                         sg->h2.as<__nv_bfloat16>(), da2);
     sg_gw2_kernel<<<tiles, 256, SMEM_GW2, s>>>(da2, sg->h1.as<__nv_bfloat16>(), ws, hs, g + SG_NW1);
     // da1 = [h1 > 0] (layer 2 transposed: W2 with flipped taps, channels swapped) * da2
-    sg_conv32_kernel<false, SG_EPI_GATE_F32><<<dim3(tiles.x, tiles.y, 2), 256, SMEM_CONV, s>>>(
-        da2, ws, hs, wk + WK_W2T, grid, sg->h1.as<__nv_bfloat16>(), da1);
+    sg_dl2_kernel<<<dim3(tiles.x, tiles.y, 2), 256, SMEM_CONV, s>>>(da2, ws, hs, wk + WK_W2T,
+                                                                    sg->h1.as<__nv_bfloat16>(), da1);
     sg_gw1_kernel<<<tiles, 256, SMEM_GW1, s>>>(da1, grid, ws, hs, g);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
