@@ -491,9 +491,13 @@ __global__ void __launch_bounds__(COV_THREADS) knn_wide_window_kernel(
     }
 }
 
-// Exact k-NN by the tree for the listed queries (one thread each; list[t] = (original index, an
-// upper bound on its k-th squared distance: the window's k-th, or +inf)).  The walk collects every
-// point within the bound, so it starts tight; leaves are read eight points at a time.
+// Exact k-NN by the tree for the listed queries (list[t] = (original index, an upper bound on its
+// k-th squared distance: the window's k-th, or +inf)), one warp per query: the warp's lanes walk the
+// tree together (warp_knn: up to 32 boxes or points per dependent step), collecting every point
+// within the bound, so the walk starts tight.  These are the few points neither image window
+// settled (depth edges, grazing surfaces); one thread each, their walks were long chains of
+// dependent loads run by a handful of warps.  Lane 0 then builds the covariance.  If the walk's
+// stack would overflow, lane 0 walks alone (same answer: both walks are exact).
 template <int KMAX>
 __global__ void __launch_bounds__(COV_THREADS) knn_list_kernel(IndexView ix, const int2* __restrict__ list,
                                                                const int* __restrict__ count,
@@ -502,33 +506,43 @@ __global__ void __launch_bounds__(COV_THREADS) knn_list_kernel(IndexView ix, con
                                                                int mode, float p, float* __restrict__ covs,
                                                                int32_t* __restrict__ knn_out)
 {
+    __shared__ int2 wstack[COV_THREADS / 32][WARP_STACK];
     const int n = *ix.n, B = ix.B, m = *count;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = w0; t < m; t += nwarps) {
         const int2 e = list[t];
         const int qi = e.x;
         const float4 q = make_float4(orig[3l * qi], orig[3l * qi + 1], orig[3l * qi + 2], __int_as_float(qi));
-        float bound = __int_as_float(e.y);
-        unsigned long long Lk[KMAX];
-        const unsigned long long lim = dkey(bound, 0x7fffffff);  // accepts every point within the bound
+        const unsigned long long lim = dkey(__int_as_float(e.y), 0x7fffffff);  // accepts every point within the bound
+        unsigned long long key;
+        int pos;
+        const bool ok = warp_knn(ix, n, q.x, q.y, q.z, k, lim, -1, -1, -1, wstack[threadIdx.x >> 5], key, pos);
+        unsigned long long Lk[KMAX];  // lane 0: slots KMAX - k .. KMAX - 1 hold the k keys, ascending
 #pragma unroll
-        for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : lim;
-        traverse(ix, q.x, q.y, q.z, bound, [&](int lf) {
-            const int beg = lf * B, end = min(beg + B, n);
-            for (int u0 = beg; u0 < end; u0 += 8) {
-                float4 pp[8];
+        for (int a = 0; a < KMAX; ++a) {
+            const int src = a - (KMAX - k);
+            const unsigned long long v = __shfl_sync(0xffffffffu, key, src >= 0 ? src : 0);
+            Lk[a] = src >= 0 ? v : 0ull;
+        }
+        if (lane == 0) {
+            if (!ok) {
+                float bound = __int_as_float(e.y);
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    pp[j] = u0 + j < end ? ix.pts[u0 + j] : make_float4(GSICP_INF, GSICP_INF, GSICP_INF,
-                                                                        __int_as_float(0x7fffffff));
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const unsigned long long key = dkey(point_d2(q.x, q.y, q.z, pp[j]), __float_as_int(pp[j].w));
-                    if (key < Lk[KMAX - 1]) key_insert(Lk, key);
-                }
+                for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : lim;
+                traverse(ix, q.x, q.y, q.z, bound, [&](int lf) {
+                    const int beg = lf * B, end = min(beg + B, n);
+                    for (int u = beg; u < end; ++u) {
+                        const float4 pp = ix.pts[u];
+                        const unsigned long long kk = dkey(point_d2(q.x, q.y, q.z, pp), __float_as_int(pp.w));
+                        if (kk < Lk[KMAX - 1]) key_insert(Lk, kk);
+                    }
+                    bound = key_d2(Lk[KMAX - 1]);
+                });
             }
-            bound = key_d2(Lk[KMAX - 1]);
-        });
-        finish_cov<KMAX>(Lk, k, q, ByIndex{orig}, SameIndex{}, zin, eps, mode, p, covs, knn_out, nullptr, 0);
+            finish_cov<KMAX>(Lk, k, q, ByIndex{orig}, SameIndex{}, zin, eps, mode, p, covs, knn_out, nullptr, 0);
+        }
+        __syncwarp();
     }
 }
 
