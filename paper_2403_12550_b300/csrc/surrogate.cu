@@ -404,9 +404,14 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    bool failed = false, prefetched = false;
-    uint32_t pending_bar = 0, pending_parity = 0;
-    if (tid == 0) failed = !tc_wait(bar_b, 0);
+    // copies and MMAs this CTA started and has not yet seen complete (thread 0's bookkeeping): on a
+    // wait that runs out they are waited for again before the CTA leaves
+    bool failed = false, b_pending = true, a_pending = (int)blockIdx.x < ntiles, m_pending = false;
+    uint32_t a_bar = smem_u32(&bars[1]), a_parity = 0, m_parity = 0;
+    if (tid == 0) {
+        failed = !tc_wait(bar_b, 0);
+        b_pending = failed;
+    }
     int k = 0;
     if (!__syncthreads_or(failed)) {
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
@@ -416,8 +421,8 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
             bool bad = false;
             if (tid == 0) {
                 bad = !tc_wait(smem_u32(&bars[1 + buf]), (k >> 1) & 1);
-                prefetched = false;
                 if (!bad) {
+                    a_pending = false;
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     // the 50 descriptors differ only in their start address (the low 14 bits, in
                     // 16-byte units, which no offset here carries out of): base + constant
@@ -435,15 +440,17 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                                  ::"r"(bar_m) : "memory");
+                    m_pending = true;
+                    m_parity = k & 1;
                     // the next tile's copy into the other buffer (its last reader, the previous
                     // tile's MMAs, has completed)
                     const int next = tile + gridDim.x;
                     if (next < ntiles) {
-                        pending_bar = smem_u32(&bars[1 + (buf ^ 1)]);
-                        pending_parity = ((k + 1) >> 1) & 1;
+                        a_bar = smem_u32(&bars[1 + (buf ^ 1)]);
+                        a_parity = ((k + 1) >> 1) & 1;
                         tc_load_tile(&tmap, a0 + (buf ^ 1) * TC_A_BYTES, (next % tiles_x) * TC_TW,
-                                     (next / tiles_x) * TC_TH, pending_bar);
-                        prefetched = true;
+                                     (next / tiles_x) * TC_TH, a_bar);
+                        a_pending = true;
                     }
                 }
             }
@@ -455,6 +462,7 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
                 failed = true;
                 break;
             }
+            m_pending = false;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
             const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
@@ -506,7 +514,10 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
     }
     if (failed && tid == 0) {
         *reinterpret_cast<volatile unsigned*>(err) = 1u;  // pinned host word
-        if (prefetched) tc_wait(pending_bar, pending_parity);  // no copy may land after the CTA is gone
+        // no copy may land and no MMA may read after the CTA is gone (each wait bounded again)
+        if (b_pending) tc_wait(bar_b, 0);
+        if (a_pending) tc_wait(a_bar, a_parity);
+        if (m_pending) tc_wait(bar_m, m_parity);
     }
     __syncthreads();
     if (warp == 0) {
