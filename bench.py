@@ -585,7 +585,7 @@ def surrogate_cpu_baseline(frames, seq, budget_s: float = 15.0) -> dict:
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": done / el, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": done / el, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
             "sample": f"{done} frame(s) of the held-out sequence: FP64 network forward + covariances + registration "
                       f"against a map from the previous frame ({el:.1f} s)"}
 

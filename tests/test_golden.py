@@ -1,0 +1,106 @@
+"""The hand-worked examples under tests/golden/ (regularisation and scale aligning of Sec. 3.1 and
+Sec. 3.2 on six-point stars; the SE(3) exponential of the pose update) against the oracle and,
+for the covariances, against the CUDA path through the C ABI."""
+import configparser
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+from ._util import COV_REL_TOL, cov_rel_err
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+MODES = (("plane", orc.PLANE), ("ellipse", orc.ELLIPSE), ("none", orc.NONE))
+
+
+def _read(name):
+    cp = configparser.ConfigParser(inline_comment_prefixes=None)
+    cp.optionxform = str  # keys are case-sensitive (R, t)
+    with open(os.path.join(GOLDEN, name)) as fh:
+        cp.read_file(fh)
+    return {s: {k: np.array([float(x) for x in v.split()]) for k, v in cp[s].items()} for s in cp.sections()}
+
+
+STARS = _read("regularisation_star.ini")
+SE3 = _read("se3_exp.ini")
+
+
+def star_points(c):
+    """Centre plus and minus a*u, b*v, w_len*w (the six points every case is built from)."""
+    pts = []
+    for axis, length in (("u", "a"), ("v", "b"), ("w", "w_len")):
+        for sign in (1.0, -1.0):
+            pts.append(c["centre"] + sign * c[length][0] * c[axis])
+    return np.array(pts)
+
+
+def test_fixtures_are_well_formed():
+    assert set(STARS) == {"star_345", "star_axes_yxz"} and set(SE3) == {"translation_only", "quarter_turn_z",
+                                                                      "half_turn_x"}
+    for c in STARS.values():
+        F = np.stack([c["u"], c["v"], c["w"]])
+        np.testing.assert_allclose(F @ F.T, np.eye(3), atol=1e-15)
+        assert c["a"][0] < c["b"][0] < c["w_len"][0]
+        for key, _ in MODES:
+            assert c[key].shape == (6,)
+
+
+@pytest.mark.parametrize("case", sorted(STARS))
+def test_oracle_regularise_on_the_worked_raw_covariances(case):
+    c = STARS[case]
+    eps = c["eps"][0]
+    for key, mode in MODES[:2]:
+        out, _gap, flags = orc.regularise(c["none"], mode, eps)
+        assert flags == 0
+        np.testing.assert_allclose(out, c[key], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("case", sorted(STARS))
+@pytest.mark.parametrize("p", [0.0, 1.5])
+def test_oracle_source_covariances_on_the_star(case, p):
+    c = STARS[case]
+    pts = star_points(c)
+    z = pts[:, 2].copy()
+    for key, mode in MODES:
+        out = orc.source_covariances(pts, z, k=20, eps=c["eps"][0], reg_mode=mode, p=p)
+        np.testing.assert_allclose(out["raw"], np.tile(c["none"], (6, 1)), rtol=1e-12, atol=1e-15)
+        # eps reaches the oracle as a float32 (as the C ABI passes it), which moves each entry of the
+        # plane and ellipse forms by at most that rounding of eps (about 5e-11 for 1e-3)
+        deps = abs(float(np.float32(c["eps"][0])) - c["eps"][0])
+        expect = c[key][None] * z[:, None] ** (-2.0 * p)
+        np.testing.assert_allclose(out["covs"], expect, rtol=1e-12, atol=deps * z.min() ** (-2.0 * p) + 1e-14)
+
+
+@pytest.mark.parametrize("case", sorted(SE3))
+def test_oracle_se3_exp(case):
+    c = SE3[case]
+    T = orc.se3_exp(c["xi"])
+    np.testing.assert_allclose(T[:3, :3], c["R"].reshape(3, 3), atol=1e-15)
+    np.testing.assert_allclose(T[:3, 3], c["t"], atol=1e-15)
+    np.testing.assert_array_equal(T[3], [0, 0, 0, 1])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", sorted(STARS))
+@pytest.mark.parametrize("p", [0.0, 1.5])
+def test_cuda_source_covariances_on_the_star(case, p):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_12550_b300 as g
+    c = STARS[case]
+    pts = star_points(c).astype(np.float32)
+    z = pts[:, 2].copy()
+    ctx = g.Context()
+    try:
+        for key, mode in MODES:
+            covs = g.gsicp_source_covariances(ctx, torch.from_numpy(pts).cuda(), torch.from_numpy(z).cuda(),
+                                              g.CovParams(20, float(c["eps"][0]), mode, p))
+            covs = covs.cpu().numpy().astype(np.float64)
+            expect = c[key][None] * z.astype(np.float64)[:, None] ** (-2.0 * p)
+            err = cov_rel_err(covs, expect)
+            assert err.max() <= COV_REL_TOL, (key, err)
+    finally:
+        ctx.close()
