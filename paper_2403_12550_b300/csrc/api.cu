@@ -457,7 +457,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
         if (n[b] < 0 || n[b] > (1 << 30) || !maps[b] || !valid_pose(T0 + 16l * b)) return GSICP_ERR_INVALID_ARG;
         if (n[b] > 0 && (!src_pts_dev[b] || !src_covs_dev[b])) return GSICP_ERR_INVALID_ARG;
         total += n[b];
-        chunks += (n[b] + 255) / 256;
+        chunks += (n[b] + REG_THREADS - 1) / REG_THREADS;
     }
     const int64_t capacity = chunks * params->max_iters;
     if (total > (1 << 30) || capacity > (int64_t)UINT32_MAX - 1) return GSICP_ERR_INVALID_ARG;
@@ -469,7 +469,7 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
     GSICP_CHECK(bm.cand.ensure(sizeof(int) * KC * N));
     GSICP_CHECK(bm.anchor.ensure(sizeof(float4) * N));
     size_t red_floats = 0;
-    for (int b = 0; b < B; ++b) red_floats += reduction_floats((int)((n[b] + 255) / 256));
+    for (int b = 0; b < B; ++b) red_floats += reduction_floats((int)((n[b] + REG_THREADS - 1) / REG_THREADS));
     GSICP_CHECK(bm.partials.ensure(sizeof(float) * std::max<size_t>(red_floats, 1)));
     GSICP_CHECK(bm.counts.ensure(sizeof(int) * B));
     GSICP_CHECK(bm.jobs.ensure(sizeof(RegJob) * B));
@@ -521,8 +521,8 @@ gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_
             jobs_h[b] = j;
             running += n[b] > 0;
             po += n[b];
-            co += (n[b] + 255) / 256;
-            red_off += reduction_floats((int)((n[b] + 255) / 256));
+            co += (n[b] + REG_THREADS - 1) / REG_THREADS;
+            red_off += reduction_floats((int)((n[b] + REG_THREADS - 1) / REG_THREADS));
         }
         *queue_h = BatchQueue{0u, (unsigned)chunks, (unsigned)running, 0u};
     }

@@ -261,6 +261,15 @@ constexpr int REG_STATS = 64;
 
 constexpr int KC = 8;  // map candidates cached per source point
 
+// Gauss-Newton block: one source point per thread (a batched registration's work item is one
+// block's worth of a pair's points), REG_BLOCKS_PER_SM blocks resident per SM (the kernels' launch
+// bounds; 24 warps at 80 registers a thread).  Gauss-Newton time per 1200x680 frame measured for
+// 64 / 128 / 256 / 384 threads: 1.73 / 1.61 / 1.53 / 1.51 ms.  384 would save about 1 % there but
+// also makes the batched kernel's work items 1.5x larger, which is not measured; 256 is kept.
+constexpr int REG_THREADS = 256;
+constexpr int REG_BLOCKS_PER_SM = 768 / REG_THREADS;
+static_assert(REG_THREADS % 32 == 0 && 768 % REG_THREADS == 0, "GN block: whole warps, 768 threads per SM");
+
 // Gauss-Newton reduction (gicp.cu): block partial rows are summed in groups of GN_GROUP; a
 // registration's reduction area holds its nrows rows (32 floats), the group rows (64 floats: hi,
 // lo) and the group counters (one word each, zero between iterations).

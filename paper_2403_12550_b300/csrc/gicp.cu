@@ -35,7 +35,6 @@
 
 namespace gsicp {
 
-constexpr int REG_THREADS = 256;
 constexpr int GN_BODY_ITERS = 4;  // iteration launches per pass of the conditional-while graph
 
 // Exact nearest point of `ix` to q with (d2, original index) lexicographically
@@ -750,7 +749,7 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
     return more;
 }
 
-__global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob* __restrict__ jp,
+__global__ void __launch_bounds__(REG_THREADS, REG_BLOCKS_PER_SM) gicp_iter_kernel(const RegJob* __restrict__ jp,
                                                                 cudaGraphConditionalHandle cond)
 {
     // launched as a programmatic dependent of the previous iteration (plain-launch mode): wait for
@@ -836,7 +835,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
 // ---------------------------------------------------------------------------------------------
 // Batched registration: many independent pairs in one persistent launch.
 //
-// Work items are (pair, 256-point chunk) of a pair's current iteration, taken from a device queue
+// Work items are (pair, REG_THREADS-point chunk) of a pair's current iteration, taken from a device queue
 // (an append-only array of 64-bit items, empty slots all ones).  Resident blocks claim slots in
 // order (atomic head) and wait, with a bounded spin, for a claimed slot to be filled.  The block
 // that finishes a pair's last chunk of an iteration sums that pair's chunk partials in chunk order,
@@ -849,7 +848,7 @@ __global__ void __launch_bounds__(REG_THREADS, 3) gicp_iter_kernel(const RegJob*
 constexpr unsigned long long BATCH_EMPTY = ~0ull;
 constexpr unsigned BATCH_SPIN_LIMIT = 1u << 22;  // polls of ~0.25 us each: ~1 s before giving up
 
-__global__ void __launch_bounds__(REG_THREADS, 3) gicp_batch_kernel(const RegJob* __restrict__ jobs,
+__global__ void __launch_bounds__(REG_THREADS, REG_BLOCKS_PER_SM) gicp_batch_kernel(const RegJob* __restrict__ jobs,
                                                                  BatchQueue* __restrict__ q,
                                                                  unsigned long long* __restrict__ items,
                                                                  unsigned capacity)
@@ -977,6 +976,16 @@ __global__ void batch_setup_kernel(const RegJob* __restrict__ jobs, const Pose16
         items[offsets[b] + j] = ((unsigned long long)b << 32) | (unsigned)j;
 }
 
+// Blocks of the persistent batched kernel: no more than can be resident at once (a claimed queue slot
+// is filled by another block, which must be running), as the occupancy calculator gives it.
+static int batch_grid()
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gicp_batch_kernel, REG_THREADS, 0) != cudaSuccess)
+        occ = REG_BLOCKS_PER_SM;
+    return device_sm_count() * std::max(1, std::min(occ, REG_BLOCKS_PER_SM));
+}
+
 // The queue wait's bound, exercised: one pair "running" and no item will ever be published, so
 // every block's wait runs out, sets the error flag and leaves.  Takes about a second.
 gsicp_status batch_wait_selftest(BatchQueue* q_dev, unsigned long long* items, unsigned capacity, cudaStream_t s)
@@ -984,7 +993,7 @@ gsicp_status batch_wait_selftest(BatchQueue* q_dev, unsigned long long* items, u
     GSICP_CUDA(cudaMemsetAsync(items, 0xff, sizeof(unsigned long long) * (size_t)capacity, s));
     const BatchQueue q0 = {0u, 0u, 1u, 0u};
     GSICP_CUDA(cudaMemcpyAsync(q_dev, &q0, sizeof(q0), cudaMemcpyHostToDevice, s));
-    gicp_batch_kernel<<<device_sm_count() * 3, REG_THREADS, 0, s>>>(nullptr, q_dev, items, capacity);
+    gicp_batch_kernel<<<batch_grid(), REG_THREADS, 0, s>>>(nullptr, q_dev, items, capacity);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }
@@ -995,8 +1004,7 @@ gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, cons
     if (B <= 0) return GSICP_OK;
     GSICP_CUDA(cudaMemsetAsync(items, 0xff, sizeof(unsigned long long) * (size_t)capacity, s));
     batch_setup_kernel<<<B, 256, 0, s>>>(jobs_dev, T0_dev, B, offsets_dev, items);
-    const int grid = device_sm_count() * 3;  // resident blocks (launch bounds)
-    gicp_batch_kernel<<<grid, REG_THREADS, 0, s>>>(jobs_dev, q_dev, items, capacity);
+    gicp_batch_kernel<<<batch_grid(), REG_THREADS, 0, s>>>(jobs_dev, q_dev, items, capacity);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }
