@@ -12,6 +12,7 @@ Citations (sections / equations of the paper, arXiv 2403.12550) sit in
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 
@@ -42,7 +43,24 @@ def _load():
     path = lib_path()
     if not os.path.exists(path):
         build()
-    lib = C.CDLL(path)
+    _lib = _bind(C.CDLL(path))
+    return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Route every call of this module to another build of the C oracle while the block runs: the
+    tests that plant a mistake in a copy of ``gsicp_oracle.c`` use it to show that a pin catches it."""
+    global _lib
+    saved = _lib
+    _lib = _bind(C.CDLL(os.path.abspath(path)))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _bind(lib):
     lib.orc_depth_to_points.restype = C.c_long
     lib.orc_depth_to_points.argtypes = [_F, C.c_int, C.c_int, _D, C.c_int, C.c_double, C.c_double, _D, _D, C.c_long]
     lib.orc_kdtree_build.restype = C.c_void_p
@@ -65,7 +83,6 @@ def _load():
                                  C.POINTER(C.c_int), _D, C.POINTER(C.c_long)]
     lib.orc_register_fixed.argtypes = [_D, _D, C.c_long, _D, _D, _D, C.POINTER(RegParams), _D,
                                        C.POINTER(C.c_int), _D]
-    _lib = lib
     return lib
 
 

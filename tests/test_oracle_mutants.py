@@ -1,0 +1,90 @@
+"""The pins catch plausible mistakes: each case plants one mistake in a copy of the C oracle
+(a dropped term, a wrong sign, index or power, a transposed operand), builds the copy, and checks
+that the pins named for it fail on the copy while they pass on the real oracle.  CPU only."""
+import os
+import shutil
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from oracle.build import compile_shared
+
+from . import test_golden as golden
+from . import test_oracle_pins as pins
+
+HERE = os.path.dirname(os.path.abspath(orc.__file__))
+
+# (name, text in gsicp_oracle.c, planted text, pins that must catch it)
+MUTANTS = [
+    ("combined covariance without the rotation of C^s",
+     "Sig[a] = Ct[a] + RCs[a];", "Sig[a] = Ct[a] + Cs[a];",
+     [pins.test_linearisation_is_invariant_to_the_source_and_map_frames]),
+    ("weight Sigma instead of Sigma^-1",
+     "if (inv_sym3(Sig, W6) != 0) return;", "memcpy(W6, Sig, sizeof(W6));",
+     [pins.test_cost_tends_to_point_to_plane_error_in_the_flat_limit]),
+    ("R C R instead of R C R^T",
+     "s += RS[3 * r + j] * R[3 * c + j];", "s += RS[3 * r + j] * R[3 * j + c];",
+     [pins.test_linearisation_is_invariant_to_the_source_and_map_frames]),
+    ("plane eps on the largest axis",
+     "double lam[3] = {eps, 1.0, 1.0};", "double lam[3] = {1.0, 1.0, eps};",
+     [pins.test_regularisation_closed_forms, lambda: golden.test_oracle_regularise_on_the_worked_raw_covariances("star_345")]),
+    ("ellipse scaled by the largest scale, not the median",
+     "double lam[3] = {r0, 1.0, w[2] / w[1]};", "double lam[3] = {r0 * w[1] / w[2], w[1] / w[2], 1.0};",
+     [pins.test_regularisation_closed_forms]),
+    ("spectrum rebuilt as V^T diag V",
+     "s += V[3 * r + j] * lam[j] * V[3 * c + j];", "s += V[3 * j + r] * lam[j] * V[3 * j + c];",
+     [pins.test_regularisation_closed_forms]),
+    ("scale aligning by z^-p instead of z^-2p",
+     "pow(z[i], -2.0 * p)", "pow(z[i], -p)",
+     [pins.test_scale_aligning_is_z_power, lambda: golden.test_oracle_source_covariances_on_the_star("star_345", 1.5)]),
+    ("covariance divided by k - 1",
+     "for (int a = 0; a < 6; ++a) C[a] /= kk;", "for (int a = 0; a < 6; ++a) C[a] /= (kk - 1);",
+     [pins.test_raw_covariance_equals_numpy_cov_of_brute_force_neighbours]),
+    ("Jacobi rotation of the eigenvectors with a wrong sign",
+     "Q[r][q] = s * qrp + c * qrq;", "Q[r][q] = -s * qrp + c * qrq;",
+     [pins.test_eigh3_matches_lapack]),
+    ("SE(3) exp: translation factor with sin(th)/th",
+     "Vm[i] = id + B * K[i] + Cc * K2[i];", "Vm[i] = id + A * K[i] + Cc * K2[i];",
+     [lambda: pins.test_se3_exp_matches_expm(1.0), lambda: golden.test_oracle_se3_exp("quarter_turn_z")]),
+    ("Jacobian d d / d v = +I",
+     "J[6 * r + 3 + c] = (r == c) ? -1.0 : 0.0;", "J[6 * r + 3 + c] = (r == c) ? 1.0 : 0.0;",
+     [pins.test_jacobian_matches_finite_differences]),
+    ("Gauss-Newton step +H^-1 b",
+     "nb[a] = -b[a];", "nb[a] = b[a];",
+     [pins.test_exact_recovery_on_noise_free_room]),
+    ("distance ties to the larger index",
+     "(d == e && i < j)", "(d == e && i > j)",
+     [pins.test_knn_ties_break_to_smaller_index]),
+    ("k-d tree prunes the far side too early",
+     "if (diff * diff <= L->d[L->k - 1])", "if (diff * diff <= 0.25 * L->d[L->k - 1])",
+     [lambda: pins.test_knn_tree_equals_brute_force(2000, 20, 200), lambda: pins.test_radius_nn_tree_equals_brute_force(0)]),
+    ("back-projection with cx in place of cy",
+     "((double)v - cy) * d / fy", "((double)v - cx) * d / fy",
+     [pins.test_depth_to_points_on_analytic_plane]),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+@pytest.mark.parametrize("case", range(len(MUTANTS)), ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(case, workdir):
+    name, old, new, catchers = MUTANTS[case]
+    with open(os.path.join(HERE, "gsicp_oracle.c")) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    d = workdir / f"m{case}"
+    d.mkdir()
+    shutil.copy(os.path.join(HERE, "gsicp_oracle.h"), d / "gsicp_oracle.h")
+    (d / "gsicp_oracle.c").write_text(src.replace(old, new))
+    lib = compile_shared(str(d / "gsicp_oracle.c"), str(d / "liboracle.so"))
+    for pin in catchers:
+        pin()  # passes on the real oracle
+        with orc.library(lib):
+            with pytest.raises(AssertionError):
+                pin()
+    # the real oracle is back in place afterwards
+    np.testing.assert_allclose(orc.se3_exp(np.zeros(6)), np.eye(4))

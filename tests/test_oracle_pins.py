@@ -345,6 +345,57 @@ def test_registration_invariants():
     assert r2["iters"] == r["iters"]
 
 
+def _rotate6(Q, c6):
+    return np.array([(Q @ _sym(c) @ Q.T)[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]] for c in c6])
+
+
+def test_linearisation_is_invariant_to_the_source_and_map_frames():
+    # Moving the source cloud by a rigid motion G = (Q, u) -- points G x, covariances Q C Q^T --
+    # and the pose to T G^-1 leaves every world-frame residual, combined covariance and Jacobian of
+    # the left update as it was: cost, H and b are unchanged.  Moving the map instead (means G mu,
+    # covariances Q C Q^T, pose G T) rotates every residual and combined covariance together, so
+    # the cost d^T Sigma^-1 d is unchanged.  Both need Sigma = C^t + R C^s R^T with anisotropic
+    # covariances on both sides.
+    src32, tgt32, T_gt = pair_config1(3, 1, n=1500)
+    s, t = src32.astype(np.float64), tgt32.astype(np.float64)
+    cs = orc.source_covariances(s, k=20, reg_mode=orc.PLANE)["covs"]
+    ct = orc.source_covariances(t, k=20, reg_mode=orc.ELLIPSE)["covs"]
+    m = orc.Map(t, ct)
+    T = T_gt @ random_offset(np.random.default_rng(13), 1.0, 0.01)
+    ref = orc.linearise(s, cs, m, T, 0.1)
+    assert ref["inliers"] > 500
+    G = make_pose(rot_axis_angle([0.3, -0.8, 0.5], 0.7), [0.4, -1.1, 2.0])
+    Q = G[:3, :3]
+    mv = orc.linearise(transform_points(G, s), _rotate6(Q, cs), m, T @ inv_pose(G), 0.1)
+    np.testing.assert_array_equal(mv["corr"], ref["corr"])
+    assert mv["cost"] == pytest.approx(ref["cost"], rel=1e-10)
+    np.testing.assert_allclose(mv["H"], ref["H"], rtol=1e-9, atol=1e-10 * np.abs(ref["H"]).max())
+    np.testing.assert_allclose(mv["b"], ref["b"], rtol=1e-9, atol=1e-9 * np.abs(ref["b"]).max())
+    mm = orc.linearise(s, cs, orc.Map(transform_points(G, t), _rotate6(Q, ct)), G @ T, 0.1)
+    np.testing.assert_array_equal(mm["corr"], ref["corr"])
+    assert mm["cost"] == pytest.approx(ref["cost"], rel=1e-10)
+
+
+def test_cost_tends_to_point_to_plane_error_in_the_flat_limit():
+    # G-ICP generalises point-to-plane ICP: with source covariances 0 and each target a plane,
+    # C^t = I - (1 - eps) n n^T, a residual d costs |d|^2 + (1/eps - 1)(n.d)^2, so eps * cost tends
+    # to the point-to-plane error sum (n.d)^2 as eps -> 0, and the cost is never below sum |d|^2.
+    rng = np.random.default_rng(14)
+    tgt = np.stack(np.meshgrid(np.arange(5), np.arange(5), np.arange(4)), -1).reshape(-1, 3) * 0.5
+    n = rng.normal(size=tgt.shape)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    delta = rng.uniform(-0.02, 0.02, size=tgt.shape)
+    src = tgt - delta   # at T = I the residual of pair i is mu - x = delta_i
+    p2p = float(np.sum(np.sum(n * delta, axis=1) ** 2))
+    d2 = float(np.sum(delta * delta))
+    for eps in (1e-3, 1e-6):
+        ct = np.array([(np.eye(3) - (1 - eps) * np.outer(v, v))[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]] for v in n])
+        lin = orc.linearise(src, np.zeros((len(src), 6)), orc.Map(tgt, ct), np.eye(4), 0.1)
+        assert lin["inliers"] == len(src) and np.array_equal(lin["corr"], np.arange(len(src)))
+        assert lin["cost"] >= d2 * (1 - 1e-12)
+        assert abs(eps * lin["cost"] - p2p) <= 2 * eps * d2 + 1e-12 * p2p
+
+
 def test_degenerate_when_too_few_inliers():
     src32, tgt32, _ = pair_config1(2, 0, n=500)
     s, t = src32.astype(np.float64), tgt32.astype(np.float64) + 10.0  # far apart: no correspondences
