@@ -1,6 +1,8 @@
-"""The pins catch plausible mistakes: each case plants one mistake in a copy of the C oracle
-(a dropped term, a wrong sign, index or power, a transposed operand), builds the copy, and checks
-that the pins named for it fail on the copy while they pass on the real oracle.  CPU only."""
+"""The pins catch plausible mistakes: each case plants one mistake in a copy of an oracle
+(a dropped term, a wrong sign, index or power, a transposed operand) -- the C oracle, built with
+gcc, or the surrogate's numpy oracle, loaded as a module of its own -- and checks that the pins
+named for it fail on the copy while they pass on the real oracle.  CPU only."""
+import importlib.util
 import os
 import shutil
 
@@ -12,6 +14,7 @@ from oracle.build import compile_shared
 
 from . import test_golden as golden
 from . import test_oracle_pins as pins
+from . import test_surrogate_oracle as spins
 
 HERE = os.path.dirname(os.path.abspath(orc.__file__))
 
@@ -88,3 +91,58 @@ def test_pins_catch_planted_mistake(case, workdir):
                 pin()
     # the real oracle is back in place afterwards
     np.testing.assert_allclose(orc.se3_exp(np.zeros(6)), np.eye(4))
+
+
+# (name, text in oracle/surrogate.py, planted text, names of the surrogate pins that must catch it)
+SURROGATE_MUTANTS = [
+    ("layer 1 not centred",
+     "a += (Ps - Ms * P) @ W1[:, :, dy, dx].T", "a += Ps @ W1[:, :, dy, dx].T",
+     ["test_layer1_equals_brute_force", "test_translation_and_scale_invariance"]),
+    ("convolution with the kernel flipped",
+     "y += _shift(x, dy - R, dx - R) @ W[:, :, dy, dx].T", "y += _shift(x, R - dy, R - dx) @ W[:, :, dy, dx].T",
+     ["test_conv_equals_brute_force"]),
+    ("bfloat16 by truncation",
+     "np.rint(m * 256.0)", "np.trunc(m * 256.0)",
+     ["test_bf16_rounding"]),
+    ("plane covariance with 1 + eps",
+     "k = 1.0 - eps", "k = 1.0 + eps",
+     ["test_plane_covariance_equals_c_oracle_regularisation"]),
+    ("scale aligning by z^-p",
+     "s = np.asarray(z, dtype=np.float64) ** (-2.0 * p)", "s = np.asarray(z, dtype=np.float64) ** (-p)",
+     ["test_plane_covariance_equals_c_oracle_regularisation"]),
+    ("loss 1 + n^T T n",
+     "return float(np.mean(1.0 - q))", "return float(np.mean(1.0 + q))",
+     ["test_loss_values"]),
+    ("gradient without the ReLU gate of layer 2",
+     'da2 = dh2 * (f["a2"] > 0) * Mf', "da2 = dh2 * Mf",
+     ["test_gradient_matches_finite_differences"]),
+    ("gradient without the normalisation's projection",
+     "dv_valid[ok] = (dLdn - n * np.sum(n * dLdn, axis=1, keepdims=True)) / nrm[ok][:, None]",
+     "dv_valid[ok] = dLdn / nrm[ok][:, None]",
+     ["test_gradient_matches_finite_differences"]),
+    ("layer-3 back-propagation shifted the wrong way",
+     "dh2 += _shift(dv @ W3r[:, :, dy, dx], R - dy, R - dx)", "dh2 += _shift(dv @ W3r[:, :, dy, dx], dy - R, dx - R)",
+     ["test_gradient_matches_finite_differences"]),
+    ("Adam without bias correction",
+     "mh = m / (1 - b1 ** t)", "mh = m",
+     ["test_adam_first_step_and_convergence"]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SURROGATE_MUTANTS)), ids=[m[0] for m in SURROGATE_MUTANTS])
+def test_surrogate_pins_catch_planted_mistake(case, monkeypatch):
+    name, old, new, catchers = SURROGATE_MUTANTS[case]
+    path = os.path.join(HERE, "surrogate.py")
+    with open(path) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    spec = importlib.util.spec_from_loader("oracle._planted_surrogate", loader=None)
+    mutant = importlib.util.module_from_spec(spec)
+    exec(compile(src.replace(old, new), path, "exec"), mutant.__dict__)
+    for pin_name in catchers:
+        pin = getattr(spins, pin_name)
+        pin()  # passes on the real oracle
+        with monkeypatch.context() as mp:
+            mp.setattr(spins, "sg", mutant)
+            with pytest.raises(AssertionError):
+                pin()
