@@ -614,6 +614,32 @@ def test_tracker_policy_static_camera(g, ctx):
     trk.close()
 
 
+def test_tracker_mapping_only_keyframe_matches_oracle(g, ctx):
+    """A mapping-only keyframe that sees new geometry (Sec. 3, Additional Keyframe Selection for
+    Mapping) extends the mapping map only, in the library's tracker as in the oracle's."""
+    from oracle.tracker import Tracker as OTracker
+    from synth import look_pose
+    intr = Intrinsics(48, 36, 40.0, 40.0, 23.5, 17.5)
+    scene = make_room(2)
+    P = look_pose(scene.centre + np.array([0.3, -0.2, 0.0]), 0.7, 0.2)
+    depth = raycast_depth(scene, P, intr)
+    d2 = depth.copy()
+    d2[:, 44:] += 0.5  # new geometry in the last 4 columns, under 15 % of the points
+    trk = g.Tracker(ctx, 1, 0.1, 10.0, g.CovParams(20, 1e-3, g.PLANE, 0.0), g.RegParams(0.1, 30, 1e-6, 1e-6, 6))
+    otrk = OTracker(intr.as_array(), stride=1, p=0.0)
+    for f in range(11):
+        dep = d2 if f == 10 else depth
+        T, info = trk.frame(cu(dep), intr.as_array(), P if f == 0 else None)
+        To, io = otrk.frame(dep, P if f == 0 else None)
+        assert info["kind"] == io["kind"], f
+        assert (info["added_tracking"], info["added_mapping"]) == (io["added_tracking"], io["added_mapping"]), f
+        dr, dt = pose_diff(T, To)
+        assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL
+    assert info["kind"] == 2 and info["added_tracking"] == 0 and info["added_mapping"] > 0
+    assert trk.map_sizes() == (len(otrk.track_means), len(otrk.map_means))
+    trk.close()
+
+
 def test_tracker_sequence_matches_oracle(g, ctx):
     """TUM-shaped sequence, 45 frames: the library's tracker and the oracle's take the same
     keyframe decisions, grow maps of the same size (up to points at the overlap radius) and track

@@ -1,7 +1,7 @@
 """The pins catch plausible mistakes: each case plants one mistake in a copy of an oracle
 (a dropped term, a wrong sign, index or power, a transposed operand) -- the C oracle, built with
-gcc, or the surrogate's numpy oracle, loaded as a module of its own -- and checks that the pins
-named for it fail on the copy while they pass on the real oracle.  CPU only."""
+gcc, or the surrogate's or the tracking loop's Python oracle, loaded as a module of its own -- and
+checks that the pins named for it fail on the copy while they pass on the real oracle.  CPU only."""
 import importlib.util
 import os
 import shutil
@@ -15,6 +15,7 @@ from oracle.build import compile_shared
 from . import test_golden as golden
 from . import test_oracle_pins as pins
 from . import test_surrogate_oracle as spins
+from . import test_tracker_policy as tpins
 
 HERE = os.path.dirname(os.path.abspath(orc.__file__))
 
@@ -129,20 +130,56 @@ SURROGATE_MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("case", range(len(SURROGATE_MUTANTS)), ids=[m[0] for m in SURROGATE_MUTANTS])
-def test_surrogate_pins_catch_planted_mistake(case, monkeypatch):
-    name, old, new, catchers = SURROGATE_MUTANTS[case]
-    path = os.path.join(HERE, "surrogate.py")
+# (name, text in oracle/tracker.py, planted text, names of the tracking-loop pins that must catch it)
+TRACKER_MUTANTS = [
+    ("non-overlap filter inverted",
+     "keep = idx < 0", "keep = idx >= 0",
+     ["test_schedule_and_overlap_on_a_static_camera"]),
+    ("forced keyframe one frame late",
+     "self.since_kf >= self.kf[1]", "self.since_kf > self.kf[1]",
+     ["test_schedule_and_overlap_on_a_static_camera"]),
+    ("mapping-only keyframes extend the tracking map",
+     'if info["kind"] == 1:\n                info["added_tracking"]', 'if info["kind"] >= 1:\n                info["added_tracking"]',
+     ["test_mapping_only_keyframe_extends_only_the_mapping_map"]),
+    ("inlier-ratio test reversed",
+     'info["inlier_ratio"] < self.kf[0]', 'info["inlier_ratio"] > self.kf[0]',
+     ["test_low_inlier_ratio_makes_a_keyframe"]),
+]
+
+
+def _planted_module(file_name, old, new, name):
+    path = os.path.join(HERE, file_name)
     with open(path) as fh:
         src = fh.read()
     assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
-    spec = importlib.util.spec_from_loader("oracle._planted_surrogate", loader=None)
+    spec = importlib.util.spec_from_loader("oracle._planted_" + file_name[:-3], loader=None)
     mutant = importlib.util.module_from_spec(spec)
+    mutant.__package__ = "oracle"  # relative imports resolve to the real oracle package
     exec(compile(src.replace(old, new), path, "exec"), mutant.__dict__)
+    return mutant
+
+
+@pytest.mark.parametrize("case", range(len(SURROGATE_MUTANTS)), ids=[m[0] for m in SURROGATE_MUTANTS])
+def test_surrogate_pins_catch_planted_mistake(case, monkeypatch):
+    name, old, new, catchers = SURROGATE_MUTANTS[case]
+    mutant = _planted_module("surrogate.py", old, new, name)
     for pin_name in catchers:
         pin = getattr(spins, pin_name)
         pin()  # passes on the real oracle
         with monkeypatch.context() as mp:
             mp.setattr(spins, "sg", mutant)
+            with pytest.raises(AssertionError):
+                pin()
+
+
+@pytest.mark.parametrize("case", range(len(TRACKER_MUTANTS)), ids=[m[0] for m in TRACKER_MUTANTS])
+def test_tracker_pins_catch_planted_mistake(case, monkeypatch):
+    name, old, new, catchers = TRACKER_MUTANTS[case]
+    mutant = _planted_module("tracker.py", old, new, name)
+    for pin_name in catchers:
+        pin = getattr(tpins, pin_name)
+        pin()  # passes on the real oracle
+        with monkeypatch.context() as mp:
+            mp.setattr(tpins, "Tracker", mutant.Tracker)
             with pytest.raises(AssertionError):
                 pin()

@@ -42,3 +42,19 @@ def test_low_inlier_ratio_makes_a_keyframe():
     _, info = trk.frame(d2, P)
     assert info["inlier_ratio"] < 0.85 and info["kind"] == 1
     assert 0 < info["added_tracking"] <= (d2[:, 32:] > 0).sum()
+
+
+def test_mapping_only_keyframe_extends_only_the_mapping_map():
+    # Sec. 3, Additional Keyframe Selection for Mapping: a mapping-only keyframe's new Gaussians go
+    # to the mapping map; tracking goes on against the keyframes' map alone
+    depth, P = _static_frames()
+    trk = Tracker(SMALL.as_array(), stride=1, p=0.0, force_every=30, mapping_every=10, min_inlier_ratio=0.85)
+    trk.frame(depth, P)
+    n_track, n_map = len(trk.track_means), len(trk.map_means)
+    d2 = depth.copy()
+    d2[:, 44:] += 0.5  # the last 4 of 48 columns move 0.5 m back: new geometry, under 15 % of the points
+    for f in range(1, 11):
+        _, info = trk.frame(d2 if f == 10 else depth)
+    assert info["kind"] == 2 and info["inlier_ratio"] >= 0.85
+    assert info["added_tracking"] == 0 and len(trk.track_means) == n_track
+    assert info["added_mapping"] > 0 and len(trk.map_means) == n_map + info["added_mapping"]
