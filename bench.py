@@ -502,6 +502,7 @@ def run_sequence(args, world, rank, local):
     import torch
 
     import paper_2403_12550_b300 as g
+    from paper_2403_12550_b300.trajectory import ate_rmse, ate_rmse_aligned
     from synth import sequence_config3
 
     torch.cuda.set_device(local)
@@ -531,7 +532,7 @@ def run_sequence(args, world, rank, local):
         one_pass()
     lat, est, kinds, sizes = one_pass()
     lat_ms = np.array(lat[1:]) * 1e3  # frame 0 only builds the first map
-    ate = float(np.sqrt(np.mean([np.sum((a[:3, 3] - b[:3, 3]) ** 2) for a, b in zip(est, seq["poses"])])))
+    ate = ate_rmse(est, seq["poses"])
     out = {
         "metric": SEQ_METRIC, "value": world * len(lat_ms) / (lat_ms.sum() / 1e3), "unit": "frames/s",
         "n_gpus": world, "steps": len(lat_ms), "warmup": args.warmup, "ms_per_step": float(lat_ms.mean()),
@@ -541,7 +542,8 @@ def run_sequence(args, world, rank, local):
                    "k": K_NN, "reg": "plane", "p": P_ALIGN},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
                        "max": float(lat_ms.max())},
-        "ate_m": ate, "keyframes": kinds.count(g.KEYFRAME), "mapping_keyframes": kinds.count(g.MAPPING_KEYFRAME),
+        "ate_m": ate, "ate_aligned_m": ate_rmse_aligned(est, seq["poses"]),
+        "keyframes": kinds.count(g.KEYFRAME), "mapping_keyframes": kinds.count(g.MAPPING_KEYFRAME),
         "map_sizes": list(sizes),
     }
     if rank == 0:
@@ -602,6 +604,7 @@ def run_surrogate(args, world, rank, local):
 
     import paper_2403_12550_b300 as g
     from paper_2403_12550_b300 import surrogate as S
+    from paper_2403_12550_b300.trajectory import ate_rmse, ate_rmse_aligned
     from synth import sequence_config5
 
     torch.cuda.set_device(local)
@@ -645,7 +648,7 @@ def run_surrogate(args, world, rank, local):
     lat_e, _, _, _ = one_pass(True, e2e=True)
 
     def ate(est):
-        return float(np.sqrt(np.mean([np.sum((a[:3, 3] - b[:3, 3]) ** 2) for a, b in zip(est, seq["poses"])])))
+        return ate_rmse(est, seq["poses"])
 
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1800.0
@@ -666,6 +669,7 @@ def run_surrogate(args, world, rank, local):
         "latency_ms": {"p50": float(np.percentile(lat_s, 50)), "p99": float(np.percentile(lat_s, 99)),
                        "knn_p50": float(np.percentile(lat_k, 50)), "knn_p99": float(np.percentile(lat_k, 99))},
         "ate_m": ate(est_s), "ate_knn_m": ate(est_k), "ate_gap_m": ate(est_s) - ate(est_k),
+        "ate_aligned_m": ate_rmse_aligned(est_s, seq["poses"]), "ate_knn_aligned_m": ate_rmse_aligned(est_k, seq["poses"]),
         "surrogate_frames": int(sum(i["cov_source"] == 1 for i in inf_s)),
         "fell_back": int(sum(i["fell_back"] for i in inf_s)),
         "layer_ms": {"grid_l1": float(layers[:, 0].mean()), "l2_tensor": l2_ms, "l3_tensor_cov": float(layers[:, 2].mean())}

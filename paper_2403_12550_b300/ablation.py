@@ -15,10 +15,7 @@ import numpy as np
 import torch
 
 import paper_2403_12550_b300 as g
-
-
-def ate_rmse(est, gt) -> float:
-    return float(np.sqrt(np.mean([np.sum((a[:3, 3] - b[:3, 3]) ** 2) for a, b in zip(est, gt)])))
+from paper_2403_12550_b300.trajectory import ate_rmse, ate_rmse_aligned
 
 
 def run(depths, poses, intr, reg_mode: int, p: float, ctx) -> dict:
@@ -32,7 +29,7 @@ def run(depths, poses, intr, reg_mode: int, p: float, ctx) -> dict:
     dt = time.perf_counter() - t0
     sizes = trk.map_sizes()
     trk.close()
-    return dict(ate_m=ate_rmse(est, poses), keyframes=kinds.count(g.KEYFRAME),
+    return dict(ate_m=ate_rmse(est, poses), ate_aligned_m=ate_rmse_aligned(est, poses), keyframes=kinds.count(g.KEYFRAME),
                 mapping_keyframes=kinds.count(g.MAPPING_KEYFRAME), map_size=sizes[0], seconds=dt)
 
 

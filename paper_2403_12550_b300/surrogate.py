@@ -26,6 +26,8 @@ import time
 
 import numpy as np
 
+from .trajectory import ate_rmse, ate_rmse_aligned
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS_PATH = os.path.join(HERE, "data", "cov_surrogate.npy")
 N_WEIGHTS = 30400
@@ -130,13 +132,6 @@ def train(seed: int = 0, n_frames: int = 2000, n_scenes: int = 20, epochs: int =
 
 # ----------------------------------------------------------------------------- evaluation
 
-def ate_rmse(est, gt) -> float:
-    """Absolute trajectory error: RMSE of the camera positions (no alignment: both trajectories
-    start from the ground-truth first pose)."""
-    d = np.array([e[:3, 3] - t[:3, 3] for e, t in zip(est, gt)])
-    return float(np.sqrt(np.mean(np.sum(d * d, axis=1))))
-
-
 def evaluate(weights=None, seed: int = 0, n_frames: int = 500, fallback_ratio: float = 1.1, calib_every: int = 30,
              keyframe_knn: bool = True, workers: int | None = None, frames=None, log=print, modes=("knn", "surrogate")) -> dict:
     import torch
@@ -177,7 +172,7 @@ def evaluate(weights=None, seed: int = 0, n_frames: int = 500, fallback_ratio: f
             est.append(T)
             infos.append(info)
         wall = time.perf_counter() - t0
-        res = dict(frames_per_s=n_frames / wall, ate_m=ate_rmse(est, gt),
+        res = dict(frames_per_s=n_frames / wall, ate_m=ate_rmse(est, gt), ate_aligned_m=ate_rmse_aligned(est, gt),
                    p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
                    keyframes=int(sum(i["kind"] == g.KEYFRAME for i in infos)),
                    surrogate_frames=int(sum(i["cov_source"] == 1 for i in infos)),
