@@ -36,7 +36,7 @@ WORKLOAD = "replica-shaped frame: 1200x680 depth, stride 2 (~204k pts), 2.04M-Ga
 STRIDE, Z_MIN, Z_MAX = 2, 0.1, 10.0
 K_NN, EPS, P_ALIGN = 20, 1e-3, 1.5
 MAX_DIST, MAX_ITERS, TOL = 0.1, 30, 1e-6
-# bytes the method must move per unit:
+# algorithmic bytes the method must move per unit (the roofline numerators):
 BYTES_PER_POINT_ITER = 72      # x 12 + C_s 24 + mu 12 + C_t 24
 BYTES_PER_POINT_COV = 40       # read x 12 + z 4, write C 24
 BYTES_PER_MAP_GAUSSIAN = 84 + 48  # read mean 12 + cov 24 (x2: bbox/morton and gather) + write 16 + 32
@@ -349,16 +349,16 @@ def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-def cpu_baseline(f, seed, budget_s: float = 10.0):
+def cpu_baseline(f, seed, sample_s: float = 10.0):
     """The oracle on this host's cores: whole frames of the same workload, repeated until about
-    ``budget_s`` seconds have passed (at least one)."""
+    ``sample_s`` seconds have passed (at least one)."""
     omap = oracle_setup(f)
     frames, t0 = 0, time.perf_counter()
     while True:
         r = oracle_frame(f, omap)
         frames += 1
         dt = time.perf_counter() - t0
-        if dt >= budget_s:
+        if dt >= sample_s:
             break
     return {"value": frames / dt, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
             "sample": f"{frames} full frames in {dt:.1f} s (each: a1 + k-NN covariances of ~204k points + "
@@ -375,8 +375,8 @@ def run_reference(args, world, rank):
     t0 = time.perf_counter()
     oracle_frame(f, omap)
     t_full = time.perf_counter() - t0
-    budget = 150.0  # seconds for the whole run
-    frac = min(1.0, budget / max((args.steps + args.warmup) * t_full, 1e-9))
+    run_s = 150.0  # seconds of oracle work for the whole run
+    frac = min(1.0, run_s / max((args.steps + args.warmup) * t_full, 1e-9))
     for _ in range(max(args.warmup - 1, 0)):
         oracle_frame(f, omap, frac)
     times = []
@@ -556,11 +556,11 @@ SURR_METRIC = "G-ICP tracking frames/s with learned covariances (640x480 held-ou
 FLOP_PER_PIXEL_L2 = 2 * 32 * 32 * 25
 
 
-def surrogate_cpu_baseline(frames, seq, budget_s: float = 15.0) -> dict:
+def surrogate_cpu_baseline(frames, seq, sample_s: float = 15.0) -> dict:
     """The oracle on this host's cores for the learned-covariance workload: per frame the FP64 network
     forward and covariances, then the FP64 registration against a map built from the previous frame
     (its oracle k-NN covariances, in the world frame by the ground-truth pose); frames in order until
-    about budget_s of work."""
+    about sample_s of work."""
     import oracle as orc
     from oracle import surrogate as sgo
     from paper_2403_12550_b300 import surrogate as S
@@ -584,7 +584,7 @@ def surrogate_cpu_baseline(frames, seq, budget_s: float = 15.0) -> dict:
         mcw = np.stack([Cw[:, 0, 0], Cw[:, 0, 1], Cw[:, 0, 2], Cw[:, 1, 1], Cw[:, 1, 2], Cw[:, 2, 2]], 1)
         orc.register(P[M], covs, orc.Map(wm, mcw), seq["poses"][f - 1], MAX_DIST, MAX_ITERS, TOL, TOL, 6)
         done += 1
-        if time.perf_counter() - t0 > budget_s:
+        if time.perf_counter() - t0 > sample_s:
             break
     el = time.perf_counter() - t0
     return {"value": done / el, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",

@@ -7,7 +7,8 @@ import numpy as np
 import oracle as orc
 from synth import REPLICA_INTR, frame_config2, pair_config1, transform_points
 
-# Tolerances ("Parity bars").
+# Tolerances: poses within 1e-4 rad and 1e-5 m and covariances within 1e-4 relative Frobenius of
+# the FP64 oracle; k-NN sets identical except swaps among candidates whose distances tie within 1e-6.
 POSE_ROT_TOL = 1e-4      # rad
 POSE_TRANS_TOL = 1e-5    # m
 COV_REL_TOL = 1e-4       # relative Frobenius
