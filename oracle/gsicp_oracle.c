@@ -29,6 +29,9 @@
  *   - the weight W = Sigma^-1 is held fixed while linearising;
  *   - left perturbation T <- exp(xi^) T, xi = (omega, v);
  *   - stop when |d omega| < tol_rot and |d v| < tol_trans.
+ *
+ * Parity unpinned: the ellipse floor at eps and the line-like threshold RANK_TOL are readings with
+ * nothing outside this file to check them against (the tests exercise them, they cannot pin them).
  */
 #include "gsicp_oracle.h"
 
