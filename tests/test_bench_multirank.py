@@ -36,3 +36,15 @@ def test_single_rank_is_unchanged():
     import bench
     assert bench.max_over_ranks(3.0, 1, "cpu") == 3.0
     assert bench.job_throughput(1, 20, 0.5) == pytest.approx(40.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
+    # under torchrun the oracle arm runs and prints on rank 0 alone; another rank returns at once
+    import argparse
+    import time
+
+    import bench
+    monkeypatch.setattr(bench, "oracle_setup", lambda f: pytest.fail("rank 1 must not run the oracle"))
+    t0 = time.perf_counter()
+    bench.run_reference(argparse.Namespace(steps=3, warmup=3, seed=0), 2, 1)
+    assert time.perf_counter() - t0 < 1.0 and capsys.readouterr().out == ""
