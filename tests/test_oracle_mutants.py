@@ -144,6 +144,9 @@ TRACKER_MUTANTS = [
     ("inlier-ratio test reversed",
      'info["inlier_ratio"] < self.kf[0]', 'info["inlier_ratio"] > self.kf[0]',
      ["test_low_inlier_ratio_makes_a_keyframe"]),
+    ("motion model composed in the wrong order",
+     "T = T1 @ (inv2 @ T1)", "T = T1 @ (T1 @ inv2)",
+     ["test_constant_velocity_prediction_on_a_screw_trajectory"]),
 ]
 
 
@@ -181,5 +184,6 @@ def test_tracker_pins_catch_planted_mistake(case, monkeypatch):
         pin()  # passes on the real oracle
         with monkeypatch.context() as mp:
             mp.setattr(tpins, "Tracker", mutant.Tracker)
+            mp.setattr("oracle.tracker._predict", mutant._predict)
             with pytest.raises(AssertionError):
                 pin()

@@ -58,3 +58,23 @@ def test_mapping_only_keyframe_extends_only_the_mapping_map():
     assert info["kind"] == 2 and info["inlier_ratio"] >= 0.85
     assert info["added_tracking"] == 0 and len(trk.track_means) == n_track
     assert info["added_mapping"] > 0 and len(trk.map_means) == n_map + info["added_mapping"]
+
+
+def test_constant_velocity_prediction_on_a_screw_trajectory():
+    # the motion model (a reading: constant velocity) predicts T_k exactly on T_k = T_0 D^k, and
+    # returns a proper rotation for a slightly non-orthonormal input
+    from oracle.tracker import _predict
+    from synth import make_pose, rot_axis_angle
+    T0 = make_pose(rot_axis_angle([0.3, -0.2, 0.9], 0.4), [1.0, -2.0, 0.5])
+    D = make_pose(rot_axis_angle([0.5, 1.0, -0.3], 0.05), [0.02, -0.01, 0.03])
+    traj = [T0]
+    for _ in range(6):
+        traj.append(traj[-1] @ D)
+    for k in range(2, 7):
+        np.testing.assert_allclose(_predict(traj[k - 1], traj[k - 2]), traj[k], atol=1e-12)
+    np.testing.assert_array_equal(_predict(traj[3], None), traj[3])
+    bent = traj[4].copy()
+    bent[:3, :3] *= 1.0 + 1e-4
+    R = _predict(bent, traj[3])[:3, :3]
+    np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+    assert abs(np.linalg.det(R) - 1.0) < 1e-12
