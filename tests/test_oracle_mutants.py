@@ -63,6 +63,10 @@ MUTANTS = [
     ("k-d tree prunes the far side too early",
      "if (diff * diff <= L->d[L->k - 1])", "if (diff * diff <= 0.25 * L->d[L->k - 1])",
      [lambda: pins.test_knn_tree_equals_brute_force(2000, 20, 200), lambda: pins.test_radius_nn_tree_equals_brute_force(0)]),
+    ("Gaussians moved by R^T instead of R",
+     "pts_out[3 * i + r] = R[3 * r] * x[0] + R[3 * r + 1] * x[1] + R[3 * r + 2] * x[2] + t[r];",
+     "pts_out[3 * i + r] = R[r] * x[0] + R[3 + r] * x[1] + R[6 + r] * x[2] + t[r];",
+     [pins.test_transform_gaussians_is_a_rigid_motion]),
     ("back-projection with cx in place of cy",
      "((double)v - cy) * d / fy", "((double)v - cx) * d / fy",
      [pins.test_depth_to_points_on_analytic_plane]),

@@ -209,6 +209,33 @@ def _hat(xi):
     return M
 
 
+def test_transform_gaussians_is_a_rigid_motion():
+    # moving Gaussians by T keeps pairwise distances and each covariance's spectrum, moves the
+    # camera-frame origin to T's translation, and two moves compose as their product T2 T1
+    rng = np.random.default_rng(15)
+    p = rng.normal(size=(40, 3))
+    c6 = np.array([(lambda A: (A @ A.T)[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]])(rng.normal(size=(3, 3)))
+                   for _ in range(40)])
+    T1, T2 = random_offset(rng, 50.0, 1.0), random_offset(rng, 120.0, 2.0)
+    q, d = orc.transform_gaussians(T1, p, c6)
+    iu = np.triu_indices(40, 1)
+    dist = lambda a: np.linalg.norm(a[:, None] - a[None], axis=-1)[iu]
+    np.testing.assert_allclose(dist(q), dist(p), rtol=1e-12)
+    for a, b in zip(c6, d):
+        np.testing.assert_allclose(np.linalg.eigvalsh(_sym(b)), np.linalg.eigvalsh(_sym(a)), rtol=1e-10, atol=1e-12)
+    o, _ = orc.transform_gaussians(T1, np.zeros((1, 3)))
+    np.testing.assert_allclose(o[0], T1[:3, 3], atol=1e-15)
+    q2, d2 = orc.transform_gaussians(T2, q, d)
+    q12, d12 = orc.transform_gaussians(T2 @ T1, p, c6)
+    np.testing.assert_allclose(q2, q12, atol=1e-12)
+    np.testing.assert_allclose(d2, d12, atol=1e-12 * np.abs(d12).max())
+    # a handedness check: the x and y axes move to vectors whose cross product is the moved z axis
+    ax, _ = orc.transform_gaussians(T1, np.eye(3))
+    e = ax - T1[:3, 3]
+    np.testing.assert_allclose(np.cross(e[0], e[1]), e[2], atol=1e-12)
+    np.testing.assert_allclose(e, T1[:3, :3].T, atol=1e-12)
+
+
 @pytest.mark.parametrize("scale", [0.0, 1e-12, 1e-7, 1e-4, 1e-3, 0.1, 1.0, 3.0])
 def test_se3_exp_matches_expm(scale):
     rng = np.random.default_rng(int(scale * 1e6) % 1000)
