@@ -57,6 +57,12 @@ MUTANTS = [
     ("Gauss-Newton step +H^-1 b",
      "nb[a] = -b[a];", "nb[a] = b[a];",
      [pins.test_exact_recovery_on_noise_free_room]),
+    ("back substitution with L for L^T",
+     "for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];", "for (int k = i + 1; k < 6; ++k) s -= L[6 * i + k] * x[k];",
+     [pins.test_one_gauss_newton_step_solves_the_normal_equations]),
+    ("pose update on the right",
+     "    pose_mul(E, T, T);", "    pose_mul(T, E, T);",
+     [pins.test_one_gauss_newton_step_solves_the_normal_equations]),
     ("distance ties to the larger index",
      "(d == e && i < j)", "(d == e && i > j)",
      [pins.test_knn_ties_break_to_smaller_index]),

@@ -307,6 +307,24 @@ def test_gradient_and_hessian_match_finite_differences():
     np.testing.assert_allclose(Hn, 2 * lin0["H"], rtol=1e-4, atol=1e-4 * np.abs(lin0["H"]).max())
 
 
+def test_one_gauss_newton_step_solves_the_normal_equations():
+    # one iteration from T0 moves to exp(delta^) T0 with H delta = -b for the H, b of the
+    # linearisation at T0: the step recovered by the matrix logarithm (scipy) solves the system
+    from scipy.linalg import logm
+    src32, tgt32, T_gt = pair_config1(2, 1, n=1500)
+    s, t = src32.astype(np.float64), tgt32.astype(np.float64)
+    cs = orc.source_covariances(s, k=20, reg_mode=orc.PLANE)["covs"]
+    ct = orc.source_covariances(t, k=20, reg_mode=orc.PLANE)["covs"]
+    m = orc.Map(t, ct)
+    T0 = T_gt @ random_offset(np.random.default_rng(16), 2.0, 0.02)
+    lin = orc.linearise(s, cs, m, T0, 0.1)
+    r = orc.register(s, cs, m, T0, 0.1, 1)
+    assert r["iters"] == 1 and np.allclose(r["H"], lin["H"], rtol=1e-12) and np.allclose(r["b"], lin["b"], rtol=1e-12)
+    L = np.real(logm(r["T"] @ np.linalg.inv(T0)))
+    delta = np.array([L[2, 1], L[0, 2], L[1, 0], L[0, 3], L[1, 3], L[2, 3]])
+    np.testing.assert_allclose(lin["H"] @ delta, -lin["b"], rtol=1e-7, atol=1e-8 * np.abs(lin["b"]).max())
+
+
 def _kabsch(P, Q):
     """Least-squares rigid transform mapping P onto Q (Umeyama/Kabsch, via SVD)."""
     mp, mq = P.mean(0), Q.mean(0)
