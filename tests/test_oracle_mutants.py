@@ -48,6 +48,9 @@ MUTANTS = [
     ("Jacobi rotation of the eigenvectors with a wrong sign",
      "Q[r][q] = s * qrp + c * qrq;", "Q[r][q] = -s * qrp + c * qrq;",
      [pins.test_eigh3_matches_lapack]),
+    ("eigenvalues sorted in descending order",
+     "if (d[order[j]] < d[order[i]])", "if (d[order[j]] > d[order[i]])",
+     [pins.test_eigh3_matches_lapack, pins.test_regularisation_closed_forms]),
     ("SE(3) exp: translation factor with sin(th)/th",
      "Vm[i] = id + B * K[i] + Cc * K2[i];", "Vm[i] = id + A * K[i] + Cc * K2[i];",
      [lambda: pins.test_se3_exp_matches_expm(1.0), lambda: golden.test_oracle_se3_exp("quarter_turn_z")]),
@@ -134,6 +137,14 @@ SURROGATE_MUTANTS = [
     ("layer-3 back-propagation shifted the wrong way",
      "dh2 += _shift(dv @ W3r[:, :, dy, dx], R - dy, R - dx)", "dh2 += _shift(dv @ W3r[:, :, dy, dx], dy - R, dx - R)",
      ["test_gradient_matches_finite_differences"]),
+    ("grid back-projection with cx in place of cy",
+     "P = np.stack([(u - cx) * dz / fx, (v - cy) * dz / fy, dz], axis=-1)",
+     "P = np.stack([(u - cx) * dz / fx, (v - cx) * dz / fy, dz], axis=-1)",
+     ["test_point_grid_equals_c_oracle_points"]),
+    ("k-NN projector with the wrong sign",
+     "return (np.eye(3)[None] - full * s[:, None, None]) / (1.0 - eps)",
+     "return (np.eye(3)[None] + full * s[:, None, None]) / (1.0 - eps)",
+     ["test_plane_covariance_equals_c_oracle_regularisation"]),
     ("Adam without bias correction",
      "mh = m / (1 - b1 ** t)", "mh = m",
      ["test_adam_first_step_and_convergence"]),
