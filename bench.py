@@ -359,7 +359,8 @@ def oracle_frame(f, omap, frac: float = 1.0, seed: int = 0):
 
 
 def oracle_threads():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    import oracle as orc
+    return orc.threads()
 
 
 def orc_points(f):
@@ -370,7 +371,9 @@ def orc_points(f):
 def cpu_baseline(f, seed, sample_s: float = 10.0):
     """The oracle on this host's cores: whole steps of the same workload (map-index rebuild, a1,
     covariances, registration), repeated until about ``sample_s`` seconds have passed (at least one)."""
+    import oracle as orc
     omap = oracle_setup(f)
+    cores = orc.threads()
     frames, t_index, t0 = 0, 0.0, time.perf_counter()
     while True:
         r, _, _, ti = oracle_frame(f, omap)
@@ -379,8 +382,17 @@ def cpu_baseline(f, seed, sample_s: float = 10.0):
         dt = time.perf_counter() - t0
         if dt >= sample_s:
             break
-    return {"value": frames / dt, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
+    # one more step on a single thread
+    orc.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle_frame(f, omap)
+        t_single = time.perf_counter() - t1
+    finally:
+        orc.set_threads(cores)
+    return {"value": frames / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "tracking_only_frames_per_s": frames / (dt - t_index),
+            "single_thread": {"value": 1.0 / t_single, "unit": "frames/s", "sample": "1 full step on one thread"},
             "sample": f"{frames} full steps in {dt:.1f} s (each: k-d tree rebuild over the 2.04M map means + a1 + "
                       f"k-NN covariances of ~204k points + {r['iters']} GN iterations), FP64 C oracle with OpenMP "
                       f"over points (the k-d tree build is serial: {1e3 * t_index / frames:.0f} ms a step); the map's "

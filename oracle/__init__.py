@@ -83,7 +83,18 @@ def _bind(lib):
                                  C.POINTER(C.c_int), _D, C.POINTER(C.c_long)]
     lib.orc_register_fixed.argtypes = [_D, _D, C.c_long, _D, _D, _D, C.POINTER(RegParams), _D,
                                        C.POINTER(C.c_int), _D]
+    lib.orc_set_threads.argtypes = [C.c_int]
+    lib.orc_threads.restype = C.c_int
     return lib
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for the oracle's per-point loops from now on (n <= 0: all processors)."""
+    _load().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().orc_threads())
 
 
 def _d(a, shape_last=None) -> np.ndarray:

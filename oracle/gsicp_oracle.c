@@ -37,6 +37,7 @@
 
 #include <float.h>
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -749,3 +750,11 @@ int orc_register_fixed(const double* src, const double* covs_s, long n, const do
     if (cost) *cost = c;
     return status;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* threads                                                                                    */
+/* ------------------------------------------------------------------------------------------ */
+
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+
+int orc_threads(void) { return omp_get_max_threads(); }

@@ -101,6 +101,11 @@ int orc_register_fixed(const double* src, const double* covs_s, long n, const do
                        const double* covs_t, const double T0[16], const orc_reg_params* prm,
                        double T_out[16], int* iters, double* cost);
 
+/* OpenMP threads used by the per-point loops from now on (n <= 0: all processors), and how many
+ * that is.  Results do not depend on it. */
+void orc_set_threads(int n);
+int orc_threads(void);
+
 #ifdef __cplusplus
 }
 #endif
