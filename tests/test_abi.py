@@ -6,6 +6,7 @@ import re
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -124,3 +125,20 @@ def test_product_never_touches_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower(), f
+
+
+def test_binding_rejects_host_or_mistyped_tensors_before_the_call():
+    # the binding hands the library device pointers only: a host tensor, another dtype, a strided
+    # view or a wrong row width is refused in Python, before any C call
+    import torch
+    import paper_2403_12550_b300 as g
+    for bad in (torch.zeros(4, 3), torch.zeros(4, 3, dtype=torch.float64), torch.zeros(3, 4).t()):
+        with pytest.raises(TypeError):
+            g._dev(bad, cols=3)
+    assert g._dev(None) is None
+    pose = g._pose(np.arange(16.0).reshape(4, 4))
+    assert list(pose) == list(np.arange(16.0))
+    with pytest.raises(g.GsicpError) as e:
+        g._check(g.ERR_INVALID_ARG, "somewhere")
+    assert "somewhere" in str(e.value)
+    assert g._check(g.ERR_DEGENERATE, "x", allow=(g.ERR_DEGENERATE,)) == g.ERR_DEGENERATE
