@@ -104,3 +104,39 @@ def test_cuda_source_covariances_on_the_star(case, p):
             assert err.max() <= COV_REL_TOL, (key, err)
     finally:
         ctx.close()
+
+
+def test_fixture_values_follow_from_their_derivation():
+    # the stored numbers are the closed forms written in the fixtures, evaluated exactly (rational
+    # arithmetic for the stars, sympy's symbolic matrix exponential for SE(3)), independent of
+    # the oracle: a typo in a fixture fails here
+    from fractions import Fraction as F
+
+    import sympy as sp
+
+    def exact(v):
+        return [F(str(x)) for x in v]
+
+    def outer(a, b):
+        return [[a[i] * b[j] for j in range(3)] for i in range(3)]
+
+    def six(M):
+        return [M[0][0], M[0][1], M[0][2], M[1][1], M[1][2], M[2][2]]
+
+    for c in STARS.values():
+        u, v, w = exact(c["u"]), exact(c["v"]), exact(c["w"])
+        a, b, wl, eps = F(str(c["a"][0])), F(str(c["b"][0])), F(str(c["w_len"][0])), F(str(c["eps"][0]))
+        uu, vv, ww = outer(u, u), outer(v, v), outer(w, w)
+        S = [[a * a * uu[i][j] + b * b * vv[i][j] + wl * wl * ww[i][j] for j in range(3)] for i in range(3)]
+        raw = [[S[i][j] / 3 for j in range(3)] for i in range(3)]
+        plane = [[(1 if i == j else 0) - (1 - eps) * uu[i][j] for j in range(3)] for i in range(3)]
+        ellipse = [[S[i][j] / (b * b) for j in range(3)] for i in range(3)]
+        for key, M in (("none", raw), ("plane", plane), ("ellipse", ellipse)):
+            np.testing.assert_allclose(c[key], [float(x) for x in six(M)], rtol=1e-15, atol=1e-15)
+
+    for c in SE3.values():
+        wx, wy, wz, vx, vy, vz = (sp.nsimplify(x, [sp.pi]) for x in c["xi"])
+        X = sp.Matrix([[0, -wz, wy, vx], [wz, 0, -wx, vy], [-wy, wx, 0, vz], [0, 0, 0, 0]])
+        E = sp.simplify(X.exp())
+        np.testing.assert_allclose(np.array(E[:3, :3].evalf(), dtype=float).ravel(), c["R"], atol=1e-15)
+        np.testing.assert_allclose(np.array(E[:3, 3].evalf(), dtype=float).ravel(), c["t"], atol=1e-15)
