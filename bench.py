@@ -517,6 +517,8 @@ def run_batch(args, world, rank, local):
         "gpu_launches": K * batch_launches(n_pts),
         "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = batch_cpu_baseline(pairs)
     if rank == 0:
         print(json.dumps(out), flush=True)
     for m in maps:
@@ -527,6 +529,53 @@ def run_batch(args, world, rank, local):
 # ----------------------------------------------------------------------------- tracking sequence
 
 SEQ_METRIC = "tracked frames/s and per-frame latency (640x480 sequence, keyframe appends, tracking loop)"
+
+
+def batch_cpu_baseline(pairs, sample_s: float = 15.0) -> dict:
+    """The oracle on the same pairs, in a seeded random order, until about sample_s seconds of
+    registration: each pair's covariances and k-d tree built untimed (as the batched step takes
+    them prebuilt), its registration from T0 = I timed.  The whole batch's time is estimated from
+    the sample's time per source point (registration cost is linear in the points)."""
+    import oracle as orc
+    done, reg_s, pts = 0, 0.0, 0
+    total = sum(len(p["src"]) for p in pairs)
+    for i in np.random.default_rng(0).permutation(len(pairs)):
+        p = pairs[i]
+        cs = orc.source_covariances(p["src"], k=K_NN, eps=EPS, reg_mode=orc.PLANE)["covs"]
+        ct = orc.source_covariances(p["tgt"], k=K_NN, eps=EPS, reg_mode=orc.PLANE)["covs"]
+        m = orc.Map(p["tgt"], ct)
+        t0 = time.perf_counter()
+        orc.register(p["src"], cs, m, np.eye(4), MAX_DIST, MAX_ITERS, TOL, TOL, 6)
+        reg_s += time.perf_counter() - t0
+        done += 1
+        pts += len(p["src"])
+        if reg_s >= sample_s:
+            break
+    batch_s = reg_s * total / pts
+    return {"value": len(pairs) / batch_s, "unit": "registrations/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"{done} of the {len(pairs)} pairs in a seeded random order ({pts} of {total} source points), "
+                      f"registration only ({reg_s:.1f} s); the batch's time scaled from the sample's time per "
+                      f"source point; FP64 C oracle with OpenMP over points"}
+
+
+def sequence_cpu_baseline(seq, n_frames: int, sample_s: float = 20.0) -> dict:
+    """The oracle's tracking loop (same keyframe policy) over the sequence's frames in order until
+    about sample_s seconds of work; every frame's full tracker step is timed."""
+    from oracle.tracker import Tracker as OTracker
+    trk = OTracker(seq["intr"].as_array(), stride=STRIDE, z_min=Z_MIN, z_max=Z_MAX, k=K_NN, eps=EPS, p=P_ALIGN,
+                   max_dist=MAX_DIST, max_iters=MAX_ITERS, tol_rot=TOL, tol_trans=TOL)
+    done, el = 0, 0.0
+    for f in range(n_frames):
+        depth = seq["depth"](f)
+        t0 = time.perf_counter()
+        trk.frame(depth, seq["poses"][0] if f == 0 else None)
+        el += time.perf_counter() - t0
+        done += 1
+        if el >= sample_s:
+            break
+    return {"value": done / el, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"the first {done} of {n_frames} frames through the oracle's tracking loop ({el:.1f} s; "
+                      f"frame 0 builds the first map)"}
 
 
 def run_sequence(args, world, rank, local):
@@ -580,6 +629,8 @@ def run_sequence(args, world, rank, local):
         "keyframes": kinds.count(g.KEYFRAME), "mapping_keyframes": kinds.count(g.MAPPING_KEYFRAME),
         "map_sizes": list(sizes),
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = sequence_cpu_baseline(seq, args.frames)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
