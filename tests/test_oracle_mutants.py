@@ -124,6 +124,9 @@ SURROGATE_MUTANTS = [
     ("scale aligning by z^-p",
      "s = np.asarray(z, dtype=np.float64) ** (-2.0 * p)", "s = np.asarray(z, dtype=np.float64) ** (-p)",
      ["test_plane_covariance_equals_c_oracle_regularisation"]),
+    ("isotropic fallback without scale aligning's square",
+     "        s = z[~ok] ** (-2.0 * p)", "        s = z[~ok] ** (-p)",
+     ["test_zero_prediction_gives_isotropic_covariance_and_full_loss"]),
     ("loss 1 + n^T T n",
      "return float(np.mean(1.0 - q))", "return float(np.mean(1.0 + q))",
      ["test_loss_values"]),

@@ -173,3 +173,17 @@ def test_adam_first_step_and_convergence():
     for t in range(1, 3001):
         w, m, s = sg.adam_step(w, w.copy(), m, s, t, 0.05)
     assert np.abs(w).max() < 0.05
+
+
+def test_zero_prediction_gives_isotropic_covariance_and_full_loss():
+    # where the network predicts v = 0 the normal is undefined: the covariance is z^(-2p) I (the
+    # plane form has no direction to use) and the pixel counts as loss 1
+    M = np.ones((1, 2), bool)
+    P = np.array([[[0.0, 0.0, 2.0], [0.1, 0.0, 4.0]]])
+    v = np.array([[[0.0, 0.0, 0.0], [0.0, 0.0, 3.0]]])
+    C, ok = sg.covariances(v, M, P, 1e-3, 1.5)
+    assert ok.tolist() == [False, True]
+    np.testing.assert_allclose(C[0], np.array([1, 0, 0, 1, 0, 1]) * 2.0 ** -3, rtol=1e-15)
+    np.testing.assert_allclose(C[1], sg.plane_covariance(np.array([0.0, 0.0, 1.0]), 4.0, 1e-3, 1.5), rtol=1e-15)
+    T = np.repeat(np.diag([0.0, 0.0, 1.0])[None], 2, axis=0)
+    assert sg.loss(v, M, T) == pytest.approx(0.5, abs=1e-15)
