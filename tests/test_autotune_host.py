@@ -1,0 +1,64 @@
+"""The batch autotuner's host logic on CPU: every candidate index shape is built and timed, its
+maps are released, the fastest wins (ties to the earlier candidate), and a keyed result is reused."""
+import pytest
+
+from paper_2403_12550_b300 import RegParams
+from paper_2403_12550_b300 import autotune as at
+
+
+class _Map:
+    live = 0
+
+    def __init__(self, shape):
+        self.shape = shape
+        _Map.live += 1
+
+    def close(self):
+        _Map.live -= 1
+
+
+@pytest.fixture()
+def fake_maps(monkeypatch):
+    built = []
+
+    def build(ctx, t, c, bucket, cell):
+        built.append((bucket, cell))
+        return _Map((bucket, cell))
+    monkeypatch.setattr(at, "gsicp_build_map_index", build)
+    monkeypatch.setattr(at.torch.cuda, "get_device_name", lambda *a: "fake")
+    at._CACHE.clear()
+    yield built
+    at._CACHE.clear()
+
+
+def test_fastest_shape_wins_and_maps_are_released(fake_maps):
+    ms = {(16, 0.008): 3.0, (8, 0.008): 2.5, (32, 0.008): 4.0, (16, 0.005): 2.5, (16, 0.012): 2.7, (8, 0.005): 9.0}
+    seen = []
+
+    def timer(ctx, srcs, scovs, maps, T0s, params, reps):
+        assert len(maps) == 2 and reps == 3 and _Map.live == 2
+        seen.append(maps[0].shape)
+        return ms[maps[0].shape]
+    r = at.tune_index_params(None, [0, 1], [0, 1], ["t0", "t1"], ["c0", "c1"], None, RegParams(), timer=timer)
+    assert seen == list(at.CANDIDATES) and len(fake_maps) == 2 * len(at.CANDIDATES)
+    assert (r["bucket"], r["cell"]) == (8, 0.008)  # 2.5 ms, first of the two tied
+    assert r["ms"] == ms and _Map.live == 0
+
+
+def test_keyed_result_is_reused(fake_maps):
+    calls = []
+
+    def timer(*a):
+        calls.append(1)
+        return 1.0
+    r1 = at.tune_index_params(None, [0], [0], ["t"], ["c"], None, RegParams(), key="w", timer=timer)
+    r2 = at.tune_index_params(None, [0], [0], ["t"], ["c"], None, RegParams(), key="w", timer=timer)
+    assert r1 is r2 and len(calls) == len(at.CANDIDATES)
+
+
+def test_maps_are_released_when_timing_fails(fake_maps):
+    def timer(*a):
+        raise RuntimeError("batch failed")
+    with pytest.raises(RuntimeError):
+        at.tune_index_params(None, [0], [0], ["t"], ["c"], None, RegParams(), timer=timer)
+    assert _Map.live == 0
