@@ -25,6 +25,7 @@ def _read(name):
 
 STARS = _read("regularisation_star.ini")
 SE3 = _read("se3_exp.ini")
+LIN = _read("linearise_single.ini")
 
 
 def star_points(c):
@@ -39,6 +40,10 @@ def star_points(c):
 def test_fixtures_are_well_formed():
     assert set(STARS) == {"star_345", "star_axes_yxz"} and set(SE3) == {"translation_only", "quarter_turn_z",
                                                                       "half_turn_x"}
+    assert set(LIN) == {"identity_pose", "quarter_turn_z"}
+    for c in LIN.values():
+        assert c["T"].shape == (16,) and c["H"].shape == (36,) and c["b"].shape == (6,)
+        np.testing.assert_array_equal(c["H"].reshape(6, 6), c["H"].reshape(6, 6).T)
     for c in STARS.values():
         F = np.stack([c["u"], c["v"], c["w"]])
         np.testing.assert_allclose(F @ F.T, np.eye(3), atol=1e-15)
@@ -134,9 +139,38 @@ def test_fixture_values_follow_from_their_derivation():
         for key, M in (("none", raw), ("plane", plane), ("ellipse", ellipse)):
             np.testing.assert_allclose(c[key], [float(x) for x in six(M)], rtol=1e-15, atol=1e-15)
 
+    for c in LIN.values():
+        T = sp.Matrix(4, 4, [sp.nsimplify(v) for v in c["T"]])
+        R, t = T[:3, :3], T[:3, 3]
+        x = sp.Matrix([sp.nsimplify(v) for v in c["x"]])
+        mu = sp.Matrix([sp.nsimplify(v) for v in c["mu"]])
+
+        def sym3(v):
+            a, b_, c_, d_, e_, f_ = (sp.nsimplify(q) for q in v)
+            return sp.Matrix([[a, b_, c_], [b_, d_, e_], [c_, e_, f_]])
+        y = R * x + t
+        d = mu - y
+        W = (sym3(c["ct"]) + R * sym3(c["cs"]) * R.T).inv()
+        Y = sp.Matrix([[0, -y[2], y[1]], [y[2], 0, -y[0]], [-y[1], y[0], 0]])
+        J = Y.row_join(-sp.eye(3))
+        np.testing.assert_allclose(float((d.T * W * d)[0]), c["cost"][0], rtol=1e-15)
+        np.testing.assert_allclose(np.array((J.T * W * d).evalf(), dtype=float).ravel(), c["b"], atol=1e-15)
+        np.testing.assert_allclose(np.array((J.T * W * J).evalf(), dtype=float).ravel(), c["H"], atol=1e-15)
+
     for c in SE3.values():
         wx, wy, wz, vx, vy, vz = (sp.nsimplify(x, [sp.pi]) for x in c["xi"])
         X = sp.Matrix([[0, -wz, wy, vx], [wz, 0, -wx, vy], [-wy, wx, 0, vz], [0, 0, 0, 0]])
         E = sp.simplify(X.exp())
         np.testing.assert_allclose(np.array(E[:3, :3].evalf(), dtype=float).ravel(), c["R"], atol=1e-15)
         np.testing.assert_allclose(np.array(E[:3, 3].evalf(), dtype=float).ravel(), c["t"], atol=1e-15)
+
+
+@pytest.mark.parametrize("case", sorted(LIN))
+def test_oracle_linearise_one_correspondence(case):
+    c = LIN[case]
+    m = orc.Map(c["mu"][None], c["ct"][None])
+    lin = orc.linearise(c["x"][None], c["cs"][None], m, c["T"].reshape(4, 4), 0.5)
+    assert lin["inliers"] == 1
+    assert lin["cost"] == pytest.approx(c["cost"][0], rel=1e-12)
+    np.testing.assert_allclose(lin["b"], c["b"], atol=1e-15)
+    np.testing.assert_allclose(lin["H"], c["H"].reshape(6, 6), atol=1e-15)

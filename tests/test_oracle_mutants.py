@@ -23,7 +23,8 @@ HERE = os.path.dirname(os.path.abspath(orc.__file__))
 MUTANTS = [
     ("combined covariance without the rotation of C^s",
      "Sig[a] = Ct[a] + RCs[a];", "Sig[a] = Ct[a] + Cs[a];",
-     [pins.test_linearisation_is_invariant_to_the_source_and_map_frames]),
+     [pins.test_linearisation_is_invariant_to_the_source_and_map_frames,
+      lambda: golden.test_oracle_linearise_one_correspondence("quarter_turn_z")]),
     ("weight Sigma instead of Sigma^-1",
      "if (inv_sym3(Sig, W6) != 0) return;", "memcpy(W6, Sig, sizeof(W6));",
      [pins.test_cost_tends_to_point_to_plane_error_in_the_flat_limit]),
