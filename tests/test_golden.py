@@ -26,6 +26,7 @@ def _read(name):
 STARS = _read("regularisation_star.ini")
 SE3 = _read("se3_exp.ini")
 LIN = _read("linearise_single.ini")
+D2P = _read("depth_to_points_small.ini")
 
 
 def star_points(c):
@@ -174,3 +175,13 @@ def test_oracle_linearise_one_correspondence(case):
     assert lin["cost"] == pytest.approx(c["cost"][0], rel=1e-12)
     np.testing.assert_allclose(lin["b"], c["b"], atol=1e-15)
     np.testing.assert_allclose(lin["H"], c["H"].reshape(6, 6), atol=1e-15)
+
+
+@pytest.mark.parametrize("stride", [1, 2])
+def test_oracle_depth_to_points_small_image(stride):
+    img = D2P["image"]
+    depth = img["depth"].reshape(3, 4).astype(np.float32)
+    pts, z = orc.depth_to_points(depth, img["intr"], stride, *img["range"])
+    expect = D2P[f"stride_{stride}"]["points"].reshape(-1, 3)
+    np.testing.assert_array_equal(pts, expect)
+    np.testing.assert_array_equal(z, expect[:, 2])

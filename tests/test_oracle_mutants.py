@@ -79,7 +79,7 @@ MUTANTS = [
      [pins.test_transform_gaussians_is_a_rigid_motion]),
     ("back-projection with cx in place of cy",
      "((double)v - cy) * d / fy", "((double)v - cx) * d / fy",
-     [pins.test_depth_to_points_on_analytic_plane]),
+     [pins.test_depth_to_points_on_analytic_plane, lambda: golden.test_oracle_depth_to_points_small_image(1)]),
 ]
 
 
