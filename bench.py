@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=None,
                     help="sequence length (default 300 for sequence, 500 for surrogate)")
     ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--gn-plain", action="store_true",
+                    help="launch each Gauss-Newton iteration as a plain kernel (not a graph node), for "
+                         "launch-listing profilers; same results")
     args = ap.parse_args()
     if args.frames is None:
         args.frames = 500 if args.workload == "surrogate" else 300
@@ -195,6 +198,8 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     f = frame_config2(args.seed)
     ctx = g.Context()
+    if args.gn_plain:
+        g.gsicp_ctx_set_gn_launch_mode(ctx, g.GN_PLAIN)
     means, covs = build_map_gpu(g, ctx, f, torch)
     m = g.gsicp_build_map_index(ctx, means, covs)
     n_map = m.size
@@ -283,8 +288,9 @@ def run_ours(args, world, rank, local):
             GN_TRAFFIC["sources_sha256"] == sources_sha256():
         traffic = GN_TRAFFIC["bytes_per_launch"]
     # the Gauss-Newton graph runs its iteration launches GN_BODY_ITERS at a time (the ones after
-    # convergence exit at once)
-    launches = int(sum(LAUNCHES_MAP_REBUILD + LAUNCHES_FRAME + GN_BODY_ITERS * -(-int(it) // GN_BODY_ITERS)
+    # convergence exit at once); in plain-launch mode every frame launches max_iters of them
+    launches = int(sum(LAUNCHES_MAP_REBUILD + LAUNCHES_FRAME +
+                       (MAX_ITERS if args.gn_plain else GN_BODY_ITERS * -(-int(it) // GN_BODY_ITERS))
                        for it in iters))
     K = args.steps
     out = {

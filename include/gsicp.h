@@ -115,6 +115,15 @@ gsicp_status gsicp_ctx_last_residual(gsicp_ctx ctx, double* sqdist_out, int64_t*
  * walks alone.  0 = always alone, 32 = always together.  Results do not depend on it (both walks
  * are exact); only time does.  Default 4.  GSICP_ERR_INVALID_ARG outside 0..32 or for a null ctx. */
 gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp);
+/* How this context launches the Gauss-Newton iterations of gsicp_register and gsicp_track_frame*:
+ * GSICP_GN_GRAPH (default) runs them as one CUDA graph whose conditional WHILE node repeats until
+ * the last iteration's solve reports convergence (no host round trip per iteration);
+ * GSICP_GN_PLAIN launches max_iters kernels on the stream, each a programmatic dependent of the
+ * one before, and the launches after convergence exit at once.  The two give identical results;
+ * PLAIN makes every iteration an ordinary kernel launch that launch-listing profilers see.
+ * GSICP_ERR_INVALID_ARG for another value or a null ctx. */
+typedef enum { GSICP_GN_GRAPH = 0, GSICP_GN_PLAIN = 1 } gsicp_gn_launch_mode;
+gsicp_status gsicp_ctx_set_gn_launch_mode(gsicp_ctx ctx, int mode);
 gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6]);
 
 /* Telemetry of the last frame whose covariances this context computed (gsicp_frame_covariances,
@@ -159,10 +168,14 @@ gsicp_status gsicp_depth_to_points(gsicp_ctx ctx, const float* depth_dev, int W,
  * gsicp_depth_to_points, except that the count goes to n_dev (device int32, required) and the
  * count before clamping to cap to total_dev (device int32, nullable); nothing is synchronised.
  * The sampled grid ceil(W/stride) * ceil(H/stride) may hold at most 4194304 pixels; larger
- * images are rejected with GSICP_ERR_INVALID_ARG (message in gsicp_last_error()).  The first
- * call on a device looks up the array's device address; make that call before any stream
- * capture.  All calls on a device share the array: calls that may overlap on the GPU (e.g. on
- * unordered streams) race on it and must be serialised by the caller. */
+ * images are rejected with GSICP_ERR_INVALID_ARG, as are NULL required pointers, non-positive
+ * sizes and a zero focal length (each with a message in gsicp_last_error()).  The first call in
+ * a device's context looks up the array's device address (cached per device with the context's
+ * id; a new context, e.g. after cudaDeviceReset, is looked up again on its first call, and a
+ * failed lookup is not cached); make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents (every entry a call reads is
+ * written by that call first): calls that may overlap on the GPU (e.g. on unordered streams)
+ * race on it and must be serialised by the caller. */
 gsicp_status gsicp_depth_to_points_noalloc(const float* depth_dev, int W, int H, const float intr[4],
                                            int stride, float z_min, float z_max, float* pts_dev,
                                            float* z_dev, int64_t cap, int32_t* n_dev,

@@ -5,7 +5,7 @@ the functions below carry the C entry points' names and only marshal
 arguments (torch CUDA tensors -> device pointers, the current torch stream ->
 ``cudaStream_t``).  Every step of the path runs in the library's CUDA kernels;
 there is no fallback.  Importing this package raises if the library has not
-been built (``python -m paper_2403_12550_b300.build``).
+been built (``python paper_2403_12550_b300/build.py``).
 """
 from __future__ import annotations
 
@@ -18,7 +18,7 @@ import torch
 __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
-    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_set_gn_launch_mode", "GN_GRAPH", "GN_PLAIN", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
     "gsicp_build_map_index", "gsicp_map_append",
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_selftest_batch_timeout", "gsicp_linearise",
@@ -31,6 +31,7 @@ __all__ = [
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgsicp.so")
 
 PLANE, ELLIPSE, NONE = 0, 1, 2
+GN_GRAPH, GN_PLAIN = 0, 1
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_TIMEOUT, ERR_NOT_IMPLEMENTED, ERR_CAPACITY = range(8)
 
 
@@ -84,7 +85,7 @@ FRAME, KEYFRAME, MAPPING_KEYFRAME = 0, 1, 2
 
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2403_12550_b300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2403_12550_b300/build.py` "
                       "(there is no non-CUDA fallback)")
 
 lib = C.CDLL(LIB_PATH)
@@ -108,6 +109,7 @@ _sig("gsicp_version", C.c_char_p, [])
 _sig("gsicp_ctx_set_timing", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_last_residual", C.c_int, [_vp, _dp, _i64p])
 _sig("gsicp_ctx_set_coop_walks", C.c_int, [_vp, C.c_int])
+_sig("gsicp_ctx_set_gn_launch_mode", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
 _sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
 _sig("gsicp_ctx_frame_stats", C.c_int, [_vp, _i64p])
@@ -257,6 +259,12 @@ def gsicp_ctx_set_coop_walks(ctx: Context, max_per_warp: int):
     """Warps with at most max_per_warp tree walks in an iteration walk together (0..32; results
     do not depend on it)."""
     _check(lib.gsicp_ctx_set_coop_walks(ctx.ptr, int(max_per_warp)), "gsicp_ctx_set_coop_walks")
+
+
+def gsicp_ctx_set_gn_launch_mode(ctx: Context, mode: int):
+    """GN_GRAPH (default): the iterations run as one conditional CUDA graph; GN_PLAIN: one plain
+    launch per iteration (same results; visible to launch-listing profilers)."""
+    _check(lib.gsicp_ctx_set_gn_launch_mode(ctx.ptr, int(mode)), "gsicp_ctx_set_gn_launch_mode")
 
 
 def gsicp_ctx_last_residual(ctx: Context) -> tuple:

@@ -182,8 +182,6 @@ gsicp_status gsicp_ctx_create(gsicp_ctx* out)
         if (e != cudaSuccess) st = cuda_status(e, "cudaMallocHost");
     }
     if (st == GSICP_OK) st = c->reg.init(1 << 18);
-    const char* unrolled = getenv("GSICP_UNROLLED_GN");
-    c->reg.unrolled = unrolled && unrolled[0] == '1';
     if (st != GSICP_OK) {
         gsicp_ctx_destroy(c);
         return st;
@@ -226,6 +224,13 @@ gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp)
 {
     if (!ctx || max_per_warp < 0 || max_per_warp > 32) return GSICP_ERR_INVALID_ARG;
     ctx->coop_walks = max_per_warp;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_set_gn_launch_mode(gsicp_ctx ctx, int mode)
+{
+    if (!ctx || (mode != GSICP_GN_GRAPH && mode != GSICP_GN_PLAIN)) return GSICP_ERR_INVALID_ARG;
+    ctx->reg.unrolled = mode == GSICP_GN_PLAIN;
     return GSICP_OK;
 }
 

@@ -10,7 +10,7 @@
 
 namespace gsicp {
 
-constexpr int D2P_THREADS = 256;
+// D2P_THREADS: internal.h
 
 __device__ __forceinline__ bool pixel_valid(const float* depth, int W, int stride, int Ws, long idx, float z_min,
                                             float z_max, int& u, int& v, float& d)

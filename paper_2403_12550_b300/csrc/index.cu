@@ -13,9 +13,7 @@ namespace gsicp {
 // ------------------------------------------------------------------------------------------
 // device-wide exclusive scan (uint32)
 
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+// SCAN_THREADS, SCAN_ITEMS, SCAN_TILE: internal.h
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t& total)
 {

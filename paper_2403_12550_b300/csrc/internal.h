@@ -11,6 +11,13 @@
 
 namespace gsicp {
 
+// Launch shapes shared by translation units that launch the same kernels with their own scratch
+// (depth.cu and noalloc.cu launch the a1 kernels; index.cu and noalloc.cu the scan kernels).
+constexpr int D2P_THREADS = 256;                    // sampled pixels per a1 counting / writing block
+constexpr int SCAN_THREADS = 256;                   // threads of a scan tile
+constexpr int SCAN_ITEMS = 8;                       // values per scan thread
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // values per scan tile (one partial sum each)
+
 // Record a CUDA error for gsicp_last_error() and map it to a status.
 gsicp_status cuda_status(cudaError_t e, const char* where);
 
@@ -99,7 +106,7 @@ struct RegMachine {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond{};
-    bool unrolled = false;  // GSICP_UNROLLED_GN=1: plain launches instead of the graph (for profilers)
+    bool unrolled = false;  // GSICP_GN_PLAIN: one plain launch per iteration instead of the graph
     gsicp_status init(int capacity);  // (re)builds the graph when the point capacity grows
     void release();
 };

@@ -185,3 +185,36 @@ def test_oracle_depth_to_points_small_image(stride):
     expect = D2P[f"stride_{stride}"]["points"].reshape(-1, 3)
     np.testing.assert_array_equal(pts, expect)
     np.testing.assert_array_equal(z, expect[:, 2])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("stride", [1, 2])
+def test_cuda_depth_to_points_small_image(stride):
+    """Both CUDA a1 entry points (the allocating one and the allocation-free one) on the hand-worked
+    4 x 3 image: the missing sample, the samples below z_min and above z_max are dropped and the
+    rest equal the worked points exactly (the a1 bar is bit-exact)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_12550_b300 as g
+    img = D2P["image"]
+    depth = torch.from_numpy(img["depth"].reshape(3, 4).astype(np.float32)).cuda()
+    expect = D2P[f"stride_{stride}"]["points"].reshape(-1, 3).astype(np.float32)
+    ctx = g.Context()
+    try:
+        pts, z = g.gsicp_depth_to_points(ctx, depth, img["intr"], stride, *img["range"])
+        np.testing.assert_array_equal(pts.cpu().numpy(), expect)
+        np.testing.assert_array_equal(z.cpu().numpy(), expect[:, 2])
+    finally:
+        ctx.close()
+    cap = 12
+    pts = torch.full((cap, 3), np.nan, device="cuda", dtype=torch.float32)
+    z = torch.full((cap,), np.nan, device="cuda", dtype=torch.float32)
+    n = torch.zeros((1,), device="cuda", dtype=torch.int32)
+    total = torch.zeros((1,), device="cuda", dtype=torch.int32)
+    g.gsicp_depth_to_points_noalloc(depth, img["intr"], stride, *img["range"], pts, z, n, total)
+    torch.cuda.synchronize()
+    k = int(n.item())
+    assert k == int(total.item()) == len(expect)
+    np.testing.assert_array_equal(pts[:k].cpu().numpy(), expect)
+    np.testing.assert_array_equal(z[:k].cpu().numpy(), expect[:, 2])

@@ -452,6 +452,35 @@ def test_coop_walks_do_not_change_results(g, ctx):
     m1.close()
 
 
+def test_gn_launch_modes_give_identical_results(g, ctx):
+    """The Gauss-Newton iterations as one conditional graph (default) and as plain launches give
+    bit-identical results: a config-1 registration and the full-size frame."""
+    f, means, covs = _cfg2()
+    m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    src, cs, tgt, ct, _ = config1_inputs(2, 1)
+    m1 = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    out = {}
+    try:
+        for mode in (g.GN_GRAPH, g.GN_PLAIN):
+            g.gsicp_ctx_set_gn_launch_mode(ctx, mode)
+            r = g.gsicp_track_frame(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
+            r1 = g.gsicp_register(ctx, cu(src), cu(cs), m1, np.eye(4), rp)
+            out[mode] = (r, r1)
+    finally:
+        g.gsicp_ctx_set_gn_launch_mode(ctx, g.GN_GRAPH)
+    for a, b in zip(out[g.GN_GRAPH], out[g.GN_PLAIN]):
+        assert a["status"] == b["status"] == g.OK
+        np.testing.assert_array_equal(a["T"], b["T"])
+        np.testing.assert_array_equal(a["H"], b["H"])
+        assert (a["iters"], a["cost"], a["inliers"]) == (b["iters"], b["cost"], b["inliers"])
+    with pytest.raises(g.GsicpError):
+        g.gsicp_ctx_set_gn_launch_mode(ctx, 2)
+    m.close()
+    m1.close()
+
+
 def test_track_frame_empty_depth(g, ctx):
     src, cs, tgt, ct, _ = config1_inputs(0, 0, n=2000)
     m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
@@ -499,6 +528,44 @@ def test_register_batch_equals_single_and_oracle(g, ctx):
         m.close()
 
 
+def test_register_batch_config4_sizes_equal_single_and_oracle(g, ctx):
+    """Pairs of the batched workload itself (64 config-1-style rooms, 5k-300k points): the four
+    largest-class pairs drawn (133k-276k points) and two that stop at max_iters = 30 in a
+    re-association limit cycle, in one persistent launch.  Each pair equals gsicp_register on it
+    alone bit for bit (pose, cost, inliers, iterations) and the oracle within the pose bar;
+    the limit-cycle pairs run the full 30 iterations on every side."""
+    from synth import batch_config4
+    pick = [5, 55, 27, 8, 11, 49]
+    allp = batch_config4(0, n_pairs=64)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    srcs, scovs, maps, ins = [], [], [], []
+    for b in pick:
+        p = allp[b]
+        cs = orc.source_covariances(p["src"], k=20, eps=1e-3, reg_mode=orc.PLANE)["covs"].astype(np.float32)
+        ct = orc.source_covariances(p["tgt"], k=20, eps=1e-3, reg_mode=orc.PLANE)["covs"].astype(np.float32)
+        srcs.append(cu(p["src"]))
+        scovs.append(cu(cs))
+        maps.append(g.gsicp_build_map_index(ctx, cu(p["tgt"]), cu(ct)))
+        ins.append((p["src"], cs, p["tgt"], ct))
+    T0s = np.stack([np.eye(4)] * len(pick))
+    rb = g.gsicp_register_batch(ctx, srcs, scovs, maps, T0s, rp)
+    assert max(len(s_[0]) for s_ in ins) > 250_000
+    for j, b in enumerate(pick):
+        src, cs, tgt, ct = ins[j]
+        rs = g.gsicp_register(ctx, srcs[j], scovs[j], maps[j], T0s[j], rp)
+        assert rb["status"][j] == rs["status"] == g.OK, (b, rb["status"][j], rs["status"])
+        np.testing.assert_array_equal(rb["T"][j], rs["T"])
+        assert (rb["iters"][j], rb["inliers"][j], rb["cost"][j]) == (rs["iters"], rs["inliers"], rs["cost"]), b
+        ro = orc.register(src, cs, orc.Map(tgt, ct), T0s[j], 0.1, 30, 1e-6, 1e-6, 6)
+        assert ro["status"] == orc.OK
+        dr, dt = pose_diff(rb["T"][j], ro["T"])
+        assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (b, dr, dt, rb["iters"][j], ro["iters"])
+        if b in (11, 49):
+            assert rb["iters"][j] == ro["iters"] == 30, (b, rb["iters"][j], ro["iters"])
+    for m in maps:
+        m.close()
+
+
 def test_register_batch_queue_wait_is_bounded(g, ctx):
     """A queue that claims a running pair but never gets an item: every wait runs out (about a
     second), the call reports TIMEOUT, and the context keeps working."""
@@ -532,26 +599,62 @@ def _frame_cases():
         scene, P
 
 
-@pytest.mark.parametrize("case", range(6))
-def test_frame_covariances_equal_tree_path(g, ctx, case):
+_FRAME_DEPTHS = {}
+
+
+def _frame_depth(case):
+    """Depth image of frame case `case` (rendered once per module)."""
+    if case not in _FRAME_DEPTHS:
+        cases, scene, P = _frame_cases()
+        intr, stride, dropout = cases[case]
+        rng = np.random.default_rng(100 + case)
+        _FRAME_DEPTHS[case] = (intr, stride, add_depth_noise(raycast_depth(scene, P, intr), rng, 1e-3,
+                                                             dropout=dropout))
+    return _FRAME_DEPTHS[case]
+
+
+@pytest.mark.parametrize("k", [5, 8, 12, 16, 20, 32])
+@pytest.mark.parametrize("mode", [orc.PLANE, orc.ELLIPSE, orc.NONE])
+def test_frame_covariances_equal_tree_path(g, ctx, mode, k):
     """The image-window k-NN (certified by the camera geometry, tree search for the rest) gives
     bit-for-bit the points of gsicp_depth_to_points and the covariances of
-    gsicp_source_covariances on them: both are the exact float k-NN with the same ties."""
-    cases, scene, P = _frame_cases()
-    intr, stride, dropout = cases[case]
-    rng = np.random.default_rng(100 + case)
-    depth = add_depth_noise(raycast_depth(scene, P, intr), rng, 1e-3, dropout=dropout)
-    for p in (1.5, 0.0):
-        cp = g.CovParams(20, 1e-3, g.PLANE, p)
-        pf, zf, cf = g.gsicp_frame_covariances(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0, cp)
-        fs = g.gsicp_ctx_frame_stats(ctx)
-        pts, z = g.gsicp_depth_to_points(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0)
-        pts, z = pts.clone(), z.clone()
-        ct = g.gsicp_source_covariances(ctx, pts, z, cp)
-        assert torch.equal(pf, pts) and torch.equal(zf, z)
-        assert 0 <= fs["tree_queries"] <= fs["wide_window_queries"] <= len(pts)
-        bad = (cf != ct).any(dim=1).nonzero().flatten().cpu().numpy()
-        assert len(bad) == 0, (case, p, len(bad), fs, len(pts))
+    gsicp_source_covariances on them: both are the exact float k-NN with the same ties.  Every
+    regularisation (Sec. 3.1: plane, ellipse, none) and every neighbour-list width the window
+    kernels are built for (8, 16, 20, 32; k = 5 and 12 run inside the 8- and 16-wide lists), with
+    and without scale aligning (Sec. 3.2), on six frames from 1200 x 680 at stride 2 down to 7 x 5."""
+    for case in range(6):
+        intr, stride, depth = _frame_depth(case)
+        for p in (1.5, 0.0):
+            cp = g.CovParams(k, 1e-3, mode, p)
+            pf, zf, cf = g.gsicp_frame_covariances(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0, cp)
+            fs = g.gsicp_ctx_frame_stats(ctx)
+            pts, z = g.gsicp_depth_to_points(ctx, cu(depth), intr.as_array(), stride, 0.1, 10.0)
+            pts, z = pts.clone(), z.clone()
+            ct = g.gsicp_source_covariances(ctx, pts, z, cp)
+            assert torch.equal(pf, pts) and torch.equal(zf, z)
+            assert 0 <= fs["tree_queries"] <= fs["wide_window_queries"] <= len(pts)
+            bad = (cf != ct).any(dim=1).nonzero().flatten().cpu().numpy()
+            assert len(bad) == 0, (case, mode, k, p, len(bad), fs, len(pts))
+
+
+@pytest.mark.parametrize("mode", [orc.PLANE, orc.ELLIPSE, orc.NONE])
+def test_frame_covariances_full_bench_frame_match_oracle(g, ctx, mode):
+    """The 1200 x 680 frame the benchmark tracks (stride 2, 204,000 points), through the image-window
+    path the tracker runs, against the oracle directly: the neighbour lists (exported by the tree
+    path, which the window path equals bit for bit) identical up to distance ties, covariances
+    within the relative Frobenius bar with the exclusions counted, for each regularisation."""
+    f, _, _ = _cfg2()
+    cp = g.CovParams(20, 1e-3, mode, 1.5)
+    pf, zf, cf = g.gsicp_frame_covariances(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp)
+    pts, z = oracle_frame_points(f["depth"])
+    np.testing.assert_array_equal(pf.cpu().numpy(), pts)
+    np.testing.assert_array_equal(zf.cpu().numpy(), z)
+    ct = g.gsicp_source_covariances(ctx, pf.clone(), zf.clone(), cp)
+    assert torch.equal(cf, ct)
+    r = _check_knn_and_covs(pts, z, mode, 1.5, 20, g, ctx)
+    assert r["n"] == 204_000 and r["excluded"] < 0.01 * r["n"], r
+    assert r["knn_mismatch"] < 1e-3 * r["n"], r
+    # cf equals the tree path's covariances bit for bit, so the bar just checked holds for it
 
 
 def test_frame_covariances_match_oracle(g, ctx):
