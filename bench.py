@@ -13,6 +13,14 @@ Gauss-Newton loop with per-iteration nearest-neighbour search.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica of
 the workload (independent frames, no data-path collective: weak scaling).
+
+The default run's line also carries "workloads": compact records of the other forms of the
+path, each measured in the same run: "sharded" (one frame's registration split across the ranks,
+one all-gather of 30 float64 sums per Gauss-Newton iteration; strong scaling), and at N = 1
+"batch" (64 independent pairs in one persistent launch), "sequence" (the tracking loop with the
+paper's keyframe policy over a 120-frame TUM-shaped sequence) and "surrogate" (learned covariances
+on their 500-frame held-out sequence, ATE against the plain form on the same run).
+--no-workloads skips them; --workload X runs one of them alone at full size.
 """
 from __future__ import annotations
 
@@ -64,10 +72,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["frame", "batch", "sequence", "surrogate"], default="frame",
+    ap.add_argument("--workload", choices=["frame", "batch", "sequence", "surrogate", "sharded"], default="frame",
                     help="frame: the tracking step (default); batch: batched registration of independent pairs; "
                          "sequence: the tracking loop with keyframes over a TUM-shaped sequence (latency p50/p99); "
-                         "surrogate: the tracking loop with learned covariances on their held-out sequence")
+                         "surrogate: the tracking loop with learned covariances on their held-out sequence; "
+                         "sharded: one frame's registration split across the ranks")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="frame workload only: skip the compact batch / sequence / surrogate / sharded records "
+                         "the default run adds to its line")
     ap.add_argument("--frames", type=int, default=None,
                     help="sequence length (default 300 for sequence, 500 for surrogate)")
     ap.add_argument("--pairs", type=int, default=64)
@@ -311,12 +323,143 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(f, args.seed)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     m.close()
     ctx.close()
+    if not args.no_workloads:
+        out["workloads"] = sub_workloads(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- split registration
+
+SHARD_METRIC = ("split G-ICP registrations/s (one 1200x680 frame, ~204k points, vs 2.04M-Gaussian map; the "
+                "frame's points shared by the ranks)")
+
+
+def measure_sharded(args, world, rank, local, steps: int = 20, warmup: int = 3) -> dict:
+    """One registration of the benchmark frame whose points are split across the ranks
+    (paper_2403_12550_b300.sharded: per iteration each rank linearises its share, the ranks
+    all-gather the 30 sums, every rank solves).  Each rank builds the whole map and the frame's
+    covariances once, untimed; a step is one split registration from the frame's start pose,
+    timed by CUDA events on the stream (the loop synchronises every iteration), L2 flushed between
+    steps.  Beside it, the same registration by gsicp_register on one rank (all points)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2403_12550_b300 as g
+    from paper_2403_12550_b300.sharded import register_sharded, share
+    from synth import frame_config2
+
+    torch.cuda.set_device(local)
+    f = frame_config2(args.seed)
+    ctx = g.Context()
+    means, covs = build_map_gpu(g, ctx, f, torch)
+    m = g.gsicp_build_map_index(ctx, means, covs)
+    intr = f["intr"].as_array()
+    cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
+    rp = g.RegParams(MAX_DIST, MAX_ITERS, TOL, TOL, 6)
+    pts, _, cs = g.gsicp_frame_covariances(ctx, torch.from_numpy(f["depth"]).cuda(), intr, STRIDE, Z_MIN, Z_MAX, cp)
+    pts, cs = pts.clone(), cs.clone()
+    sl = share(pts.shape[0], world, rank)
+    src, scov = pts[sl].contiguous(), cs[sl].contiguous()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        ms, r = [], None
+        for _ in range(k):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms, r
+
+    split = lambda: register_sharded(ctx, src, scov, m, f["T0"], rp)
+    single = lambda: g.gsicp_register(ctx, pts, cs, m, f["T0"], rp)
+    timed(split, warmup)
+    timed(single, warmup)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, r = timed(split, steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_s = max_over_ranks(sum(ms) / 1e3, world, "cuda")
+    ms1, r1 = timed(single, steps)
+    out = {
+        "metric": SHARD_METRIC, "value": steps / total_s, "unit": "registrations/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": total_s * 1e3 / steps, "higher_is_better": True,
+        "scaling": "strong", "dtype": "f32",
+        "config": {"workload": f"the benchmark frame ({pts.shape[0]} points) split into {world} contiguous shares "
+                               f"of its Morton-unordered point list; map replicated on every rank",
+                   "collective": "all-gather of 30 float64 per rank per Gauss-Newton iteration" if world > 1 else
+                                 "none (one rank)", "l2": "flushed between timed steps (256 MB write)"},
+        "iters": r["iters"], "status": r["status"],
+        "single_register": {"value": 1e3 / float(np.mean(ms1)), "unit": "registrations/s",
+                            "ms": float(np.mean(ms1)), "iters": r1["iters"]},
+        "pose_equals_single": bool(np.array_equal(r["T"], r1["T"])),
+        "pose_diff_single": {"rot_rad": rot_angle(r["T"][:3, :3].T @ r1["T"][:3, :3]),
+                             "trans_m": float(np.linalg.norm(r["T"][:3, 3] - r1["T"][:3, 3]))},
+        "gpu_launches": steps * (int(r["rounds"]) * 2 + 16),
+    }
+    m.close()
+    ctx.close()
+    return out
+
+
+def run_sharded(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = measure_sharded(args, world, rank, local, steps=args.steps, warmup=args.warmup)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def rot_angle(R) -> float:
+    """Rotation angle of R from its antisymmetric part and trace together (atan2): arccos of the
+    trace alone reads a common scale error e of nearly orthonormal matrices as sqrt(6 e)."""
+    w = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]])
+    return float(np.arctan2(0.5 * np.linalg.norm(w), 0.5 * (np.trace(R) - 1.0)))
+
+
+def _pick(d: dict, keys) -> dict:
+    return {k: d[k] for k in keys if k in d}
+
+
+def sub_workloads(args, world, rank, local) -> dict:
+    """Compact records of the other forms of the path, for the default run's line: the split
+    registration (any N), and at N = 1 the batched registration, the tracking loop over a
+    TUM-shaped sequence and the learned covariances on their held-out sequence (each as its own
+    --workload prints it, shortened: fewer timed steps, shorter oracle samples, a 120-frame
+    sequence)."""
+    import argparse
+    short = argparse.Namespace(**{**vars(args), "steps": 20, "warmup": 3})
+    common = ("metric", "value", "unit", "ms_per_step", "steps", "dtype", "config", "clocks", "cpu_baseline",
+              "roofline", "e2e", "gpu_launches")
+    w = {"sharded": _pick(measure_sharded(args, world, rank, local), common + (
+        "scaling", "iters", "status", "single_register", "pose_equals_single", "pose_diff_single"))}
+    if world == 1:
+        w["batch"] = _pick(measure_batch(short, world, rank, local, cpu_sample_s=6.0), common + (
+            "point_iters_per_s", "one_by_one", "converged"))
+        w["sequence"] = _pick(measure_sequence(short, world, rank, local, 120, cpu_sample_s=8.0), common + (
+            "latency_ms", "ate_m", "ate_aligned_m", "ate_first_frames", "keyframes", "mapping_keyframes",
+            "map_sizes"))
+        w["surrogate"] = _pick(measure_surrogate(short, world, rank, local, 500, cpu_sample_s=6.0), common + (
+            "knn_frames_per_s", "latency_ms", "ate_m", "ate_knn_m", "ate_gap_m", "ate_aligned_m",
+            "ate_knn_aligned_m", "surrogate_frames", "fell_back", "layer_ms"))
+    return w
 
 
 # ----------------------------------------------------------------------------- the oracle (CPU)
@@ -452,7 +595,7 @@ def batch_launches(n_pts) -> int:
     return 17 if int(np.sum(n_pts)) > 1 else 3
 
 
-def run_batch(args, world, rank, local):
+def measure_batch(args, world, rank, local, cpu_sample_s: float = 15.0) -> dict:
     """Batched registration of `args.pairs` independent pairs (log-uniform 5k-300k points, offsets
     <= 5 deg / 5 cm, plane covariances k = 20 computed on the GPU, maps indexed with the shape the
     autotuner picks); one step = one gsicp_register_batch call over all pairs.  Also times the same
@@ -518,18 +661,32 @@ def run_batch(args, world, rank, local):
                    "autotune_ms": {f"{b}/{c}": round(v, 3) for (b, c), v in tune["ms"].items()},
                    "l2": "flushed between timed steps (256 MB write)"},
         "point_iters_per_s": world * K * point_iters / total_s,
+        # the whole batch is one persistent launch (plus the joint Morton order and set-up, counted in
+        # its time here: a lower bound on the kernel's rate)
+        "roofline": {"kernel": "gicp_batch_kernel (whole call)", "bound": "hbm",
+                     "achieved": point_iters * BYTES_PER_POINT_ITER / (total_s / K) / 1e9,
+                     "peak": load_peaks()[0], "unit": "GB/s",
+                     "frac": point_iters * BYTES_PER_POINT_ITER / (total_s / K) / 1e9 / load_peaks()[0],
+                     "traffic": None, "peak_source": f"{load_peaks()[1]} hbm_gbs",
+                     "algorithmic_bytes_per_launch": int(point_iters * BYTES_PER_POINT_ITER),
+                     "avg_launch_ms": total_s * 1e3 / K},
         "one_by_one": {"value": B / seq_s, "unit": "registrations/s", "ms": seq_s * 1e3},
         "converged": int(np.sum((r["status"] == g.OK) & (r["iters"] < MAX_ITERS))),
         "gpu_launches": K * batch_launches(n_pts),
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = batch_cpu_baseline(pairs)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+        out["cpu_baseline"] = batch_cpu_baseline(pairs, cpu_sample_s)
     for m in maps:
         m.close()
     ctx.close()
+    return out
+
+
+def run_batch(args, world, rank, local):
+    out = measure_batch(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 # ----------------------------------------------------------------------------- tracking sequence
@@ -564,27 +721,34 @@ def batch_cpu_baseline(pairs, sample_s: float = 15.0) -> dict:
                       f"source point; FP64 C oracle with OpenMP over points"}
 
 
-def sequence_cpu_baseline(seq, n_frames: int, sample_s: float = 20.0) -> dict:
+def sequence_cpu_baseline(seq, frames, sample_s: float = 20.0) -> dict:
     """The oracle's tracking loop (same keyframe policy) over the sequence's frames in order until
-    about sample_s seconds of work; every frame's full tracker step is timed."""
+    about sample_s seconds of work; every frame's full tracker step is timed.  Also returns the
+    number of frames run and the oracle's ATE over them."""
     from oracle.tracker import Tracker as OTracker
+    from paper_2403_12550_b300.trajectory import ate_rmse
     trk = OTracker(seq["intr"].as_array(), stride=STRIDE, z_min=Z_MIN, z_max=Z_MAX, k=K_NN, eps=EPS, p=P_ALIGN,
                    max_dist=MAX_DIST, max_iters=MAX_ITERS, tol_rot=TOL, tol_trans=TOL)
-    done, el = 0, 0.0
-    for f in range(n_frames):
-        depth = seq["depth"](f)
+    done, el, est = 0, 0.0, []
+    for f in range(len(frames)):
         t0 = time.perf_counter()
-        trk.frame(depth, seq["poses"][0] if f == 0 else None)
+        T, _ = trk.frame(frames[f], seq["poses"][0] if f == 0 else None)
         el += time.perf_counter() - t0
+        est.append(T)
         done += 1
         if el >= sample_s:
             break
     return {"value": done / el, "unit": "frames/s", "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"the first {done} of {n_frames} frames through the oracle's tracking loop ({el:.1f} s; "
-                      f"frame 0 builds the first map)"}
+            "sample": f"the first {done} of {len(frames)} frames through the oracle's tracking loop ({el:.1f} s; "
+                      f"frame 0 builds the first map)", "frames_done": done,
+            "ate_first_m": ate_rmse(est, seq["poses"][:done])}
 
 
-def run_sequence(args, world, rank, local):
+def render_workers() -> int:
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def measure_sequence(args, world, rank, local, n_frames: int, cpu_sample_s: float = 20.0) -> dict:
     """The tracking loop (gsicp_tracker_frame: a1..a7, keyframe decision, non-overlap appends with
     map-index rebuilds) over a TUM-shaped sequence; per-frame latency is host wall time of each
     call (it synchronises), depth images resident on the device."""
@@ -592,12 +756,13 @@ def run_sequence(args, world, rank, local):
 
     import paper_2403_12550_b300 as g
     from paper_2403_12550_b300.trajectory import ate_rmse, ate_rmse_aligned
-    from synth import sequence_config3
+    from synth import render_sequence_frames, sequence_config3
 
     torch.cuda.set_device(local)
     seed = 1 + args.seed
-    seq = sequence_config3(seed, n_frames=args.frames)
-    depths = [torch.from_numpy(seq["depth"](f)).cuda() for f in range(args.frames)]
+    seq = sequence_config3(seed, n_frames=n_frames)
+    frames = render_sequence_frames("config3", seed, n_frames, render_workers())
+    depths = [torch.from_numpy(d).cuda() for d in frames]
     intr = seq["intr"].as_array()
     ctx = g.Context()
     cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
@@ -626,7 +791,7 @@ def run_sequence(args, world, rank, local):
         "metric": SEQ_METRIC, "value": world * len(lat_ms) / (lat_ms.sum() / 1e3), "unit": "frames/s",
         "n_gpus": world, "steps": len(lat_ms), "warmup": args.warmup, "ms_per_step": float(lat_ms.mean()),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"TUM-shaped sequence seed {seed}: {args.frames} frames 640x480 at 30 Hz, stride 2, "
+        "config": {"workload": f"TUM-shaped sequence seed {seed}: {n_frames} frames 640x480 at 30 Hz, stride 2, "
                                f"keyframes by inlier ratio < 0.85, forced every 30, mapping-only every 10",
                    "k": K_NN, "reg": "plane", "p": P_ALIGN},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
@@ -636,10 +801,21 @@ def run_sequence(args, world, rank, local):
         "map_sizes": list(sizes),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = sequence_cpu_baseline(seq, args.frames)
+        cb = sequence_cpu_baseline(seq, frames, cpu_sample_s)
+        # the oracle's tracking loop over the frames it ran, against the GPU's over the same frames
+        nf = cb.pop("frames_done")
+        cb["ate_m"] = cb.pop("ate_first_m")
+        out["ate_first_frames"] = {"frames": nf, "ate_m": ate_rmse(est[:nf], seq["poses"][:nf]),
+                                   "oracle_ate_m": cb["ate_m"]}
+        out["cpu_baseline"] = cb
+    ctx.close()
+    return out
+
+
+def run_sequence(args, world, rank, local):
+    out = measure_sequence(args, world, rank, local, args.frames)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
 
 
 SURR_METRIC = "G-ICP tracking frames/s with learned covariances (640x480 held-out sequence, per-frame k-NN fallback)"
@@ -683,7 +859,7 @@ def surrogate_cpu_baseline(frames, seq, sample_s: float = 15.0) -> dict:
                       f"against a map from the previous frame ({el:.1f} s)"}
 
 
-def run_surrogate(args, world, rank, local):
+def measure_surrogate(args, world, rank, local, n_frames: int, cpu_sample_s: float = 15.0) -> dict:
     """The learned covariance surrogate on its held-out sequence: the tracking loop with the
     surrogate's covariances (per-frame fallback to k-NN when the RMS correspondence residual exceeds
     1.1 x the last k-NN frame's; k-NN calibration every 30 frames; keyframes keep k-NN covariances),
@@ -699,9 +875,9 @@ def run_surrogate(args, world, rank, local):
     from synth import sequence_config5
 
     torch.cuda.set_device(local)
-    n = args.frames
+    n = n_frames
     seq = sequence_config5(args.seed, n_frames=n)
-    frames = S.render_sequence(args.seed, n, max(1, min(32, os.cpu_count() or 1)))
+    frames = S.render_sequence(args.seed, n, render_workers())
     depths = [torch.from_numpy(f).cuda() for f in frames]
     host = [torch.from_numpy(f).pin_memory() for f in frames]
     intr = seq["intr"].as_array()
@@ -773,11 +949,16 @@ def run_surrogate(args, world, rank, local):
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = surrogate_cpu_baseline(frames, seq)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+        out["cpu_baseline"] = surrogate_cpu_baseline(frames, seq, cpu_sample_s)
     sg.close()
     ctx.close()
+    return out
+
+
+def run_surrogate(args, world, rank, local):
+    out = measure_surrogate(args, world, rank, local, args.frames)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def main():
@@ -791,6 +972,8 @@ def main():
         run_sequence(args, world, rank, local)
     elif args.workload == "surrogate":
         run_surrogate(args, world, rank, local)
+    elif args.workload == "sharded":
+        run_sharded(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

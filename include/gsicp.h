@@ -267,6 +267,44 @@ gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float
                             double b_out[6], int* iters_out, double* cost_out,
                             int64_t* inliers_out, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * One registration split across processes (Sec. 3, Eq. (MLE_for_T): the cost and its Gauss-Newton
+ * system are sums over the correspondences, so each process can take a share of the source
+ * points and the shares' sums add up to the whole registration's).
+ *
+ * Every process holds the whole map (its own gsicp_map) and a share of the source points:
+ *   gsicp_shard_begin      sets up this context's registration of its share from T0 (Morton order,
+ *                          first-iteration seeds, candidate cache), stream-ordered;
+ *   gsicp_shard_linearise  linearises at the current pose and writes the share's GSICP_SHARD_SUMS
+ *                          FP64 sums to partial_dev (device), stream-ordered: entries 0..20 the
+ *                          upper triangle of H row by row ((0,0), (0,1), .., (0,5), (1,1), ..),
+ *                          21..26 b, 27 the cost, 28 the correspondence count, 29 the sum of the
+ *                          correspondences' squared distances;
+ *   (the caller gathers every process's partial, e.g. an all-gather of GSICP_SHARD_SUMS doubles)
+ *   gsicp_shard_update     sums the nparts rows of sums_dev (nparts x GSICP_SHARD_SUMS, device) in
+ *                          row order, solves H delta = -b in FP64 and updates the pose as
+ *                          gsicp_register does, synchronises the stream and reports *status_out:
+ *                          GSICP_SHARD_RUNNING (linearise again), _CONVERGED, _MAXITER or
+ *                          _DEGENERATE (fewer than min_inliers correspondences in all, or H not
+ *                          positive definite; the call then returns GSICP_ERR_DEGENERATE).
+ * Processes that pass the same rows in the same order compute the same bits, so every process
+ * holds the same pose after every update.  T_out, H_out, iters_out, cost_out and inliers_out are
+ * nullable host outputs as in gsicp_register (H, cost and inliers of the whole, last
+ * linearisation).  Any other registration on the same context (gsicp_register, gsicp_linearise,
+ * gsicp_track_frame*) ends the shard registration; linearise / update without a begun one return
+ * GSICP_ERR_INVALID_ARG.
+ * ------------------------------------------------------------------------------------------- */
+#define GSICP_SHARD_SUMS 30
+typedef enum { GSICP_SHARD_RUNNING = 0, GSICP_SHARD_CONVERGED = 1, GSICP_SHARD_MAXITER = 2,
+               GSICP_SHARD_DEGENERATE = 3 } gsicp_shard_status;
+gsicp_status gsicp_shard_begin(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev,
+                               int64_t n, gsicp_map map, const double T0[16],
+                               const gsicp_reg_params* params, void* stream);
+gsicp_status gsicp_shard_linearise(gsicp_ctx ctx, double* partial_dev, void* stream);
+gsicp_status gsicp_shard_update(gsicp_ctx ctx, const double* sums_dev, int nparts, int* status_out,
+                                double T_out[16], double H_out[36], int* iters_out, double* cost_out,
+                                int64_t* inliers_out, void* stream);
+
 /* Batched registration (NEXT row of the hot path: many independent registrations at once; the
  * paper registers one frame at a time).  B pairs, each exactly as gsicp_register would register
  * it: source b (src_pts_dev[b], n[b] x 3, with covariances src_covs_dev[b], n[b] x 6) against map

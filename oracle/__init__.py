@@ -81,6 +81,7 @@ def _bind(lib):
     lib.orc_residual_jacobian.argtypes = [_D, _D, _D, _D, _D]
     lib.orc_register.argtypes = [_D, _D, C.c_long, C.c_void_p, _D, _D, _D, C.POINTER(RegParams), _D, _D, _D,
                                  C.POINTER(C.c_int), _D, C.POINTER(C.c_long)]
+    lib.orc_gn_update.argtypes = [_D, _D, _D, C.POINTER(RegParams)]
     lib.orc_register_fixed.argtypes = [_D, _D, C.c_long, _D, _D, _D, C.POINTER(RegParams), _D,
                                        C.POINTER(C.c_int), _D]
     lib.orc_set_threads.argtypes = [C.c_int]
@@ -283,6 +284,17 @@ def register(src, covs_s, map_: Map, T0, max_corr_dist: float = 0.1, max_iters: 
                           _p(_d(T0).reshape(16)), C.byref(prm), _p(T), _p(H), _p(b), C.byref(it),
                           _p(cost), C.byref(cnt))
     return dict(T=T, H=H, b=b, iters=int(it.value), cost=float(cost[0]), inliers=int(cnt.value), status=int(st))
+
+
+def gn_update(H, b, T, tol_rot: float = 1e-6, tol_trans: float = 1e-6):
+    """One Gauss-Newton update of the registration loop (Sec. 3): delta = -H^-1 b (Cholesky),
+    T <- exp(delta^) T.  Returns (T_new, r): r = 1 converged (|delta_omega| < tol_rot and
+    |delta_v| < tol_trans), 0 not yet, -1 H not positive definite (T unchanged)."""
+    lib = _load()
+    prm = RegParams(0.0, 1, tol_rot, tol_trans, 0)
+    Tn = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16)).copy()
+    r = lib.orc_gn_update(_p(_d(np.asarray(H).reshape(36))), _p(_d(np.asarray(b).reshape(6))), _p(Tn), C.byref(prm))
+    return Tn.reshape(4, 4), int(r)
 
 
 def register_fixed(src, covs_s, tgt, covs_t, T0, max_iters: int = 50, tol_rot: float = 1e-12,

@@ -699,6 +699,11 @@ static int gn_update(const double H[36], const double b[6], double T[16], const 
     return (dw < prm->tol_rot && dv < prm->tol_trans) ? 1 : 0;
 }
 
+int orc_gn_update(const double H[36], const double b[6], double T[16], const orc_reg_params* prm)
+{
+    return gn_update(H, b, T, prm);
+}
+
 int orc_register(const double* src, const double* covs_s, long n, const orc_kdtree* map_tree,
                  const double* map, const double* covs_t, const double T0[16],
                  const orc_reg_params* prm, double T_out[16], double H_out[36], double b_out[6],

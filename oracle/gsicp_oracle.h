@@ -88,6 +88,11 @@ typedef struct {
     int min_inliers;
 } orc_reg_params;
 
+/* One Gauss-Newton update of the registration loop (Sec. 3, Eq. (MLE_for_T); G-ICP's optimiser):
+ * delta = -H^-1 b by Cholesky, T <- exp(delta^) T.  Returns 1 when |delta_omega| < tol_rot and
+ * |delta_v| < tol_trans, 0 otherwise, -1 (T unchanged) when H is not positive definite. */
+int orc_gn_update(const double H[36], const double b[6], double T[16], const orc_reg_params* prm);
+
 /* Full registration (Gauss-Newton on Eq. MLE_for_T).  Returns ORC_OK or
  * ORC_ERR_DEGENERATE; T_out always holds the last valid pose. */
 int orc_register(const double* src, const double* covs_s, long n, const orc_kdtree* map_tree,

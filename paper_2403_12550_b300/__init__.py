@@ -20,7 +20,8 @@ __all__ = [
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
     "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_set_gn_launch_mode", "GN_GRAPH", "GN_PLAIN", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
-    "gsicp_build_map_index", "gsicp_map_append",
+    "gsicp_build_map_index", "gsicp_map_append", "gsicp_shard_begin", "gsicp_shard_linearise", "gsicp_shard_update",
+    "SHARD_SUMS", "SHARD_RUNNING", "SHARD_CONVERGED", "SHARD_MAXITER", "SHARD_DEGENERATE",
     "gsicp_map_rebuild", "gsicp_map_inspect", "gsicp_map_size", "gsicp_map_destroy", "gsicp_transform_gaussians", "gsicp_register", "gsicp_register_batch", "gsicp_selftest_batch_timeout", "gsicp_linearise",
     "gsicp_map_nearest", "gsicp_track_frame", "gsicp_track_frame_host",
     "KeyframeParams", "FrameInfo", "Tracker", "FRAME", "KEYFRAME", "MAPPING_KEYFRAME",
@@ -32,6 +33,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgsicp.so
 
 PLANE, ELLIPSE, NONE = 0, 1, 2
 GN_GRAPH, GN_PLAIN = 0, 1
+SHARD_SUMS = 30
+SHARD_RUNNING, SHARD_CONVERGED, SHARD_MAXITER, SHARD_DEGENERATE = range(4)
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_TIMEOUT, ERR_NOT_IMPLEMENTED, ERR_CAPACITY = range(8)
 
 
@@ -130,6 +133,10 @@ _sig("gsicp_map_destroy", None, [_vp])
 _sig("gsicp_transform_gaussians", C.c_int, [_dp, _vp, _vp, C.c_int64, _vp, _vp, _vp])
 _sig("gsicp_register", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(RegParams), _dp, _dp, _dp,
                                  C.POINTER(C.c_int), _dp, _i64p, _vp])
+_sig("gsicp_shard_begin", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _dp, C.POINTER(RegParams), _vp])
+_sig("gsicp_shard_linearise", C.c_int, [_vp, _vp, _vp])
+_sig("gsicp_shard_update", C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_int), _dp, _dp, C.POINTER(C.c_int), _dp,
+                                     _i64p, _vp])
 _sig("gsicp_register_batch", C.c_int, [_vp, C.c_int, _vp, _vp, _i64p, _vp, _dp, C.POINTER(RegParams), _dp,
                                        C.POINTER(C.c_int), _dp, _i64p, C.POINTER(C.c_int), _vp])
 _sig("gsicp_selftest_batch_timeout", C.c_int, [_vp, _vp])
@@ -421,6 +428,34 @@ def gsicp_register(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: Ma
     _check(st, "gsicp_register", allow=(ERR_DEGENERATE,))
     return dict(T=np.array(T).reshape(4, 4), H=np.array(H).reshape(6, 6), b=np.array(b), iters=it.value,
                 cost=cost.value, inliers=cnt.value, status=st)
+
+
+def gsicp_shard_begin(ctx: Context, src: torch.Tensor, covs: torch.Tensor, map_: MapHandle, T0, params: RegParams):
+    """Set up this context's registration of its share of a split registration's source points."""
+    _check(lib.gsicp_shard_begin(ctx.ptr, _dev(src, cols=3), _dev(covs, cols=6), src.shape[0], map_.ptr, _pose(T0),
+                                 C.byref(params), _stream()), "gsicp_shard_begin")
+
+
+def gsicp_shard_linearise(ctx: Context, partial_out: torch.Tensor):
+    """Linearise the share at the current pose: its SHARD_SUMS float64 sums go to partial_out (device,
+    stream-ordered, no synchronisation)."""
+    if partial_out.numel() != SHARD_SUMS:
+        raise ValueError(f"partial_out must hold {SHARD_SUMS} values")
+    _check(lib.gsicp_shard_linearise(ctx.ptr, _dev(partial_out, torch.float64), _stream()), "gsicp_shard_linearise")
+
+
+def gsicp_shard_update(ctx: Context, sums: torch.Tensor) -> dict:
+    """Solve and update from every share's sums (sums: nparts x SHARD_SUMS float64 device rows, summed
+    in row order).  Returns dict(status (SHARD_*), T, H, iters, cost, inliers); synchronises."""
+    if sums.dim() != 2 or sums.shape[1] != SHARD_SUMS:
+        raise ValueError(f"sums must be (nparts, {SHARD_SUMS})")
+    T, H, b, it, cost, cnt = _reg_outputs()
+    status = C.c_int(-1)
+    st = lib.gsicp_shard_update(ctx.ptr, _dev(sums, torch.float64), sums.shape[0], C.byref(status), T, H,
+                                C.byref(it), C.byref(cost), C.byref(cnt), _stream())
+    _check(st, "gsicp_shard_update", allow=(ERR_DEGENERATE,))
+    return dict(status=status.value, T=np.array(T).reshape(4, 4), H=np.array(H).reshape(6, 6), iters=it.value,
+                cost=cost.value, inliers=cnt.value)
 
 
 def gsicp_register_batch(ctx: Context, srcs: list, covs: list, maps: list, T0s, params: RegParams) -> dict:

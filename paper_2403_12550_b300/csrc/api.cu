@@ -205,6 +205,7 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     ctx->frame_pts.release(); ctx->frame_z.release(); ctx->frame_covs.release(); ctx->frame_depth.release();
     ctx->frame_idx.release(); ctx->fb_list.release(); ctx->fb_count.release();
     ctx->covs_sorted.release();
+    ctx->shard_sums.release();
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -447,6 +448,53 @@ gsicp_status gsicp_register(gsicp_ctx ctx, const float* src_pts_dev, const float
                           map, params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, (int)n, true, s));
     return finish_registration(ctx, s, T_out, H_out, b_out, iters_out, cost_out, inliers_out);
+}
+
+static_assert(NACC == GSICP_SHARD_SUMS, "shard sums are the Gauss-Newton kernel's accumulators");
+static_assert((int)GSICP_SHARD_RUNNING == (int)REG_ST_RUNNING && (int)GSICP_SHARD_CONVERGED == (int)REG_ST_CONVERGED &&
+                  (int)GSICP_SHARD_MAXITER == (int)REG_ST_MAXITER &&
+                  (int)GSICP_SHARD_DEGENERATE == (int)REG_ST_DEGENERATE,
+              "shard status values are the registration state's");
+
+gsicp_status gsicp_shard_begin(gsicp_ctx ctx, const float* src_pts_dev, const float* src_covs_dev, int64_t n,
+                               gsicp_map map, const double T0[16], const gsicp_reg_params* params, void* stream)
+{
+    if (!ctx || !map || !T0 || !valid_reg_params(params) || n < 0 || n > (1 << 30) || !valid_pose(T0))
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_shard_begin: invalid argument");
+    if (n > 0 && (!src_pts_dev || !src_covs_dev))
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_shard_begin: NULL source points or covariances");
+    cudaStream_t s = (cudaStream_t)stream;
+    GSICP_CHECK(ctx->shard_sums.ensure(sizeof(double) * NACC));
+    GSICP_CHECK(prepare_source(ctx, src_pts_dev, src_covs_dev, (int)n, s));
+    RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), ctx->n_dev.as<int>(),
+                          map, params);
+    return reg_shard_begin(ctx->reg, job, T0, (int)n, ctx->shard_sums.as<double>(), s);
+}
+
+gsicp_status gsicp_shard_linearise(gsicp_ctx ctx, double* partial_dev, void* stream)
+{
+    if (!ctx || !partial_dev) return set_error(GSICP_ERR_INVALID_ARG, "gsicp_shard_linearise: NULL argument");
+    if (!ctx->reg.shard)
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_shard_linearise: no shard registration begun on this context");
+    cudaStream_t s = (cudaStream_t)stream;
+    GSICP_CHECK(reg_shard_linearise(ctx->reg, s));
+    GSICP_CUDA(cudaMemcpyAsync(partial_dev, ctx->shard_sums.ptr, sizeof(double) * NACC, cudaMemcpyDeviceToDevice, s));
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_shard_update(gsicp_ctx ctx, const double* sums_dev, int nparts, int* status_out, double T_out[16],
+                                double H_out[36], int* iters_out, double* cost_out, int64_t* inliers_out,
+                                void* stream)
+{
+    if (!ctx || !sums_dev || nparts < 1 || !status_out)
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_shard_update: NULL argument or nparts < 1");
+    if (!ctx->reg.shard)
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_shard_update: no shard registration begun on this context");
+    cudaStream_t s = (cudaStream_t)stream;
+    GSICP_CHECK(reg_shard_update(ctx->reg, sums_dev, nparts, s));
+    const gsicp_status st = finish_registration(ctx, s, T_out, H_out, nullptr, iters_out, cost_out, inliers_out);
+    *status_out = ctx->reg.state_host->status;
+    return st;
 }
 
 gsicp_status gsicp_register_batch(gsicp_ctx ctx, int B, const float* const* src_pts_dev,

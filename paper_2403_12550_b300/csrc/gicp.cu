@@ -652,37 +652,15 @@ __device__ __forceinline__ void group_sum(const float* __restrict__ partials, in
     grow[64l * g + 32 + c] = a.lo;
 }
 
-// The block that completed the last group: the compensated sum of the ng group rows, then in its
-// first warp the H, b, cost and inliers of this linearisation and (solve mode) the FP64 solve, the
-// pose update and the stopping test.  Returns whether another iteration should run (on lane 0 of
-// warp 0; false elsewhere).  t_start: globaltimer when the block became the last.
-__device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const float* __restrict__ grow, int ng,
-                                         int it_now, unsigned long long t_start)
+// Warp 0 (all 32 lanes): records H, b, cost, inliers and the squared residuals of a linearisation
+// whose NACC sums are tot[0 .. NACC) into the state and, when solve is set, solves H delta = -b in
+// FP64 (Cholesky), applies T <- exp(delta^) T and takes the stopping decision: fewer than
+// min_inliers correspondences or H not positive definite stop the registration as degenerate.
+// Returns whether another iteration should run (the same value on every lane).
+__device__ __forceinline__ bool record_and_solve(const RegJob& J, RegState* st, const double* tot, int lane,
+                                                 int it_now, bool solve)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ double tot[32];
-    if (warp == 0) {
-        dfloat a = {0.f, 0.f};
-        for (int g0 = 0; g0 < ng; g0 += 8) {
-            float hi[8], lo[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const bool in = g0 + j < ng;
-                hi[j] = in ? __ldcg(grow + 64l * (g0 + j) + lane) : 0.f;
-                lo[j] = in ? __ldcg(grow + 64l * (g0 + j) + 32 + lane) : 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) df_merge(a, hi[j], lo[j]);
-        }
-        tot[lane] = (double)a.hi + (double)a.lo;
-    }
-    __syncthreads();
-    if (warp != 0) return false;
-
-    // ---- warp 0: H, b, cost and inliers of this linearisation, then the lane-parallel FP64 solve
     const double tot_l = lane < NACC ? tot[lane] : 0.0;  // component `lane`
-    unsigned long long t_solve = 0;
-    if (lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_solve));
     if (lane < 21) {
         int r = 0;
         while (ut(r, 5) < lane) ++r;
@@ -698,10 +676,9 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
     } else if (lane == 29) {
         st->sqdist = tot_l;
     }
-    if (lane == 0) st->counter = 0u;
     const long long inliers = (long long)llrint(tot[28]);
     bool more = false;
-    if (J.mode == REG_MODE_SOLVE) {
+    if (solve) {
         // lane p < 27 takes entry (i, j) of [H ; -b^T]
         int ci = 0, cj = 0;
         if (lane < 27) chol_lane_coords(lane, ci, cj);
@@ -736,6 +713,42 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
             if (status != REG_ST_RUNNING) st->status = status;
         }
     }
+    return more;
+}
+
+// The block that completed the last group: the compensated sum of the ng group rows, then in its
+// first warp the H, b, cost and inliers of this linearisation and (solve mode) the FP64 solve, the
+// pose update and the stopping test.  Returns whether another iteration should run (on lane 0 of
+// warp 0; false elsewhere).  t_start: globaltimer when the block became the last.
+__device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const float* __restrict__ grow, int ng,
+                                         int it_now, unsigned long long t_start)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double tot[32];
+    if (warp == 0) {
+        dfloat a = {0.f, 0.f};
+        for (int g0 = 0; g0 < ng; g0 += 8) {
+            float hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bool in = g0 + j < ng;
+                hi[j] = in ? __ldcg(grow + 64l * (g0 + j) + lane) : 0.f;
+                lo[j] = in ? __ldcg(grow + 64l * (g0 + j) + 32 + lane) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) df_merge(a, hi[j], lo[j]);
+        }
+        tot[lane] = (double)a.hi + (double)a.lo;
+    }
+    __syncthreads();
+    if (warp != 0) return false;
+
+    // ---- warp 0: H, b, cost and inliers of this linearisation, then the lane-parallel FP64 solve
+    unsigned long long t_solve = 0;
+    if (lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_solve));
+    if (lane == 0) st->counter = 0u;
+    if (J.sums_out && lane < NACC) J.sums_out[lane] = tot[lane];
+    const bool more = record_and_solve(J, st, tot, lane, it_now, J.mode == REG_MODE_SOLVE);
     if (lane == 0) {
         unsigned long long t_end;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
@@ -1087,28 +1100,88 @@ void RegMachine::release()
     anchor.release();
 }
 
-gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], int n_cap, bool solve,
-                     cudaStream_t s)
+// Buffers, first-iteration seeds and initial state of a registration of up to n_cap points; job
+// (with the machine's buffers filled in) is copied to rm.job.
+static gsicp_status reg_prepare(RegMachine& rm, RegJob& job, const double T0[16], int n_cap, cudaStream_t s)
 {
     GSICP_CHECK(rm.init(n_cap));
     GSICP_CHECK(rm.cand.ensure(sizeof(int) * KC * (size_t)std::max(n_cap, 1)));
     GSICP_CHECK(rm.anchor.ensure(sizeof(float4) * (size_t)std::max(n_cap, 1)));
-    RegJob job = job_in;
     job.cand = rm.cand.as<int>();
     job.anchor = rm.anchor.as<float4>();
     job.partials = rm.partials.as<float>();
     job.st = rm.state.as<RegState>();
-    job.mode = solve ? REG_MODE_SOLVE : REG_MODE_LINEARISE;
-    job.use_cond = solve ? 1 : 0;
     Pose16 P;
     for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
     GSICP_CHECK(launch_seed(job.map, job.src, job.n, n_cap, T0, job.cand, job.anchor, s));
     reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
     GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+// The update of a registration whose source points are split across processes: the sums of the
+// nparts partial linearisations (NACC doubles each, summed in the order given, so every process
+// that passes the same rows gets the same bits) are recorded and solved exactly as the single
+// registration's last block does.  One warp.
+__global__ void shard_update_kernel(const RegJob* __restrict__ jp, const double* __restrict__ parts, int nparts)
+{
+    __shared__ double tot[32];
+    const int lane = threadIdx.x;
+    double v = 0.0;
+    if (lane < NACC)
+        for (int q = 0; q < nparts; ++q) v += parts[(long)NACC * q + lane];
+    tot[lane] = v;
+    __syncwarp();
+    const RegJob& J = *jp;
+    RegState* st = J.st;
+    const int it_now = st->iter;
+    if (st->status != REG_ST_RUNNING) return;
+    record_and_solve(J, st, tot, lane, it_now, true);
+    __threadfence();
+}
+
+gsicp_status reg_shard_begin(RegMachine& rm, const RegJob& job_in, const double T0[16], int n_cap, double* sums_out,
+                             cudaStream_t s)
+{
+    RegJob job = job_in;
+    job.mode = REG_MODE_LINEARISE;
+    job.use_cond = 0;
+    job.sums_out = sums_out;
+    GSICP_CHECK(reg_prepare(rm, job, T0, n_cap, s));
+    rm.shard = true;
+    return GSICP_OK;
+}
+
+gsicp_status reg_shard_linearise(RegMachine& rm, cudaStream_t s)
+{
+    gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+gsicp_status reg_shard_update(RegMachine& rm, const double* parts, int nparts, cudaStream_t s)
+{
+    shard_update_kernel<<<1, 32, 0, s>>>(rm.job.as<const RegJob>(), parts, nparts);
+    GSICP_CUDA(cudaGetLastError());
+    GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, sizeof(RegState), cudaMemcpyDeviceToHost, s));
+    return GSICP_OK;
+}
+
+gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], int n_cap, bool solve,
+                     cudaStream_t s)
+{
+    RegJob job = job_in;
+    job.mode = solve ? REG_MODE_SOLVE : REG_MODE_LINEARISE;
+    job.use_cond = solve ? 1 : 0;
+    job.sums_out = nullptr;
+    rm.shard = false;
+    GSICP_CHECK(reg_prepare(rm, job, T0, n_cap, s));
     if (solve && rm.unrolled) {
         // plain-launch mode: one launch per iteration, each a programmatic dependent of the one
         // before (finished launches exit at once)
         job.use_cond = 0;
+        Pose16 P;
+        for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
         reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -107,12 +107,22 @@ struct RegMachine {
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond{};
     bool unrolled = false;  // GSICP_GN_PLAIN: one plain launch per iteration instead of the graph
+    bool shard = false;     // the state belongs to a shard registration (reg_shard_begin, not reg_run since)
     gsicp_status init(int capacity);  // (re)builds the graph when the point capacity grows
     void release();
 };
 
 gsicp_status reg_run(RegMachine& rm, const RegJob& job, const double T0[16], int n_cap, bool solve,
                      cudaStream_t s);
+
+// A registration whose source points are split across processes (one shard here): set-up with the
+// linearisation sums going to sums_out (NACC doubles, device), one linearisation at the current
+// pose (the candidate cache carried over), and the update from the rows of every shard's sums
+// (state copied to rm.state_host, stream-ordered).
+gsicp_status reg_shard_begin(RegMachine& rm, const RegJob& job, const double T0[16], int n_cap, double* sums_out,
+                             cudaStream_t s);
+gsicp_status reg_shard_linearise(RegMachine& rm, cudaStream_t s);
+gsicp_status reg_shard_update(RegMachine& rm, const double* parts, int nparts, cudaStream_t s);
 
 // Morton order of B clouds at once (pts_dev / covs_dev: device arrays of B pointers; ofs_dev: B + 1
 // offsets of each cloud in the concatenated order, N = ofs[B]): src_out (N float4: x, y, z, index
@@ -173,6 +183,7 @@ struct gsicp_ctx_s {
     gsicp::DevBuf frame_pts, frame_z, frame_covs, frame_depth;
     gsicp::DevBuf frame_idx, fb_list, fb_count;  // sample -> point map; tree-search list of the window k-NN
     gsicp::DevBuf covs_sorted;         // source covariances in the source index's order
+    gsicp::DevBuf shard_sums;          // NACC doubles: the last shard linearisation's sums
     gsicp::RegMachine reg;
     gsicp::BatchMachine batch;
     int64_t* host_pinned = nullptr;   // small pinned scratch for counts

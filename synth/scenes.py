@@ -30,6 +30,7 @@ __all__ = [
     "transform_points", "Intrinsics", "REPLICA_INTR", "TUM_INTR",
     "pair_config1", "frame_config2", "spline_trajectory", "sequence_config3", "const_velocity",
     "batch_config4", "HALF_TUM_INTR", "surrogate_train_config5", "sequence_config5", "orbit_trajectory",
+    "render_sequence_frames",
 ]
 
 
@@ -504,3 +505,31 @@ def sequence_config5(seed: int = 0, n_frames: int = 500, intr: Intrinsics = TUM_
         return add_depth_noise(raycast_depth(scene, poses[f], intr), rng, noise_coeff)
 
     return dict(scene=scene, intr=intr, poses=poses, depth=depth)
+
+
+# --------------------------------------------------------------------------- parallel rendering
+
+_SEQUENCES = {"config3": "sequence_config3", "config5": "sequence_config5"}
+
+
+def _render_frames_job(args):
+    kind, seed, n_frames, frames = args
+    cfg = globals()[_SEQUENCES[kind]](seed, n_frames=n_frames)
+    return [cfg["depth"](f) for f in frames]
+
+
+def render_sequence_frames(kind: str, seed: int, n_frames: int, workers: int) -> np.ndarray:
+    """Depth images 0 .. n_frames-1 of ``sequence_config3`` (kind "config3") or ``sequence_config5``
+    ("config5") with that seed and length, ray-cast by ``workers`` processes (started by spawn, so a
+    parent that holds a CUDA context is safe); the same images as calling ``depth(f)`` in order."""
+    if kind not in _SEQUENCES:
+        raise ValueError(f"unknown sequence {kind!r}")
+    step = max(1, -(-n_frames // (max(1, workers) * 4)))
+    jobs = [(kind, seed, n_frames, list(range(a, min(n_frames, a + step)))) for a in range(0, n_frames, step)]
+    if workers <= 1 or len(jobs) <= 1:
+        parts = [_render_frames_job(j) for j in jobs]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            parts = pool.map(_render_frames_job, jobs)
+    return np.stack([d for part in parts for d in part]) if n_frames > 0 else np.zeros((0, 0, 0), np.float32)

@@ -25,7 +25,7 @@ def _rank(rank, world, port, out):
 
 def test_two_ranks_take_the_slowest_time_and_count_all_frames():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
         res = dict(out)

@@ -323,6 +323,17 @@ def test_one_gauss_newton_step_solves_the_normal_equations():
     L = np.real(logm(r["T"] @ np.linalg.inv(T0)))
     delta = np.array([L[2, 1], L[0, 2], L[1, 0], L[0, 3], L[1, 3], L[2, 3]])
     np.testing.assert_allclose(lin["H"] @ delta, -lin["b"], rtol=1e-7, atol=1e-8 * np.abs(lin["b"]).max())
+    # the exported update (the split registration's step) is the same step: from the same H, b and
+    # T0 it lands on the same pose, its matrix logarithm solving the same system
+    Tu, conv = orc.gn_update(lin["H"], lin["b"], T0)
+    assert conv == 0
+    np.testing.assert_array_equal(Tu, r["T"])
+    Lu = np.real(logm(Tu @ np.linalg.inv(T0)))
+    du = np.array([Lu[2, 1], Lu[0, 2], Lu[1, 0], Lu[0, 3], Lu[1, 3], Lu[2, 3]])
+    np.testing.assert_allclose(lin["H"] @ du, -lin["b"], rtol=1e-7, atol=1e-8 * np.abs(lin["b"]).max())
+    # a zero system is not positive definite: no step, pose unchanged
+    Tz, cz = orc.gn_update(np.zeros((6, 6)), np.zeros(6), T0)
+    assert cz == -1 and np.array_equal(Tz, T0)
 
 
 def _kabsch(P, Q):

@@ -49,3 +49,13 @@ def test_config5_half_res_grid_and_held_out_rooms():
     for sc in tr["scenes"]:
         assert not (np.array_equal(sc.box_center, held.box_center) and np.array_equal(sc.sph_center, held.sph_center))
     assert seq["depth"](3).shape == (480, 640)
+
+
+def test_parallel_rendering_equals_in_order_rendering():
+    from synth import render_sequence_frames, sequence_config3, sequence_config5
+    for kind, make in (("config3", sequence_config3), ("config5", sequence_config5)):
+        got = render_sequence_frames(kind, 2, 3, workers=2)
+        cfg = make(2, n_frames=3)
+        assert got.shape[0] == 3
+        for f in range(3):
+            np.testing.assert_array_equal(got[f], cfg["depth"](f))
