@@ -213,12 +213,17 @@ def run_ours(args, world, rank, local):
     if args.gn_plain:
         g.gsicp_ctx_set_gn_launch_mode(ctx, g.GN_PLAIN)
     means, covs = build_map_gpu(g, ctx, f, torch)
-    m = g.gsicp_build_map_index(ctx, means, covs)
-    n_map = m.size
     intr = f["intr"].as_array()
     cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
     rp = g.RegParams(MAX_DIST, MAX_ITERS, TOL, TOL, 6)
     depth_dev = torch.from_numpy(f["depth"]).cuda()
+    # the map index's shape and the context's cooperative-walk threshold, picked by the autotuner on
+    # this frame (untimed; every candidate gives the same poses)
+    from paper_2403_12550_b300.autotune import tune_frame
+    tune = tune_frame(ctx, depth_dev, intr, STRIDE, Z_MIN, Z_MAX, cp, means, covs, f["T0"], rp,
+                      key=f"frame-{f['depth'].shape}-{means.shape[0]}")
+    m = g.gsicp_build_map_index(ctx, means, covs, tune["bucket"], tune["cell"])
+    n_map = m.size
     depth_host = torch.from_numpy(f["depth"]).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -309,7 +314,12 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": job_throughput(world, K, total_s), "unit": "frames/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(npts, n_map, world), "gn_iters_mean": it_mean,
+        "config": {**workload_config(npts, n_map, world),
+                   "autotuned": {"index_bucket": tune["bucket"], "index_cell_m": tune["cell"],
+                                 "coop_walks": tune["coop"],
+                                 "frame_ms": {f"{b}/{c * 1e3:g}mm": round(v, 4) for (b, c), v in tune["ms"].items()},
+                                 "coop_frame_ms": {str(c): round(v, 4) for c, v in tune["coop_ms"].items()}}},
+        "gn_iters_mean": it_mean,
         "point_iters_per_s": world * float(npts) * sum(iters) / total_s,
         "phases_ms": {k: round(v, 4) for k, v in ph.items()},
         "tracking_only_frames_per_s": world * K / (total_s - sum(index_ms) / 1e3),

@@ -76,7 +76,7 @@ typedef struct {
  * hash grid of the Morton cells for the common short-range searches. */
 typedef struct {
     int bucket;          /* points per leaf: 8, 16 or 32 (0 = default 16) */
-    float cell;          /* grid cell size in metres (0 = default 0.008); coarsened automatically
+    float cell;          /* grid cell size in metres (0 = default 0.012); coarsened automatically
                             when 1024 cells per axis do not cover the map's bounding cube */
 } gsicp_index_params;
 
