@@ -99,7 +99,12 @@ static gsicp_status finish_registration(gsicp_ctx ctx, cudaStream_t s, double T_
 
 constexpr float CACHE_SLACK = 0.01f;  // m beyond max_corr_dist kept in the candidate cache (gicp.cu)
 constexpr float CACHE_STEP = 0.002f;  // m: points that moved more since their last search skip the cache
-constexpr float MAP_CELL = 0.008f;    // m: default map grid cell
+// m: default map grid cell.  With the benchmark frame's map (2.04M Gaussians from ten 1200x680 views,
+// ~3.6 per occupied 8 mm cell) 12 mm cells cut the Gauss-Newton loop from ~1.6 to ~1.25 ms against
+// 8 mm: their 2x2x2 block certifies more nearest-point searches and more complete candidate lists, so
+// fewer points walk the tree; larger cells cost more in the scans of the block (see autotune.py for
+// a per-map choice).
+constexpr float MAP_CELL = 0.012f;
 
 static RegJob make_job(gsicp_ctx ctx, const float4* src, const float4* covs_s, const int* n_dev, gsicp_map map,
                        const gsicp_reg_params* prm)
@@ -417,7 +422,7 @@ void gsicp_map_destroy(gsicp_map map)
     map->index.boxes.release();
     map->index.covs.release();
     map->index.keys.release();
-    map->index.cell.release();
+    map->index.grid_meta.release();
     map->index.quant.release();
     map->index.grid.release();
     map->means.release();

@@ -37,11 +37,10 @@ struct IndexView {
     const float4* covs;   // optional: 2 float4 per sorted point (xx,xy,xz,yy | yz,zz,-,-)
     const int* n;         // device count of valid points
     const uint32_t* keys; // sorted 30-bit Morton keys of the valid points (map indices only)
-    const int* cell;      // SEED_BITS-bit key prefix -> first sorted position with that prefix or above
-                          // (2^SEED_BITS + 1 entries; map indices only)
     const float4* quant;  // (lo.x, lo.y, lo.z, scale): Morton quantisation of this index
-    const int4* grid;     // hash table of occupied grid cells (map indices only), see grid_find
-    uint32_t grid_mask;   // table capacity - 1 (power of two); 0 when there is no grid
+    const int4* grid;     // hash table of occupied grid cells (map indices only; null: no grid), see grid_find
+    const uint32_t* grid_mask;  // device word: the table's live capacity - 1 (a power of two, sized on
+                                // the device from the number of occupied cells)
     int L;                // leaves (power of two)
     int B;                // points per leaf (8, 16 or 32)
 };
@@ -69,8 +68,6 @@ __device__ __forceinline__ int2 grid_find(const int4* __restrict__ table, uint32
     }
     return make_int2(0, 0);
 }
-
-constexpr int SEED_BITS = 21;  // 7 bits per axis: cells of 1/128 of the bounding cube
 
 // 30-bit Morton key of a point under the index's quantisation (clamped to the cube).
 __device__ __forceinline__ uint32_t morton_of(float4 qz, float x, float y, float z)

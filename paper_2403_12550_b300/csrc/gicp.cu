@@ -1298,14 +1298,13 @@ __device__ __forceinline__ void seed_point(const IndexView& map, int m, float4 q
                                            float4* __restrict__ anchor)
 {
     int seed = -1;
-    if (m > 0 && map.keys && map.cell) {
+    if (m > 0 && map.keys) {
         const float y0 = fmaf(Rt[0], x.x, fmaf(Rt[1], x.y, fmaf(Rt[2], x.z, Rt[3])));
         const float y1 = fmaf(Rt[4], x.x, fmaf(Rt[5], x.y, fmaf(Rt[6], x.z, Rt[7])));
         const float y2 = fmaf(Rt[8], x.x, fmaf(Rt[9], x.y, fmaf(Rt[10], x.z, Rt[11])));
         const uint32_t key = morton_of(qz, y0, y1, y2);
-        const uint32_t pre = key >> (30 - SEED_BITS);
-        int lo = map.cell[pre], hi = map.cell[pre + 1];
-        while (lo < hi) {  // Morton-nearest position within the query's cell
+        int lo = 0, hi = m;
+        while (lo < hi) {  // first sorted position whose key is not below the query's
             const int mid = (lo + hi) >> 1;
             if (map.keys[mid] < key) lo = mid + 1;
             else hi = mid;

@@ -287,13 +287,19 @@ static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, u
 // ------------------------------------------------------------------------------------------
 // index build kernels
 
+// bb: min[3] | max[3] (order-preserving encodings) | finished-block counter.  Set to the empty box
+// and zero once when the scratch is allocated; every bbox_quant_kernel leaves it so again.
 __global__ void bbox_init_kernel(uint32_t* bb)
 {
     if (threadIdx.x < 3) bb[threadIdx.x] = 0xffffffffu;      // min (ordered encoding)
-    else if (threadIdx.x < 6) bb[threadIdx.x] = 0u;          // max
+    else if (threadIdx.x < 7) bb[threadIdx.x] = 0u;          // max, counter
 }
 
-__global__ void bbox_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, uint32_t* bb)
+// Bounding box of the valid points, then (last block to finish) the Morton quantisation: cells of
+// size `cell` when 1024 of them cover the bounding cube, else 1024 cells across the cube; the
+// box words and the counter are reset for the next build.
+__global__ void bbox_quant_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, uint32_t* bb,
+                                  float cell, float4* __restrict__ quant)
 {
     const int n = *n_dev;
     float lo[3] = {GSICP_INF, GSICP_INF, GSICP_INF}, hi[3] = {-GSICP_INF, -GSICP_INF, -GSICP_INF};
@@ -315,6 +321,7 @@ __global__ void bbox_kernel(const float* __restrict__ pts, const int* __restrict
     }
     // one atomic per block and coordinate: same-address atomics from every warp serialise in L2
     __shared__ float slo[3][32], shi[3][32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) {
 #pragma unroll
@@ -338,8 +345,27 @@ __global__ void bbox_kernel(const float* __restrict__ pts, const int* __restrict
                 atomicMin(&bb[a], f2ord(lo[a]));
                 atomicMax(&bb[3 + a], f2ord(hi[a]));
             }
+            __threadfence();
+            last = atomicAdd(&bb[6], 1u) == gridDim.x - 1;
         }
     }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    uint32_t w[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) w[a] = __ldcg(&bb[a]);
+    const float lx = ord2f(w[0]), ly = ord2f(w[1]), lz = ord2f(w[2]);
+    const float ext = fmaxf(fmaxf(ord2f(w[3]) - lx, ord2f(w[4]) - ly), ord2f(w[5]) - lz);
+    float scale = ext > 0.f ? 1024.f / ext : 0.f;
+    if (cell > 0.f && !(ext > 1024.f * cell)) scale = 1.f / cell;
+    *quant = make_float4(lx, ly, lz, scale);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        bb[a] = 0xffffffffu;
+        bb[3 + a] = 0u;
+    }
+    bb[6] = 0u;
 }
 
 // 30-bit Morton key of each valid point over the bounding cube; padding slots get
@@ -356,29 +382,43 @@ __global__ void morton_kernel(const float* __restrict__ pts, const int* __restri
     }
 }
 
-// Quantisation of the Morton grid: cells of size `cell` when 1024 of them cover the bounding
-// cube, else 1024 cells across the cube.
-__global__ void quant_kernel(const uint32_t* __restrict__ bb, float cell, float4* __restrict__ quant)
+// The live size of the cell hash table: a power of two at least twice the number of occupied
+// cells (load factor <= 1/2), at least 1024, at most the allocated capacity.  meta: [0] live
+// capacity - 1, [1] occupied cells (counted by gather_leaf_kernel; reset here for the next build).
+__global__ void grid_size_kernel(uint32_t* __restrict__ meta, uint32_t max_capacity)
 {
-    const float lx = ord2f(bb[0]), ly = ord2f(bb[1]), lz = ord2f(bb[2]);
-    const float ext = fmaxf(fmaxf(ord2f(bb[3]) - lx, ord2f(bb[4]) - ly), ord2f(bb[5]) - lz);
-    float scale = ext > 0.f ? 1024.f / ext : 0.f;
-    if (cell > 0.f && !(ext > 1024.f * cell)) scale = 1.f / cell;
-    *quant = make_float4(lx, ly, lz, scale);
+    const uint32_t cells = meta[1];
+    uint32_t cap = 1024;
+    while (cap < 2u * cells && cap < max_capacity) cap <<= 1;
+    meta[0] = min(cap, max_capacity) - 1u;
+    meta[1] = 0u;
 }
 
-__global__ void grid_insert_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
-                                   int4* __restrict__ table, uint32_t mask)
+__global__ void grid_clear_kernel(int4* __restrict__ table, const uint32_t* __restrict__ meta, uint32_t max_capacity)
+{
+    const uint32_t live = meta[0] + 1u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < min(live, max_capacity); i += gridDim.x * blockDim.x)
+        table[i] = make_int4((int)GRID_EMPTY, 0, 0, 0);
+}
+
+// One entry per occupied cell: the thread of a cell's first sorted point finds the cell's end by
+// reading on while the key repeats (cells hold a handful of points) and inserts (key, start, end).
+__global__ void grid_fill_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
+                                 int4* __restrict__ table, const uint32_t* __restrict__ meta)
 {
     const int n = *n_dev;
+    const uint32_t mask = meta[0];
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const uint32_t key = keys[s];
         if (s > 0 && keys[s - 1] == key) continue;  // not the first point of its cell
+        int end = s + 1;
+        while (end < n && keys[end] == key) ++end;
         uint32_t slot = grid_hash(key) & mask;
         for (uint32_t probe = 0; probe <= mask; ++probe) {
             const uint32_t prev = atomicCAS(reinterpret_cast<unsigned int*>(&table[slot].x), GRID_EMPTY, key);
-            if (prev == GRID_EMPTY || prev == key) {
+            if (prev == GRID_EMPTY) {  // each key is inserted by one thread only
                 table[slot].y = s;
+                table[slot].z = end;
                 break;
             }
             slot = (slot + 1) & mask;
@@ -386,81 +426,59 @@ __global__ void grid_insert_kernel(const uint32_t* __restrict__ keys, const int*
     }
 }
 
-__global__ void grid_end_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
-                                int4* __restrict__ table, uint32_t mask)
+// The sorted copy (one slot per thread, block b = slots [256 b, 256 b + 256)): points (x, y, z,
+// original index) and covariances gathered in sorted order, padding slots beyond n set to +inf;
+// the sorted keys copied out (keys_out, nullable); the occupied cells counted into
+// grid_meta[1] (nullable); and the leaf boxes, each leaf's B slots being B consecutive lanes of
+// one warp (B divides 32).
+__global__ void __launch_bounds__(256) gather_leaf_kernel(const float* __restrict__ pts, const float* __restrict__ covs,
+                                                          const uint32_t* __restrict__ order,
+                                                          const uint32_t* __restrict__ skeys,
+                                                          const int* __restrict__ n_dev, int total, int L, int B,
+                                                          float4* __restrict__ spts, float4* __restrict__ scovs,
+                                                          float4* __restrict__ boxes, uint32_t* __restrict__ keys_out,
+                                                          int keys_n, uint32_t* __restrict__ grid_meta)
 {
     const int n = *n_dev;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const uint32_t key = keys[s];
-        if (s + 1 < n && keys[s + 1] == key) continue;  // not the last point of its cell
-        uint32_t slot = grid_hash(key) & mask;
-        for (uint32_t probe = 0; probe <= mask; ++probe) {
-            if ((uint32_t)table[slot].x == key) {
-                table[slot].z = s + 1;
-                break;
-            }
-            slot = (slot + 1) & mask;
-        }
-    }
-}
-
-// cell[p] = first sorted position whose key prefix (top SEED_BITS bits) is >= p.
-__global__ void cell_table_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
-                                  int* __restrict__ cell)
-{
-    const int n = *n_dev;
-    const int ncell = 1 << SEED_BITS;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p <= ncell; p += gridDim.x * blockDim.x) {
-        const uint32_t target = (uint32_t)p << (30 - SEED_BITS);
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (keys[mid] < target) lo = mid + 1;
-            else hi = mid;
-        }
-        cell[p] = p == ncell ? n : lo;
-    }
-}
-
-__global__ void gather_kernel(const float* __restrict__ pts, const float* __restrict__ covs,
-                              const uint32_t* __restrict__ order, const int* __restrict__ n_dev, int total,
-                              float4* __restrict__ spts, float4* __restrict__ scovs)
-{
-    const int n = *n_dev;
-    for (long s = (long)blockIdx.x * blockDim.x + threadIdx.x; s < total; s += (long)gridDim.x * blockDim.x) {
+    const long s = (long)blockIdx.x * 256 + threadIdx.x;
+    float4 p = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, __int_as_float(-1));
+    bool starts = false;
+    if (s < total) {
         if (s < n) {
             const uint32_t i = order[s];
-            spts[s] = make_float4(pts[3l * i], pts[3l * i + 1], pts[3l * i + 2], __int_as_float((int)i));
+            p = make_float4(pts[3l * i], pts[3l * i + 1], pts[3l * i + 2], __int_as_float((int)i));
             if (scovs) {
                 const float* c = covs + 6l * i;
                 scovs[2 * s] = make_float4(c[0], c[1], c[2], c[3]);
                 scovs[2 * s + 1] = make_float4(c[4], c[5], 0.f, 0.f);
             }
-        } else {
-            spts[s] = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, __int_as_float(-1));
-            if (scovs) {
-                scovs[2 * s] = make_float4(0.f, 0.f, 0.f, 0.f);
-                scovs[2 * s + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            starts = s == 0 || skeys[s - 1] != skeys[s];
+        } else if (scovs) {
+            scovs[2 * s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            scovs[2 * s + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        spts[s] = p;
+        if (keys_out && s < keys_n) keys_out[s] = skeys[s];
+    }
+    if (grid_meta) {
+        const int c = __syncthreads_count(starts);
+        if (threadIdx.x == 0 && c) atomicAdd(&grid_meta[1], (uint32_t)c);
+    }
+    // leaf box over the leaf's valid points (padding slots hold +inf and contribute nothing)
+    const bool valid = s < n;
+    float lo[3] = {valid ? p.x : GSICP_INF, valid ? p.y : GSICP_INF, valid ? p.z : GSICP_INF};
+    float hi[3] = {valid ? p.x : -GSICP_INF, valid ? p.y : -GSICP_INF, valid ? p.z : -GSICP_INF};
+    for (int o = B >> 1; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
     }
-}
-
-__global__ void leaf_box_kernel(const float4* __restrict__ spts, const int* __restrict__ n_dev, int L, int B,
-                                float4* __restrict__ boxes)
-{
-    const int n = *n_dev;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
-        float4 lo = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, 0.f);
-        float4 hi = make_float4(-GSICP_INF, -GSICP_INF, -GSICP_INF, 0.f);
-        const int beg = l * B, end = min(beg + B, n);
-        for (int s = beg; s < end; ++s) {
-            float4 p = spts[s];
-            lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
-            hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
-        }
-        boxes[2l * (L + l)] = lo;
-        boxes[2l * (L + l) + 1] = hi;
+    if (s < total && (threadIdx.x & (B - 1)) == 0) {
+        const long leaf = s / B;
+        boxes[2l * (L + leaf)] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        boxes[2l * (L + leaf) + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
     }
 }
 
@@ -529,46 +547,49 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
     GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * sort_n));
     GSICP_CHECK(scr.v0.ensure(sizeof(uint32_t) * sort_n));
     GSICP_CHECK(scr.v1.ensure(sizeof(uint32_t) * sort_n));
-    GSICP_CHECK(scr.bbox.ensure(sizeof(uint32_t) * 8));
     const int sms = device_sm_count();
     const int grid = std::max(1, std::min((cap + 255) / 256, sms * 8));
     GSICP_CHECK(out.quant.ensure(sizeof(float4)));
-    bbox_init_kernel<<<1, 32, 0, s>>>(scr.bbox.as<uint32_t>());
-    bbox_kernel<<<std::max(1, std::min((cap + 255) / 256, sms * 2)), 256, 0, s>>>(pts, n_dev,
-                                                                                 scr.bbox.as<uint32_t>());
-    quant_kernel<<<1, 1, 0, s>>>(scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>());
+    const void* bb_before = scr.bbox.ptr;
+    GSICP_CHECK(scr.bbox.ensure(sizeof(uint32_t) * 8));
+    if (!scr.bbox_ready || scr.bbox.ptr != bb_before) {
+        bbox_init_kernel<<<1, 32, 0, s>>>(scr.bbox.as<uint32_t>());
+        scr.bbox_ready = true;
+    }
+    bbox_quant_kernel<<<std::max(1, std::min((cap + 255) / 256, sms * 2)), 256, 0, s>>>(
+        pts, n_dev, scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>());
     morton_kernel<<<grid, 256, 0, s>>>(pts, n_dev, cap, out.quant.as<float4>(), scr.k0.as<uint32_t>(),
                                        scr.v0.as<uint32_t>());
     GSICP_CUDA(cudaGetLastError());
     GSICP_CHECK(radix_sort_pairs(scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
                                  scr.v1.as<uint32_t>(), cap, 30, scr.hist, scr.sums, s));
-    const int ggrid = std::max(1, std::min((total + 255) / 256, sms * 8));
-    gather_kernel<<<ggrid, 256, 0, s>>>(pts, covs, scr.v0.as<uint32_t>(), n_dev, total, out.pts.as<float4>(),
-                                        covs ? out.covs.as<float4>() : nullptr);
-    leaf_box_kernel<<<std::max(1, std::min((L + 255) / 256, sms * 8)), 256, 0, s>>>(out.pts.as<float4>(), n_dev,
-                                                                                    L, B, out.boxes.as<float4>());
+    uint32_t grid_capacity = 0;
+    if (with_grid) {
+        grid_capacity = 1024;
+        while (grid_capacity < 2u * (uint32_t)sort_n) grid_capacity <<= 1;
+        GSICP_CHECK(out.grid.ensure(sizeof(int4) * (size_t)grid_capacity));
+        const void* meta_before = out.grid_meta.ptr;
+        GSICP_CHECK(out.grid_meta.ensure(sizeof(uint32_t) * 4));
+        if (!out.has_grid || out.grid_meta.ptr != meta_before)
+            GSICP_CUDA(cudaMemsetAsync(out.grid_meta.ptr, 0, sizeof(uint32_t) * 4, s));
+    }
+    out.has_grid = with_grid;
+    if (with_seed) GSICP_CHECK(out.keys.ensure(sizeof(uint32_t) * (size_t)sort_n));
+    gather_leaf_kernel<<<(total + 255) / 256, 256, 0, s>>>(
+        pts, covs, scr.v0.as<uint32_t>(), scr.k0.as<uint32_t>(), n_dev, total, L, B, out.pts.as<float4>(),
+        covs ? out.covs.as<float4>() : nullptr, out.boxes.as<float4>(), with_seed ? out.keys.as<uint32_t>() : nullptr,
+        sort_n, with_grid ? out.grid_meta.as<uint32_t>() : nullptr);
     for (int count = L; count > 1; count = count / std::min(256, count)) {
         const int blocks = count / std::min(256, count);
         level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
     }
     if (with_grid) {
-        uint32_t capacity = 1024;
-        while (capacity < 2u * (uint32_t)sort_n) capacity <<= 1;
-        GSICP_CHECK(out.grid.ensure(sizeof(int4) * (size_t)capacity));
-        out.grid_mask = capacity - 1;
-        GSICP_CUDA(cudaMemsetAsync(out.grid.ptr, 0xff, sizeof(int4) * (size_t)capacity, s));
-        grid_insert_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(), out.grid_mask);
-        grid_end_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(), out.grid_mask);
-    } else {
-        out.grid_mask = 0;
-    }
-    if (with_seed) {
-        GSICP_CHECK(out.keys.ensure(sizeof(uint32_t) * (size_t)sort_n));
-        GSICP_CHECK(out.cell.ensure(sizeof(int) * ((size_t(1) << SEED_BITS) + 1)));
-        GSICP_CUDA(cudaMemcpyAsync(out.keys.ptr, scr.k0.ptr, sizeof(uint32_t) * (size_t)sort_n,
-                                   cudaMemcpyDeviceToDevice, s));
-        cell_table_kernel<<<std::min(((1 << SEED_BITS) + 256) / 256, sms * 8), 256, 0, s>>>(
-            out.keys.as<uint32_t>(), n_dev, out.cell.as<int>());
+        const int ggrid = std::max(1, std::min((cap + 255) / 256, sms * 8));
+        grid_size_kernel<<<1, 1, 0, s>>>(out.grid_meta.as<uint32_t>(), grid_capacity);
+        grid_clear_kernel<<<std::max(1, std::min((int)(grid_capacity / 256), sms * 8)), 256, 0, s>>>(
+            out.grid.as<int4>(), out.grid_meta.as<uint32_t>(), grid_capacity);
+        grid_fill_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(),
+                                               out.grid_meta.as<uint32_t>());
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
@@ -632,7 +653,7 @@ __global__ void seg_quant_kernel(const uint32_t* __restrict__ bb, int B, float4*
     const uint32_t* q = bb + 6 * b;
     const float lx = ord2f(q[0]), ly = ord2f(q[1]), lz = ord2f(q[2]);
     const float ext = fmaxf(fmaxf(ord2f(q[3]) - lx, ord2f(q[4]) - ly), ord2f(q[5]) - lz);
-    quant[b] = make_float4(lx, ly, lz, ext > 0.f ? 1024.f / ext : 0.f);  // as quant_kernel with no cell
+    quant[b] = make_float4(lx, ly, lz, ext > 0.f ? 1024.f / ext : 0.f);  // as bbox_quant_kernel with no cell
 }
 
 __global__ void seg_morton_kernel(const float* const* __restrict__ ptrs, const int64_t* __restrict__ ofs, int B,
@@ -684,6 +705,7 @@ gsicp_status batch_morton_order(const float* const* pts_dev, const float* const*
     GSICP_CHECK(quant.ensure(sizeof(float4) * (size_t)B));
     const int sms = device_sm_count();
     const int grid = (int)std::max<long>(1, std::min<long>((N + 255) / 256, sms * 8));
+    scr.bbox_ready = false;  // the segmented boxes below leave the words in another state
     seg_bbox_init_kernel<<<(6 * B + 255) / 256, 256, 0, s>>>(scr.bbox.as<uint32_t>(), B);
     seg_bbox_kernel<<<grid, 256, 0, s>>>(pts_dev, ofs_dev, B, N, scr.bbox.as<uint32_t>());
     seg_quant_kernel<<<(B + 255) / 256, 256, 0, s>>>(scr.bbox.as<uint32_t>(), B, quant.as<float4>());
@@ -709,10 +731,9 @@ IndexView IndexBufs::view() const
     v.covs = covs.ptr ? covs.as<const float4>() : nullptr;
     v.n = n_ptr;
     v.keys = keys.ptr ? keys.as<const uint32_t>() : nullptr;
-    v.cell = cell.ptr ? cell.as<const int>() : nullptr;
     v.quant = quant.as<const float4>();
-    v.grid = grid_mask ? grid.as<const int4>() : nullptr;
-    v.grid_mask = grid_mask;
+    v.grid = has_grid ? grid.as<const int4>() : nullptr;
+    v.grid_mask = has_grid ? grid_meta.as<const uint32_t>() : nullptr;
     v.L = L;
     v.B = B;
     return v;

@@ -46,9 +46,10 @@ struct DevBuf {
 // Buffers of one spatial index (either owned by a map or scratch of a context).
 struct IndexBufs {
     DevBuf pts, boxes, covs;
-    DevBuf keys, cell, quant;    // seeding structures (built when with_seed is set)
+    DevBuf keys, quant;          // sorted Morton keys (built when with_seed is set), quantisation
     DevBuf grid;                 // cell hash table (built when with_grid is set)
-    uint32_t grid_mask = 0;
+    DevBuf grid_meta;            // device words: [0] live capacity - 1, [1] occupied cells
+    bool has_grid = false;
     const int* n_ptr = nullptr;  // device count of valid points (set by build_index)
     int L = 0, B = 16, cap = 0;
     IndexView view() const;
@@ -57,6 +58,7 @@ struct IndexBufs {
 // Scratch for building an index: sort keys/values (double-buffered), histogram, scan sums, bbox.
 struct BuildScratch {
     DevBuf k0, k1, v0, v1, hist, sums, bbox;
+    bool bbox_ready = false;     // bbox holds the empty box and a zero block counter (reset by each use)
 };
 
 // Build an index over the first *n_dev of `cap` points (pts n x 3, covs n x 6 optional).

@@ -331,7 +331,8 @@ __device__ __forceinline__ float grid_block8(const IndexView& ix, float4 qz, flo
 {
 #pragma unroll
     for (int c = 0; c < 8; ++c) rng[c] = make_int2(0, 0);
-    if (!ix.grid_mask || !(qz.w > 0.f)) return -1.f;
+    if (!ix.grid || !(qz.w > 0.f)) return -1.f;
+    const uint32_t mask = *ix.grid_mask;
     const float cellsz = 1.f / qz.w;
     const int bx = (int)floorf((q0 - qz.x) * qz.w - 0.5f);
     const int by = (int)floorf((q1 - qz.y) * qz.w - 0.5f);
@@ -346,12 +347,12 @@ __device__ __forceinline__ float grid_block8(const IndexView& ix, float4 qz, flo
         const int ix_ = bx + (c & 1), iy = by + ((c >> 1) & 1), iz = bz + (c >> 2);
         const bool in = (unsigned)ix_ < 1024u && (unsigned)iy < 1024u && (unsigned)iz < 1024u;
         key[c] = in ? (spread10(ix_) << 2) | (spread10(iy) << 1) | spread10(iz) : GRID_EMPTY;
-        e[c] = in ? ix.grid[grid_hash(key[c]) & ix.grid_mask] : make_int4(-1, 0, 0, 0);
+        e[c] = in ? ix.grid[grid_hash(key[c]) & mask] : make_int4(-1, 0, 0, 0);
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         if (key[c] == GRID_EMPTY || (uint32_t)e[c].x == GRID_EMPTY) continue;
-        rng[c] = (uint32_t)e[c].x == key[c] ? make_int2(e[c].y, e[c].z) : grid_find(ix.grid, ix.grid_mask, key[c]);
+        rng[c] = (uint32_t)e[c].x == key[c] ? make_int2(e[c].y, e[c].z) : grid_find(ix.grid, mask, key[c]);
     }
     return cert;
 }
