@@ -48,7 +48,7 @@ MAX_DIST, MAX_ITERS, TOL = 0.1, 30, 1e-6
 BYTES_PER_POINT_ITER = 72      # x 12 + C_s 24 + mu 12 + C_t 24
 BYTES_PER_POINT_COV = 40       # read x 12 + z 4, write C 24
 BYTES_PER_MAP_GAUSSIAN = 84 + 48  # read mean 12 + cov 24 (x2: bbox/morton and gather) + write 16 + 32
-REGSTATE_BYTES = 544 + 4       # pose/H/b/cost/iters/status record + point count read back per frame
+REGSTATE_BYTES = 616 + 4       # registration state record (pose, H, b, cost, iters, status) + point count per frame
 L2_FLUSH_BYTES = 256 << 20
 GN_BODY_ITERS = 4              # iteration launches per pass of the Gauss-Newton graph (gicp.cu)
 # kernels launched per timed step (counted from the ncu launch list of this workload):

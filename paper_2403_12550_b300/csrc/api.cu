@@ -236,7 +236,7 @@ gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp)
 gsicp_status gsicp_ctx_set_gn_launch_mode(gsicp_ctx ctx, int mode)
 {
     if (!ctx || (mode != GSICP_GN_GRAPH && mode != GSICP_GN_PLAIN)) return GSICP_ERR_INVALID_ARG;
-    ctx->reg.unrolled = mode == GSICP_GN_PLAIN;
+    ctx->reg.mode = mode;
     return GSICP_OK;
 }
 
@@ -269,6 +269,11 @@ gsicp_status gsicp_ctx_reg_stats(gsicp_ctx ctx, int n, int32_t* refreshes_out, i
                                  int32_t* solve_ns_out, int32_t* main_ns_out)
 {
     if (!ctx || n < 0 || !ctx->reg.state_host) return GSICP_ERR_INVALID_ARG;
+    // a registration copies back only the state's head; the telemetry is read here, on demand
+    GSICP_CUDA(cudaDeviceSynchronize());
+    GSICP_CUDA(cudaMemcpy(reinterpret_cast<char*>(ctx->reg.state_host) + REG_STATE_HEAD,
+                          ctx->reg.state.as<char>() + REG_STATE_HEAD, sizeof(RegState) - REG_STATE_HEAD,
+                          cudaMemcpyDeviceToHost));
     const RegState& st = *ctx->reg.state_host;
     for (int i = 0; i < n; ++i) {
         const bool in = i < REG_STATS;

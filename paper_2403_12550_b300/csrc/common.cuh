@@ -10,6 +10,8 @@
 // rounded operations (see sq3) -- pruning never drops an admissible point.
 #pragma once
 
+#include <stddef.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -255,6 +257,8 @@ struct RegState {
     unsigned long long t_arrive[64];       // latest block arrival at the reduction
 };
 constexpr int REG_STATS = 64;
+// bytes of RegState before its telemetry: what a registration copies back to the host
+constexpr size_t REG_STATE_HEAD = offsetof(RegState, refreshes);
 
 constexpr int KC = 8;  // map candidates cached per source point
 

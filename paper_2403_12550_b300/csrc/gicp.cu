@@ -1163,7 +1163,7 @@ gsicp_status reg_shard_update(RegMachine& rm, const double* parts, int nparts, c
 {
     shard_update_kernel<<<1, 32, 0, s>>>(rm.job.as<const RegJob>(), parts, nparts);
     GSICP_CUDA(cudaGetLastError());
-    GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, sizeof(RegState), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, REG_STATE_HEAD, cudaMemcpyDeviceToHost, s));
     return GSICP_OK;
 }
 
@@ -1176,7 +1176,7 @@ gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], 
     job.sums_out = nullptr;
     rm.shard = false;
     GSICP_CHECK(reg_prepare(rm, job, T0, n_cap, s));
-    if (solve && rm.unrolled) {
+    if (solve && rm.mode == GSICP_GN_PLAIN) {
         // plain-launch mode: one launch per iteration, each a programmatic dependent of the one
         // before (finished launches exit at once)
         job.use_cond = 0;
@@ -1203,7 +1203,7 @@ gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], 
         gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
         GSICP_CUDA(cudaGetLastError());
     }
-    GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, sizeof(RegState), cudaMemcpyDeviceToHost, s));
+    GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, REG_STATE_HEAD, cudaMemcpyDeviceToHost, s));
     return GSICP_OK;
 }
 

@@ -108,7 +108,7 @@ struct RegMachine {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond{};
-    bool unrolled = false;  // GSICP_GN_PLAIN: one plain launch per iteration instead of the graph
+    int mode = 0;           // gsicp_gn_launch_mode: the conditional graph or plain launches
     bool shard = false;     // the state belongs to a shard registration (reg_shard_begin, not reg_run since)
     gsicp_status init(int capacity);  // (re)builds the graph when the point capacity grows
     void release();
