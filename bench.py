@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=None,
                     help="sequence length (default 300 for sequence, 500 for surrogate)")
     ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--shape", default=None,
+                    help="BUCKET,CELL_M,COOP: use this map-index shape and cooperative-walk threshold instead of "
+                         "the autotuner's choice (e.g. for profiling runs)")
     ap.add_argument("--gn-plain", action="store_true",
                     help="launch each Gauss-Newton iteration as a plain kernel (not a graph node), for "
                          "launch-listing profilers; same results")
@@ -220,8 +223,13 @@ def run_ours(args, world, rank, local):
     # the map index's shape and the context's cooperative-walk threshold, picked by the autotuner on
     # this frame (untimed; every candidate gives the same poses)
     from paper_2403_12550_b300.autotune import tune_frame
-    tune = tune_frame(ctx, depth_dev, intr, STRIDE, Z_MIN, Z_MAX, cp, means, covs, f["T0"], rp,
-                      key=f"frame-{f['depth'].shape}-{means.shape[0]}")
+    if args.shape:
+        b_, c_, k_ = args.shape.split(",")
+        tune = dict(bucket=int(b_), cell=float(c_), coop=int(k_), ms={}, coop_ms={})
+        g.gsicp_ctx_set_coop_walks(ctx, tune["coop"])
+    else:
+        tune = tune_frame(ctx, depth_dev, intr, STRIDE, Z_MIN, Z_MAX, cp, means, covs, f["T0"], rp,
+                          key=f"frame-{f['depth'].shape}-{means.shape[0]}")
     m = g.gsicp_build_map_index(ctx, means, covs, tune["bucket"], tune["cell"])
     n_map = m.size
     depth_host = torch.from_numpy(f["depth"]).pin_memory()
@@ -253,9 +261,13 @@ def run_ours(args, world, rank, local):
             flush.zero_()                       # L2 flush between timed steps (not timed)
             a, b, c = ev[i]
             a.record(stream)
+            torch.cuda.nvtx.range_push("map_rebuild")  # NVTX ranges: profilers can select the phases
             rebuild()                           # a4: map index over 2.04M Gaussians
+            torch.cuda.nvtx.range_pop()
             b.record(stream)
+            torch.cuda.nvtx.range_push("track_frame")
             r = step()                          # a1 -> a2+a3 -> a5-a7 (synchronises)
+            torch.cuda.nvtx.range_pop()
             c.record(stream)
             phases.append(g.gsicp_ctx_phase_times(ctx))
             iters.append(r["iters"])

@@ -214,6 +214,8 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     delete ctx;
 }
 
@@ -819,7 +821,16 @@ gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = sizeof(float) * (size_t)W * (size_t)H;
     GSICP_CHECK(ctx->frame_depth.ensure(bytes));
-    GSICP_CUDA(cudaMemcpyAsync(ctx->frame_depth.ptr, depth_host, bytes, cudaMemcpyHostToDevice, s));
+    // The depth image goes up on the context's own copy stream, so that it overlaps whatever the
+    // caller queued on `stream` before this call (e.g. a map-index rebuild); `stream` waits for it
+    // before a1.  The buffer is free: the previous call on this context synchronised its stream.
+    if (!ctx->copy_stream) {
+        GSICP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        GSICP_CUDA(cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
+    }
+    GSICP_CUDA(cudaMemcpyAsync(ctx->frame_depth.ptr, depth_host, bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    GSICP_CUDA(cudaEventRecord(ctx->copy_done, ctx->copy_stream));
+    GSICP_CUDA(cudaStreamWaitEvent(s, ctx->copy_done, 0));
     return track_frame_impl(ctx, ctx->frame_depth.as<float>(), W, H, intr, stride, z_min, z_max, cov_params, map, T0,
                             reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out, s, nullptr);
 }

@@ -192,6 +192,8 @@ struct gsicp_ctx_s {
     bool timing = false;
     int coop_walks = gsicp::COOP_WALKS_DEFAULT;  // RegJob::coop_max of this context's registrations
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;  // host-buffer entry points' uploads (overlap the caller's queue)
+    cudaEvent_t copy_done = nullptr;
     double phase_ms[6] = {0, 0, 0, 0, 0, 0};
 };
 
