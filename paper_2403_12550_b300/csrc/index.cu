@@ -243,30 +243,41 @@ __global__ void __launch_bounds__(RS_THREADS) os_pass_kernel(const uint32_t* __r
     }
 }
 
-// Sorts (k0, v0) into (k0, v0) using (k1, v1) as the ping-pong buffer; `bits` <= 32.
-static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int bits,
-                                     DevBuf& hist, DevBuf& sums, cudaStream_t s)
+// Scratch layout of a sort (uint32 words): digit counts [4][256] | their exclusive scans [4][256] |
+// finished-block counter | error flag | tile counter per pass [4] | look-back status per pass
+// [4][tiles][256].  One memset clears everything a sort needs before its first kernel.
+struct RadixScratch {
+    uint32_t *H, *O, *done, *err, *tile_ctr, *status;
+    int n, tiles, passes, real;
+};
+constexpr size_t RS_HEADER = 2 * 4 * 256 + 2 + 4;
+
+static gsicp_status radix_prepare(DevBuf& hist, int n, int bits, cudaStream_t s, RadixScratch& r)
 {
-    (void)sums;
-    if (n <= 1) return GSICP_OK;
     if (n > (int)OS_VALUE) return GSICP_ERR_INVALID_ARG;
-    const int tiles = (n + RS_TILE - 1) / RS_TILE;
-    int passes = (bits + 7) / 8;
-    if (passes & 1) ++passes;  // even count: the result lands back in (k0, v0)
-    const int real = std::min(passes, 4);
-    // layout: counts [4][256] | offsets [4][256] | done | error | - | tile counter | status [tiles][256]
-    const size_t status_off = 2 * 4 * 256 + 4;
-    GSICP_CHECK(hist.ensure(sizeof(uint32_t) * (status_off + 256 * (size_t)tiles)));
-    uint32_t* H = hist.as<uint32_t>();
-    uint32_t* O = H + 4 * 256;
-    uint32_t* done = H + 2 * 4 * 256;
-    uint32_t* err = done + 1;
-    uint32_t* status = H + status_off;
-    uint32_t* tile_ctr = status - 1;  // cleared with the status words before each pass
-    GSICP_CUDA(cudaMemsetAsync(H, 0, sizeof(uint32_t) * (status_off), s));
-    const int hgrid = std::max(1, std::min(tiles, device_sm_count() * 4));
-    os_hist_kernel<<<hgrid, RS_THREADS, 0, s>>>(k0, n, real, H, O, done);
-    for (int p = 0; p < passes; ++p) {
+    r.n = n;
+    r.tiles = std::max(1, (n + RS_TILE - 1) / RS_TILE);
+    r.passes = (bits + 7) / 8;
+    if (r.passes & 1) ++r.passes;  // even count: the result lands back in (k0, v0)
+    r.real = std::min(r.passes, 4);
+    const size_t words = RS_HEADER + 4 * 256 * (size_t)r.tiles;
+    GSICP_CHECK(hist.ensure(sizeof(uint32_t) * words));
+    r.H = hist.as<uint32_t>();
+    r.O = r.H + 4 * 256;
+    r.done = r.H + 2 * 4 * 256;
+    r.err = r.done + 1;
+    r.tile_ctr = r.err + 1;
+    r.status = r.H + RS_HEADER;
+    GSICP_CUDA(cudaMemsetAsync(r.H, 0, sizeof(uint32_t) * (RS_HEADER + 256 * (size_t)r.tiles * r.real), s));
+    return GSICP_OK;
+}
+
+// The one-sweep passes of a prepared sort whose digit counts and offsets are in place.
+static gsicp_status radix_passes(const RadixScratch& r, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                                 cudaStream_t s)
+{
+    const int n = r.n;
+    for (int p = 0; p < r.passes; ++p) {
         const int shift = 8 * p;
         uint32_t* ki = (p & 1) ? k1 : k0;
         uint32_t* vi = (p & 1) ? v1 : v0;
@@ -277,11 +288,24 @@ static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, u
             GSICP_CUDA(cudaMemcpyAsync(vo, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
             continue;
         }
-        GSICP_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * (1 + 256 * (size_t)tiles), s));
-        os_pass_kernel<<<tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, O + 256 * p, status, tile_ctr, err);
+        os_pass_kernel<<<r.tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, r.O + 256 * p,
+                                                      r.status + 256 * (size_t)r.tiles * p, r.tile_ctr + p, r.err);
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
+}
+
+// Sorts (k0, v0) into (k0, v0) using (k1, v1) as the ping-pong buffer; `bits` <= 32.
+static gsicp_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int bits,
+                                     DevBuf& hist, DevBuf& sums, cudaStream_t s)
+{
+    (void)sums;
+    if (n <= 1) return GSICP_OK;
+    RadixScratch r;
+    GSICP_CHECK(radix_prepare(hist, n, bits, s, r));
+    const int hgrid = std::max(1, std::min(r.tiles, device_sm_count() * 4));
+    os_hist_kernel<<<hgrid, RS_THREADS, 0, s>>>(k0, n, r.real, r.H, r.O, r.done);
+    return radix_passes(r, k0, v0, k1, v1, s);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -368,17 +392,46 @@ __global__ void bbox_quant_kernel(const float* __restrict__ pts, const int* __re
     bb[6] = 0u;
 }
 
-// 30-bit Morton key of each valid point over the bounding cube; padding slots get
-// 0xffffffff so they sort after every valid point.
-__global__ void morton_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, int cap,
-                              const float4* __restrict__ quant, uint32_t* __restrict__ keys,
-                              uint32_t* __restrict__ vals)
+// 30-bit Morton key of each valid point over the bounding cube (padding slots get 0xffffffff, so
+// they sort after every valid point), with the digit counts of the sort's four 8-bit passes taken
+// on the way (as os_hist_kernel does for keys already in memory): per-block counts in shared
+// memory, added to H, and the last block to finish writes their exclusive scans to O.
+__global__ void __launch_bounds__(RS_THREADS) morton_hist_kernel(const float* __restrict__ pts,
+                                                                 const int* __restrict__ n_dev, int cap,
+                                                                 const float4* __restrict__ quant,
+                                                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                                 uint32_t* __restrict__ H, uint32_t* __restrict__ O,
+                                                                 uint32_t* __restrict__ done)
 {
+    __shared__ uint32_t h[4][256];
+    __shared__ uint32_t ws[32];
+    __shared__ bool last;
+    for (int j = threadIdx.x; j < 4 * 256; j += RS_THREADS) (&h[0][0])[j] = 0u;
+    __syncthreads();
     const int n = *n_dev;
     const float4 qz = *quant;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (long)gridDim.x * blockDim.x) {
-        keys[i] = i < n ? morton_of(qz, pts[3 * i + 0], pts[3 * i + 1], pts[3 * i + 2]) : 0xffffffffu;
+    for (long i = (long)blockIdx.x * RS_THREADS + threadIdx.x; i < cap; i += (long)gridDim.x * RS_THREADS) {
+        const uint32_t k = i < n ? morton_of(qz, pts[3 * i + 0], pts[3 * i + 1], pts[3 * i + 2]) : 0xffffffffu;
+        keys[i] = k;
         vals[i] = (uint32_t)i;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < 4 * 256; j += RS_THREADS) {
+        const uint32_t v = (&h[0][0])[j];
+        if (v) atomicAdd(&H[j], v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int p = 0; p < 4; ++p) {
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(__ldcg(&H[p * 256 + threadIdx.x]), ws, total);
+        O[p * 256 + threadIdx.x] = ex;
     }
 }
 
@@ -401,24 +454,48 @@ __global__ void grid_clear_kernel(int4* __restrict__ table, const uint32_t* __re
         table[i] = make_int4((int)GRID_EMPTY, 0, 0, 0);
 }
 
-// One entry per occupied cell: the thread of a cell's first sorted point finds the cell's end by
-// reading on while the key repeats (cells hold a handful of points) and inserts (key, start, end).
+// One entry per occupied cell (key, start, end).  A warp takes 32 consecutive sorted positions:
+// the cells that start among them end at the next start among them, and the one that starts last
+// (or, with no start among them, none) may run on past them; its end is found by the whole warp
+// reading 32 keys at a time until the key changes.  Each start lane then inserts its cell.
 __global__ void grid_fill_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
                                  int4* __restrict__ table, const uint32_t* __restrict__ meta)
 {
     const int n = *n_dev;
     const uint32_t mask = meta[0];
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const uint32_t key = keys[s];
-        if (s > 0 && keys[s - 1] == key) continue;  // not the first point of its cell
-        int end = s + 1;
-        while (end < n && keys[end] == key) ++end;
+    const int lane = threadIdx.x & 31;
+    const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+    for (long base = (((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nwarps * 32) {
+        const long s = base + lane;
+        const uint32_t key = s < n ? keys[s] : 0u;
+        const bool start = s < n && (s == 0 || keys[s - 1] != key);
+        const unsigned starts = __ballot_sync(0xffffffffu, start);
+        if (starts == 0u) continue;
+        const int last = 31 - __clz(starts);
+        // the end of the last cell starting here: the first position past this run whose key differs
+        long tail_end = base + 32;
+        const uint32_t last_key = __shfl_sync(0xffffffffu, key, last);
+        if (tail_end < n) {
+            for (long c = tail_end;; c += 32) {
+                const long q = c + lane;
+                const bool stop = q >= n || keys[q] != last_key;
+                const unsigned st = __ballot_sync(0xffffffffu, stop);
+                if (st != 0u) {
+                    tail_end = c + __ffs(st) - 1;
+                    break;
+                }
+            }
+        }
+        tail_end = min(tail_end, (long)n);
+        if (!start) continue;
+        const unsigned later = starts & ~((2u << lane) - 1u);  // starts after this lane (lane < 31)
+        const long end = lane == last ? tail_end : base + __ffs(later) - 1;
         uint32_t slot = grid_hash(key) & mask;
         for (uint32_t probe = 0; probe <= mask; ++probe) {
             const uint32_t prev = atomicCAS(reinterpret_cast<unsigned int*>(&table[slot].x), GRID_EMPTY, key);
             if (prev == GRID_EMPTY) {  // each key is inserted by one thread only
-                table[slot].y = s;
-                table[slot].z = end;
+                table[slot].y = (int)s;
+                table[slot].z = (int)end;
                 break;
             }
             slot = (slot + 1) & mask;
@@ -558,11 +635,15 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
     }
     bbox_quant_kernel<<<std::max(1, std::min((cap + 255) / 256, sms * 2)), 256, 0, s>>>(
         pts, n_dev, scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>());
-    morton_kernel<<<grid, 256, 0, s>>>(pts, n_dev, cap, out.quant.as<float4>(), scr.k0.as<uint32_t>(),
-                                       scr.v0.as<uint32_t>());
+    // keys and the sort's digit counts in one pass; 30-bit keys take four 8-bit passes
+    RadixScratch rs;
+    GSICP_CHECK(radix_prepare(scr.hist, std::max(cap, 1), 30, s, rs));
+    morton_hist_kernel<<<grid, RS_THREADS, 0, s>>>(pts, n_dev, cap, out.quant.as<float4>(), scr.k0.as<uint32_t>(),
+                                                   scr.v0.as<uint32_t>(), rs.H, rs.O, rs.done);
     GSICP_CUDA(cudaGetLastError());
-    GSICP_CHECK(radix_sort_pairs(scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
-                                 scr.v1.as<uint32_t>(), cap, 30, scr.hist, scr.sums, s));
+    if (cap > 1)
+        GSICP_CHECK(radix_passes(rs, scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
+                                 scr.v1.as<uint32_t>(), s));
     uint32_t grid_capacity = 0;
     if (with_grid) {
         grid_capacity = 1024;
