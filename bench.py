@@ -84,8 +84,8 @@ def parse():
                     help="sequence length (default 300 for sequence, 500 for surrogate)")
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--shape", default=None,
-                    help="BUCKET,CELL_M,COOP: use this map-index shape and cooperative-walk threshold instead of "
-                         "the autotuner's choice (e.g. for profiling runs)")
+                    help="BUCKET,CELL_M,COOP[,BLOCK]: use this map-index shape, cooperative-walk threshold and "
+                         "Gauss-Newton block size instead of the autotuner's choice (e.g. for profiling runs)")
     ap.add_argument("--gn-plain", action="store_true",
                     help="launch each Gauss-Newton iteration as a plain kernel (not a graph node), for "
                          "launch-listing profilers; same results")
@@ -224,9 +224,11 @@ def run_ours(args, world, rank, local):
     # this frame (untimed; every candidate gives the same poses)
     from paper_2403_12550_b300.autotune import tune_frame
     if args.shape:
-        b_, c_, k_ = args.shape.split(",")
-        tune = dict(bucket=int(b_), cell=float(c_), coop=int(k_), ms={}, coop_ms={})
+        b_, c_, k_, *bs_ = args.shape.split(",")
+        tune = dict(bucket=int(b_), cell=float(c_), coop=int(k_), block=int(bs_[0]) if bs_ else 256, ms={},
+                    coop_ms={}, block_ms={})
         g.gsicp_ctx_set_coop_walks(ctx, tune["coop"])
+        g.gsicp_ctx_set_gn_block(ctx, tune["block"])
     else:
         tune = tune_frame(ctx, depth_dev, intr, STRIDE, Z_MIN, Z_MAX, cp, means, covs, f["T0"], rp,
                           key=f"frame-{f['depth'].shape}-{means.shape[0]}")
@@ -328,9 +330,10 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**workload_config(npts, n_map, world),
                    "autotuned": {"index_bucket": tune["bucket"], "index_cell_m": tune["cell"],
-                                 "coop_walks": tune["coop"],
+                                 "coop_walks": tune["coop"], "gn_block": tune["block"],
                                  "frame_ms": {f"{b}/{c * 1e3:g}mm": round(v, 4) for (b, c), v in tune["ms"].items()},
-                                 "coop_frame_ms": {str(c): round(v, 4) for c, v in tune["coop_ms"].items()}}},
+                                 "coop_frame_ms": {str(c): round(v, 4) for c, v in tune["coop_ms"].items()},
+                                 "block_frame_ms": {str(c): round(v, 4) for c, v in tune["block_ms"].items()}}},
         "gn_iters_mean": it_mean,
         "point_iters_per_s": world * float(npts) * sum(iters) / total_s,
         "phases_ms": {k: round(v, 4) for k, v in ph.items()},

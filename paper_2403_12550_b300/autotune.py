@@ -4,8 +4,9 @@ return the fastest.  Results are kept per (device, workload key) for the life of
 * ``tune_index_params`` (batched registration): the map index's shape (points per BVH leaf, grid
   cell size), timing gsicp_register_batch.
 * ``tune_frame`` (one frame tracked against a map): the map index's shape, timing
-  gsicp_track_frame, then the cooperative-walk threshold of the context (how many tree walks a
-  warp of 32 source points takes together) on the chosen shape.
+  gsicp_track_frame, then on the chosen shape the cooperative-walk threshold of the context (how
+  many tree walks a warp of 32 source points takes together), then the Gauss-Newton kernel's block
+  size (source points per block).
 
 Every candidate returns the same result (the searches are exact), so only time is compared.  The
 cell size matters most: a larger cell's 2x2x2 block certifies more nearest-point searches and more
@@ -17,13 +18,14 @@ from __future__ import annotations
 import torch
 
 from . import (IndexParams, MapHandle, RegParams, gsicp_build_map_index,  # noqa: F401
-               gsicp_ctx_set_coop_walks, gsicp_register_batch, gsicp_track_frame)
+               gsicp_ctx_set_coop_walks, gsicp_ctx_set_gn_block, gsicp_register_batch, gsicp_track_frame)
 
 # (points per leaf, grid cell in metres)
 CANDIDATES = ((16, 0.012), (8, 0.012), (32, 0.012), (16, 0.008), (16, 0.005), (8, 0.008))
 FRAME_CANDIDATES = ((8, 0.012), (16, 0.012), (8, 0.010), (16, 0.010), (8, 0.013), (16, 0.013), (8, 0.008),
                     (16, 0.008), (8, 0.016))
 COOP_CANDIDATES = (4, 2, 8, 0)
+BLOCK_CANDIDATES = (256, 128, 384)
 
 _CACHE: dict = {}
 
@@ -85,17 +87,19 @@ def frame_ms(ctx, depth, intr, stride, z_min, z_max, cov_params, map_, T0, param
 
 
 def tune_frame(ctx, depth, intr, stride: int, z_min: float, z_max: float, cov_params, means, covs, T0,
-               params: RegParams, candidates=FRAME_CANDIDATES, coop_candidates=COOP_CANDIDATES, reps: int = 3,
-               key: str | None = None, timer=frame_ms) -> dict:
-    """Returns dict(bucket, cell, coop, ms: {(bucket, cell): ms}, coop_ms: {coop: ms}) for tracking
-    frames like `depth` (a sample frame, its intrinsics and a1 settings, start pose T0) against the
-    map Gaussians means / covs.  Each index shape is built, timed (best of `reps` frames) and
-    released; then the context's cooperative-walk threshold is timed on the fastest shape and left
-    set to the fastest.  Ties go to the earlier candidate."""
+               params: RegParams, candidates=FRAME_CANDIDATES, coop_candidates=COOP_CANDIDATES,
+               block_candidates=BLOCK_CANDIDATES, reps: int = 3, key: str | None = None, timer=frame_ms) -> dict:
+    """Returns dict(bucket, cell, coop, block, ms: {(bucket, cell): ms}, coop_ms: {coop: ms},
+    block_ms: {block: ms}) for tracking frames like `depth` (a sample frame, its intrinsics and a1
+    settings, start pose T0) against the map Gaussians means / covs.  Each index shape is built,
+    timed (best of `reps` frames) and released; then, on the fastest shape, the context's
+    cooperative-walk threshold and then its Gauss-Newton block size are timed, each left set to the
+    fastest.  Ties go to the earlier candidate."""
     ck = (torch.cuda.get_device_name(), key) if key is not None else None
     if ck is not None and ck in _CACHE:
         res = _CACHE[ck]
         gsicp_ctx_set_coop_walks(ctx, res["coop"])
+        gsicp_ctx_set_gn_block(ctx, res["block"])
         return res
     times = {}
     for bucket, cell in candidates:
@@ -105,17 +109,22 @@ def tune_frame(ctx, depth, intr, stride: int, z_min: float, z_max: float, cov_pa
         finally:
             m.close()
     bucket, cell = min(times, key=times.get)
-    coop_times = {}
+    coop_times, block_times = {}, {}
     m = gsicp_build_map_index(ctx, means, covs, bucket, cell)
     try:
         for c in coop_candidates:
             gsicp_ctx_set_coop_walks(ctx, c)
             coop_times[c] = timer(ctx, depth, intr, stride, z_min, z_max, cov_params, m, T0, params, reps)
+        coop = min(coop_times, key=coop_times.get)
+        gsicp_ctx_set_coop_walks(ctx, coop)
+        for bs in block_candidates:
+            gsicp_ctx_set_gn_block(ctx, bs)
+            block_times[bs] = timer(ctx, depth, intr, stride, z_min, z_max, cov_params, m, T0, params, reps)
     finally:
         m.close()
-    coop = min(coop_times, key=coop_times.get)
-    gsicp_ctx_set_coop_walks(ctx, coop)
-    res = dict(bucket=bucket, cell=cell, coop=coop, ms=times, coop_ms=coop_times)
+    block = min(block_times, key=block_times.get)
+    gsicp_ctx_set_gn_block(ctx, block)
+    res = dict(bucket=bucket, cell=cell, coop=coop, block=block, ms=times, coop_ms=coop_times, block_ms=block_times)
     if ck is not None:
         _CACHE[ck] = res
     return res

@@ -242,6 +242,14 @@ gsicp_status gsicp_ctx_set_gn_launch_mode(gsicp_ctx ctx, int mode)
     return GSICP_OK;
 }
 
+gsicp_status gsicp_ctx_set_gn_block(gsicp_ctx ctx, int points_per_block)
+{
+    if (!ctx || (points_per_block != 128 && points_per_block != 256 && points_per_block != 384))
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_ctx_set_gn_block: 128, 256 or 384 points per block");
+    ctx->reg.bs = points_per_block;
+    return GSICP_OK;
+}
+
 gsicp_status gsicp_ctx_phase_times(gsicp_ctx ctx, double out[6])
 {
     if (!ctx || !out) return GSICP_ERR_INVALID_ARG;

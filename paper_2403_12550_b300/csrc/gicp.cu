@@ -597,9 +597,10 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
 
 // Block-wide sum of acc into row[0 .. NACC) (row[NACC ..32) zeroed; visible device-wide on return
 // to thread 0 after its __threadfence); returns the number of threads with refreshed != 0.
+template <int BS = REG_THREADS>
 __device__ __forceinline__ int block_partial(const float (&acc)[NACC], int refreshed, float* row)
 {
-    __shared__ float red[REG_THREADS / 32][NACC];
+    __shared__ float red[BS / 32][NACC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < NACC; ++a) {
@@ -613,7 +614,7 @@ __device__ __forceinline__ int block_partial(const float (&acc)[NACC], int refre
         float v = 0.f;
         if (threadIdx.x < NACC) {
 #pragma unroll
-            for (int w = 0; w < REG_THREADS / 32; ++w) v += red[w][threadIdx.x];
+            for (int w = 0; w < BS / 32; ++w) v += red[w][threadIdx.x];
         }
         row[threadIdx.x] = v;
         __threadfence();
@@ -762,8 +763,11 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
     return more;
 }
 
-__global__ void __launch_bounds__(REG_THREADS, REG_BLOCKS_PER_SM) gicp_iter_kernel(const RegJob* __restrict__ jp,
-                                                                cudaGraphConditionalHandle cond)
+// One Gauss-Newton iteration, BS source points per block (one per thread): 128, 256 (the batched
+// kernel's chunk, which makes the two paths' sums the same bits) or 384, with 768 threads per SM.
+template <int BS>
+__global__ void __launch_bounds__(BS, 768 / BS) gicp_iter_kernel(const RegJob* __restrict__ jp,
+                                                                 cudaGraphConditionalHandle cond)
 {
     // launched as a programmatic dependent of the previous iteration (plain-launch mode): wait for
     // it to complete (a no-op otherwise) before reading the pose and status it wrote
@@ -800,15 +804,15 @@ __global__ void __launch_bounds__(REG_THREADS, REG_BLOCKS_PER_SM) gicp_iter_kern
     // One source point per thread (the grid covers the context's capacity; the hardware block
     // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
     // the reduction order, hence the result, deterministic).
-    __shared__ int2 wstack[REG_THREADS / 32][WARP_STACK];
+    __shared__ int2 wstack[BS / 32][WARP_STACK];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
-    const int block_refreshed = block_partial(acc, refreshed, J.partials + 32l * blockIdx.x);
+    const int block_refreshed = block_partial<BS>(acc, refreshed, J.partials + 32l * blockIdx.x);
     // this block's share is written: the next iteration's launch may begin (its blocks wait in
     // griddepcontrol.wait until this grid, the last block's solve included, has completed)
     asm volatile("griddepcontrol.launch_dependents;");
     const int nrows = gridDim.x, ngroups = (nrows + GN_GROUP - 1) / GN_GROUP, g = blockIdx.x / GN_GROUP;
-    const int nb = (n + REG_THREADS - 1) / REG_THREADS;  // rows of blocks that held points (the rest are zero)
+    const int nb = (n + BS - 1) / BS;  // rows of blocks that held points (the rest are zero)
     unsigned* gctr = group_counters(J.partials, nrows, ngroups);
     float* grow = group_rows(J.partials, nrows);
     __shared__ bool am_last;
@@ -843,6 +847,22 @@ __global__ void __launch_bounds__(REG_THREADS, REG_BLOCKS_PER_SM) gicp_iter_kern
     // registration of these points sums
     const bool more = finalize(J, st, grow, (nb + GN_GROUP - 1) / GN_GROUP, it_now, t_start);
     if (threadIdx.x == 0 && J.use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+static const void* iter_kernel(int bs)
+{
+    return bs == 128 ? (const void*)gicp_iter_kernel<128>
+                     : (bs == 384 ? (const void*)gicp_iter_kernel<384> : (const void*)gicp_iter_kernel<256>);
+}
+
+// One plain launch of the iteration kernel of the machine's block size.
+static gsicp_status launch_iter(const RegMachine& rm, cudaStream_t s)
+{
+    const RegJob* jp = rm.job.as<const RegJob>();
+    cudaGraphConditionalHandle cond = rm.cond;
+    void* args[] = {(void*)&jp, (void*)&cond};
+    GSICP_CUDA(cudaLaunchKernel(iter_kernel(rm.bs), dim3(rm.grid), dim3(rm.bs), args, 0, s));
+    return GSICP_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1026,13 +1046,14 @@ gsicp_status batch_run(const RegJob* jobs_dev, int B, const Pose16* T0_dev, cons
 
 gsicp_status RegMachine::init(int capacity)
 {
-    const int want = std::max(1, (std::max(capacity, 1) + REG_THREADS - 1) / REG_THREADS);
-    if (exec && want <= grid) return GSICP_OK;
+    const int want = std::max(1, (std::max(capacity, 1) + bs - 1) / bs);
+    if (exec && want <= grid && built_bs == bs) return GSICP_OK;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
-    grid = std::max(want, grid);
+    grid = built_bs == bs ? std::max(want, grid) : want;  // grid counts blocks of bs points
+    built_bs = bs;
     GSICP_CHECK(partials.ensure(sizeof(float) * reduction_floats(grid)));
     GSICP_CUDA(cudaMemset(partials.ptr, 0, sizeof(float) * reduction_floats(grid)));  // group counters start at 0
     GSICP_CHECK(job.ensure(sizeof(RegJob)));
@@ -1055,9 +1076,9 @@ gsicp_status RegMachine::init(int capacity)
     const RegJob* jptr = job.as<const RegJob>();
     void* args[] = {(void*)&jptr, (void*)&cond};
     cudaKernelNodeParams kp = {};
-    kp.func = (void*)gicp_iter_kernel;
+    kp.func = const_cast<void*>(iter_kernel(bs));
     kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(REG_THREADS);
+    kp.blockDim = dim3(bs);
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
     cudaGraphNode_t knode[GN_BODY_ITERS];
@@ -1154,9 +1175,7 @@ gsicp_status reg_shard_begin(RegMachine& rm, const RegJob& job_in, const double 
 
 gsicp_status reg_shard_linearise(RegMachine& rm, cudaStream_t s)
 {
-    gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
-    GSICP_CUDA(cudaGetLastError());
-    return GSICP_OK;
+    return launch_iter(rm, s);
 }
 
 gsicp_status reg_shard_update(RegMachine& rm, const double* parts, int nparts, cudaStream_t s)
@@ -1188,20 +1207,20 @@ gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], 
         attr.val.programmaticStreamSerializationAllowed = 1;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(rm.grid);
-        cfg.blockDim = dim3(REG_THREADS);
+        cfg.blockDim = dim3(rm.bs);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         const RegJob* jp = rm.job.as<const RegJob>();
+        void* args[] = {(void*)&jp, (void*)&rm.cond};
         for (int i = 0; i < job.max_iters; ++i)
-            GSICP_CUDA(cudaLaunchKernelEx(&cfg, gicp_iter_kernel, jp, rm.cond));
+            GSICP_CUDA(cudaLaunchKernelExC(&cfg, iter_kernel(rm.bs), args));
         GSICP_CUDA(cudaGetLastError());
     } else if (solve) {
         GSICP_CUDA(cudaGraphLaunch(rm.exec, s));
     } else {
-        gicp_iter_kernel<<<rm.grid, REG_THREADS, 0, s>>>(rm.job.as<const RegJob>(), rm.cond);
-        GSICP_CUDA(cudaGetLastError());
+        GSICP_CHECK(launch_iter(rm, s));
     }
     GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, REG_STATE_HEAD, cudaMemcpyDeviceToHost, s));
     return GSICP_OK;

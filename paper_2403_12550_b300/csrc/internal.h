@@ -109,6 +109,8 @@ struct RegMachine {
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond{};
     int mode = 0;           // gsicp_gn_launch_mode: the conditional graph or plain launches
+    int bs = 256;           // source points per block of the iteration kernel (128, 256 or 384)
+    int built_bs = 0;       // block size the graph and the reduction rows were built for
     bool shard = false;     // the state belongs to a shard registration (reg_shard_begin, not reg_run since)
     gsicp_status init(int capacity);  // (re)builds the graph when the point capacity grows
     void release();

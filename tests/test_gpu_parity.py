@@ -481,6 +481,38 @@ def test_gn_launch_modes_give_identical_results(g, ctx):
     m1.close()
 
 
+def test_gn_block_sizes_meet_the_oracle(g, ctx):
+    """128, 256 and 384 source points per Gauss-Newton block: the rows of the reduction change with
+    the block, so the sums' order does, but every size lands on the oracle's pose within the bar (the
+    full-size frame and a config-1 pair); 256 stays the batched kernel's bits (checked by the batch
+    tests)."""
+    f, means, covs = _cfg2()
+    m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    src, cs, tgt, ct, _ = config1_inputs(0, 0)
+    m1 = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    pts, z = oracle_frame_points(f["depth"])
+    cso = orc.source_covariances(pts, z, k=20, eps=1e-3, reg_mode=orc.PLANE, p=1.5)["covs"]
+    ro = orc.register(pts, cso, orc.Map(means, covs), f["T0"], 0.1, 30, 1e-6, 1e-6, 6)
+    ro1 = orc.register(src, cs, orc.Map(tgt, ct), np.eye(4), 0.1, 30, 1e-6, 1e-6, 6)
+    try:
+        for bs in (128, 384, 256):
+            g.gsicp_ctx_set_gn_block(ctx, bs)
+            r = g.gsicp_track_frame(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
+            r1 = g.gsicp_register(ctx, cu(src), cu(cs), m1, np.eye(4), rp)
+            for a, b in ((r, ro), (r1, ro1)):
+                assert a["status"] == g.OK
+                dr, dt = pose_diff(a["T"], b["T"])
+                assert dr < POSE_ROT_TOL and dt < POSE_TRANS_TOL, (bs, dr, dt, a["iters"], b["iters"])
+    finally:
+        g.gsicp_ctx_set_gn_block(ctx, 256)
+    with pytest.raises(g.GsicpError):
+        g.gsicp_ctx_set_gn_block(ctx, 64)
+    m.close()
+    m1.close()
+
+
 def test_track_frame_empty_depth(g, ctx):
     src, cs, tgt, ct, _ = config1_inputs(0, 0, n=2000)
     m = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
