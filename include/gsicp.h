@@ -115,6 +115,14 @@ gsicp_status gsicp_ctx_last_residual(gsicp_ctx ctx, double* sqdist_out, int64_t*
  * walks alone.  0 = always alone, 32 = always together.  Results do not depend on it (both walks
  * are exact); only time does.  Default 4.  GSICP_ERR_INVALID_ARG outside 0..32 or for a null ctx. */
 gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp);
+/* Search tuning: in the first `iters` Gauss-Newton iterations of this context's registrations, a
+ * warp in which more than the cooperative-walk threshold of points need a tree walk for their
+ * nearest map point walks the tree once for all of them (a packet walk: a node is visited when any
+ * of those points' bound reaches it; each point keeps its own nearest), instead of each point
+ * walking alone.  It pays where the warp's points are close together and nearly all search, as in
+ * the first iteration.  Results do not depend on it (every walk is exact).  Default 1; 0 = never.
+ * GSICP_ERR_INVALID_ARG outside 0 .. 10000 or for a null ctx. */
+gsicp_status gsicp_ctx_set_packet_iters(gsicp_ctx ctx, int iters);
 /* How this context launches the Gauss-Newton iterations of gsicp_register and gsicp_track_frame*:
  * GSICP_GN_GRAPH (default) runs them as one CUDA graph whose conditional WHILE node repeats until
  * the last iteration's solve reports convergence (no host round trip per iteration);

@@ -18,7 +18,7 @@ import torch
 __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
-    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_set_gn_launch_mode", "gsicp_ctx_set_gn_block", "GN_GRAPH", "GN_PLAIN", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_set_gn_launch_mode", "gsicp_ctx_set_gn_block", "gsicp_ctx_set_packet_iters", "GN_GRAPH", "GN_PLAIN", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
     "gsicp_build_map_index", "gsicp_map_append", "gsicp_shard_begin", "gsicp_shard_linearise", "gsicp_shard_update",
     "SHARD_SUMS", "SHARD_RUNNING", "SHARD_CONVERGED", "SHARD_MAXITER", "SHARD_DEGENERATE",
@@ -114,6 +114,7 @@ _sig("gsicp_ctx_last_residual", C.c_int, [_vp, _dp, _i64p])
 _sig("gsicp_ctx_set_coop_walks", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_set_gn_launch_mode", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_set_gn_block", C.c_int, [_vp, C.c_int])
+_sig("gsicp_ctx_set_packet_iters", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
 _sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
 _sig("gsicp_ctx_frame_stats", C.c_int, [_vp, _i64p])
@@ -278,6 +279,11 @@ def gsicp_ctx_set_gn_launch_mode(ctx: Context, mode: int):
 def gsicp_ctx_set_gn_block(ctx: Context, points_per_block: int):
     """Source points per block of the Gauss-Newton iterations: 128, 256 (default) or 384."""
     _check(lib.gsicp_ctx_set_gn_block(ctx.ptr, int(points_per_block)), "gsicp_ctx_set_gn_block")
+
+
+def gsicp_ctx_set_packet_iters(ctx: Context, iters: int):
+    """Iterations (from the first) whose busy warps walk for their nearest points together."""
+    _check(lib.gsicp_ctx_set_packet_iters(ctx.ptr, int(iters)), "gsicp_ctx_set_packet_iters")
 
 
 def gsicp_ctx_last_residual(ctx: Context) -> tuple:

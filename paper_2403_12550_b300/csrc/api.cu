@@ -112,6 +112,7 @@ static RegJob make_job(gsicp_ctx ctx, const float4* src, const float4* covs_s, c
     RegJob job;
     memset(&job, 0, sizeof(job));
     job.coop_max = ctx->coop_walks;
+    job.packet_iters = ctx->packet_iters;
     job.src = src;
     job.covs_s = covs_s;
     job.slack = CACHE_SLACK;
@@ -239,6 +240,14 @@ gsicp_status gsicp_ctx_set_gn_launch_mode(gsicp_ctx ctx, int mode)
 {
     if (!ctx || (mode != GSICP_GN_GRAPH && mode != GSICP_GN_PLAIN)) return GSICP_ERR_INVALID_ARG;
     ctx->reg.mode = mode;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_set_packet_iters(gsicp_ctx ctx, int iters)
+{
+    if (!ctx || iters < 0 || iters > 10000)
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_ctx_set_packet_iters: 0 .. 10000 iterations");
+    ctx->packet_iters = iters;
     return GSICP_OK;
 }
 

@@ -310,6 +310,7 @@ struct RegJob {
     int use_cond;          // 1 when launched inside the conditional-while graph
     int coop_max;          // warps with at most this many tree walks do them together (0: never)
     double* sums_out;      // optional: the NACC FP64 sums of each linearisation (shard registrations)
+    int packet_iters;      // iterations (from the first) whose busy warps walk for their nearest points together
 };
 
 constexpr int COOP_WALKS_DEFAULT = 4;  // default RegJob::coop_max

@@ -244,7 +244,7 @@ __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegSt
 // choice returns the same nearest point and leaves the same cache state.
 __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], const float (&Rl)[9],
                                         const float (&t)[3], const float (&tl)[3], int s, bool active, int nmap,
-                                        float (&acc)[NACC], int2* wstack)
+                                        float (&acc)[NACC], int2* wstack, bool packet)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -471,6 +471,27 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                     }
                 }
             }
+        }
+    }
+    // Many in this warp, all after their nearest point, in an iteration that walks in packets: the
+    // warp walks once for all of them (each lane first scans its own previous or seed leaf).
+    if (packet && __popc(__ballot_sync(FULL, walk != 0)) > J.coop_max && !__any_sync(FULL, walk == 2)) {
+        const bool mine = walk == 1;
+        auto offer = [&](int u, const float4& p) {
+            const float d2 = point_d2(y0, y1, y2, p);
+            const int oi = __float_as_int(p.w);
+            if (before(d2, oi, best_d2, best_oi)) {
+                best_d2 = d2;
+                best_oi = oi;
+                best_pos = u;
+            }
+        };
+        if (mine && h0 >= 0)
+            scan_points4(J.map.pts, h0 * B, min(h0 * B + B, nmap), [&](int u, const float4& p) { offer(u, p); });
+        if (packet_nn8(J.map, nmap, mine, y0, y1, y2, best_d2, mine ? h0 : -1, wstack, offer) && mine) {
+            reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+            J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
+            walk = 0;
         }
     }
     // Many in this warp (or a cooperative walk ran out of stack): each point walks alone.
@@ -806,7 +827,8 @@ __global__ void __launch_bounds__(BS, 768 / BS) gicp_iter_kernel(const RegJob* _
     // the reduction order, hence the result, deterministic).
     __shared__ int2 wstack[BS / 32][WARP_STACK];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
+    const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5],
+                                   it_now < J.packet_iters);
     const int block_refreshed = block_partial<BS>(acc, refreshed, J.partials + 32l * blockIdx.x);
     // this block's share is written: the next iteration's launch may begin (its blocks wait in
     // griddepcontrol.wait until this grid, the last block's solve included, has completed)
@@ -936,7 +958,8 @@ __global__ void __launch_bounds__(REG_THREADS, REG_BLOCKS_PER_SM) gicp_batch_ker
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
         const int s = c * REG_THREADS + threadIdx.x;
-        const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5]);
+        const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5],
+                                       it_now < J.packet_iters);
         block_partial(acc, refreshed, J.partials + 32l * c);
         const int ngroups = (nchunks + GN_GROUP - 1) / GN_GROUP, g = c / GN_GROUP;
         unsigned* gctr = group_counters(J.partials, nchunks, ngroups);

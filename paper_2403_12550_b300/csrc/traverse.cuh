@@ -208,6 +208,95 @@ __device__ __forceinline__ void packet_traverse(const IndexView& ix, bool active
     }
 }
 
+constexpr int WARP_STACK = 256;  // entries of a warp's shared-memory walk stack
+
+// Packet nearest-point walk: the warp walks the tree once for the nearest point of every lane with
+// `active` set (all 32 lanes call it, converged).  The node stack is the warp's (shared memory,
+// entries pushed by lane 0): a node is expanded when at least one active lane's bound reaches its
+// box; an internal node's eight descendants three levels down are loaded by every lane (the same
+// addresses: broadcast loads) and each active lane tests them against its own query and bound; a
+// leaf's points are read the same way and each active lane offers them to its own best.  The warp
+// pays for the union of its lanes' nodes instead of their divergent sum, which pays when the lanes'
+// queries are close together and all search (the first iteration, where most points are ~2 cm off
+// the map).  Exactness is the per-lane argument of traverse(): a node is skipped only when no
+// active lane's bound reaches its box, and bounds only shrink.  Returns false (lane results
+// unchanged since the call's start are still valid bounds, but incomplete) if the stack would
+// overflow; the caller then walks each lane alone.  Leaves skip0 (per lane) were scanned by the
+// caller.  offer(u, p) updates the calling lane's best with point u.
+template <class OfferFn>
+__device__ __forceinline__ bool packet_nn8(const IndexView& ix, int nmap, bool active, float qx, float qy, float qz,
+                                           const float& bound, int skip0, int2* __restrict__ stk, OfferFn&& offer)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int L = ix.L, B = ix.B;
+    int sp = 0;
+    if (lane == 0) {  // entry nodes: the 1, 2 or 4 nodes at depth (log2 L) mod 3
+        const int first = 1 << ((31 - __clz(L)) % 3);
+        for (int c = first; c < 2 * first; ++c) stk[sp++] = make_int2(c, 0);
+    }
+    sp = __shfl_sync(FULL, sp, 0);
+    __syncwarp();
+    while (sp > 0) {
+        const int node = stk[sp - 1].x;
+        --sp;
+        const float4* bx = ix.boxes + 2 * node;
+        const float dn = box_d2(qx, qy, qz, bx[0], bx[1]);
+        if (__ballot_sync(FULL, active && dn <= bound) == 0u) continue;
+        if (node >= L) {
+            const int lf = node - L, beg = lf * B, end = min(beg + B, nmap);
+            const bool mine = active && lf != skip0;
+            for (int u0 = beg; u0 < end; u0 += 4) {
+                float4 pp[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) pp[j] = u0 + j < end ? ix.pts[u0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (mine && u0 + j < end) offer(u0 + j, pp[j]);
+            }
+            continue;
+        }
+        // eight descendants three levels down: nodes 8 node .. 8 node + 7
+        const float4* cb = ix.boxes + 16 * node;
+        unsigned need = 0u;
+        float dmin = GSICP_INF;
+        int cmin = -1;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float d = box_d2(qx, qy, qz, cb[2 * c], cb[2 * c + 1]);
+            const bool ok = active && d <= bound;
+            if (__ballot_sync(FULL, ok)) need |= 1u << c;
+            if (ok && d < dmin) {
+                dmin = d;
+                cmin = c;
+            }
+        }
+        if (need == 0u) continue;
+        // the child nearest for most active lanes goes on top (visited first), the rest below it
+        int top = -1, topn = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int votes = __popc(__ballot_sync(FULL, cmin == c));
+            if ((need >> c) & 1u && votes > topn) {
+                topn = votes;
+                top = c;
+            }
+        }
+        if (top < 0) top = __ffs(need) - 1;
+        if (sp + __popc(need) > WARP_STACK) return false;
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (((need >> c) & 1u) && c != top) stk[sp++] = make_int2(8 * node + c, 0);
+            stk[sp++] = make_int2(8 * node + top, 0);
+        }
+        sp = __shfl_sync(FULL, sp, 0);
+        __syncwarp();
+    }
+    return true;
+}
+
 // Warp-cooperative exact search for the kk (1 <= kk <= 32) nearest points of ONE query: all 32
 // lanes call it, converged, with the same arguments.  The list of the kk smallest (squared
 // distance, index) keys below lim_key is kept ascending in lanes 0 .. kk-1 (lane 0 may start with
@@ -221,8 +310,6 @@ __device__ __forceinline__ void packet_traverse(const IndexView& ix, bool active
 // the argument of traverse(): a box is dropped only when its lower bound exceeds the current bound,
 // which only shrinks.  Returns false, list incomplete, if the stack would overflow; the caller
 // then searches this query alone.
-constexpr int WARP_STACK = 256;
-
 __device__ __forceinline__ bool warp_knn(const IndexView& ix, int nmap, float qx, float qy, float qz, int kk,
                                          unsigned long long lim_key, int init_pos, int skip0, int skip1,
                                          int2* __restrict__ stk, unsigned long long& lkey, int& lpos)
