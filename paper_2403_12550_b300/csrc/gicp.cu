@@ -119,6 +119,7 @@ __device__ bool warp_chol_solve6(double a, int lane, double x[6])
 // Taylor coefficients in t^2 of sin(t)/t, (1 - cos t)/t^2 and (t - sin t)/t^3:
 // (-1)^m / (2m + o)!, o = 1, 2, 3.  Nine terms leave a remainder below 1e-22 for t < 0.5.
 constexpr int EXP_TERMS = 9;
+static_assert(EXP_TERMS == 9, "the exponential's series is evaluated as a degree-8 polynomial (Estrin)");
 constexpr double inv_factorial(int k)
 {
     double f = 1.0;
@@ -135,8 +136,9 @@ __constant__ double c_exp_series[3][EXP_TERMS] = {GSICP_SERIES(1), GSICP_SERIES(
 // T <- exp(xi^) T with xi = (omega, v) the same on every lane: the rotation by Rodrigues'
 // formula E = I + A K + B K^2 and the translation V v with V = I + B K + C K^2 (K = [omega]x,
 // A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3, t = |omega|).  Lane 4r + c < 12
-// returns the new T(r, c); T is read from memory (row-major 4x4, last row 0 0 0 1).
-__device__ double warp_se3_left_update(const double xi[6], const double* T, int lane)
+// returns the new T(r, c); Tc holds T(0, c), T(1, c), T(2, c) for the lane's c = lane mod 4 (the
+// pose is row-major 4x4 with last row 0 0 0 1).
+__device__ double warp_se3_left_update(const double xi[6], const double (&Tc)[3], int lane)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
@@ -145,9 +147,12 @@ __device__ double warp_se3_left_update(const double xi[6], const double* T, int 
     double A, Bc, Cc;
     if (th2 < 0.25) {
         const int o = min(lane, 2);  // lanes 0, 1, 2 evaluate A, B, C
-        double f = c_exp_series[o][EXP_TERMS - 1];
-#pragma unroll
-        for (int m = EXP_TERMS - 2; m >= 0; --m) f = fma(f, th2, c_exp_series[o][m]);
+        // the degree-8 polynomial in t^2 by Estrin's scheme: four dependent steps instead of eight
+        const double* c = c_exp_series[o];
+        const double x2 = th2 * th2, x4 = x2 * x2, x8 = x4 * x4;
+        const double p01 = fma(c[1], th2, c[0]), p23 = fma(c[3], th2, c[2]);
+        const double p45 = fma(c[5], th2, c[4]), p67 = fma(c[7], th2, c[6]);
+        const double f = fma(c[8], x8, fma(fma(p67, x2, p45), x4, fma(p23, x2, p01)));
         A = __shfl_sync(FULL, f, 0);
         Bc = __shfl_sync(FULL, f, 1);
         Cc = __shfl_sync(FULL, f, 2);
@@ -174,7 +179,7 @@ __device__ double warp_se3_left_update(const double xi[6], const double* T, int 
     const double e0 = __shfl_sync(FULL, E, 3 * tr), e1 = __shfl_sync(FULL, E, 3 * tr + 1),
                  e2 = __shfl_sync(FULL, E, 3 * tr + 2);
     const double tv = __shfl_sync(FULL, Vv, 3 * tr);
-    return fma(e0, T[tc], fma(e1, T[4 + tc], fma(e2, T[8 + tc], tc == 3 ? tv : 0.0)));
+    return fma(e0, Tc[0], fma(e1, Tc[1], fma(e2, Tc[2], tc == 3 ? tv : 0.0)));
 }
 
 __device__ __forceinline__ void pose_to_float(RegState* st)
@@ -701,6 +706,9 @@ __device__ __forceinline__ bool record_and_solve(const RegJob& J, RegState* st, 
     const long long inliers = (long long)llrint(tot[28]);
     bool more = false;
     if (solve) {
+        // the pose's column entries this lane combines (lane 4r + c: T(0..2, c)), read before the solve
+        const int tcol = lane & 3;
+        const double Tc[3] = {st->T[tcol], st->T[4 + tcol], st->T[8 + tcol]};
         // lane p < 27 takes entry (i, j) of [H ; -b^T]
         int ci = 0, cj = 0;
         if (lane < 27) chol_lane_coords(lane, ci, cj);
@@ -711,7 +719,7 @@ __device__ __forceinline__ bool record_and_solve(const RegJob& J, RegState* st, 
         if (inliers < J.min_inliers || !warp_chol_solve6(a, lane, delta)) {
             status = REG_ST_DEGENERATE;
         } else {
-            const double Tn = warp_se3_left_update(delta, st->T, lane);
+            const double Tn = warp_se3_left_update(delta, Tc, lane);
             __syncwarp();
             if (lane < 12) {
                 st->T[lane] = Tn;

@@ -416,9 +416,11 @@ def test_track_frame_config2_matches_oracle(g, ctx):
 
 
 def test_coop_walks_do_not_change_results(g, ctx):
-    """The cooperative tree walk (a whole warp per query) and the per-point walk are both exact:
-    the full-size frame and a config-1 registration give bit-identical poses, systems, iteration
-    counts and refresh counts whichever is used (0 = never together, 32 = always)."""
+    """The cooperative tree walk (a whole warp per query), the packet walk (a warp for all of its
+    points' nearest points) and the per-point walk are all exact: the full-size frame and a
+    config-1 registration give bit-identical poses, systems, iteration counts and refresh counts
+    whichever is used (threshold 0 = never together, 32 = always; packet walks in none, the first,
+    or every iteration)."""
     f, means, covs = _cfg2()
     m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
     cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
@@ -427,19 +429,22 @@ def test_coop_walks_do_not_change_results(g, ctx):
     m1 = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
     T1 = random_offset(np.random.default_rng(7), 5.0, 0.05)
     out = {}
+    settings = ((0, 0), (4, 0), (32, 0), (4, 1), (0, 30))  # (cooperative-walk threshold, packet iterations)
     try:
-        for c in (0, 4, 32):
+        for c, pk in settings:
             g.gsicp_ctx_set_coop_walks(ctx, c)
+            g.gsicp_ctx_set_packet_iters(ctx, pk)
             r = g.gsicp_track_frame(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
             st = g.gsicp_ctx_reg_stats(ctx, r["iters"])
             r1 = g.gsicp_register(ctx, cu(src), cu(cs), m1, T1, rp)
-            out[c] = (r, st["refreshes"], r1)
+            out[(c, pk)] = (r, st["refreshes"], r1)
     finally:
         g.gsicp_ctx_set_coop_walks(ctx, 4)
-    r0, ref0, r10 = out[0]
+        g.gsicp_ctx_set_packet_iters(ctx, 1)
+    r0, ref0, r10 = out[(0, 0)]
     assert r0["status"] == g.OK and r10["status"] == g.OK
-    for c in (4, 32):
-        r, ref, r1 = out[c]
+    for key in settings[1:]:
+        r, ref, r1 = out[key]
         for key in ("T", "H"):
             np.testing.assert_array_equal(r[key], r0[key])
             np.testing.assert_array_equal(r1[key], r10[key])
