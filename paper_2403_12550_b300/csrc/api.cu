@@ -212,6 +212,7 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
     ctx->frame_idx.release(); ctx->fb_list.release(); ctx->fb_count.release();
     ctx->covs_sorted.release();
     ctx->shard_sums.release();
+    ctx->morton_samples.release();
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -697,6 +698,33 @@ gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* querie
 
 // a1 -> source index -> a2+a3 for one depth frame, into the context's frame buffers (points in
 // row-major order, their covariances in the same order and in the source index's order).
+// The sample indices of a Ws x Hs grid (Ws, Hs <= 1024) in 2D Morton order of (column, row), kept by the
+// context for the grid it was last built for (made on the host, uploaded once per grid size).
+static gsicp_status sample_morton_order(gsicp_ctx ctx, int Ws, int Hs)
+{
+    if (ctx->morton_w == Ws && ctx->morton_h == Hs && ctx->morton_samples.ptr) return GSICP_OK;
+    auto spread = [](uint32_t v) {
+        v &= 0x3ffu;
+        v = (v | (v << 8)) & 0x00ff00ffu;
+        v = (v | (v << 4)) & 0x0f0f0f0fu;
+        v = (v | (v << 2)) & 0x33333333u;
+        v = (v | (v << 1)) & 0x55555555u;
+        return v;
+    };
+    const size_t n = (size_t)Ws * Hs;
+    std::vector<std::pair<uint32_t, int>> code(n);
+    for (int j = 0; j < Hs; ++j)
+        for (int i = 0; i < Ws; ++i) code[(size_t)j * Ws + i] = {spread((uint32_t)i) | (spread((uint32_t)j) << 1), j * Ws + i};
+    std::sort(code.begin(), code.end());
+    std::vector<int> order(n);
+    for (size_t k = 0; k < n; ++k) order[k] = code[k].second;
+    GSICP_CHECK(ctx->morton_samples.ensure(sizeof(int) * std::max<size_t>(n, 1)));
+    GSICP_CUDA(cudaMemcpy(ctx->morton_samples.ptr, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    ctx->morton_w = Ws;
+    ctx->morton_h = Hs;
+    return GSICP_OK;
+}
+
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                       int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
                                       int cap, cudaStream_t s, gsicp_surrogate sg)
@@ -716,7 +744,16 @@ gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int
                                        ctx->frame_z.as<float>(), cap, nd, ctx->total_dev.as<int>(), ctx->a1_counts,
                                        ctx->a1_sums, s, ctx->frame_idx.as<int>()));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
-    GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
+    if (Ws <= 1024 && Hs <= 1024) {
+        // the frame's points are near one another exactly where their samples are: index them in
+        // the 2D Morton order of the samples (a compaction, no sort)
+        GSICP_CHECK(sample_morton_order(ctx, Ws, Hs));
+        GSICP_CHECK(build_index_pixel_order(ctx->frame_pts.as<float>(), ctx->frame_idx.as<int>(),
+                                            ctx->morton_samples.as<int>(), Ws * Hs, cap, nd, 32, ctx->src_index,
+                                            ctx->build, s));
+    } else {
+        GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
+    }
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
     if (sg)
         GSICP_CHECK(surrogate_forward(sg, ctx->frame_pts.as<float>(), ctx->frame_idx.as<int>(), Ws, Hs,

@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256) gather_leaf_kernel(const float* __restric
                 scovs[2 * s] = make_float4(c[0], c[1], c[2], c[3]);
                 scovs[2 * s + 1] = make_float4(c[4], c[5], 0.f, 0.f);
             }
-            starts = s == 0 || skeys[s - 1] != skeys[s];
+            starts = grid_meta && (s == 0 || skeys[s - 1] != skeys[s]);
         } else if (scovs) {
             scovs[2 * s] = make_float4(0.f, 0.f, 0.f, 0.f);
             scovs[2 * s + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -671,6 +671,65 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
             out.grid.as<int4>(), out.grid_meta.as<uint32_t>(), grid_capacity);
         grid_fill_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(),
                                                out.grid_meta.as<uint32_t>());
+    }
+    GSICP_CUDA(cudaGetLastError());
+    return GSICP_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Index of a depth frame's points in the 2D Morton order of their samples
+
+// Valid samples (idx_img[sample] >= 0) among the 256 Morton-ordered samples of each block.
+__global__ void pix_count_kernel(const int* __restrict__ idx_img, const int* __restrict__ msamp, int nsamp,
+                                 uint32_t* __restrict__ counts)
+{
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const bool ok = k < nsamp && idx_img[msamp[k]] >= 0;
+    const int c = __syncthreads_count(ok);
+    if (threadIdx.x == 0) counts[blockIdx.x] = (uint32_t)c;
+}
+
+// The point index of every valid sample, in the samples' Morton order (stable compaction).
+__global__ void pix_write_kernel(const int* __restrict__ idx_img, const int* __restrict__ msamp, int nsamp,
+                                 const uint32_t* __restrict__ offs, uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t ws[32];
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int pi = k < nsamp ? idx_img[msamp[k]] : -1;
+    uint32_t total;
+    const uint32_t rank = block_exclusive_scan(pi >= 0 ? 1u : 0u, ws, total);
+    if (pi >= 0) order[offs[blockIdx.x] + rank] = (uint32_t)pi;
+}
+
+gsicp_status build_index_pixel_order(const float* pts, const int* idx_img, const int* msamp, int nsamp, int cap,
+                                     const int* n_dev, int bucket, IndexBufs& out, BuildScratch& scr, cudaStream_t s)
+{
+    if (bucket != 8 && bucket != 16 && bucket != 32) return GSICP_ERR_INVALID_ARG;
+    const int B = bucket;
+    const int L = std::max(1, ceil_pow2(((long)cap + B - 1) / B));
+    const int total = L * B;
+    GSICP_CHECK(out.pts.ensure(sizeof(float4) * (size_t)total));
+    GSICP_CHECK(out.boxes.ensure(sizeof(float4) * 4 * (size_t)L));
+    out.L = L;
+    out.B = B;
+    out.cap = cap;
+    out.n_ptr = n_dev;
+    out.has_grid = false;
+    GSICP_CHECK(out.quant.ensure(sizeof(float4)));
+    const int nb = std::max(1, (nsamp + 255) / 256);
+    GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * 2 * (size_t)nb));
+    GSICP_CHECK(scr.v0.ensure(sizeof(uint32_t) * (size_t)std::max(cap, 1)));
+    uint32_t* counts = scr.k1.as<uint32_t>();
+    uint32_t* offs = counts + nb;
+    pix_count_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, counts);
+    GSICP_CHECK(exclusive_scan_u32(counts, offs, nb, scr.sums, s));
+    pix_write_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, offs, scr.v0.as<uint32_t>());
+    gather_leaf_kernel<<<(total + 255) / 256, 256, 0, s>>>(pts, nullptr, scr.v0.as<uint32_t>(), nullptr, n_dev, total,
+                                                           L, B, out.pts.as<float4>(), nullptr, out.boxes.as<float4>(),
+                                                           nullptr, 0, nullptr);
+    for (int count = L; count > 1; count = count / std::min(256, count)) {
+        const int blocks = count / std::min(256, count);
+        level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;

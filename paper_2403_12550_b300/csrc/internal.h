@@ -68,6 +68,12 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
                          IndexBufs& out, BuildScratch& scr, cudaStream_t s, bool with_seed = false,
                          float cell = 0.f, bool with_grid = false);
 
+// Index of a depth frame's points (pts: a1 output, idx_img: sample -> point index or -1) with the
+// points in the 2D Morton order of their samples: msamp lists the nsamp sample indices of the grid
+// in that order (sample_morton_order).  No sort: a compaction of the valid samples in that order.
+gsicp_status build_index_pixel_order(const float* pts, const int* idx_img, const int* msamp, int nsamp, int cap,
+                                     const int* n_dev, int bucket, IndexBufs& out, BuildScratch& scr, cudaStream_t s);
+
 // First-iteration search seeds: for each Morton-ordered source point x_s, the map position found by
 // a Morton-key lookup of T0 x_s (cand[s][0], -1 if none); every cache entry is marked "search".
 gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_dev, int cap, const double T0[16],
@@ -187,6 +193,8 @@ struct gsicp_ctx_s {
     gsicp::DevBuf frame_pts, frame_z, frame_covs, frame_depth;
     gsicp::DevBuf frame_idx, fb_list, fb_count;  // sample -> point map; tree-search list of the window k-NN
     gsicp::DevBuf covs_sorted;         // source covariances in the source index's order
+    gsicp::DevBuf morton_samples;      // sample indices of the frame grid in 2D Morton order
+    int morton_w = 0, morton_h = 0;    // the grid they are for
     gsicp::DevBuf shard_sums;          // NACC doubles: the last shard linearisation's sums
     gsicp::RegMachine reg;
     gsicp::BatchMachine batch;

@@ -232,7 +232,8 @@ def test_tracker_fallback_policy(g, ctx):
 
 def test_track_frame_surrogate_equals_register_on_its_covariances(g, ctx):
     """gsicp_track_frame_surrogate is a1 + the network + the registration: the same pose, system and
-    counts as gsicp_register on the points and covariances gsicp_surrogate_covariances returns."""
+    counts (to the rounding of the sums' order) as gsicp_register on the points and covariances
+    gsicp_surrogate_covariances returns."""
     from paper_2403_12550_b300 import surrogate as S
     from synth import TUM_INTR, sequence_config5
     seq = sequence_config5(0, n_frames=500)  # frames 0 and 3 of the held-out sequence (~4 cm apart)
@@ -256,9 +257,13 @@ def test_track_frame_surrogate_equals_register_on_its_covariances(g, ctx):
     pts, z, covs = g.gsicp_surrogate_covariances(ctx, sg, d, intr, 2, 0.1, 10.0, cp)
     rr = g.gsicp_register(ctx, pts.contiguous(), covs.contiguous(), m, T, rp)
     assert rt["status"] == rr["status"] == g.OK and rt["n_points"] == len(pts)
-    np.testing.assert_array_equal(rt["T"], rr["T"])
-    np.testing.assert_array_equal(rt["H"], rr["H"])
-    assert (rt["iters"], rt["inliers"], rt["cost"]) == (rr["iters"], rr["inliers"], rr["cost"])
+    # the frame entry point orders a frame's points by their samples (2D Morton order) and
+    # gsicp_register an arbitrary cloud by its points (3D Morton order): the same terms summed in
+    # another order, so the results agree to rounding
+    np.testing.assert_allclose(rt["T"], rr["T"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(rt["H"], rr["H"], rtol=1e-6, atol=1e-6 * np.abs(rr["H"]).max())
+    assert (rt["iters"], rt["inliers"]) == (rr["iters"], rr["inliers"])
+    assert abs(rt["cost"] - rr["cost"]) <= 1e-6 * abs(rr["cost"])
     # and the result is a sensible pose: within 5 mm of the ground truth (started 4 cm away)
     Tg = seq["poses"][3]
     assert np.linalg.norm(rt["T"][:3, 3] - Tg[:3, 3]) < 0.005
