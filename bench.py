@@ -47,21 +47,23 @@ MAX_DIST, MAX_ITERS, TOL = 0.1, 30, 1e-6
 # algorithmic bytes the method must move per unit (the roofline numerators):
 BYTES_PER_POINT_ITER = 72      # x 12 + C_s 24 + mu 12 + C_t 24
 BYTES_PER_POINT_COV = 40       # read x 12 + z 4, write C 24
-BYTES_PER_MAP_GAUSSIAN = 84 + 48  # read mean 12 + cov 24 (x2: bbox/morton and gather) + write 16 + 32
+BYTES_PER_MAP_GAUSSIAN = 132  # means for the bounds 12, means for the keys 12 + keys 4, one sort pass 4 + 8,
+                              # gather: index 4 + mean and cov 36 read, packed 16 + 32 written; cell keys 4
 REGSTATE_BYTES = 616 + 4       # registration state record (pose, H, b, cost, iters, status) + point count per frame
 L2_FLUSH_BYTES = 256 << 20
 GN_BODY_ITERS = 4              # iteration launches per pass of the Gauss-Newton graph (gicp.cu)
 # kernels launched per timed step (counted from the ncu launch list of this workload):
-LAUNCHES_MAP_REBUILD = 18  # count reset 1, bbox 2, quantise 1, Morton keys 1, radix sort 5 (digit counts + 4
-                           # passes), gather 1, leaf boxes 1, box levels 3, grid insert/end 2, seed table 1
-LAUNCHES_FRAME = 24        # a1 5 (count, 3 scan, write), source index 13, k-NN covariances 4 (9x9 window,
-                           # 25x25 window, tree, reorder), GN seed 1, GN set-up 1; plus one Gauss-Newton
-                           # launch per iteration
+LAUNCHES_MAP_REBUILD = 14  # count reset 1, bbox + quantise 1, Morton keys + digit counts 1, radix sort 4,
+                           # gather + leaf boxes 1, box levels 3, cell table size/clear/fill 3
+LAUNCHES_FRAME = 19        # a1 5 (count, 3 scan, write), source index 8 (count, 3 scan, write, gather +
+                           # leaf boxes, 2 box levels), k-NN covariances 4 (9x9 window, 25x25 window, tree,
+                           # reorder), GN seed 1, GN set-up 1; plus one Gauss-Newton launch per iteration
+                           # (plain-launch mode: one more set-up launch)
 # DRAM bytes per gicp_iter_kernel launch (read + write, mean over the iterations of one frame of this
 # workload, ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the CUDA sources whose
 # SHA-256 is given; reported as null once any of them has changed.
-GN_TRAFFIC = {"bytes_per_launch": 36227089,
-              "sources_sha256": "77a60b0e2272881a492838397f3f905a31b8176fb9e29dea6e85d8d02dc27c4f"}
+GN_TRAFFIC = {"bytes_per_launch": 31048397,
+              "sources_sha256": "06a4640bbb07fdb5cdaffd9ec5c5f6ed262fffe15b9e6a7cf4822f8e545cb3da"}
 
 
 def parse():
@@ -321,7 +323,7 @@ def run_ours(args, world, rank, local):
     # the Gauss-Newton graph runs its iteration launches GN_BODY_ITERS at a time (the ones after
     # convergence exit at once); in plain-launch mode every frame launches max_iters of them
     launches = int(sum(LAUNCHES_MAP_REBUILD + LAUNCHES_FRAME +
-                       (MAX_ITERS if args.gn_plain else GN_BODY_ITERS * -(-int(it) // GN_BODY_ITERS))
+                       (MAX_ITERS + 1 if args.gn_plain else GN_BODY_ITERS * -(-int(it) // GN_BODY_ITERS))
                        for it in iters))
     K = args.steps
     out = {
