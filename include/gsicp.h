@@ -123,6 +123,15 @@ gsicp_status gsicp_ctx_set_coop_walks(gsicp_ctx ctx, int max_per_warp);
  * the first iteration.  Results do not depend on it (every walk is exact).  Default 1; 0 = never.
  * GSICP_ERR_INVALID_ARG outside 0 .. 10000 or for a null ctx. */
 gsicp_status gsicp_ctx_set_packet_iters(gsicp_ctx ctx, int iters);
+/* Search tuning: a source point whose query moved more than `meters` since its last search
+ * (Gauss-Newton iterations where the pose still moves a lot) searches for its nearest map point
+ * alone; one that moved less builds a cache of its nearest map points and the radius within which
+ * that list is complete, which later iterations check in place of a search while the point stays
+ * within it (Sec. 3: correspondences are searched again each iteration).  Results do not depend
+ * on it: every search and every cache check returns the nearest point by the same distance;
+ * 0 = never build caches.  Default 0.001 (1 mm).  GSICP_ERR_INVALID_ARG for a negative or
+ * non-finite value or a null ctx. */
+gsicp_status gsicp_ctx_set_cache_step(gsicp_ctx ctx, float meters);
 /* How this context launches the Gauss-Newton iterations of gsicp_register and gsicp_track_frame*:
  * GSICP_GN_GRAPH (default) runs them as one CUDA graph whose conditional WHILE node repeats until
  * the last iteration's solve reports convergence (no host round trip per iteration);

@@ -18,7 +18,7 @@ import torch
 __all__ = [
     "GsicpError", "CovParams", "RegParams", "IndexParams", "Context", "MapHandle",
     "PLANE", "ELLIPSE", "NONE", "LIB_PATH", "lib",
-    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_set_gn_launch_mode", "gsicp_ctx_set_gn_block", "gsicp_ctx_set_packet_iters", "GN_GRAPH", "GN_PLAIN", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
+    "gsicp_ctx_create", "gsicp_ctx_destroy", "gsicp_ctx_set_timing", "gsicp_ctx_last_residual", "gsicp_ctx_set_coop_walks", "gsicp_ctx_set_gn_launch_mode", "gsicp_ctx_set_gn_block", "gsicp_ctx_set_packet_iters", "gsicp_ctx_set_cache_step", "GN_GRAPH", "GN_PLAIN", "gsicp_ctx_phase_times", "gsicp_ctx_reg_stats", "gsicp_ctx_frame_stats", "gsicp_status_string", "gsicp_last_error", "gsicp_version",
     "gsicp_depth_to_points", "gsicp_depth_to_points_noalloc", "gsicp_source_covariances", "gsicp_frame_covariances",
     "gsicp_build_map_index", "gsicp_map_append", "gsicp_shard_begin", "gsicp_shard_linearise", "gsicp_shard_update",
     "SHARD_SUMS", "SHARD_RUNNING", "SHARD_CONVERGED", "SHARD_MAXITER", "SHARD_DEGENERATE",
@@ -115,6 +115,7 @@ _sig("gsicp_ctx_set_coop_walks", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_set_gn_launch_mode", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_set_gn_block", C.c_int, [_vp, C.c_int])
 _sig("gsicp_ctx_set_packet_iters", C.c_int, [_vp, C.c_int])
+_sig("gsicp_ctx_set_cache_step", C.c_int, [_vp, C.c_float])
 _sig("gsicp_ctx_phase_times", C.c_int, [_vp, _dp])
 _sig("gsicp_ctx_reg_stats", C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp])
 _sig("gsicp_ctx_frame_stats", C.c_int, [_vp, _i64p])
@@ -284,6 +285,11 @@ def gsicp_ctx_set_gn_block(ctx: Context, points_per_block: int):
 def gsicp_ctx_set_packet_iters(ctx: Context, iters: int):
     """Iterations (from the first) whose busy warps walk for their nearest points together."""
     _check(lib.gsicp_ctx_set_packet_iters(ctx.ptr, int(iters)), "gsicp_ctx_set_packet_iters")
+
+
+def gsicp_ctx_set_cache_step(ctx: Context, meters: float):
+    """Motion (m) since a point's last search above which it searches without building a cache."""
+    _check(lib.gsicp_ctx_set_cache_step(ctx.ptr, float(meters)), "gsicp_ctx_set_cache_step")
 
 
 def gsicp_ctx_last_residual(ctx: Context) -> tuple:

@@ -98,7 +98,6 @@ static gsicp_status finish_registration(gsicp_ctx ctx, cudaStream_t s, double T_
 }
 
 constexpr float CACHE_SLACK = 0.01f;  // m beyond max_corr_dist kept in the candidate cache (gicp.cu)
-constexpr float CACHE_STEP = 0.002f;  // m: points that moved more since their last search skip the cache
 // m: default map grid cell.  With the benchmark frame's map (2.04M Gaussians from ten 1200x680 views,
 // ~3.6 per occupied 8 mm cell) 12 mm cells cut the Gauss-Newton loop from ~1.6 to ~1.25 ms against
 // 8 mm: their 2x2x2 block certifies more nearest-point searches and more complete candidate lists, so
@@ -116,7 +115,7 @@ static RegJob make_job(gsicp_ctx ctx, const float4* src, const float4* covs_s, c
     job.src = src;
     job.covs_s = covs_s;
     job.slack = CACHE_SLACK;
-    job.cache_step = CACHE_STEP;
+    job.cache_step = ctx->cache_step;
     job.n = n_dev;
     job.map = map->index.view();
     job.corr_out = nullptr;
@@ -249,6 +248,14 @@ gsicp_status gsicp_ctx_set_packet_iters(gsicp_ctx ctx, int iters)
     if (!ctx || iters < 0 || iters > 10000)
         return set_error(GSICP_ERR_INVALID_ARG, "gsicp_ctx_set_packet_iters: 0 .. 10000 iterations");
     ctx->packet_iters = iters;
+    return GSICP_OK;
+}
+
+gsicp_status gsicp_ctx_set_cache_step(gsicp_ctx ctx, float meters)
+{
+    if (!ctx || !(meters >= 0.f) || !isfinite(meters))
+        return set_error(GSICP_ERR_INVALID_ARG, "gsicp_ctx_set_cache_step: a finite distance >= 0 (m)");
+    ctx->cache_step = meters;
     return GSICP_OK;
 }
 

@@ -269,6 +269,16 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
         return sq3(__fsub_rn(__fsub_rn(p.x, y0), l0), __fsub_rn(__fsub_rn(p.y, y1), l1),
                    __fsub_rn(__fsub_rn(p.z, y2), l2));
     };
+    // Nearest-point searches choose by the hi + lo distance but prune boxes with distances from
+    // hi: a point whose hi + lo distance is below d is within d + |lo| + rounding of hi, so a walk
+    // bounded by the inflated square wb(d^2) drops no point that could still win.  |lo| is at most
+    // half an ulp of hi per coordinate (|y| 2^-24 each, sqrt 3 |y| 2^-24 in all); the rest covers
+    // the float rounding of the distances (a few ulps, relative).
+    float ymag = 0.f;
+    auto walk_bound = [&](float d2) {
+        const float d = sqrtf(d2) * (1.f + 1e-6f) + ymag * 2.4e-7f + 1e-9f;
+        return d * d;
+    };
     // the nearest by hi + lo among a sorted KC list (positions P, -1 = none)
     auto pick_exact = [&](const int (&P)[KC]) {
         best_d2 = J.max_d2;
@@ -295,10 +305,10 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
         transform_df(R, Rl, t[0], tl[0], x.x, x.y, x.z, y0, l0);
         transform_df(R + 3, Rl + 3, t[1], tl[1], x.x, x.y, x.z, y1, l1);
         transform_df(R + 6, Rl + 6, t[2], tl[2], x.x, x.y, x.z, y2, l2);
+        ymag = fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2)));
         // cache state through L2: in a persistent launch another SM wrote it in the last iteration
-        const int4 ca4 = __ldcg(reinterpret_cast<const int4*>(J.cand) + 2l * s);
-        const int4 cb4 = __ldcg(reinterpret_cast<const int4*>(J.cand) + 2l * s + 1);
-        const int cp[KC] = {ca4.x, ca4.y, ca4.z, ca4.w, cb4.x, cb4.y, cb4.z, cb4.w};
+        int cp[KC];
+        cand_load(J.cand, s, cp);
         const float4 anc = __ldcg(J.anchor + s);
         bool resolved = false;
         if (anc.w > 0.f) {
@@ -324,16 +334,17 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                     e_pos = cp[j];
                 }
             }
-            const float delta = sqrtf(sq3(y0 - anc.x, y1 - anc.y, y2 - anc.z)) + 2e-6f;
+            const float delta = sqrtf(sq3(y0 - anc.x, y1 - anc.y, y2 - anc.z)) + 2e-6f + ymag * 4.8e-7f;
             const float bnd = best_pos >= 0 ? sqrtf(best_d2) : max_d;
-            // margins (1e-5 relative, 2e-6 m) exceed float rounding of the distances, so the
-            // nearest point is among the cached ones (by either distance)
+            // margins (1e-5 relative; 2e-6 m plus twice the largest hi-to-(hi + lo) distance,
+            // sqrt 3 |y| 2^-24, on each side) exceed the float rounding of the distances, so the
+            // nearest point is among the cached ones by either distance
             resolved = anc.w - delta >= bnd * (1.f + 1e-5f);
-            if (resolved) {
-                best_d2 = e_d2;
-                best_oi = e_oi;
-                best_pos = e_pos;
-            }
+            // the nearest by hi + lo among the cached points: the answer if resolved, else where the
+            // search below starts (it chooses by hi + lo too)
+            best_d2 = e_d2;
+            best_oi = e_oi;
+            best_pos = e_pos;
         }
         if (!resolved) {
             refreshed = 1;
@@ -355,7 +366,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                     for (int c = 0; c < 8; ++c)
                         for (int u = rng[c].x; u < rng[c].y; ++u) {
                             const float4 p = J.map.pts[u];
-                            const float d2 = point_d2(y0, y1, y2, p);
+                            const float d2 = exact_d2(p);
                             const int oi = __float_as_int(p.w);
                             if (before(d2, oi, best_d2, best_oi)) {
                                 best_d2 = d2;
@@ -364,10 +375,12 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                             }
                         }
                 }
+                // certified when the best is nearer than the block's faces: cert already holds a
+                // margin (1e-5 m) far above |lo|
                 if (!(best_pos >= 0 && best_d2 <= cert2)) {
                     walk = 1;
                 } else {
-                    reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+                    cand_store1(J.cand, s, best_pos);
                     J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
                 }
             } else {
@@ -393,8 +406,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                     const float rc =
                         fminf(cert, key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : GSICP_INF) *
                         (1.f - 1e-6f);
-                    reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
-                    reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
+                    cand_store(J.cand, s, P);
                     J.anchor[s] = make_float4(y0, y1, y2, rc);
                     pick_exact(P);
                 } else {
@@ -414,67 +426,51 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
             const int mode = __shfl_sync(FULL, walk, o);
             const float q0 = __shfl_sync(FULL, y0, o), q1 = __shfl_sync(FULL, y1, o),
                         q2 = __shfl_sync(FULL, y2, o);
-            const unsigned long long lk =
-                __shfl_sync(FULL, walk == 1 ? dkey(best_d2, best_oi) : dkey(lim, 0x7fffffff), o);
-            const int ip = __shfl_sync(FULL, best_pos, o);
+            // a nearest-point walk collects the KC nearest by hi within the inflated bound of the
+            // best so far, and both kinds choose among their list by hi + lo
+            const unsigned long long lk = __shfl_sync(FULL, dkey(walk == 1 ? walk_bound(best_d2) : lim, 0x7fffffff), o);
             const int k0 = __shfl_sync(FULL, h0, o), k1 = __shfl_sync(FULL, h1, o);
             const int so = __shfl_sync(FULL, s, o);
             unsigned long long key;
             int pos;
-            if (!warp_knn(J.map, nmap, q0, q1, q2, mode == 1 ? 1 : KC, lk, mode == 1 ? ip : -1, k0, k1, wstack, key,
-                          pos))
+            if (!warp_knn(J.map, nmap, q0, q1, q2, KC, lk, -1, k0, k1, wstack, key, pos))
                 continue;  // stack overflow: lane o walks alone below
-            if (mode == 1) {
-                const unsigned long long k = __shfl_sync(FULL, key, 0);
-                const int p = __shfl_sync(FULL, pos, 0);
-                if (lane == o) {
-                    best_d2 = key_d2(k);
-                    best_oi = key_idx(k);
-                    best_pos = p;
-                    walk = 0;
-                    reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
-                    J.anchor[s] = make_float4(y0, y1, y2, -1.f);
+            // the nearest by hi + lo among the list: lane j < KC tests entry j
+            const float m0 = __shfl_sync(FULL, l0, o), m1 = __shfl_sync(FULL, l1, o), m2 = __shfl_sync(FULL, l2, o);
+            unsigned long long ek = ~0ull;
+            if (lane < KC && pos >= 0) {
+                const float4 p = J.map.pts[pos];
+                const float ed2 = sq3(__fsub_rn(__fsub_rn(p.x, q0), m0), __fsub_rn(__fsub_rn(p.y, q1), m1),
+                                      __fsub_rn(__fsub_rn(p.z, q2), m2));
+                const int oi = __float_as_int(p.w);
+                if (before(ed2, oi, J.max_d2, 0x7fffffff)) ek = dkey(ed2, oi);
+            }
+            int ep = pos;
+#pragma unroll
+            for (int off = 1; off < KC; off <<= 1) {
+                const unsigned long long ok = __shfl_xor_sync(FULL, ek, off);
+                const int op = __shfl_xor_sync(FULL, ep, off);
+                if (ok < ek) {
+                    ek = ok;
+                    ep = op;
                 }
-            } else {
+            }
+            ek = __shfl_sync(FULL, ek, 0);
+            ep = ek != ~0ull ? __shfl_sync(FULL, ep, 0) : -1;
+            if (mode == 2) {
                 const unsigned long long klast = __shfl_sync(FULL, key, KC - 1);
                 const float rc = (key_idx(klast) != 0x7fffffff ? sqrtf(key_d2(klast)) : Rs) * (1.f - 1e-6f);
                 if (lane < KC) J.cand[(long)KC * so + lane] = pos;
                 if (lane == 0) J.anchor[so] = make_float4(q0, q1, q2, rc);
-                // the nearest by hi + lo among the list: lane j < KC tests entry j
-                const float m0 = __shfl_sync(FULL, l0, o), m1 = __shfl_sync(FULL, l1, o),
-                            m2 = __shfl_sync(FULL, l2, o);
-                unsigned long long ek = ~0ull;
-                if (lane < KC && pos >= 0) {
-                    const float4 p = J.map.pts[pos];
-                    const float ed2 = sq3(__fsub_rn(__fsub_rn(p.x, q0), m0), __fsub_rn(__fsub_rn(p.y, q1), m1),
-                                          __fsub_rn(__fsub_rn(p.z, q2), m2));
-                    const int oi = __float_as_int(p.w);
-                    if (before(ed2, oi, J.max_d2, 0x7fffffff)) ek = dkey(ed2, oi);
-                }
-                int ep = pos;
-#pragma unroll
-                for (int off = 1; off < KC; off <<= 1) {
-                    const unsigned long long ok = __shfl_xor_sync(FULL, ek, off);
-                    const int op = __shfl_xor_sync(FULL, ep, off);
-                    if (ok < ek) {
-                        ek = ok;
-                        ep = op;
-                    }
-                }
-                ek = __shfl_sync(FULL, ek, 0);
-                ep = __shfl_sync(FULL, ep, 0);
-                if (lane == o) {
-                    walk = 0;
-                    if (ek != ~0ull) {
-                        best_d2 = key_d2(ek);
-                        best_oi = key_idx(ek);
-                        best_pos = ep;
-                    } else {
-                        best_d2 = J.max_d2;
-                        best_oi = 0x7fffffff;
-                        best_pos = -1;
-                    }
-                }
+            } else if (lane == 0) {
+                cand_store1(J.cand, so, ep);
+                J.anchor[so] = make_float4(q0, q1, q2, -1.f);  // position of this search, no cache
+            }
+            if (lane == o) {
+                walk = 0;
+                best_d2 = ek != ~0ull ? key_d2(ek) : J.max_d2;
+                best_oi = ek != ~0ull ? key_idx(ek) : 0x7fffffff;
+                best_pos = ep;
             }
         }
     }
@@ -482,41 +478,45 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
     // warp walks once for all of them (each lane first scans its own previous or seed leaf).
     if (packet && __popc(__ballot_sync(FULL, walk != 0)) > J.coop_max && !__any_sync(FULL, walk == 2)) {
         const bool mine = walk == 1;
+        float wb = walk_bound(best_d2);
         auto offer = [&](int u, const float4& p) {
-            const float d2 = point_d2(y0, y1, y2, p);
+            const float d2 = exact_d2(p);
             const int oi = __float_as_int(p.w);
             if (before(d2, oi, best_d2, best_oi)) {
                 best_d2 = d2;
                 best_oi = oi;
                 best_pos = u;
+                wb = walk_bound(d2);
             }
         };
         if (mine && h0 >= 0)
             scan_points4(J.map.pts, h0 * B, min(h0 * B + B, nmap), [&](int u, const float4& p) { offer(u, p); });
-        if (packet_nn8(J.map, nmap, mine, y0, y1, y2, best_d2, mine ? h0 : -1, wstack, offer) && mine) {
-            reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+        if (packet_nn8(J.map, nmap, mine, y0, y1, y2, wb, mine ? h0 : -1, wstack, offer) && mine) {
+            cand_store1(J.cand, s, best_pos);
             J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
             walk = 0;
         }
     }
     // Many in this warp (or a cooperative walk ran out of stack): each point walks alone.
     if (walk == 1) {
+        float wb = walk_bound(best_d2);
         auto scan1 = [&](int lf) {
             scan_points4(J.map.pts, lf * B, min(lf * B + B, nmap), [&](int u, const float4& p) {
-                const float d2 = point_d2(y0, y1, y2, p);
+                const float d2 = exact_d2(p);
                 const int oi = __float_as_int(p.w);
                 if (before(d2, oi, best_d2, best_oi)) {
                     best_d2 = d2;
                     best_oi = oi;
                     best_pos = u;
+                    wb = walk_bound(d2);
                 }
             });
         };
         if (h0 >= 0) scan1(h0);
-        traverse8(J.map, y0, y1, y2, best_d2, [&](int lf) {
+        traverse8(J.map, y0, y1, y2, wb, [&](int lf) {
             if (lf != h0) scan1(lf);
         });
-        reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(best_pos, -1, -1, -1);
+        cand_store1(J.cand, s, best_pos);
         J.anchor[s] = make_float4(y0, y1, y2, -1.f);  // position of this search, no cache
     } else if (walk == 2) {
         unsigned long long Lk[KC];
@@ -540,8 +540,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
             if (lf != h0 && lf != h1) scan_leaf(lf);
         });
         const float rc = (key_idx(Lk[KC - 1]) != 0x7fffffff ? sqrtf(key_d2(Lk[KC - 1])) : Rs) * (1.f - 1e-6f);
-        reinterpret_cast<int4*>(J.cand)[2l * s] = make_int4(P[0], P[1], P[2], P[3]);
-        reinterpret_cast<int4*>(J.cand)[2l * s + 1] = make_int4(P[4], P[5], P[6], P[7]);
+        cand_store(J.cand, s, P);
         J.anchor[s] = make_float4(y0, y1, y2, rc);
         pick_exact(P);
     }
@@ -623,18 +622,30 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
 
 // Block-wide sum of acc into row[0 .. NACC) (row[NACC ..32) zeroed; visible device-wide on return
 // to thread 0 after its __threadfence); returns the number of threads with refreshed != 0.
+static_assert(NACC <= 32, "one partial row of 32 floats, one component per lane");
 template <int BS = REG_THREADS>
 __device__ __forceinline__ int block_partial(const float (&acc)[NACC], int refreshed, float* row)
 {
     __shared__ float red[BS / 32][NACC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Transposed butterfly: at each step a lane keeps half of its values and adds the partner's
+    // copy of that half, so that lane c ends with component c's warp sum in 31 shuffles (5 per
+    // component for a butterfly of each).  Every partial sum is the pairwise sum a butterfly of
+    // that component forms (float addition commutes exactly), so the bits are the same.
+    float v[32];
 #pragma unroll
-    for (int a = 0; a < NACC; ++a) {
-        float v = acc[a];
+    for (int a = 0; a < 32; ++a) v[a] = a < NACC ? acc[a] : 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][a] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float send = up ? v[j] : v[j + o];
+            const float keep = up ? v[j + o] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
     }
+    if (lane < NACC) red[warp][lane] = v[0];
     const int count = __syncthreads_count(refreshed);
     if (threadIdx.x < 32) {
         float v = 0.f;
@@ -1361,8 +1372,10 @@ __device__ __forceinline__ void seed_point(const IndexView& map, int m, float4 q
         }
         seed = min(lo, m - 1);
     }
-    reinterpret_cast<int4*>(cand)[2l * s] = make_int4(seed, -1, -1, -1);
-    reinterpret_cast<int4*>(cand)[2l * s + 1] = make_int4(-1, -1, -1, -1);
+    int P[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) P[j] = j == 0 ? seed : -1;
+    cand_store(cand, s, P);
     anchor[s] = make_float4(0.f, 0.f, 0.f, -2.f);  // no previous search
 }
 

@@ -457,6 +457,46 @@ def test_coop_walks_do_not_change_results(g, ctx):
     m1.close()
 
 
+def test_cache_step_does_not_change_results(g, ctx):
+    """Every search (grid block, per-point, packet and cooperative walks, a cache check) returns the
+    nearest map point by the same hi + lo distance, so the cache step, which only decides when a
+    point builds a cache instead of searching alone, leaves poses, systems, iteration counts and
+    inliers bit-identical: the full-size frame and a config-1 registration; 0 = never cache."""
+    f, means, covs = _cfg2()
+    m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    src, cs, tgt, ct, _ = config1_inputs(1, 2)
+    m1 = g.gsicp_build_map_index(ctx, cu(tgt), cu(ct))
+    T1 = random_offset(np.random.default_rng(7), 5.0, 0.05)
+    out = {}
+    steps = (0.001, 0.0, 0.0003, 0.0007, 0.002, 0.005)
+    try:
+        for step in steps:
+            g.gsicp_ctx_set_cache_step(ctx, step)
+            r = g.gsicp_track_frame(ctx, cu(f["depth"]), REPLICA_INTR.as_array(), 2, 0.1, 10.0, cp, m, f["T0"], rp)
+            refreshes = sum(g.gsicp_ctx_reg_stats(ctx, r["iters"])["refreshes"])
+            r1 = g.gsicp_register(ctx, cu(src), cu(cs), m1, T1, rp)
+            out[step] = (r, r1, refreshes)
+    finally:
+        g.gsicp_ctx_set_cache_step(ctx, 0.001)
+    r0, r10, _ = out[steps[0]]
+    assert r0["status"] == g.OK and r10["status"] == g.OK
+    for step in steps[1:]:
+        r, r1, _ = out[step]
+        for key in ("T", "H"):
+            np.testing.assert_array_equal(r[key], r0[key])
+            np.testing.assert_array_equal(r1[key], r10[key])
+        assert (r["iters"], r["cost"], r["inliers"]) == (r0["iters"], r0["cost"], r0["inliers"])
+        assert (r1["iters"], r1["cost"], r1["inliers"]) == (r10["iters"], r10["cost"], r10["inliers"])
+    assert out[0.0][2] > out[0.001][2]  # with no caches every point searches in every iteration
+    for bad in (-1e-3, float("nan"), float("inf")):
+        with pytest.raises(RuntimeError):
+            g.gsicp_ctx_set_cache_step(ctx, bad)
+    m.close()
+    m1.close()
+
+
 def test_gn_launch_modes_give_identical_results(g, ctx):
     """The Gauss-Newton iterations as one conditional graph (default) and as plain launches give
     bit-identical results: a config-1 registration and the full-size frame."""
