@@ -143,7 +143,7 @@ typedef enum { GSICP_GN_GRAPH = 0, GSICP_GN_PLAIN = 1 } gsicp_gn_launch_mode;
 gsicp_status gsicp_ctx_set_gn_launch_mode(gsicp_ctx ctx, int mode);
 /* Source points per thread block of this context's Gauss-Newton iterations (gsicp_register,
  * gsicp_linearise, gsicp_track_frame*, the shard calls): 128, 256 (default) or 384, one point per
- * thread, 768 threads per SM.  A block's points form one row of the reduction, so the block size
+ * thread.  A block's points form one row of the reduction, so the block size
  * fixes the order of the sums: poses agree to rounding across sizes, and at 256 they equal
  * gsicp_register_batch's (whose work items are 256 points) bit for bit.  Takes effect at the next
  * registration.  GSICP_ERR_INVALID_ARG for another value or a null ctx. */

@@ -804,9 +804,12 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
 }
 
 // One Gauss-Newton iteration, BS source points per block (one per thread): 128, 256 (the batched
-// kernel's chunk, which makes the two paths' sums the same bits) or 384, with 768 threads per SM.
+// kernel's chunk, which makes the two paths' sums the same bits) or 384.  The launch bounds ask for
+// 1024 threads per SM, i.e. 64 registers a thread at 128 and 256 (a few spills in the walks; per
+// 1200x680 frame 1.17 against 1.185 ms with the 80 registers of 768 threads per SM: the cache-hit
+// iterations are bound by memory latency and gain from the extra warps); 384 stays at 768.
 template <int BS>
-__global__ void __launch_bounds__(BS, 768 / BS) gicp_iter_kernel(const RegJob* __restrict__ jp,
+__global__ void __launch_bounds__(BS, 1024 / BS) gicp_iter_kernel(const RegJob* __restrict__ jp,
                                                                  cudaGraphConditionalHandle cond)
 {
     // launched as a programmatic dependent of the previous iteration (plain-launch mode): wait for
