@@ -222,8 +222,9 @@ def run_ours(args, world, rank, local):
     cp = g.CovParams(K_NN, EPS, g.PLANE, P_ALIGN)
     rp = g.RegParams(MAX_DIST, MAX_ITERS, TOL, TOL, 6)
     depth_dev = torch.from_numpy(f["depth"]).cuda()
-    # the map index's shape and the context's cooperative-walk threshold, picked by the autotuner on
-    # this frame (untimed; every candidate gives the same poses)
+    # the map index's shape, the context's cooperative-walk threshold and its Gauss-Newton block size,
+    # picked by the autotuner on this frame (untimed; every shape and threshold gives the same poses
+    # bit for bit; the block size fixes the order of the sums, so poses agree to rounding)
     from paper_2403_12550_b300.autotune import tune_frame
     if args.shape:
         b_, c_, k_, *bs_ = args.shape.split(",")
