@@ -77,3 +77,52 @@ def config2_inputs(seed: int = 0):
 __all__ = ["POSE_ROT_TOL", "POSE_TRANS_TOL", "COV_REL_TOL", "KNN_TIE_REL", "PLANE_GAP_EXCLUDE", "rot_angle",
            "pose_diff", "sym", "cov_rel_err", "config1_inputs", "oracle_frame_points", "oracle_map_from_views",
            "config2_inputs", "transform_points"]
+
+
+def near_tie_pairs(seed: int, d: float, n_side: int = 16, spacing: float = 0.4):
+    """Source points whose two nearest map points are equidistant to within the float rounding of
+    the transformed query, arranged so that the rounded query (hi alone) and the exact query
+    disagree on which is nearer.
+
+    A grid of n_side^3 float32 source points near (5, 5, 5) m (where an ulp of a coordinate is
+    4.8e-7 m) and a pose with a rotation, so that y = R x + t is not a float.  For each point, two
+    float32 map points at distance ~d from y in FP64: a at a random direction, b chosen among random
+    directions at the same radius so that the FP64 distances differ by more than `gap` (well above
+    what the distances' own float rounding can flip) while the distances from float32(y) order the
+    two the other way round by more than `gap`, when a direction doing so is found (else the first
+    candidate).  Returns src, covs_s, means, covs (map: point i's pair at 2i, 2i + 1), T,
+    nearest (FP64 nearest map index per point), flipped (bool: the rounded query picks the other)."""
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) - (n_side - 1) / 2) * spacing
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    src = (np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1) + np.array([5.3, 4.9, 5.7])).astype(np.float32)
+    ax = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    ang = 0.21
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    R = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = [0.37, -0.21, 0.13]
+    y = src.astype(np.float64) @ R.T + T[:3, 3]
+    yh = y.astype(np.float32).astype(np.float64)
+    gap = 2e-9 if d < 0.01 else 2e-8
+    n = len(src)
+    means = np.empty((2 * n, 3), np.float32)
+    flipped = np.zeros(n, bool)
+    for i in range(n):
+        u = rng.normal(size=3)
+        a = (y[i] + d * u / np.linalg.norm(u)).astype(np.float32)
+        da = np.linalg.norm(a - y[i])
+        V = rng.normal(size=(256, 3))
+        B = (y[i] + da * V / np.linalg.norm(V, axis=1, keepdims=True)).astype(np.float32)
+        db = np.linalg.norm(B - y[i], axis=1)
+        ha, hb = np.linalg.norm(a - yh[i]), np.linalg.norm(B - yh[i], axis=1)
+        ok = (np.abs(da - db) > gap) & (np.abs(ha - hb) > gap) & (np.sign(da - db) != np.sign(ha - hb))
+        j = int(np.argmax(ok)) if ok.any() else 0
+        flipped[i] = bool(ok[j])
+        means[2 * i], means[2 * i + 1] = a, B[j]
+    d2 = ((means.astype(np.float64).reshape(n, 2, 3) - y[:, None, :]) ** 2).sum(-1)
+    nearest = 2 * np.arange(n) + np.argmin(d2, axis=1)
+    covs_s = np.tile(np.array([1e-4, 0, 0, 1e-4, 0, 1e-4], np.float32), (n, 1))
+    covs = np.tile(np.array([1e-4, 0, 0, 1e-4, 0, 1e-4], np.float32), (2 * n, 1))
+    return src, covs_s, means, covs, T, nearest.astype(np.int32), flipped

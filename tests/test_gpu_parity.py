@@ -457,6 +457,31 @@ def test_coop_walks_do_not_change_results(g, ctx):
     m1.close()
 
 
+@pytest.mark.parametrize("d", [0.003, 0.04])
+def test_near_ties_follow_the_exact_query_on_every_search_path(g, ctx, d):
+    """Pairs of map points equidistant from y = T x to within the float rounding of y, where the
+    rounded query (hi alone) orders the two the other way round: every search path -- the grid
+    block (d = 3 mm, certified), and beyond it (d = 40 mm) per-point, cooperative and packet walks
+    -- returns the nearest by the hi + lo query, i.e. the oracle's FP64 correspondence, bit for bit."""
+    from ._util import near_tie_pairs
+    src, cs, means, covs, T, nearest, flipped = near_tie_pairs(5, d)
+    assert flipped.mean() > 0.9
+    lo = orc.linearise(src, cs, orc.Map(means, covs), T, 0.1)
+    np.testing.assert_array_equal(lo["corr"], nearest)
+    m = g.gsicp_build_map_index(ctx, cu(means), cu(covs))
+    try:
+        for coop, pk in ((0, 0), (32, 0), (2, 1), (0, 1)):
+            g.gsicp_ctx_set_coop_walks(ctx, coop)
+            g.gsicp_ctx_set_packet_iters(ctx, pk)
+            lg = g.gsicp_linearise(ctx, cu(src), cu(cs), m, T, 0.1)
+            np.testing.assert_array_equal(lg["corr"].cpu().numpy(), nearest, err_msg=f"coop {coop} packet {pk}")
+            assert lg["inliers"] == len(src)
+    finally:
+        g.gsicp_ctx_set_coop_walks(ctx, 4)
+        g.gsicp_ctx_set_packet_iters(ctx, 1)
+        m.close()
+
+
 def test_cache_step_does_not_change_results(g, ctx):
     """Every search (grid block, per-point, packet and cooperative walks, a cache check) returns the
     nearest map point by the same hi + lo distance, so the cache step, which only decides when a

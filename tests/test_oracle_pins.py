@@ -62,6 +62,26 @@ def test_knn_ties_break_to_smaller_index():
     assert idx2.tolist() == [[0, 1, 2]]
 
 
+@pytest.mark.parametrize("d", [0.003, 0.04])
+def test_correspondences_resolve_near_ties_by_the_fp64_query(d):
+    """Sec. 3 (Eq. MLE_for_T): each transformed source point y = T x takes its nearest map mean.
+    On pairs of map points equidistant from y to within the float rounding of y, where the rounded
+    query orders the two the other way round, the oracle's correspondences are the brute-force
+    nearest by the FP64 query (and the construction has teeth: the rounded query disagrees on
+    nearly every pair)."""
+    from tests._util import near_tie_pairs
+    src, cs, means, covs, T, nearest, flipped = near_tie_pairs(5, d, n_side=8)
+    assert flipped.mean() > 0.9
+    y = src.astype(np.float64) @ T[:3, :3].T + T[:3, 3]
+    d2 = ((means.astype(np.float64)[None, :, :] - y[:, None, :]) ** 2).sum(-1)
+    np.testing.assert_array_equal(np.argmin(d2, axis=1), nearest)  # brute force over the whole map
+    yh = y.astype(np.float32).astype(np.float64)
+    d2h = ((means.astype(np.float64)[None, :, :] - yh[:, None, :]) ** 2).sum(-1)
+    assert (np.argmin(d2h, axis=1) != nearest).mean() > 0.9
+    lo = orc.linearise(src, cs, orc.Map(means, covs), T, 0.1)
+    np.testing.assert_array_equal(lo["corr"], nearest)
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_radius_nn_tree_equals_brute_force(seed):
     rng = np.random.default_rng(seed)
