@@ -145,6 +145,49 @@ __device__ __forceinline__ void key_insert(unsigned long long (&L)[K], int (&P)[
     P[0] = go[0] ? p : P[0];
 }
 
+// A sorting network for N <= 32 keys: Batcher's merge exchange (Knuth, TAOCP vol. 3, 5.2.2,
+// Algorithm M) as a compile-time list of compare-exchange pairs (97 for N = 20, 191 for N = 32).
+struct SortNet {
+    unsigned char a[256], b[256];
+    int n;
+};
+constexpr SortNet make_sort_net(int N)
+{
+    SortNet net{};
+    net.n = 0;
+    int t = 0;
+    while ((1 << t) < N) ++t;
+    for (int p = t > 0 ? 1 << (t - 1) : 0; p > 0; p >>= 1) {
+        int q = 1 << (t - 1), r = 0, d = p;
+        for (;;) {
+            for (int i = 0; i < N - d; ++i)
+                if ((i & p) == r) {
+                    net.a[net.n] = (unsigned char)i;
+                    net.b[net.n] = (unsigned char)(i + d);
+                    ++net.n;
+                }
+            if (q == p) break;
+            d = q - p;
+            q >>= 1;
+            r = p;
+        }
+    }
+    return net;
+}
+// Sorts L ascending in registers (every index a compile-time constant).
+template <int N>
+__device__ __forceinline__ void sort_keys(unsigned long long (&L)[N])
+{
+    static_assert(N >= 1 && N <= 32, "network sizes up to 32");
+    constexpr SortNet net = make_sort_net(N);
+#pragma unroll
+    for (int c = 0; c < net.n; ++c) {
+        const unsigned long long x = L[net.a[c]], y = L[net.b[c]];
+        L[net.a[c]] = x < y ? x : y;
+        L[net.b[c]] = x < y ? y : x;
+    }
+}
+
 // Insert (d, i[, p]) into the list (D, I[, P]) of length K sorted by (distance, index), dropping
 // the last entry; the caller has checked that the new entry precedes the last one.  Every slot is
 // compared with the new entry independently and then shifted with selects, so the dependency

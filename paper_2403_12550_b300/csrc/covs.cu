@@ -377,22 +377,43 @@ __global__ void __launch_bounds__(WIN_TX * WIN_TY, 6) knn_window_kernel(
     if (active) {
         unsigned long long Lk[KMAX];
         const unsigned long long empty = dkey(GSICP_INF, 0x7fffffff);
-#pragma unroll
-        for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : empty;
         // keys hold the tile position of the point: tile positions are ordered like the original
         // (row-major) indices, so ties break exactly as by index, and the neighbours are read
         // back from shared memory
         const float4* tl = &tile[0][0];
-        auto visit = [&](int dy, int dx) {
+        auto key_at = [&](int dy, int dx) {
             const int pos = (ly + R + dy) * SX + (lx + R + dx);
             const float4 pp = tl[pos];
-            if (__float_as_int(pp.w) == 0x7fffffff) return;  // no point at this sample
-            const unsigned long long key = dkey(point_d2(q.x, q.y, q.z, pp), pos);
+            return __float_as_int(pp.w) == 0x7fffffff ? empty : dkey(point_d2(q.x, q.y, q.z, pp), pos);
+        };
+        // Up to KMAX = 20, the first KMAX samples of the 5 x 5 centre fill the list at once and a
+        // sorting network orders them (an insertion each would cost a pass over the list); then
+        // only the k smallest stay, in the last k slots, with zero keys in front that nothing
+        // displaces: the list that inserting them one by one gives.  (At KMAX = 32 the network's
+        // keys no longer fit in registers: the list starts empty.)
+        constexpr int NF = KMAX <= 20 ? KMAX : 0;
+        if constexpr (NF > 0) {
+#pragma unroll
+            for (int a = 0; a < KMAX; ++a) Lk[a] = key_at(a / 5 - 2, a % 5 - 2);
+            sort_keys(Lk);
+            const int sh = KMAX - k;  // shift right by sh, one power of two at a time
+#pragma unroll
+            for (int b = 1; b < KMAX; b <<= 1)
+                if (sh & b) {
+#pragma unroll
+                    for (int a = KMAX - 1; a >= 0; --a) Lk[a] = a >= b ? Lk[a - b] : 0ull;
+                }
+        } else {
+#pragma unroll
+            for (int a = 0; a < KMAX; ++a) Lk[a] = a < KMAX - k ? 0ull : empty;
+        }
+        auto visit = [&](int dy, int dx) {
+            const unsigned long long key = key_at(dy, dx);  // a missing sample: the empty key
             if (key < Lk[KMAX - 1]) key_insert(Lk, key);
         };
         // loops kept rolled: one copy of the insertion code keeps the kernel in the instruction cache
 #pragma unroll 1
-        for (int c = 0; c < 25; ++c) visit(c / 5 - 2, c % 5 - 2);
+        for (int c = NF; c < 25; ++c) visit(c / 5 - 2, c % 5 - 2);
 #pragma unroll 1
         for (int dy = -R; dy <= R; ++dy) {
             const bool mid = dy >= -2 && dy <= 2;
