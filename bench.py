@@ -55,10 +55,10 @@ GN_BODY_ITERS = 4              # iteration launches per pass of the Gauss-Newton
 # kernels launched per timed step (counted from the ncu launch list of this workload):
 LAUNCHES_MAP_REBUILD = 14  # count reset 1, bbox + quantise 1, Morton keys + digit counts 1, radix sort 4,
                            # gather + leaf boxes 1, box levels 3, cell table size/clear/fill 3
-LAUNCHES_FRAME = 19        # a1 5 (count, 3 scan, write), source index 8 (count, 3 scan, write, gather +
-                           # leaf boxes, 2 box levels), k-NN covariances 4 (9x9 window, 25x25 window, tree,
-                           # reorder), GN seed 1, GN set-up 1; plus one Gauss-Newton launch per iteration
-                           # (plain-launch mode: one more set-up launch)
+LAUNCHES_FRAME = 13        # a1 2 (counts, write), source index 5 (counts, write, gather + leaf boxes, 2 box
+                           # levels), k-NN covariances 4 (9x9 window, 25x25 window, tree, reorder), GN seed 1,
+                           # GN set-up 1; plus one Gauss-Newton launch per iteration (plain-launch mode: one
+                           # more set-up launch)
 # DRAM bytes per gicp_iter_kernel launch (read + write, mean over the iterations of one frame of this
 # workload, ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the CUDA sources whose
 # SHA-256 is given; reported as null once any of them has changed.

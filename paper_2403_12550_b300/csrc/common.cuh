@@ -145,6 +145,25 @@ __device__ __forceinline__ void key_insert(unsigned long long (&L)[K], int (&P)[
     P[0] = go[0] ? p : P[0];
 }
 
+// Sum of counts[0 .. b), computed by the whole block (all threads get it): a block's offset in
+// an order-preserving compaction whose per-block counts another launch wrote, read directly
+// instead of through a separate scan (a few hundred words per block, from L2).
+__device__ __forceinline__ uint32_t block_prefix(const uint32_t* __restrict__ counts, int b)
+{
+    __shared__ uint32_t red[32];
+    uint32_t v = 0u;
+    for (int i = threadIdx.x; i < b; i += blockDim.x) v += __ldcg(counts + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t t = 0u;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    __syncthreads();  // red may be reused by the caller's next call
+    return t;
+}
+
 // A sorting network for N <= 32 keys: Batcher's merge exchange (Knuth, TAOCP vol. 3, 5.2.2,
 // Algorithm M) as a compile-time list of compare-exchange pairs (97 for N = 20, 191 for N = 32).
 struct SortNet {

@@ -5,7 +5,8 @@
 // [z_min, z_max] becomes ((u - cx) d / fx, (v - cy) d / fy, d), in row-major
 // pixel order.  The two products/quotients are evaluated in double and
 // rounded once to float, so each coordinate is the correctly rounded value of
-// the formula.  Order-preserving compaction: per-block counts -> scan -> write.
+// the formula.  Order-preserving compaction: per-block counts, then the write, each block summing
+// the counts of the blocks before it.
 #include "internal.h"
 
 namespace gsicp {
@@ -33,11 +34,13 @@ __global__ void d2p_count_kernel(const float* __restrict__ depth, int W, int str
     if (threadIdx.x == 0) counts[blockIdx.x] = (uint32_t)c;
 }
 
-__global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
-                                 float z_min, float z_max, double fx, double fy, double cx, double cy,
-                                 const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int nblocks,
-                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev,
-                                 int* __restrict__ idx_img)
+// The block's valid pixels written from offset off (all_total: every block's valid pixels, used
+// by the last block for the counts).
+__device__ __forceinline__ void d2p_write_block(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+                                                float z_min, float z_max, double fx, double fy, double cx, double cy,
+                                                uint32_t off, bool last, uint32_t all_total, float* __restrict__ pts,
+                                                float* __restrict__ z, int cap, int* n_dev, int* total_dev,
+                                                int* __restrict__ idx_img)
 {
     __shared__ uint32_t wsum[D2P_THREADS / 32];
     const long idx = (long)blockIdx.x * D2P_THREADS + threadIdx.x;
@@ -50,7 +53,7 @@ __global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int str
     __syncthreads();
     uint32_t before = 0;
     for (int w = 0; w < warp; ++w) before += wsum[w];
-    const uint32_t pos = offs[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+    const uint32_t pos = off + before + __popc(bal & ((1u << lane) - 1u));
     if (ok && pos < (uint32_t)cap) {
         const double dd = (double)d;
         pts[3l * pos + 0] = (float)(((double)u - cx) * dd / fx);
@@ -60,11 +63,36 @@ __global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int str
     }
     // sample -> point index (-1: no point), for searches over the image grid
     if (idx_img && idx < total) idx_img[idx] = ok && pos < (uint32_t)cap ? (int)pos : -1;
-    if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
-        const uint32_t all = offs[nblocks - 1] + counts[nblocks - 1];
-        if (n_dev) *n_dev = (int)min(all, (uint32_t)cap);
-        if (total_dev) *total_dev = (int)all;
+    if (last && threadIdx.x == 0) {
+        if (n_dev) *n_dev = (int)min(all_total, (uint32_t)cap);
+        if (total_dev) *total_dev = (int)all_total;
     }
+}
+
+// Writes with the blocks' exclusive offsets from a scan (offs).
+__global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+                                 float z_min, float z_max, double fx, double fy, double cx, double cy,
+                                 const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int nblocks,
+                                 float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev,
+                                 int* __restrict__ idx_img)
+{
+    const bool last = blockIdx.x == nblocks - 1;
+    const uint32_t off = offs[blockIdx.x];
+    d2p_write_block(depth, W, stride, Ws, total, z_min, z_max, fx, fy, cx, cy, off, last,
+                    last ? off + counts[blockIdx.x] : 0u, pts, z, cap, n_dev, total_dev, idx_img);
+}
+
+// Writes with each block's offset summed from the counts of the blocks before it (no scan launches).
+__global__ void d2p_write_prefix_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+                                        float z_min, float z_max, double fx, double fy, double cx, double cy,
+                                        const uint32_t* __restrict__ counts, int nblocks, float* __restrict__ pts,
+                                        float* __restrict__ z, int cap, int* n_dev, int* total_dev,
+                                        int* __restrict__ idx_img)
+{
+    const bool last = blockIdx.x == nblocks - 1;
+    const uint32_t off = block_prefix(counts, blockIdx.x);
+    d2p_write_block(depth, W, stride, Ws, total, z_min, z_max, fx, fy, cx, cy, off, last,
+                    last ? off + __ldcg(counts + blockIdx.x) : 0u, pts, z, cap, n_dev, total_dev, idx_img);
 }
 
 gsicp_status launch_depth_to_points(const float* depth, int W, int H, const float intr[4], int stride,
@@ -74,14 +102,13 @@ gsicp_status launch_depth_to_points(const float* depth, int W, int H, const floa
     const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
     const long total = (long)Ws * Hs;
     const int nb = (int)((total + D2P_THREADS - 1) / D2P_THREADS);
-    GSICP_CHECK(counts.ensure(sizeof(uint32_t) * 2 * (size_t)nb));
+    (void)sums;
+    GSICP_CHECK(counts.ensure(sizeof(uint32_t) * (size_t)nb));
     uint32_t* cnt = counts.as<uint32_t>();
-    uint32_t* off = cnt + nb;
     d2p_count_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, Ws, total, z_min, z_max, cnt);
-    GSICP_CHECK(exclusive_scan_u32(cnt, off, nb, sums, s));
-    d2p_write_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, Ws, total, z_min, z_max, (double)intr[0],
-                                                (double)intr[1], (double)intr[2], (double)intr[3], off, cnt, nb, pts,
-                                                z, cap, n_dev, total_dev, idx_img);
+    d2p_write_prefix_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, Ws, total, z_min, z_max, (double)intr[0],
+                                                       (double)intr[1], (double)intr[2], (double)intr[3], cnt, nb, pts,
+                                                       z, cap, n_dev, total_dev, idx_img);
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

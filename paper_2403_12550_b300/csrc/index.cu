@@ -689,16 +689,18 @@ __global__ void pix_count_kernel(const int* __restrict__ idx_img, const int* __r
     if (threadIdx.x == 0) counts[blockIdx.x] = (uint32_t)c;
 }
 
-// The point index of every valid sample, in the samples' Morton order (stable compaction).
+// The point index of every valid sample, in the samples' Morton order (stable compaction); each
+// block's offset is the sum of the counts of the blocks before it.
 __global__ void pix_write_kernel(const int* __restrict__ idx_img, const int* __restrict__ msamp, int nsamp,
-                                 const uint32_t* __restrict__ offs, uint32_t* __restrict__ order)
+                                 const uint32_t* __restrict__ counts, uint32_t* __restrict__ order)
 {
     __shared__ uint32_t ws[32];
     const int k = blockIdx.x * 256 + threadIdx.x;
     const int pi = k < nsamp ? idx_img[msamp[k]] : -1;
+    const uint32_t off = block_prefix(counts, blockIdx.x);
     uint32_t total;
     const uint32_t rank = block_exclusive_scan(pi >= 0 ? 1u : 0u, ws, total);
-    if (pi >= 0) order[offs[blockIdx.x] + rank] = (uint32_t)pi;
+    if (pi >= 0) order[off + rank] = (uint32_t)pi;
 }
 
 gsicp_status build_index_pixel_order(const float* pts, const int* idx_img, const int* msamp, int nsamp, int cap,
@@ -717,13 +719,11 @@ gsicp_status build_index_pixel_order(const float* pts, const int* idx_img, const
     out.has_grid = false;
     GSICP_CHECK(out.quant.ensure(sizeof(float4)));
     const int nb = std::max(1, (nsamp + 255) / 256);
-    GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * 2 * (size_t)nb));
+    GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * (size_t)nb));
     GSICP_CHECK(scr.v0.ensure(sizeof(uint32_t) * (size_t)std::max(cap, 1)));
     uint32_t* counts = scr.k1.as<uint32_t>();
-    uint32_t* offs = counts + nb;
     pix_count_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, counts);
-    GSICP_CHECK(exclusive_scan_u32(counts, offs, nb, scr.sums, s));
-    pix_write_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, offs, scr.v0.as<uint32_t>());
+    pix_write_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, counts, scr.v0.as<uint32_t>());
     gather_leaf_kernel<<<(total + 255) / 256, 256, 0, s>>>(pts, nullptr, scr.v0.as<uint32_t>(), nullptr, n_dev, total,
                                                            L, B, out.pts.as<float4>(), nullptr, out.boxes.as<float4>(),
                                                            nullptr, 0, nullptr);
