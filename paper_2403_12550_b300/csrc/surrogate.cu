@@ -298,11 +298,12 @@ __device__ __forceinline__ void plane_cov_from_v(float v0, float v1, float v2, f
 // which a core matrix (8 rows x 16 B) is one output row's 8 pixels shifted by the tap, so the A
 // operand of every tap is the same staged tile seen through a descriptor with its own start address
 // (row stride SBO = one halo row, K stride LBO = one channel plane).  The weights (B,
-// [tap][group][output][8 channels]) arrive once per CTA by one bulk copy.  Two tile buffers: the
-// copy of the next tile is issued right after the current tile's 50 MMAs (25 taps x 2 channel
-// halves), so it runs under the MMAs and the epilogue.  One thread issues copies and MMAs; the
-// MMAs are committed to an mbarrier; the epilogue reads the accumulator (warp w: rows
-// 32w..32w+31) with tcgen05.ld.  Layer 2's epilogue applies ReLU, the validity mask and bfloat16
+// [tap][group][output][8 channels]) arrive once per CTA by one bulk copy.  Two tile buffers and two
+// accumulators in tensor memory: the next tile's 50 MMAs (25 taps x 2 channel halves) are issued
+// into the other accumulator before the current tile's epilogue and run under it; a buffer is
+// refilled with the tile after next as soon as its tile's MMAs complete.  One thread issues copies
+// and MMAs; each accumulator's MMAs are committed to its own mbarrier; the epilogue reads the
+// accumulator (warp w: rows 32w..32w+31) with tcgen05.ld.  Layer 2's epilogue applies ReLU, the validity mask and bfloat16
 // rounding and writes h2; layer 3's writes v and the point's plane covariance.  Every wait is
 // bounded: when one runs out the CTA records it in err, waits (bounded) for its copies in flight,
 // frees its tensor memory and returns.
@@ -375,99 +376,124 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
                                                          float* __restrict__ v_out, unsigned* __restrict__ err)
 {
     static_assert(kN == 32 || kN == 16, "layer 2 (N = 32) or layer 3 (N = 16)");
+    constexpr uint32_t kCols = 2 * kN < 32 ? 32u : 2u * kN;  // two accumulators (an allocation is >= 32 columns)
     extern __shared__ __align__(1024) uint8_t tc_smem_[];
     uint8_t* sB = tc_smem_ + 2 * TC_A_BYTES;
-    __shared__ __align__(8) uint64_t bars[4];  // B copy, tile buffer 0, tile buffer 1, MMA done
+    __shared__ __align__(8) uint64_t bars[5];  // B copy, tile buffers 0 and 1, MMAs done into accumulators 0 and 1
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (w + TC_TW - 1) / TC_TW, tiles_y = (h + TC_TH - 1) / TC_TH;
     const int ntiles = tiles_x * tiles_y;
     const uint32_t a0 = smem_u32(tc_smem_), b0 = smem_u32(sB);
-    const uint32_t bar_b = smem_u32(&bars[0]), bar_m = smem_u32(&bars[3]);
+    const uint32_t bar_b = smem_u32(&bars[0]);
+    auto bar_a = [&](int buf) { return smem_u32(&bars[1 + buf]); };
+    auto bar_m = [&](int acc) { return smem_u32(&bars[3 + acc]); };
+    auto tile_x0 = [&](int tile) { return (tile % tiles_x) * TC_TW; };
+    auto tile_y0 = [&](int tile) { return (tile / tiles_x) * TC_TH; };
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    const int t0 = blockIdx.x, t1 = blockIdx.x + gridDim.x;
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
+        for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;");
-        // the weights: one bulk copy; the first tile: four box copies
+        // the weights: one bulk copy; the first two tiles: four box copies each
         tc_expect(bar_b, tc_b_bytes<kN>());
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      ::"r"(b0), "l"(reinterpret_cast<uint64_t>(wb)), "r"(tc_b_bytes<kN>()), "r"(bar_b)
                      : "memory");
-        if ((int)blockIdx.x < ntiles)
-            tc_load_tile(&tmap, a0, (blockIdx.x % tiles_x) * TC_TW, (blockIdx.x / tiles_x) * TC_TH,
-                         smem_u32(&bars[1]));
+        if (t0 < ntiles) tc_load_tile(&tmap, a0, tile_x0(t0), tile_y0(t0), bar_a(0));
+        if (t1 < ntiles) tc_load_tile(&tmap, a0 + TC_A_BYTES, tile_x0(t1), tile_y0(t1), bar_a(1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
+    // thread 0: tile buffer buf's 50 MMAs (25 taps x 2 channel halves) into accumulator acc, committed
+    // to bar_m(acc); the 50 descriptors differ only in their start address (the low 14 bits, in
+    // 16-byte units, which no offset here carries out of): base + constant
+    auto issue = [&](int buf, int acc) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint64_t da0 = tc_desc(a0 + buf * TC_A_BYTES, TC_PLANE, TC_HW * 16), db0 = tc_desc(b0, kN * 16, 128);
+        const uint32_t d = tmem + (uint32_t)(acc * kN);
+#pragma unroll
+        for (int t = 0; t < SG_TAPS; ++t) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint64_t da = da0 + (uint64_t)((2 * j * TC_PLANE + ((t / 5) * TC_HW + t % 5) * 16) >> 4);
+                const uint64_t db = db0 + (uint64_t)(((t * 4 + 2 * j) * (kN * 16)) >> 4);
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(d), "l"(da), "l"(db), "r"(tc_idesc<kN>()), "r"((t | j) != 0 ? 1u : 0u));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(bar_m(acc)) : "memory");
+    };
     // copies and MMAs this CTA started and has not yet seen complete (thread 0's bookkeeping): on a
     // wait that runs out they are waited for again before the CTA leaves
-    bool failed = false, b_pending = true, a_pending = (int)blockIdx.x < ntiles, m_pending = false;
-    uint32_t a_bar = smem_u32(&bars[1]), a_parity = 0, m_parity = 0;
+    bool failed = false, b_pending = true;
+    bool a_pend[2] = {t0 < ntiles, t1 < ntiles}, m_pend[2] = {false, false};
+    uint32_t a_par[2] = {0u, 0u}, m_par[2] = {0u, 0u};
     if (tid == 0) {
         failed = !tc_wait(bar_b, 0);
         b_pending = failed;
+        if (!failed && t0 < ntiles) {
+            failed = !tc_wait(bar_a(0), 0);
+            if (!failed) {
+                a_pend[0] = false;
+                issue(0, 0);
+                m_pend[0] = true;
+            }
+        }
     }
     int k = 0;
     if (!__syncthreads_or(failed)) {
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-            const int buf = k & 1;
-            const int x0 = (tile % tiles_x) * TC_TW, y0 = (tile / tiles_x) * TC_TH;
-            const uint32_t abuf = a0 + buf * TC_A_BYTES;
+        // Tile k: its MMAs were issued one step earlier (into accumulator k mod 2); tile k + 1's are
+        // issued now, into the other accumulator, so that they run under tile k's epilogue.
+        for (int tile = t0; tile < ntiles; tile += gridDim.x, ++k) {
+            const int buf = k & 1, acc = k & 1;
+            const int next = tile + gridDim.x;
             bool bad = false;
-            if (tid == 0) {
-                bad = !tc_wait(smem_u32(&bars[1 + buf]), (k >> 1) & 1);
+            if (tid == 0 && next < ntiles) {
+                bad = !tc_wait(bar_a(buf ^ 1), ((k + 1) >> 1) & 1);
                 if (!bad) {
-                    a_pending = false;
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    // the 50 descriptors differ only in their start address (the low 14 bits, in
-                    // 16-byte units, which no offset here carries out of): base + constant
-                    const uint64_t da0 = tc_desc(abuf, TC_PLANE, TC_HW * 16), db0 = tc_desc(b0, kN * 16, 128);
-#pragma unroll
-                    for (int t = 0; t < SG_TAPS; ++t) {
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const uint64_t da = da0 + (uint64_t)((2 * j * TC_PLANE + ((t / 5) * TC_HW + t % 5) * 16) >> 4);
-                            const uint64_t db = db0 + (uint64_t)(((t * 4 + 2 * j) * (kN * 16)) >> 4);
-                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                         ::"r"(tmem), "l"(da), "l"(db), "r"(tc_idesc<kN>()), "r"((t | j) != 0 ? 1u : 0u));
-                        }
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 ::"r"(bar_m) : "memory");
-                    m_pending = true;
-                    m_parity = k & 1;
-                    // the next tile's copy into the other buffer (its last reader, the previous
-                    // tile's MMAs, has completed)
-                    const int next = tile + gridDim.x;
-                    if (next < ntiles) {
-                        a_bar = smem_u32(&bars[1 + (buf ^ 1)]);
-                        a_parity = ((k + 1) >> 1) & 1;
-                        tc_load_tile(&tmap, a0 + (buf ^ 1) * TC_A_BYTES, (next % tiles_x) * TC_TW,
-                                     (next / tiles_x) * TC_TH, a_bar);
-                        a_pending = true;
-                    }
+                    a_pend[buf ^ 1] = false;
+                    issue(buf ^ 1, acc ^ 1);
+                    m_pend[acc ^ 1] = true;
+                    m_par[acc ^ 1] = ((k + 1) >> 1) & 1;
                 }
             }
+            // the epilogue's inputs, which do not depend on the MMAs, are read while they run
+            const int x0 = tile_x0(tile), y0 = tile_y0(tile);
+            const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
+            const bool inside = x < w && y < h;
+            const long pix = (long)y * w + x;
+            const float4 g = inside ? grid[pix] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool valid = inside && g.w != 0.f;
+            const int id = kN == 16 && valid && covs ? idx_img[pix] : -1;
             if (__syncthreads_or(bad)) {
                 failed = true;
                 break;
             }
-            if (__syncthreads_or(!tc_wait(bar_m, k & 1))) {
+            if (__syncthreads_or(!tc_wait(bar_m(acc), (k >> 1) & 1))) {
                 failed = true;
                 break;
             }
-            m_pending = false;
+            if (tid == 0) {
+                m_pend[acc] = false;
+                // tile k's MMAs are done, so its buffer is free: tile k + 2's copy goes into it
+                const int after = tile + 2 * gridDim.x;
+                if (after < ntiles) {
+                    tc_load_tile(&tmap, a0 + buf * TC_A_BYTES, tile_x0(after), tile_y0(after), bar_a(buf));
+                    a_pend[buf] = true;
+                    a_par[buf] = ((k + 2) >> 1) & 1;
+                }
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-            const int pr = warp * 32 + lane, x = x0 + (pr & 7), y = y0 + (pr >> 3);
-            const bool inside = x < w && y < h;
-            const long pix = (long)y * w + x;
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kN);
             if (kN == 32) {
                 uint32_t r[32];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -482,7 +508,6 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
                              : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 if (inside) {
-                    const bool valid = grid[pix].w != 0.f;
                     float v[32];
 #pragma unroll
                     for (int q = 0; q < 32; ++q) v[q] = valid ? fmaxf(__uint_as_float(r[q]), 0.f) : 0.f;
@@ -495,8 +520,6 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
                              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 if (inside) {
-                    const float4 g = grid[pix];
-                    const bool valid = g.w != 0.f;
                     const float v0 = valid ? __uint_as_float(r[0]) : 0.f, v1 = valid ? __uint_as_float(r[1]) : 0.f,
                                 v2 = valid ? __uint_as_float(r[2]) : 0.f;
                     if (v_out) {
@@ -504,25 +527,26 @@ __global__ void __launch_bounds__(128) sg_conv_tc_kernel(const __grid_constant__
                         v_out[3 * pix + 1] = v1;
                         v_out[3 * pix + 2] = v2;
                     }
-                    const int id = valid && covs ? idx_img[pix] : -1;
                     if (id >= 0) plane_cov_from_v(v0, v1, v2, g.z, eps, p, covs + 6l * id);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();  // accumulator read before the next tile's MMAs overwrite it
+            __syncthreads();  // accumulator acc read before tile k + 2's MMAs overwrite it
         }
     }
     if (failed && tid == 0) {
         *reinterpret_cast<volatile unsigned*>(err) = 1u;  // pinned host word
         // no copy may land and no MMA may read after the CTA is gone (each wait bounded again)
         if (b_pending) tc_wait(bar_b, 0);
-        if (a_pending) tc_wait(a_bar, a_parity);
-        if (m_pending) tc_wait(bar_m, m_parity);
+        for (int b = 0; b < 2; ++b)
+            if (a_pend[b]) tc_wait(bar_a(b), a_par[b]);
+        for (int a = 0; a < 2; ++a)
+            if (m_pend[a]) tc_wait(bar_m(a), m_par[a]);
     }
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
     }
 }
 
