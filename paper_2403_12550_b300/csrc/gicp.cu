@@ -690,13 +690,9 @@ __device__ __forceinline__ void group_sum(const float* __restrict__ partials, in
     grow[64l * g + 32 + c] = a.lo;
 }
 
-// Warp 0 (all 32 lanes): records H, b, cost, inliers and the squared residuals of a linearisation
-// whose NACC sums are tot[0 .. NACC) into the state and, when solve is set, solves H delta = -b in
-// FP64 (Cholesky), applies T <- exp(delta^) T and takes the stopping decision: fewer than
-// min_inliers correspondences or H not positive definite stop the registration as degenerate.
-// Returns whether another iteration should run (the same value on every lane).
-__device__ __forceinline__ bool record_and_solve(const RegJob& J, RegState* st, const double* tot, int lane,
-                                                 int it_now, bool solve)
+// One warp (all 32 lanes): records H, b, cost, inliers and the squared residuals of a
+// linearisation whose NACC sums are tot[0 .. NACC) into the state.
+__device__ __forceinline__ void record_sums(RegState* st, const double* tot, int lane)
 {
     const double tot_l = lane < NACC ? tot[lane] : 0.0;  // component `lane`
     if (lane < 21) {
@@ -714,6 +710,15 @@ __device__ __forceinline__ bool record_and_solve(const RegJob& J, RegState* st, 
     } else if (lane == 29) {
         st->sqdist = tot_l;
     }
+}
+
+// One warp (all 32 lanes), when solve is set: solves H delta = -b of the sums tot in FP64
+// (Cholesky), applies T <- exp(delta^) T and takes the stopping decision: fewer than min_inliers
+// correspondences or H not positive definite stop the registration as degenerate.  Returns whether
+// another iteration should run (the same value on every lane).
+__device__ __forceinline__ bool solve_update(const RegJob& J, RegState* st, const double* tot, int lane, int it_now,
+                                             bool solve)
+{
     const long long inliers = (long long)llrint(tot[28]);
     bool more = false;
     if (solve) {
@@ -758,8 +763,8 @@ __device__ __forceinline__ bool record_and_solve(const RegJob& J, RegState* st, 
 }
 
 // The block that completed the last group: the compensated sum of the ng group rows, then in its
-// first warp the H, b, cost and inliers of this linearisation and (solve mode) the FP64 solve, the
-// pose update and the stopping test.  Returns whether another iteration should run (on lane 0 of
+// second warp the H, b, cost and inliers of this linearisation and, at the same time in its first
+// warp, (solve mode) the FP64 solve, the pose update and the stopping test.  Returns whether another iteration should run (on lane 0 of
 // warp 0; false elsewhere).  t_start: globaltimer when the block became the last.
 __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const float* __restrict__ grow, int ng,
                                          int it_now, unsigned long long t_start)
@@ -782,14 +787,17 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
         tot[lane] = (double)a.hi + (double)a.lo;
     }
     __syncthreads();
+    if (warp == 1) {  // H, b, cost and inliers of this linearisation, beside warp 0's solve
+        record_sums(st, tot, lane);
+        if (J.sums_out && lane < NACC) J.sums_out[lane] = tot[lane];
+    }
     if (warp != 0) return false;
 
-    // ---- warp 0: H, b, cost and inliers of this linearisation, then the lane-parallel FP64 solve
+    // ---- warp 0: the lane-parallel FP64 solve
     unsigned long long t_solve = 0;
     if (lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_solve));
     if (lane == 0) st->counter = 0u;
-    if (J.sums_out && lane < NACC) J.sums_out[lane] = tot[lane];
-    const bool more = record_and_solve(J, st, tot, lane, it_now, J.mode == REG_MODE_SOLVE);
+    const bool more = solve_update(J, st, tot, lane, it_now, J.mode == REG_MODE_SOLVE);
     if (lane == 0) {
         unsigned long long t_end;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
@@ -1202,7 +1210,8 @@ __global__ void shard_update_kernel(const RegJob* __restrict__ jp, const double*
     RegState* st = J.st;
     const int it_now = st->iter;
     if (st->status != REG_ST_RUNNING) return;
-    record_and_solve(J, st, tot, lane, it_now, true);
+    record_sums(st, tot, lane);
+    solve_update(J, st, tot, lane, it_now, true);
     __threadfence();
 }
 
