@@ -403,7 +403,16 @@ struct RegJob {
     int coop_max;          // warps with at most this many tree walks do them together (0: never)
     double* sums_out;      // optional: the NACC FP64 sums of each linearisation (shard registrations)
     int packet_iters;      // iterations (from the first) whose busy warps walk for their nearest points together
+    int* sched;            // optional (single registrations): the iteration blocks' start order, kept
+                           // from one iteration to the next (gicp.cu, sched_block); sched_ints(grid) ints
 };
+
+// Start order of a registration's iteration blocks: each block records which of SCHED_BUCKETS
+// duration classes (4.1 us doubling) it fell in, and the next iteration starts its blocks slowest
+// class first.  Layout: counts of the classes for even and odd iterations (8 ints each), then the
+// lists of block indices per parity and class (grid ints each).
+constexpr int SCHED_BUCKETS = 6;
+__host__ __device__ constexpr size_t sched_ints(int grid) { return 16 + 2 * (size_t)SCHED_BUCKETS * grid; }
 
 constexpr int COOP_WALKS_DEFAULT = 4;  // default RegJob::coop_max
 

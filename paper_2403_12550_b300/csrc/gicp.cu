@@ -219,6 +219,8 @@ __device__ __forceinline__ void transform_df(const float* Rh, const float* Rl, f
 __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegState* __restrict__ st, Pose16 T0)
 {
     *job_dst = job;
+    if (job.sched)  // no history: the first iteration starts its blocks in index order
+        for (int i = 0; i < 16; ++i) job.sched[i] = 0;
     for (int i = 0; i < 16; ++i) st->T[i] = T0.v[i];
     for (int i = 0; i < 36; ++i) st->H[i] = 0.0;
     for (int i = 0; i < 6; ++i) st->b[i] = 0.0;
@@ -811,6 +813,43 @@ __device__ __forceinline__ bool finalize(const RegJob& J, RegState* st, const fl
     return more;
 }
 
+// Which block of points this launch's block blockIdx.x processes in iteration it: blocks of the
+// previous iteration's slowest duration class first, then the next class, and so on; index order
+// when there is no complete record (the first iteration).  A block's points, partial row and group
+// follow from the block it processes, so the order changes when blocks start, not what they sum.
+// In a grid that needs more than one wave of resident blocks, starting the long blocks first keeps
+// them from beginning last and setting the iteration's end (the durations of a block's points change
+// little from one iteration to the next).
+__device__ __forceinline__ int sched_block(const int* __restrict__ sched, int G, int it)
+{
+    const int p = (it + 1) & 1;  // the record the previous iteration wrote
+    const int4 c0 = __ldcg(reinterpret_cast<const int4*>(sched + 8 * p));
+    const int2 c1 = __ldcg(reinterpret_cast<const int2*>(sched + 8 * p + 4));
+    const int cnt[SCHED_BUCKETS] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+    int total = 0;
+#pragma unroll
+    for (int k = 0; k < SCHED_BUCKETS; ++k) total += cnt[k];
+    int b = blockIdx.x;
+    if (total != G) return b;
+    const int* lists = sched + 16 + (long)p * SCHED_BUCKETS * G;
+#pragma unroll
+    for (int k = SCHED_BUCKETS - 1; k >= 0; --k) {
+        if (b < cnt[k]) return __ldcg(lists + (long)k * G + b);
+        b -= cnt[k];
+    }
+    return blockIdx.x;
+}
+
+// Records that block lb of iteration it took dt_ns (its duration class and place in the class's list).
+__device__ __forceinline__ void sched_record(int* __restrict__ sched, int G, int it, int lb, unsigned long long dt_ns)
+{
+    const unsigned q = (unsigned)min(dt_ns >> 12, 0xffffffull);
+    const int k = q == 0u ? 0 : min(SCHED_BUCKETS - 1, 32 - __clz(q));
+    const int p = it & 1;
+    const int pos = atomicAdd(sched + 8 * p + k, 1);
+    sched[16 + ((long)p * SCHED_BUCKETS + k) * G + pos] = lb;
+}
+
 // One Gauss-Newton iteration, BS source points per block (one per thread): 128, 256 (the batched
 // kernel's chunk, which makes the two paths' sums the same bits) or 384.  The launch bounds ask for
 // 1024 threads per SM, i.e. 64 registers a thread at 128 and 256 (a few spills in the walks; per
@@ -833,11 +872,14 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gicp_iter_kernel(const RegJob* 
     const int n = *J.n;
     const int nmap = *J.map.n;
     const int it_now = st->iter;
-    if (threadIdx.x == 0 && it_now < REG_STATS) {
+    __shared__ unsigned long long t_begin;  // thread 0's: kept in shared memory, not a register, over the search
+    if (threadIdx.x == 0) {
         unsigned long long t0;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-        atomicMin(&st->t_first[it_now], t0);
+        t_begin = t0;
+        if (it_now < REG_STATS) atomicMin(&st->t_first[it_now], t0);
     }
+    const int lb = J.sched ? sched_block(J.sched, gridDim.x, it_now) : blockIdx.x;  // the block of points
     float R[9], t[3], Rl[9], tl[3];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -856,25 +898,24 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gicp_iter_kernel(const RegJob* 
     // scheduler balances the uneven per-point work, and the fixed point -> block mapping keeps
     // the reduction order, hence the result, deterministic).
     __shared__ int2 wstack[BS / 32][WARP_STACK];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lb * BS + threadIdx.x;
     const int refreshed = gn_point(J, R, Rl, t, tl, s, s < n, nmap, acc, wstack[threadIdx.x >> 5],
                                    it_now < J.packet_iters);
-    const int block_refreshed = block_partial<BS>(acc, refreshed, J.partials + 32l * blockIdx.x);
+    const int block_refreshed = block_partial<BS>(acc, refreshed, J.partials + 32l * lb);
     // this block's share is written: the next iteration's launch may begin (its blocks wait in
     // griddepcontrol.wait until this grid, the last block's solve included, has completed)
     asm volatile("griddepcontrol.launch_dependents;");
-    const int nrows = gridDim.x, ngroups = (nrows + GN_GROUP - 1) / GN_GROUP, g = blockIdx.x / GN_GROUP;
+    const int nrows = gridDim.x, ngroups = (nrows + GN_GROUP - 1) / GN_GROUP, g = lb / GN_GROUP;
     const int nb = (n + BS - 1) / BS;  // rows of blocks that held points (the rest are zero)
     unsigned* gctr = group_counters(J.partials, nrows, ngroups);
     float* grow = group_rows(J.partials, nrows);
     __shared__ bool am_last;
     if (threadIdx.x == 0) {
         if (block_refreshed > 0 && it_now < REG_STATS) atomicAdd(&st->refreshes[it_now], block_refreshed);
-        if (it_now < REG_STATS) {
-            unsigned long long t1;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-            atomicMax(&st->t_arrive[it_now], t1);
-        }
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (it_now < REG_STATS) atomicMax(&st->t_arrive[it_now], t1);
+        if (J.sched) sched_record(J.sched, nrows, it_now, lb, t1 - t_begin);
         am_last = atomicAdd(&gctr[g], 1u) == (unsigned)(min(nrows - g * GN_GROUP, GN_GROUP) - 1);
     }
     __syncthreads();
@@ -893,6 +934,9 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gicp_iter_kernel(const RegJob* 
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    // every block of this iteration has read the previous iteration's record: clear its counts for
+    // the next iteration to fill
+    if (J.sched && threadIdx.x < 8) J.sched[8 * ((it_now + 1) & 1) + threadIdx.x] = 0;
     unsigned long long t_start = 0;
     if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     // the groups of the blocks that held points: the same rows, groups and order as a batched
@@ -1108,6 +1152,7 @@ gsicp_status RegMachine::init(int capacity)
     grid = built_bs == bs ? std::max(want, grid) : want;  // grid counts blocks of bs points
     built_bs = bs;
     GSICP_CHECK(partials.ensure(sizeof(float) * reduction_floats(grid)));
+    GSICP_CHECK(sched.ensure(sizeof(int) * sched_ints(grid)));
     GSICP_CUDA(cudaMemset(partials.ptr, 0, sizeof(float) * reduction_floats(grid)));  // group counters start at 0
     GSICP_CHECK(job.ensure(sizeof(RegJob)));
     GSICP_CHECK(state.ensure(sizeof(RegState)));
@@ -1168,6 +1213,7 @@ void RegMachine::release()
     if (state_host) cudaFreeHost(state_host);
     state_host = nullptr;
     partials.release();
+    sched.release();
     job.release();
     state.release();
     cand.release();
@@ -1184,6 +1230,7 @@ static gsicp_status reg_prepare(RegMachine& rm, RegJob& job, const double T0[16]
     job.cand = rm.cand.as<int>();
     job.anchor = rm.anchor.as<float4>();
     job.partials = rm.partials.as<float>();
+    job.sched = rm.sched.as<int>();
     job.st = rm.state.as<RegState>();
     Pose16 P;
     for (int i = 0; i < 16; ++i) P.v[i] = T0[i];

@@ -109,7 +109,7 @@ gsicp_status launch_permute_covs(const IndexView& ix, const float* covs, int cap
 // Registration machinery.
 struct RegMachine {
     int grid = 0;
-    DevBuf partials, job, state, cand, anchor;
+    DevBuf partials, sched, job, state, cand, anchor;
     RegState* state_host = nullptr;  // pinned
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
