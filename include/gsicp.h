@@ -129,7 +129,7 @@ gsicp_status gsicp_ctx_set_packet_iters(gsicp_ctx ctx, int iters);
  * that list is complete, which later iterations check in place of a search while the point stays
  * within it (Sec. 3: correspondences are searched again each iteration).  Results do not depend
  * on it: every search and every cache check returns the nearest point by the same distance;
- * 0 = never build caches.  Default 0.001 (1 mm).  GSICP_ERR_INVALID_ARG for a negative or
+ * 0 = never build caches.  Default 0.0005 (0.5 mm).  GSICP_ERR_INVALID_ARG for a negative or
  * non-finite value or a null ctx. */
 gsicp_status gsicp_ctx_set_cache_step(gsicp_ctx ctx, float meters);
 /* How this context launches the Gauss-Newton iterations of gsicp_register and gsicp_track_frame*:

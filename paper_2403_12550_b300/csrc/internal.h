@@ -202,7 +202,7 @@ struct gsicp_ctx_s {
     bool timing = false;
     int coop_walks = gsicp::COOP_WALKS_DEFAULT;  // RegJob::coop_max of this context's registrations
     int packet_iters = 1;              // RegJob::packet_iters of this context's registrations
-    float cache_step = 0.001f;         // RegJob::cache_step (m) of this context's registrations
+    float cache_step = 0.0005f;        // RegJob::cache_step (m) of this context's registrations
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t copy_stream = nullptr;  // host-buffer entry points' uploads (overlap the caller's queue)
     cudaEvent_t copy_done = nullptr;
