@@ -62,8 +62,8 @@ LAUNCHES_FRAME = 13        # a1 2 (counts, write), source index 5 (counts, write
 # DRAM bytes per gicp_iter_kernel launch (read + write, mean over the iterations of one frame of this
 # workload, ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the CUDA sources whose
 # SHA-256 is given; reported as null once any of them has changed.
-GN_TRAFFIC = {"bytes_per_launch": 28399087,
-              "sources_sha256": "0686628f99109b30c088f4458053d2d6c155f06dccc6edc0dbc6001f103f3ba6"}
+GN_TRAFFIC = {"bytes_per_launch": 28527804,
+              "sources_sha256": "f6399768b76c7101becce212921330cb067a984092e29d765e4ac8cd5c15c62c"}
 
 
 def parse():
@@ -106,37 +106,58 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms; the summary keeps the samples taken
+    during the timed region (from the first sample on, so that sampling is live when the region
+    starts) and one sampling period on either side of it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.05
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.rows = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "--format=csv,noheader,nounits", "-lms", str(int(self.PERIOD_S * 1e3))],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except OSError:
             self.proc = None
+        if self.proc:
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            deadline = time.time() + 3.0
+            while not self.rows and time.time() < deadline and self.proc.poll() is None:
+                time.sleep(0.005)
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
+        self.t1 = time.time()
         if self.proc:
+            time.sleep(self.PERIOD_S * 1.5)  # one more sample after the region
             self.proc.send_signal(signal.SIGTERM)
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out, _ = self.proc.communicate()
+                self.proc.wait()
+            self.thread.join(timeout=5)
 
     def summary(self):
-        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        pad = self.PERIOD_S * 1.2
+        lines = [ln for t, ln in self.rows if self.t0 - pad <= t <= self.t1 + pad]
+        rows = [r for r in csv.reader(io.StringIO("".join(lines))) if len(r) >= 9]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
@@ -144,7 +165,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "period_ms": int(self.PERIOD_S * 1e3),
+                "window_ms": round((self.t1 - self.t0) * 1e3, 1)}
 
 
 # the sources the Gauss-Newton kernel's DRAM traffic depends on: the kernel and its search, the index
@@ -344,8 +366,11 @@ def run_ours(args, world, rank, local):
         "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": int(alg), "avg_launch_ms": per_launch_ms},
-        "e2e": {"value": job_throughput(world, K, e2e_s), "unit": "frames/s", "h2d_bytes_per_step": int(f["depth"].nbytes),
-                "d2h_bytes_per_step": REGSTATE_BYTES},
+        # the host-buffer call uploads the rows a1 samples: ceil(H / stride) rows of W floats
+        "e2e": {"value": job_throughput(world, K, e2e_s), "unit": "frames/s",
+                "h2d_bytes_per_step": int(-(-f["depth"].shape[0] // STRIDE) * f["depth"].shape[1] * 4),
+                "d2h_bytes_per_step": REGSTATE_BYTES, "ms_p50": round(float(np.median(e2e_ms)), 4),
+                "ms_max": round(float(np.max(e2e_ms)), 4)},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

@@ -374,10 +374,11 @@ gsicp_status gsicp_map_nearest(gsicp_ctx ctx, gsicp_map map, const float* querie
  * (one stream synchronisation at the end).  Same semantics as calling gsicp_depth_to_points,
  * gsicp_source_covariances (z = the points' depth) and gsicp_register in sequence.
  * depth_dev is a device image; gsicp_track_frame_host takes a host image (pinned memory for an
- * asynchronous copy), uploaded inside the call on a stream of the context's own so that the copy
- * overlaps work the caller queued on `stream` before the call (a map-index rebuild, say); `stream`
- * waits for the upload before the frame's first kernel.  n_points_out (nullable) receives the
- * frame's point count.
+ * asynchronous copy), of which only the rows a1 samples (every stride-th, ceil(H / stride) x W
+ * floats) are uploaded inside the call, on a stream of the context's own so that the copy overlaps
+ * work the caller queued on `stream` before the call (a map-index rebuild, say); `stream` waits for
+ * the upload before the frame's first kernel.  n_points_out (nullable) receives the frame's point
+ * count.
  * ------------------------------------------------------------------------------------------- */
 gsicp_status gsicp_track_frame(gsicp_ctx ctx, const float* depth_dev, int W, int H,
                                const float intr[4], int stride, float z_min, float z_max,

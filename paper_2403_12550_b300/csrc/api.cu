@@ -734,7 +734,7 @@ static gsicp_status sample_morton_order(gsicp_ctx ctx, int Ws, int Hs)
 
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                       int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
-                                      int cap, cudaStream_t s, gsicp_surrogate sg)
+                                      int cap, cudaStream_t s, gsicp_surrogate sg, int row_step)
 {
     const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
     GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)cap));
@@ -749,7 +749,7 @@ gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[0], s));
     GSICP_CHECK(launch_depth_to_points(depth_dev, W, H, intr, stride, z_min, z_max, ctx->frame_pts.as<float>(),
                                        ctx->frame_z.as<float>(), cap, nd, ctx->total_dev.as<int>(), ctx->a1_counts,
-                                       ctx->a1_sums, s, ctx->frame_idx.as<int>()));
+                                       ctx->a1_sums, s, ctx->frame_idx.as<int>(), row_step));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[1], s));
     if (Ws <= 1024 && Hs <= 1024) {
         // the frame's points are near one another exactly where their samples are: index them in
@@ -808,14 +808,14 @@ gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int 
                                      gsicp_map map, const double T0[16], const gsicp_reg_params* reg_params,
                                      double T_out[16], double H_out[36], int* iters_out, double* cost_out,
                                      int64_t* inliers_out, int64_t* n_points_out, cudaStream_t s,
-                                     gsicp_surrogate sg)
+                                     gsicp_surrogate sg, int row_step)
 {
     const int64_t cap64 = (int64_t)((W + stride - 1) / stride) * ((H + stride - 1) / stride);
     if (cap64 > (1 << 30)) return GSICP_ERR_INVALID_ARG;
     const int cap = (int)cap64;
     int* nd = ctx->n_dev.as<int>();
     const bool tm = ctx->timing;
-    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s, sg));
+    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s, sg, row_step));
     RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
     GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));
@@ -880,20 +880,27 @@ gsicp_status gsicp_track_frame_host(gsicp_ctx ctx, const float* depth_host, int 
     if (!valid_frame_args(ctx, depth_host, W, H, intr, stride, cov_params, map, T0, reg_params, T_out))
         return GSICP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = sizeof(float) * (size_t)W * (size_t)H;
-    GSICP_CHECK(ctx->frame_depth.ensure(bytes));
-    // The depth image goes up on the context's own copy stream, so that it overlaps whatever the
-    // caller queued on `stream` before this call (e.g. a map-index rebuild); `stream` waits for it
+    // Only the rows a1 samples (every stride-th) go up: ceil(H / stride) rows of W floats.
+    const int Hs = (H + stride - 1) / stride;
+    const size_t row = sizeof(float) * (size_t)W;
+    GSICP_CHECK(ctx->frame_depth.ensure(row * (size_t)Hs));
+    // The depth rows go up on the context's own copy stream, so that they overlap whatever the
+    // caller queued on `stream` before this call (e.g. a map-index rebuild); `stream` waits for them
     // before a1.  The buffer is free: the previous call on this context synchronised its stream.
     if (!ctx->copy_stream) {
         GSICP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
         GSICP_CUDA(cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
     }
-    GSICP_CUDA(cudaMemcpyAsync(ctx->frame_depth.ptr, depth_host, bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    if (stride == 1)
+        GSICP_CUDA(cudaMemcpyAsync(ctx->frame_depth.ptr, depth_host, row * (size_t)H, cudaMemcpyHostToDevice,
+                                   ctx->copy_stream));
+    else
+        GSICP_CUDA(cudaMemcpy2DAsync(ctx->frame_depth.ptr, row, depth_host, row * (size_t)stride, row, (size_t)Hs,
+                                     cudaMemcpyHostToDevice, ctx->copy_stream));
     GSICP_CUDA(cudaEventRecord(ctx->copy_done, ctx->copy_stream));
     GSICP_CUDA(cudaStreamWaitEvent(s, ctx->copy_done, 0));
     return track_frame_impl(ctx, ctx->frame_depth.as<float>(), W, H, intr, stride, z_min, z_max, cov_params, map, T0,
-                            reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out, s, nullptr);
+                            reg_params, T_out, H_out, iters_out, cost_out, inliers_out, n_points_out, s, nullptr, 1);
 }
 
 }  // extern "C"

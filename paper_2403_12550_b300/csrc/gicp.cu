@@ -852,11 +852,12 @@ __device__ __forceinline__ void sched_record(int* __restrict__ sched, int G, int
 
 // One Gauss-Newton iteration, BS source points per block (one per thread): 128, 256 (the batched
 // kernel's chunk, which makes the two paths' sums the same bits) or 384.  The launch bounds ask for
-// 1024 threads per SM, i.e. 64 registers a thread at 128 and 256 (a few spills in the walks; per
-// 1200x680 frame 1.17 against 1.185 ms with the 80 registers of 768 threads per SM: the cache-hit
-// iterations are bound by memory latency and gain from the extra warps); 384 stays at 768.
+// 768 threads per SM at 256 and 384, i.e. 80 registers a thread (per 1200x680 frame, with the
+// slowest-first block order: 256 points per block 1.10 ms against 1.15 ms with the 64 registers of
+// 1024 threads per SM, whose walks spill; 384: 1.07 ms, 512 at 64 registers 1.11 ms), and 1024 at
+// 128 (64 registers).
 template <int BS>
-__global__ void __launch_bounds__(BS, 1024 / BS) gicp_iter_kernel(const RegJob* __restrict__ jp,
+__global__ void __launch_bounds__(BS, (BS == 128 ? 1024 : 768) / BS) gicp_iter_kernel(const RegJob* __restrict__ jp,
                                                                  cudaGraphConditionalHandle cond)
 {
     // launched as a programmatic dependent of the previous iteration (plain-launch mode): wait for

@@ -83,10 +83,13 @@ gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_d
 gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf& sums, cudaStream_t s);
 
 // a1: depth -> points (row-major compaction).  Writes *n_dev (clamped to cap) and *total_dev (unclamped).
+// row_step: rows of `depth` (W floats each) between sample rows; 0 = stride (the whole image), 1 when
+// only every stride-th row is in memory.
 gsicp_status launch_depth_to_points(const float* depth, int W, int H, const float intr[4], int stride,
                                     float z_min, float z_max, float* pts, float* z, int cap, int* n_dev,
                                     int* total_dev, DevBuf& counts, DevBuf& sums, cudaStream_t s,
-                                    int* idx_img = nullptr);  // optional: sample -> point index (-1 none)
+                                    int* idx_img = nullptr,  // optional: sample -> point index (-1 none)
+                                    int row_step = 0);
 
 // a2+a3: k-NN covariances of the points of `ix` (its pts hold the n points; orig gives the
 // unsorted xyz for neighbour gathering).
@@ -224,11 +227,12 @@ extern "C" {
 // surrogate (non-null sg) the covariances are its predictions instead of the k-NN ones.
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
                                float z_min, float z_max, const gsicp_cov_params* cov_params, int cap,
-                               cudaStream_t s, gsicp_surrogate sg);
+                               cudaStream_t s, gsicp_surrogate sg,
+                               int row_step = 0);  // launch_depth_to_points' row_step
 // The whole a1..a7 step of gsicp_track_frame (arguments already checked), covariances as above.
 gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
                               float z_min, float z_max, const gsicp_cov_params* cov_params, gsicp_map map,
                               const double T0[16], const gsicp_reg_params* reg_params, double T_out[16],
                               double H_out[36], int* iters_out, double* cost_out, int64_t* inliers_out,
-                              int64_t* n_points_out, cudaStream_t s, gsicp_surrogate sg);
+                              int64_t* n_points_out, cudaStream_t s, gsicp_surrogate sg, int row_step = 0);
 }  // extern "C"

@@ -21,9 +21,9 @@
 namespace gsicp {
 
 // d2p_* (depth.cu) and scan_* (index.cu) kernels, launched here with the fixed scratch.
-__global__ void d2p_count_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+__global__ void d2p_count_kernel(const float* __restrict__ depth, int W, int stride, int row_step, int Ws, long total,
                                  float z_min, float z_max, uint32_t* __restrict__ counts);
-__global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int Ws, long total,
+__global__ void d2p_write_kernel(const float* __restrict__ depth, int W, int stride, int row_step, int Ws, long total,
                                  float z_min, float z_max, double fx, double fy, double cx, double cy,
                                  const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int nblocks,
                                  float* __restrict__ pts, float* __restrict__ z, int cap, int* n_dev, int* total_dev,
@@ -164,11 +164,11 @@ extern "C" gsicp_status gsicp_depth_to_points_noalloc(const float* depth_dev, in
     uint32_t* counts = scratch;
     uint32_t* offs = scratch + NOALLOC_BLOCKS;
     uint32_t* sums = scratch + 2 * NOALLOC_BLOCKS;
-    d2p_count_kernel<<<nb, D2P_THREADS, 0, s>>>(depth_dev, W, stride, Ws, total, z_min, z_max, counts);
+    d2p_count_kernel<<<nb, D2P_THREADS, 0, s>>>(depth_dev, W, stride, stride, Ws, total, z_min, z_max, counts);
     scan_reduce_kernel<<<ns, SCAN_THREADS, 0, s>>>(counts, nb, sums);
     scan_sums_kernel<<<1, 1024, 0, s>>>(sums, ns);
     scan_apply_kernel<<<ns, SCAN_THREADS, 0, s>>>(counts, offs, nb, sums);
-    d2p_write_kernel<<<nb, D2P_THREADS, 0, s>>>(depth_dev, W, stride, Ws, total, z_min, z_max, (double)intr[0],
+    d2p_write_kernel<<<nb, D2P_THREADS, 0, s>>>(depth_dev, W, stride, stride, Ws, total, z_min, z_max, (double)intr[0],
                                         (double)intr[1], (double)intr[2], (double)intr[3], offs, counts, nb, pts_dev,
                                         z_dev, (int)cap, (int*)n_dev, (int*)total_dev, nullptr);
     GSICP_CUDA(cudaGetLastError());

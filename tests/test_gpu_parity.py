@@ -415,6 +415,29 @@ def test_track_frame_config2_matches_oracle(g, ctx):
     m.close()
 
 
+@pytest.mark.parametrize("stride", [1, 2, 3])
+def test_track_frame_host_uploads_sampled_rows(g, ctx, stride):
+    """The host-buffer frame call uploads only the rows a1 samples (every stride-th, a 2D copy);
+    its points and pose equal gsicp_track_frame's on the whole device image bit for bit, with a
+    height that is not a multiple of the stride, from a pinned tensor and from a numpy array."""
+    intr, d = _depth_case(203, 157, 11)
+    cp = g.CovParams(20, 1e-3, g.PLANE, 1.5)
+    rp = g.RegParams(0.1, 30, 1e-6, 1e-6, 6)
+    pts, z = orc.depth_to_points(d, intr.as_array(), 1, 0.1, 10.0)
+    cs = orc.source_covariances(pts, z, k=20, reg_mode=orc.PLANE)["covs"].astype(np.float32)
+    m = g.gsicp_build_map_index(ctx, cu(pts.astype(np.float32)), cu(cs))
+    T0 = random_offset(np.random.default_rng(3), 1.0, 0.01)
+    r = g.gsicp_track_frame(ctx, cu(d), intr.as_array(), stride, 0.1, 10.0, cp, m, T0, rp)
+    pinned = torch.from_numpy(np.ascontiguousarray(d)).pin_memory()
+    for host in (pinned, d):
+        rh = g.gsicp_track_frame_host(ctx, host, intr.as_array(), stride, 0.1, 10.0, cp, m, T0, rp)
+        assert rh["n_points"] == r["n_points"] > 0
+        for key in ("T", "H"):
+            np.testing.assert_array_equal(rh[key], r[key])
+        assert (rh["iters"], rh["inliers"], rh["cost"]) == (r["iters"], r["inliers"], r["cost"])
+    m.close()
+
+
 def test_coop_walks_do_not_change_results(g, ctx):
     """The cooperative tree walk (a whole warp per query), the packet walk (a warp for all of its
     points' nearest points) and the per-point walk are all exact: the full-size frame and a
