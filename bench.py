@@ -29,8 +29,6 @@ import csv
 import io
 import json
 import os
-import signal
-import subprocess
 import sys
 import time
 
@@ -105,68 +103,129 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 50 ms; the summary keeps the samples taken
-    during the timed region (from the first sample on, so that sampling is live when the region
-    starts) and one sampling period on either side of it."""
+class _Nvml:
+    """The few NVML reads the clock sampler needs, through ctypes on the driver's libnvidia-ml
+    (read-only queries; nothing is set).  A polling nvidia-smi process slowed this process's own
+    CUDA calls (host time per tracked frame +0.2 to +1.4 ms) for a while after it had exited, so
+    the clocks are read in-process from a thread instead."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    CLOCK_SM = 1
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
+
+    def __init__(self):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def handle(self, pci_bus_id: str | None, index: int):
+        C = self.C
+        h = C.c_void_p()
+        if pci_bus_id and self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), C.byref(h)) == 0:
+            return h
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(h)) == 0:
+            return h
+        raise RuntimeError("no NVML handle for the device")
+
+    def sample(self, h):
+        C = self.C
+        sm, mx, bits = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, C.byref(sm)) != 0 or \
+                self.lib.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, C.byref(mx)) != 0 or \
+                self.reasons_fn(h, C.byref(bits)) != 0:
+            raise RuntimeError("NVML query failed")
+        return float(sm.value), float(mx.value), [k for k, b in self.REASON_BITS.items() if bits.value & b]
+
+
+_NVML = None
+
+
+def _nvml():
+    """The process's NVML reader, made once (None where NVML cannot be loaded)."""
+    global _NVML
+    if _NVML is None:
+        try:
+            _NVML = _Nvml()
+        except Exception as e:
+            _NVML = False
+            print(f"bench: NVML unavailable for clock sampling ({e!r})", file=sys.stderr)
+    return _NVML or None
+
+
+class ClockSampler:
+    """SM clock, its maximum and the throttle reasons, sampled every 50 ms by a thread of this
+    process (NVML) during the timed region; the summary keeps the samples from the region and one
+    sampling period on either side of it."""
+
     PERIOD_S = 0.05
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
-        self.proc = None
-        self.rows = []
+        self.rows = []  # (time, sm_mhz, max_mhz, reasons)
         self.t0 = self.t1 = None
+        self.thread = None
+        self.handle = None
+        self.error = None
+        nv = _nvml()
+        if not nv:
+            self.error = "NVML unavailable"
+            return
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(gpu_index)
+            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+        except Exception:
+            bus = None
+        try:
+            self.handle = nv.handle(bus, gpu_index)
+        except Exception as e:
+            self.error = repr(e)
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append((time.time(), line))
+    def _sample(self):
+        sm, mx, reasons = _nvml().sample(self.handle)
+        self.rows.append((time.time(), sm, mx, reasons))
+
+    def _loop(self):
+        while not self.stop:
+            try:
+                self._sample()
+            except Exception as e:
+                self.error = f"sample: {e!r}"
+                return
+            time.sleep(self.PERIOD_S)
 
     def __enter__(self):
         import threading
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", str(int(self.PERIOD_S * 1e3))],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
-        except OSError:
-            self.proc = None
-        if self.proc:
-            self.thread = threading.Thread(target=self._read, daemon=True)
+        self.stop = False
+        if self.handle is not None:
+            self.thread = threading.Thread(target=self._loop, daemon=True)
             self.thread.start()
-            deadline = time.time() + 3.0
-            while not self.rows and time.time() < deadline and self.proc.poll() is None:
-                time.sleep(0.005)
+            deadline = time.time() + 1.0
+            while not self.rows and time.time() < deadline:
+                time.sleep(0.001)
         self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
         self.t1 = time.time()
-        if self.proc:
-            time.sleep(self.PERIOD_S * 1.5)  # one more sample after the region
-            self.proc.send_signal(signal.SIGTERM)
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                self.proc.wait()
+        if self.thread:
+            time.sleep(self.PERIOD_S * 1.2)  # one more sample after the region
+            self.stop = True
             self.thread.join(timeout=5)
 
     def summary(self):
-        pad = self.PERIOD_S * 1.2
-        lines = [ln for t, ln in self.rows if self.t0 - pad <= t <= self.t1 + pad]
-        rows = [r for r in csv.reader(io.StringIO("".join(lines))) if len(r) >= 9]
+        pad = self.PERIOD_S * 1.5
+        rows = [r for r in self.rows if self.t0 - pad <= r[0] <= self.t1 + pad]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "period_ms": int(self.PERIOD_S * 1e3),
-                "window_ms": round((self.t1 - self.t0) * 1e3, 1)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "error": self.error}
+        return {"sm_mhz": float(np.median([r[1] for r in rows])), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted({x for r in rows for x in r[3]}), "samples": len(rows),
+                "period_ms": int(self.PERIOD_S * 1e3), "window_ms": round((self.t1 - self.t0) * 1e3, 1),
+                "source": "NVML"}
 
 
 # the sources the Gauss-Newton kernel's DRAM traffic depends on: the kernel and its search, the index
@@ -275,6 +334,22 @@ def run_ours(args, world, rank, local):
     for _ in range(args.warmup):
         rebuild()
         r = step()
+    # ---- end-to-end through the host-buffer entry point (H2D depth + D2H results inside), before
+    # the clock-sampled device-timed steps: reading the clocks while this process runs CUDA calls
+    # (NVML in a thread, or a polling nvidia-smi) slows those calls for a while afterwards
+    e2e_ms = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rebuild()
+        rh = g.gsicp_track_frame_host(ctx, depth_host, intr, STRIDE, Z_MIN, Z_MAX, cp, m, f["T0"], rp)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    assert np.array_equal(rh["T"], r["T"])
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, world, "cuda")
+
     g.gsicp_ctx_set_timing(ctx, True)
     torch.cuda.synchronize()
     if world > 1:
@@ -306,20 +381,6 @@ def run_ours(args, world, rank, local):
     index_ms = [a.elapsed_time(b) for a, b, _ in ev]
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, "cuda")
     g.gsicp_ctx_set_timing(ctx, False)
-
-    # ---- end-to-end through the host-buffer entry point (H2D depth + D2H results inside)
-    e2e_ms = []
-    for i in range(args.steps + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rebuild()
-        rh = g.gsicp_track_frame_host(ctx, depth_host, intr, STRIDE, Z_MIN, Z_MAX, cp, m, f["T0"], rp)
-        t1 = time.perf_counter()
-        if i > 0:
-            e2e_ms.append((t1 - t0) * 1e3)
-    assert np.array_equal(rh["T"], r["T"])
-    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, world, "cuda")
 
     # ---- roofline of the dominant kernel, from the event-timed phases of the timed steps
     keys = ("depth_to_points", "source_index", "knn_cov", "gauss_newton")
