@@ -58,11 +58,13 @@ __device__ __forceinline__ uint32_t grid_hash(uint32_t key)
     return h ^ (h >> 16);
 }
 
-// [start, end) of the cell with this key (empty range if the cell holds no point).
-__device__ __forceinline__ int2 grid_find(const int4* __restrict__ table, uint32_t mask, uint32_t key)
+// [start, end) of the cell with this key (empty range if the cell holds no point), skipping the
+// first probes_done slots of its probe sequence (a caller that has read the home slot passes 1).
+__device__ __forceinline__ int2 grid_find(const int4* __restrict__ table, uint32_t mask, uint32_t key,
+                                          uint32_t probes_done = 0)
 {
-    uint32_t slot = grid_hash(key) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
+    uint32_t slot = (grid_hash(key) + probes_done) & mask;
+    for (uint32_t probe = probes_done; probe <= mask; ++probe) {
         const int4 e = table[slot];
         if ((uint32_t)e.x == key) return make_int2(e.y, e.z);
         if ((uint32_t)e.x == GRID_EMPTY) break;

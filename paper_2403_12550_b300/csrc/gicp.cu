@@ -366,8 +366,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                 if (cert2 > 0.f) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
-                        for (int u = rng[c].x; u < rng[c].y; ++u) {
-                            const float4 p = J.map.pts[u];
+                        scan_points4(J.map.pts, rng[c].x, rng[c].y, [&](int u, const float4& p) {
                             const float d2 = exact_d2(p);
                             const int oi = __float_as_int(p.w);
                             if (before(d2, oi, best_d2, best_oi)) {
@@ -375,7 +374,7 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                                 best_oi = oi;
                                 best_pos = u;
                             }
-                        }
+                        });
                 }
                 // certified when the best is nearer than the block's faces: cert already holds a
                 // margin (1e-5 m) far above |lo|
@@ -397,11 +396,10 @@ __device__ __forceinline__ int gn_point(const RegJob& J, const float (&R)[9], co
                 if (cert2 > 0.f) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
-                        for (int u = rng[c].x; u < rng[c].y; ++u) {
-                            const float4 p = J.map.pts[u];
+                        scan_points4(J.map.pts, rng[c].x, rng[c].y, [&](int u, const float4& p) {
                             const unsigned long long key = dkey(point_d2(y0, y1, y2, p), __float_as_int(p.w));
                             if (key < Lk[KC - 1]) key_insert(Lk, P, key, u);
-                        }
+                        });
                 }
                 if (key_idx(Lk[0]) != 0x7fffffff && key_d2(Lk[0]) <= cert2) {
                     // points outside the list: outside the block (>= cert) or beaten by the KC-th

@@ -439,7 +439,8 @@ __device__ __forceinline__ float grid_block8(const IndexView& ix, float4 qz, flo
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         if (key[c] == GRID_EMPTY || (uint32_t)e[c].x == GRID_EMPTY) continue;
-        rng[c] = (uint32_t)e[c].x == key[c] ? make_int2(e[c].y, e[c].z) : grid_find(ix.grid, mask, key[c]);
+        // the home slot holds another cell: go on probing after it
+        rng[c] = (uint32_t)e[c].x == key[c] ? make_int2(e[c].y, e[c].z) : grid_find(ix.grid, mask, key[c], 1u);
     }
     return cert;
 }
