@@ -217,6 +217,9 @@ void gsicp_ctx_destroy(gsicp_ctx ctx)
         if (e) cudaEventDestroy(e);
     if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->cov_fork) cudaEventDestroy(ctx->cov_fork);
+    if (ctx->cov_join) cudaEventDestroy(ctx->cov_join);
+    if (ctx->cov_stream) cudaStreamDestroy(ctx->cov_stream);
     delete ctx;
 }
 
@@ -734,7 +737,7 @@ static gsicp_status sample_morton_order(gsicp_ctx ctx, int Ws, int Hs)
 
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4],
                                       int stride, float z_min, float z_max, const gsicp_cov_params* cov_params,
-                                      int cap, cudaStream_t s, gsicp_surrogate sg, int row_step)
+                                      int cap, cudaStream_t s, gsicp_surrogate sg, int row_step, bool fork)
 {
     const int Ws = (W + stride - 1) / stride, Hs = (H + stride - 1) / stride;
     GSICP_CHECK(ctx->frame_pts.ensure(sizeof(float) * 3 * (size_t)cap));
@@ -762,17 +765,29 @@ gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int
         GSICP_CHECK(build_index(ctx->frame_pts.as<float>(), nullptr, cap, nd, 32, ctx->src_index, ctx->build, s));
     }
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[2], s));
+    cudaStream_t cs = s;  // the stream of the covariances
+    if (fork) {
+        if (!ctx->cov_stream) {
+            GSICP_CUDA(cudaStreamCreateWithFlags(&ctx->cov_stream, cudaStreamNonBlocking));
+            GSICP_CUDA(cudaEventCreateWithFlags(&ctx->cov_fork, cudaEventDisableTiming));
+            GSICP_CUDA(cudaEventCreateWithFlags(&ctx->cov_join, cudaEventDisableTiming));
+        }
+        GSICP_CUDA(cudaEventRecord(ctx->cov_fork, s));
+        GSICP_CUDA(cudaStreamWaitEvent(ctx->cov_stream, ctx->cov_fork, 0));
+        cs = ctx->cov_stream;
+    }
     if (sg)
         GSICP_CHECK(surrogate_forward(sg, ctx->frame_pts.as<float>(), ctx->frame_idx.as<int>(), Ws, Hs,
-                                      cov_params->eps, cov_params->p, ctx->frame_covs.as<float>(), nullptr, s));
+                                      cov_params->eps, cov_params->p, ctx->frame_covs.as<float>(), nullptr, cs));
     else
         GSICP_CHECK(launch_frame_knn_cov(ctx->src_index.view(), ctx->frame_idx.as<int>(), Ws, Hs, stride, intr,
                                          ctx->frame_pts.as<float>(), ctx->frame_z.as<float>(), cap, *cov_params,
                                          ctx->frame_covs.as<float>(), nullptr, ctx->fb_list.as<int>(),
-                                         ctx->fb_count.as<int>(), s));
+                                         ctx->fb_count.as<int>(), cs));
     GSICP_CHECK(launch_permute_covs(ctx->src_index.view(), ctx->frame_covs.as<float>(), cap,
-                                    ctx->covs_sorted.as<float4>(), s));
-    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], s));
+                                    ctx->covs_sorted.as<float4>(), cs));
+    if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[3], cs));
+    if (fork) GSICP_CUDA(cudaEventRecord(ctx->cov_join, cs));
     return GSICP_OK;
 }
 
@@ -815,9 +830,11 @@ gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int 
     const int cap = (int)cap64;
     int* nd = ctx->n_dev.as<int>();
     const bool tm = ctx->timing;
-    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s, sg, row_step));
+    // the covariances on the context's second stream, beside the registration's seeds and set-up
+    GSICP_CHECK(frame_covariances(ctx, depth_dev, W, H, intr, stride, z_min, z_max, cov_params, cap, s, sg, row_step,
+                                  true));
     RegJob job = make_job(ctx, ctx->src_index.pts.as<float4>(), ctx->covs_sorted.as<float4>(), nd, map, reg_params);
-    GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s));
+    GSICP_CHECK(reg_run(ctx->reg, job, T0, cap, true, s, ctx->cov_join));
     if (tm) GSICP_CUDA(cudaEventRecord(ctx->ev[4], s));
     if (n_points_out) GSICP_CUDA(cudaMemcpyAsync(ctx->host_pinned, nd, sizeof(int), cudaMemcpyDeviceToHost, s));
     gsicp_status st = finish_registration(ctx, s, T_out, H_out, nullptr, iters_out, cost_out, inliers_out);

@@ -1287,7 +1287,7 @@ gsicp_status reg_shard_update(RegMachine& rm, const double* parts, int nparts, c
 }
 
 gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], int n_cap, bool solve,
-                     cudaStream_t s)
+                     cudaStream_t s, cudaEvent_t gn_wait)
 {
     RegJob job = job_in;
     job.mode = solve ? REG_MODE_SOLVE : REG_MODE_LINEARISE;
@@ -1302,6 +1302,7 @@ gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], 
         Pose16 P;
         for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
         reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
+        if (gn_wait) GSICP_CUDA(cudaStreamWaitEvent(s, gn_wait, 0));
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr.val.programmaticStreamSerializationAllowed = 1;
@@ -1318,8 +1319,10 @@ gsicp_status reg_run(RegMachine& rm, const RegJob& job_in, const double T0[16], 
             GSICP_CUDA(cudaLaunchKernelExC(&cfg, iter_kernel(rm.bs), args));
         GSICP_CUDA(cudaGetLastError());
     } else if (solve) {
+        if (gn_wait) GSICP_CUDA(cudaStreamWaitEvent(s, gn_wait, 0));
         GSICP_CUDA(cudaGraphLaunch(rm.exec, s));
     } else {
+        if (gn_wait) GSICP_CUDA(cudaStreamWaitEvent(s, gn_wait, 0));
         GSICP_CHECK(launch_iter(rm, s));
     }
     GSICP_CUDA(cudaMemcpyAsync(rm.state_host, rm.state.ptr, REG_STATE_HEAD, cudaMemcpyDeviceToHost, s));

@@ -125,8 +125,11 @@ struct RegMachine {
     void release();
 };
 
+// A registration on stream s: seeds and set-up, then the Gauss-Newton launches, which first wait
+// for gn_wait when it is given (work of another stream that the iterations read, e.g. the source
+// covariances, may run beside the seeds).
 gsicp_status reg_run(RegMachine& rm, const RegJob& job, const double T0[16], int n_cap, bool solve,
-                     cudaStream_t s);
+                     cudaStream_t s, cudaEvent_t gn_wait = nullptr);
 
 // A registration whose source points are split across processes (one shard here): set-up with the
 // linearisation sums going to sums_out (NACC doubles, device), one linearisation at the current
@@ -209,6 +212,11 @@ struct gsicp_ctx_s {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t copy_stream = nullptr;  // host-buffer entry points' uploads (overlap the caller's queue)
     cudaEvent_t copy_done = nullptr;
+    // a frame's k-NN covariances run on cov_stream beside the registration's seeds and set-up on the
+    // caller's stream: cov_fork (source index built) -> cov_stream, cov_join (covariances reordered)
+    // -> the Gauss-Newton launches
+    cudaStream_t cov_stream = nullptr;
+    cudaEvent_t cov_fork = nullptr, cov_join = nullptr;
     double phase_ms[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -225,10 +233,13 @@ struct gsicp_map_s {
 extern "C" {
 // a1 -> source index -> a2+a3 of one depth frame into the context's frame buffers; with a
 // surrogate (non-null sg) the covariances are its predictions instead of the k-NN ones.
+// fork: the covariances and their reordering go on ctx->cov_stream after the source index, ending
+// with ctx->cov_join recorded there (the caller makes its stream wait for it).
 gsicp_status frame_covariances(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
                                float z_min, float z_max, const gsicp_cov_params* cov_params, int cap,
                                cudaStream_t s, gsicp_surrogate sg,
-                               int row_step = 0);  // launch_depth_to_points' row_step
+                               int row_step = 0,  // launch_depth_to_points' row_step
+                               bool fork = false);
 // The whole a1..a7 step of gsicp_track_frame (arguments already checked), covariances as above.
 gsicp_status track_frame_impl(gsicp_ctx ctx, const float* depth_dev, int W, int H, const float intr[4], int stride,
                               float z_min, float z_max, const gsicp_cov_params* cov_params, gsicp_map map,
