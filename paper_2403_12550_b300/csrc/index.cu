@@ -107,14 +107,17 @@ gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 8;                      // 32-key rounds per warp
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 2048 keys per block
+// 32-key rounds per warp: 16 (4096 keys per tile) halves the tiles of 8, with them the look-back
+// chains and the per-tile counter work (map rebuild of 2.04M Gaussians 0.243 -> 0.230 ms; 12:
+// 0.234, 24: 0.242 at 128 registers, 32: 0.228 ms at 127)
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 4096 keys per block
 
 // One kernel per 8-bit pass (digit counts of all passes first): each block takes the next tile
 // of RS_TILE keys (tile numbers handed out in the order blocks start), counts its digits, publishes
 // them, and finds its tile's offset per digit by looking back over the earlier tiles' published
 // counts until one whose offset is already complete (decoupled look-back); then it scatters its
-// keys (each warp ranks a contiguous run of 256 keys in order, 32 at a time, peers found with
+// keys (each warp ranks a contiguous run of 32 x RS_ROUNDS keys in order, 32 at a time, peers found with
 // match.any, so equal digits keep their input order: stable).  A tile only waits on tiles claimed before it, by blocks that
 // are running or done and never wait on it, so every wait ends; the spin is bounded all the same
 // (err set if a bound ever ran out).
