@@ -105,6 +105,29 @@ gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf
 // ------------------------------------------------------------------------------------------
 // stable LSD radix sort of (uint32 key, uint32 value), 8 bits per pass
 
+// Launches of the map-index build after its first kernel are programmatic dependents of the kernel
+// before them in the stream (cudaLaunchAttributeProgrammaticStreamSerialization): a launch's set-up
+// overlaps the end of the kernel before it, and its blocks wait in griddepcontrol.wait, their first
+// instruction, until that kernel has completed and its writes are visible (a no-op in a plain
+// launch).  Nothing is read before the wait, so the order of the work is that of plain launches.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args)
+{
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 // 32-key rounds per warp: 16 (4096 keys per tile) halves the tiles of 8, with them the look-back
@@ -166,6 +189,7 @@ __global__ void __launch_bounds__(RS_THREADS) os_pass_kernel(const uint32_t* __r
                                                              uint32_t* __restrict__ tile_ctr,
                                                              uint32_t* __restrict__ err)
 {
+    wait_prior_grid();
     __shared__ uint32_t wc[RS_WARPS][256];
     __shared__ uint32_t base[256];
     __shared__ int s_tile;
@@ -291,8 +315,9 @@ static gsicp_status radix_passes(const RadixScratch& r, uint32_t* k0, uint32_t* 
             GSICP_CUDA(cudaMemcpyAsync(vo, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
             continue;
         }
-        os_pass_kernel<<<r.tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, r.O + 256 * p,
-                                                      r.status + 256 * (size_t)r.tiles * p, r.tile_ctr + p, r.err);
+        GSICP_CUDA(launch_dependent(os_pass_kernel, r.tiles, RS_THREADS, s, (const uint32_t*)ki, (const uint32_t*)vi, ko,
+                                    vo, n, shift, (const uint32_t*)(r.O + 256 * p),
+                                    r.status + 256 * (size_t)r.tiles * p, r.tile_ctr + p, r.err));
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
@@ -328,6 +353,7 @@ __global__ void bbox_init_kernel(uint32_t* bb)
 __global__ void bbox_quant_kernel(const float* __restrict__ pts, const int* __restrict__ n_dev, uint32_t* bb,
                                   float cell, float4* __restrict__ quant)
 {
+    wait_prior_grid();
     const int n = *n_dev;
     float lo[3] = {GSICP_INF, GSICP_INF, GSICP_INF}, hi[3] = {-GSICP_INF, -GSICP_INF, -GSICP_INF};
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -406,6 +432,7 @@ __global__ void __launch_bounds__(RS_THREADS) morton_hist_kernel(const float* __
                                                                  uint32_t* __restrict__ H, uint32_t* __restrict__ O,
                                                                  uint32_t* __restrict__ done)
 {
+    wait_prior_grid();
     __shared__ uint32_t h[4][256];
     __shared__ uint32_t ws[32];
     __shared__ bool last;
@@ -446,6 +473,7 @@ __global__ void __launch_bounds__(RS_THREADS) morton_hist_kernel(const float* __
 // capacity - 1, [1] occupied cells (counted by gather_leaf_kernel; reset here for the next build).
 __global__ void grid_size_kernel(uint32_t* __restrict__ meta, uint32_t max_capacity)
 {
+    wait_prior_grid();
     const uint32_t cells = meta[1];
     uint32_t cap = 1024;
     while (cap < 4u * cells && cap < max_capacity) cap <<= 1;
@@ -455,6 +483,7 @@ __global__ void grid_size_kernel(uint32_t* __restrict__ meta, uint32_t max_capac
 
 __global__ void grid_clear_kernel(int4* __restrict__ table, const uint32_t* __restrict__ meta, uint32_t max_capacity)
 {
+    wait_prior_grid();
     const uint32_t live = meta[0] + 1u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < min(live, max_capacity); i += gridDim.x * blockDim.x)
         table[i] = make_int4((int)GRID_EMPTY, 0, 0, 0);
@@ -467,6 +496,7 @@ __global__ void grid_clear_kernel(int4* __restrict__ table, const uint32_t* __re
 __global__ void grid_fill_kernel(const uint32_t* __restrict__ keys, const int* __restrict__ n_dev,
                                  int4* __restrict__ table, const uint32_t* __restrict__ meta)
 {
+    wait_prior_grid();
     const int n = *n_dev;
     const uint32_t mask = meta[0];
     const int lane = threadIdx.x & 31;
@@ -522,6 +552,7 @@ __global__ void __launch_bounds__(256) gather_leaf_kernel(const float* __restric
                                                           float4* __restrict__ boxes, uint32_t* __restrict__ keys_out,
                                                           int keys_n, uint32_t* __restrict__ grid_meta)
 {
+    wait_prior_grid();
     const int n = *n_dev;
     const long s = (long)blockIdx.x * 256 + threadIdx.x;
     float4 p = make_float4(GSICP_INF, GSICP_INF, GSICP_INF, __int_as_float(-1));
@@ -570,6 +601,7 @@ __global__ void __launch_bounds__(256) gather_leaf_kernel(const float* __restric
 // consecutive nodes into their ancestors down to one node per group.
 __global__ void level_reduce_kernel(float4* __restrict__ boxes, int count)
 {
+    wait_prior_grid();
     __shared__ float4 slo[256], shi[256];
     const int g = min(256, count);
     const int t = threadIdx.x;
@@ -639,13 +671,14 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
         bbox_init_kernel<<<1, 32, 0, s>>>(scr.bbox.as<uint32_t>());
         scr.bbox_ready = true;
     }
-    bbox_quant_kernel<<<std::max(1, std::min((cap + 255) / 256, sms * 2)), 256, 0, s>>>(
-        pts, n_dev, scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>());
+    GSICP_CUDA(launch_dependent(bbox_quant_kernel, std::max(1, std::min((cap + 255) / 256, sms * 2)), 256, s, pts,
+                                n_dev, scr.bbox.as<uint32_t>(), cell, out.quant.as<float4>()));
     // keys and the sort's digit counts in one pass; 30-bit keys take four 8-bit passes
     RadixScratch rs;
     GSICP_CHECK(radix_prepare(scr.hist, std::max(cap, 1), 30, s, rs));
-    morton_hist_kernel<<<grid, RS_THREADS, 0, s>>>(pts, n_dev, cap, out.quant.as<float4>(), scr.k0.as<uint32_t>(),
-                                                   scr.v0.as<uint32_t>(), rs.H, rs.O, rs.done);
+    GSICP_CUDA(launch_dependent(morton_hist_kernel, grid, RS_THREADS, s, pts, n_dev, cap,
+                                (const float4*)out.quant.as<float4>(), scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(),
+                                rs.H, rs.O, rs.done));
     GSICP_CUDA(cudaGetLastError());
     if (cap > 1)
         GSICP_CHECK(radix_passes(rs, scr.k0.as<uint32_t>(), scr.v0.as<uint32_t>(), scr.k1.as<uint32_t>(),
@@ -662,21 +695,23 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
     }
     out.has_grid = with_grid;
     if (with_seed) GSICP_CHECK(out.keys.ensure(sizeof(uint32_t) * (size_t)sort_n));
-    gather_leaf_kernel<<<(total + 255) / 256, 256, 0, s>>>(
-        pts, covs, scr.v0.as<uint32_t>(), scr.k0.as<uint32_t>(), n_dev, total, L, B, out.pts.as<float4>(),
-        covs ? out.covs.as<float4>() : nullptr, out.boxes.as<float4>(), with_seed ? out.keys.as<uint32_t>() : nullptr,
-        sort_n, with_grid ? out.grid_meta.as<uint32_t>() : nullptr);
+    GSICP_CUDA(launch_dependent(gather_leaf_kernel, (total + 255) / 256, 256, s, pts, covs,
+                                (const uint32_t*)scr.v0.as<uint32_t>(), (const uint32_t*)scr.k0.as<uint32_t>(), n_dev,
+                                total, L, B, out.pts.as<float4>(), covs ? out.covs.as<float4>() : nullptr,
+                                out.boxes.as<float4>(), with_seed ? out.keys.as<uint32_t>() : nullptr, sort_n,
+                                with_grid ? out.grid_meta.as<uint32_t>() : nullptr));
     for (int count = L; count > 1; count = count / std::min(256, count)) {
         const int blocks = count / std::min(256, count);
-        level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
+        GSICP_CUDA(launch_dependent(level_reduce_kernel, blocks, 256, s, out.boxes.as<float4>(), count));
     }
     if (with_grid) {
         const int ggrid = std::max(1, std::min((cap + 255) / 256, sms * 8));
-        grid_size_kernel<<<1, 1, 0, s>>>(out.grid_meta.as<uint32_t>(), grid_capacity);
-        grid_clear_kernel<<<std::max(1, std::min((int)(grid_capacity / 256), sms * 8)), 256, 0, s>>>(
-            out.grid.as<int4>(), out.grid_meta.as<uint32_t>(), grid_capacity);
-        grid_fill_kernel<<<ggrid, 256, 0, s>>>(scr.k0.as<uint32_t>(), n_dev, out.grid.as<int4>(),
-                                               out.grid_meta.as<uint32_t>());
+        GSICP_CUDA(launch_dependent(grid_size_kernel, 1, 1, s, out.grid_meta.as<uint32_t>(), grid_capacity));
+        GSICP_CUDA(launch_dependent(grid_clear_kernel, std::max(1, std::min((int)(grid_capacity / 256), sms * 8)), 256,
+                                    s, out.grid.as<int4>(), (const uint32_t*)out.grid_meta.as<uint32_t>(),
+                                    grid_capacity));
+        GSICP_CUDA(launch_dependent(grid_fill_kernel, ggrid, 256, s, (const uint32_t*)scr.k0.as<uint32_t>(), n_dev,
+                                    out.grid.as<int4>(), (const uint32_t*)out.grid_meta.as<uint32_t>()));
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
