@@ -50,6 +50,14 @@ struct IndexView {
 // Grid cells.  A map index quantises positions to cells of size 1/scale (the Morton grid), so
 // the points of one cell are a contiguous run of the sorted array; the hash table maps a cell's
 // 30-bit Morton key to that run: entries (key, start, end, -), empty slots have key 0xffffffff.
+// Kernels of a dependent chain (the map-index build, a frame's a1 .. set-up) are launched as
+// programmatic dependents of the kernel before them in their stream (launch_dependent,
+// internal.h): a launch's set-up overlaps the end of the kernel before it, and its blocks wait
+// here, at their first instruction, until that kernel has completed and its writes are visible (a
+// no-op in a plain launch).  Nothing is read before the wait, so the work runs in the order of
+// plain launches.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr uint32_t GRID_EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t grid_hash(uint32_t key)

@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(COV_THREADS) knn_wide_window_kernel(
     int k, float eps, int mode, float p, float* __restrict__ covs, int32_t* __restrict__ knn_out,
     int2* __restrict__ fb2, int* __restrict__ count2)
 {
+    wait_prior_grid();
     constexpr int D = 2 * R2 + 1, NC = D * D;
     const int lane = threadIdx.x & 31;
     const int m = *count;
@@ -527,6 +528,7 @@ __global__ void __launch_bounds__(COV_THREADS) knn_list_kernel(IndexView ix, con
                                                                int mode, float p, float* __restrict__ covs,
                                                                int32_t* __restrict__ knn_out)
 {
+    wait_prior_grid();
     __shared__ int2 wstack[COV_THREADS / 32][WARP_STACK];
     const int n = *ix.n, B = ix.B, m = *count;
     const int lane = threadIdx.x & 31;
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(COV_THREADS) knn_list_kernel(IndexView ix, con
 }
 
 template <int KMAX>
-static void launch_frame_knn_t(const IndexView& ix, const int* idx_img, int Ws, int Hs, int stride,
+static gsicp_status launch_frame_knn_t(const IndexView& ix, const int* idx_img, int Ws, int Hs, int stride,
                                const float intr[4], const float* pts, const float* z, int cap,
                                const gsicp_cov_params& prm, float* covs, int32_t* knn, int2* fb_list, int* fb_count,
                                cudaStream_t s)
@@ -580,11 +582,12 @@ static void launch_frame_knn_t(const IndexView& ix, const int* idx_img, int Ws, 
                                                                  intr[3], pts, z, prm.k, prm.eps, prm.reg_mode,
                                                                  prm.p, covs, knn, fb_list, fb_count);
     const int lgrid = std::max(1, std::min((cap + COV_THREADS - 1) / COV_THREADS, device_sm_count() * 8));
-    knn_wide_window_kernel<KMAX, 12><<<lgrid, COV_THREADS, 0, s>>>(
-        fb_list, fb_count, idx_img, Ws, Hs, stride, intr[0], intr[1], intr[2], intr[3], pts, z, prm.k, prm.eps,
-        prm.reg_mode, prm.p, covs, knn, fb_list + cap, fb_count + 1);
-    knn_list_kernel<KMAX><<<lgrid, COV_THREADS, 0, s>>>(ix, fb_list + cap, fb_count + 1, pts, z, prm.k, prm.eps,
-                                                         prm.reg_mode, prm.p, covs, knn);
+    GSICP_CUDA(launch_dependent(knn_wide_window_kernel<KMAX, 12>, lgrid, COV_THREADS, s, fb_list, fb_count, idx_img, Ws,
+                                Hs, stride, intr[0], intr[1], intr[2], intr[3], pts, z, prm.k, prm.eps, prm.reg_mode,
+                                prm.p, covs, knn, fb_list + cap, fb_count + 1));
+    GSICP_CUDA(launch_dependent(knn_list_kernel<KMAX>, lgrid, COV_THREADS, s, ix, fb_list + cap, fb_count + 1, pts, z,
+                                prm.k, prm.eps, prm.reg_mode, prm.p, covs, knn));
+    return GSICP_OK;
 }
 
 gsicp_status launch_frame_knn_cov(const IndexView& ix, const int* idx_img, int Ws, int Hs, int stride,
@@ -596,10 +599,10 @@ gsicp_status launch_frame_knn_cov(const IndexView& ix, const int* idx_img, int W
     GSICP_CUDA(cudaMemsetAsync(fb_count, 0, 2 * sizeof(int), s));
     const int k = prm.k;
     int2* fl = reinterpret_cast<int2*>(fb_list);
-    if (k <= 8) launch_frame_knn_t<8>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
-    else if (k <= 16) launch_frame_knn_t<16>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
-    else if (k <= 20) launch_frame_knn_t<20>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
-    else launch_frame_knn_t<32>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s);
+    if (k <= 8) GSICP_CHECK(launch_frame_knn_t<8>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s));
+    else if (k <= 16) GSICP_CHECK(launch_frame_knn_t<16>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s));
+    else if (k <= 20) GSICP_CHECK(launch_frame_knn_t<20>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s));
+    else GSICP_CHECK(launch_frame_knn_t<32>(ix, idx_img, Ws, Hs, stride, intr, pts, z, cap, prm, covs, knn, fl, fb_count, s));
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

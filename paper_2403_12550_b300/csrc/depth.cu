@@ -92,6 +92,7 @@ __global__ void d2p_write_prefix_kernel(const float* __restrict__ depth, int W, 
                                         float* __restrict__ z, int cap, int* n_dev, int* total_dev,
                                         int* __restrict__ idx_img)
 {
+    wait_prior_grid();
     const bool last = blockIdx.x == nblocks - 1;
     const uint32_t off = block_prefix(counts, blockIdx.x);
     d2p_write_block(depth, W, stride, row_step, Ws, total, z_min, z_max, fx, fy, cx, cy, off, last,
@@ -111,9 +112,9 @@ gsicp_status launch_depth_to_points(const float* depth, int W, int H, const floa
     GSICP_CHECK(counts.ensure(sizeof(uint32_t) * (size_t)nb));
     uint32_t* cnt = counts.as<uint32_t>();
     d2p_count_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, row_step, Ws, total, z_min, z_max, cnt);
-    d2p_write_prefix_kernel<<<nb, D2P_THREADS, 0, s>>>(depth, W, stride, row_step, Ws, total, z_min, z_max, (double)intr[0],
-                                                       (double)intr[1], (double)intr[2], (double)intr[3], cnt, nb, pts,
-                                                       z, cap, n_dev, total_dev, idx_img);
+    GSICP_CUDA(launch_dependent(d2p_write_prefix_kernel, nb, D2P_THREADS, s, depth, W, stride, row_step, Ws, total,
+                                z_min, z_max, (double)intr[0], (double)intr[1], (double)intr[2], (double)intr[3],
+                                (const uint32_t*)cnt, nb, pts, z, cap, n_dev, total_dev, idx_img));
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

@@ -218,6 +218,7 @@ __device__ __forceinline__ void transform_df(const float* Rh, const float* Rl, f
 
 __global__ void reg_setup_kernel(RegJob job, RegJob* __restrict__ job_dst, RegState* __restrict__ st, Pose16 T0)
 {
+    wait_prior_grid();
     *job_dst = job;
     if (job.sched)  // no history: the first iteration starts its blocks in index order
         for (int i = 0; i < 16; ++i) job.sched[i] = 0;
@@ -1234,8 +1235,7 @@ static gsicp_status reg_prepare(RegMachine& rm, RegJob& job, const double T0[16]
     Pose16 P;
     for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
     GSICP_CHECK(launch_seed(job.map, job.src, job.n, n_cap, T0, job.cand, job.anchor, s));
-    reg_setup_kernel<<<1, 1, 0, s>>>(job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P);
-    GSICP_CUDA(cudaGetLastError());
+    GSICP_CUDA(launch_dependent(reg_setup_kernel, 1, 1, s, job, rm.job.as<RegJob>(), rm.state.as<RegState>(), P));
     return GSICP_OK;
 }
 
@@ -1473,6 +1473,7 @@ gsicp_status launch_batch_seed(const RegJob* jobs_dev, const Pose16* T0_dev, con
 __global__ void seed_kernel(IndexView map, const float4* __restrict__ src, const int* __restrict__ n_dev, Pose16 T,
                             int* __restrict__ cand, float4* __restrict__ anchor)
 {
+    wait_prior_grid();
     const int n = *n_dev, m = *map.n;
     const float4 qz = *map.quant;
     float Rt[12];
@@ -1489,7 +1490,7 @@ gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_d
     Pose16 P;
     for (int i = 0; i < 16; ++i) P.v[i] = T0[i];
     const int grid = std::max(1, std::min((cap + 255) / 256, device_sm_count() * 8));
-    seed_kernel<<<grid, 256, 0, s>>>(map, src, n_dev, P, cand, anchor);
+    GSICP_CUDA(launch_dependent(seed_kernel, grid, 256, s, map, src, n_dev, P, cand, anchor));
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }
@@ -1497,6 +1498,7 @@ gsicp_status launch_seed(const IndexView& map, const float4* src, const int* n_d
 __global__ void permute_covs_kernel(IndexView ix, const float* __restrict__ covs, int cap,
                                     float4* __restrict__ out)
 {
+    wait_prior_grid();
     const int n = *ix.n;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < min(n, cap); s += gridDim.x * blockDim.x) {
         const long i = __float_as_int(ix.pts[s].w);
@@ -1510,7 +1512,7 @@ gsicp_status launch_permute_covs(const IndexView& ix, const float* covs, int cap
 {
     if (cap <= 0) return GSICP_OK;
     const int grid = std::max(1, std::min((cap + 255) / 256, device_sm_count() * 8));
-    permute_covs_kernel<<<grid, 256, 0, s>>>(ix, covs, cap, out);
+    GSICP_CUDA(launch_dependent(permute_covs_kernel, grid, 256, s, ix, covs, cap, out));
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;
 }

@@ -105,29 +105,6 @@ gsicp_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int n, DevBuf
 // ------------------------------------------------------------------------------------------
 // stable LSD radix sort of (uint32 key, uint32 value), 8 bits per pass
 
-// Launches of the map-index build after its first kernel are programmatic dependents of the kernel
-// before them in the stream (cudaLaunchAttributeProgrammaticStreamSerialization): a launch's set-up
-// overlaps the end of the kernel before it, and its blocks wait in griddepcontrol.wait, their first
-// instruction, until that kernel has completed and its writes are visible (a no-op in a plain
-// launch).  Nothing is read before the wait, so the order of the work is that of plain launches.
-__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args)
-{
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr.val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 // 32-key rounds per warp: 16 (4096 keys per tile) halves the tiles of 8, with them the look-back
@@ -724,6 +701,7 @@ gsicp_status build_index(const float* pts, const float* covs, int cap, const int
 __global__ void pix_count_kernel(const int* __restrict__ idx_img, const int* __restrict__ msamp, int nsamp,
                                  uint32_t* __restrict__ counts)
 {
+    wait_prior_grid();
     const int k = blockIdx.x * 256 + threadIdx.x;
     const bool ok = k < nsamp && idx_img[msamp[k]] >= 0;
     const int c = __syncthreads_count(ok);
@@ -735,6 +713,7 @@ __global__ void pix_count_kernel(const int* __restrict__ idx_img, const int* __r
 __global__ void pix_write_kernel(const int* __restrict__ idx_img, const int* __restrict__ msamp, int nsamp,
                                  const uint32_t* __restrict__ counts, uint32_t* __restrict__ order)
 {
+    wait_prior_grid();
     __shared__ uint32_t ws[32];
     const int k = blockIdx.x * 256 + threadIdx.x;
     const int pi = k < nsamp ? idx_img[msamp[k]] : -1;
@@ -763,14 +742,16 @@ gsicp_status build_index_pixel_order(const float* pts, const int* idx_img, const
     GSICP_CHECK(scr.k1.ensure(sizeof(uint32_t) * (size_t)nb));
     GSICP_CHECK(scr.v0.ensure(sizeof(uint32_t) * (size_t)std::max(cap, 1)));
     uint32_t* counts = scr.k1.as<uint32_t>();
-    pix_count_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, counts);
-    pix_write_kernel<<<nb, 256, 0, s>>>(idx_img, msamp, nsamp, counts, scr.v0.as<uint32_t>());
-    gather_leaf_kernel<<<(total + 255) / 256, 256, 0, s>>>(pts, nullptr, scr.v0.as<uint32_t>(), nullptr, n_dev, total,
-                                                           L, B, out.pts.as<float4>(), nullptr, out.boxes.as<float4>(),
-                                                           nullptr, 0, nullptr);
+    GSICP_CUDA(launch_dependent(pix_count_kernel, nb, 256, s, idx_img, msamp, nsamp, counts));
+    GSICP_CUDA(launch_dependent(pix_write_kernel, nb, 256, s, idx_img, msamp, nsamp, (const uint32_t*)counts,
+                                scr.v0.as<uint32_t>()));
+    GSICP_CUDA(launch_dependent(gather_leaf_kernel, (total + 255) / 256, 256, s, pts, (const float*)nullptr,
+                                (const uint32_t*)scr.v0.as<uint32_t>(), (const uint32_t*)nullptr, n_dev, total, L, B,
+                                out.pts.as<float4>(), (float4*)nullptr, out.boxes.as<float4>(), (uint32_t*)nullptr, 0,
+                                (uint32_t*)nullptr));
     for (int count = L; count > 1; count = count / std::min(256, count)) {
         const int blocks = count / std::min(256, count);
-        level_reduce_kernel<<<blocks, 256, 0, s>>>(out.boxes.as<float4>(), count);
+        GSICP_CUDA(launch_dependent(level_reduce_kernel, blocks, 256, s, out.boxes.as<float4>(), count));
     }
     GSICP_CUDA(cudaGetLastError());
     return GSICP_OK;

@@ -5,11 +5,32 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/gsicp.h"
 #include "common.cuh"
 
 namespace gsicp {
+
+// A launch as a programmatic dependent of the kernel before it in stream s
+// (cudaLaunchAttributeProgrammaticStreamSerialization); the kernel must begin with
+// wait_prior_grid() (common.cuh).
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
+                                           Args&&... args)
+{
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Launch shapes shared by translation units that launch the same kernels with their own scratch
 // (depth.cu and noalloc.cu launch the a1 kernels; index.cu and noalloc.cu the scan kernels).
