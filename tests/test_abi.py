@@ -142,3 +142,33 @@ def test_binding_rejects_host_or_mistyped_tensors_before_the_call():
         g._check(g.ERR_INVALID_ARG, "somewhere")
     assert "somewhere" in str(e.value)
     assert g._check(g.ERR_DEGENERATE, "x", allow=(g.ERR_DEGENERATE,)) == g.ERR_DEGENERATE
+
+
+def _kernel_body_start(src: str, name: str) -> str:
+    """The first statement of __global__ kernel `name` in src (templates included)."""
+    m = re.search(r"__global__\s+void\s+(?:__launch_bounds__\((?:[^()]|\([^()]*\))*\)\s+)?" + re.escape(name) + r"\s*\(",
+                  src)
+    assert m, name
+    depth, i = 0, m.end() - 1
+    while True:  # the parameter list, then the body's opening brace
+        c = src[i]
+        depth += c == "("
+        depth -= c == ")"
+        i += 1
+        if depth == 0:
+            break
+    body = src[src.index("{", i) + 1:]
+    return body.lstrip().split(";", 1)[0]
+
+
+def test_dependent_launches_wait_for_the_kernel_before_them():
+    """A kernel launched as a programmatic dependent may start before the kernel ahead of it in the
+    stream has finished; every such kernel must wait (griddepcontrol.wait) before it reads
+    anything.  Checks each launch_dependent target and the Gauss-Newton iteration kernel."""
+    csrc = os.path.join(ROOT, "paper_2403_12550_b300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in sorted(os.listdir(csrc)) if f.endswith((".cu", ".cuh")))
+    targets = sorted(set(re.findall(r"launch_dependent\(\s*([a-z_0-9]+)", src)) - {"void"})
+    assert len(targets) >= 14, targets
+    for name in targets:
+        assert _kernel_body_start(src, name) == "wait_prior_grid()", name
+    assert "griddepcontrol.wait" in _kernel_body_start(src, "gicp_iter_kernel")
