@@ -48,3 +48,40 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     t0 = time.perf_counter()
     bench.run_reference(argparse.Namespace(steps=3, warmup=3, seed=0), 2, 1)
     assert time.perf_counter() - t0 < 1.0 and capsys.readouterr().out == ""
+
+
+def test_clock_sampler_keeps_the_timed_window_and_reports_throttling(monkeypatch):
+    """The bench's clock record (read through NVML in a thread): samples outside the timed region
+    and one sampling period around it are dropped, the SM clock is their median, and any throttle
+    reason seen inside is reported; with no NVML the record says so."""
+    import time
+    import bench
+
+    class FakeNvml:
+        def __init__(self):
+            self.calls = 0
+
+        def handle(self, bus, index):
+            return "h"
+
+        def sample(self, h):
+            self.calls += 1
+            slow = ["sw_power_cap"] if self.calls == 3 else []
+            return 1900.0 + self.calls, 2032.0, slow
+
+    fake = FakeNvml()
+    monkeypatch.setattr(bench, "_nvml", lambda: fake)
+    monkeypatch.setattr(bench.ClockSampler, "PERIOD_S", 0.01)
+    with bench.ClockSampler(0) as c:
+        time.sleep(0.08)
+    s = c.summary()
+    assert s["samples"] >= 3 and s["sm_max_mhz"] == 2032.0
+    assert 1900.0 < s["sm_mhz"] < 1900.0 + fake.calls + 1
+    assert s["reasons"] == ["sw_power_cap"]
+    early = c.t0 - 1.0  # a sample from well before the region is not counted
+    c.rows.insert(0, (early, 100.0, 2032.0, ["hw_slowdown"]))
+    assert c.summary()["reasons"] == ["sw_power_cap"] and c.summary()["sm_mhz"] > 1000.0
+    monkeypatch.setattr(bench, "_nvml", lambda: None)
+    with bench.ClockSampler(0) as c2:
+        pass
+    assert c2.summary()["reasons"] == ["unavailable"]
