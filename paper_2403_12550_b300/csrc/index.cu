@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(RS_THREADS) morton_hist_kernel(const float* __
 // cells (load factor <= 1/4: searches of empty cells, half of a query's 2x2x2 block on a surface,
 // end at the first or second slot; per 1200x680 bench frame GN 1.012 -> 0.999 ms and the map
 // rebuild 0.244 -> 0.240 ms against load factor <= 1/2), at least 1024, at most the allocated
-// capacity.  meta: [0] live capacity - 1, [1] occupied cells (counted by gather_leaf_kernel; reset
-// here for the next build).
+// capacity.  meta: [0] live
+// capacity - 1, [1] occupied cells (counted by gather_leaf_kernel; reset here for the next build).
 __global__ void grid_size_kernel(uint32_t* __restrict__ meta, uint32_t max_capacity)
 {
     wait_prior_grid();
