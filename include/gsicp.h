@@ -97,11 +97,13 @@ const char* gsicp_last_error(void);
 /* Library version, e.g. "0.1.0". */
 const char* gsicp_version(void);
 
-/* Profiling: when enabled, gsicp_track_frame / gsicp_track_frame_host record CUDA events on the
- * call's stream between their phases, and gsicp_ctx_phase_times returns the device time (ms) of
- * the last such frame: out[0] a1 depth->points, out[1] source index build, out[2] k-NN
- * covariances, out[3] Gauss-Newton loop, out[4] whole frame; out[5] = Gauss-Newton iterations.
- * Disabled by default (no events are recorded). */
+/* Profiling: when enabled, gsicp_track_frame / gsicp_track_frame_host record CUDA events between
+ * their phases, and gsicp_ctx_phase_times returns the device time (ms) of the last such frame:
+ * out[0] a1 depth->points, out[1] source index build, out[2] k-NN covariances (with their
+ * reordering; they run on a second stream of the context, beside the registration's seeds and
+ * set-up on the call's stream), out[3] Gauss-Newton loop (from the covariances' end to the
+ * registration's end), out[4] whole frame; out[5] = Gauss-Newton iterations.  Disabled by default
+ * (no events are recorded). */
 gsicp_status gsicp_ctx_set_timing(gsicp_ctx ctx, int enable);
 /* The last registration's (or linearisation's) final linearisation: *sqdist_out = the sum over its
  * inlier correspondences of |mu - T x|^2 (squared Euclidean residuals, m^2), *inliers_out
